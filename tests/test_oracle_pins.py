@@ -1,0 +1,346 @@
+"""Pins for the FP64 CPU oracle (no GPU): every check here compares the oracle
+with something other than itself -- hand-worked examples, closed forms,
+brute-force vertex enumeration, an independent LP solver (HiGHS via scipy),
+planted optima built by the generator, and invariants of the method."""
+
+import math
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import lpgen
+import oracle
+from brute import dense, vertex_enum
+from conftest import DictLP
+
+
+# ---------------------------------------------------------------- hand examples
+
+
+def test_pdhg_step_hand(golden):
+    g = golden["pdhg_step"]
+    lp = DictLP(g["lp"])
+    xn, yn = oracle.pdhg_step(lp, np.array(g["x"]), np.array(g["y"]), g["tau"], g["sigma"])
+    np.testing.assert_allclose(xn, g["x_next"], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(yn, g["y_next"], rtol=0, atol=1e-13)
+
+
+def test_kkt_hand(golden):
+    g = golden["kkt"]
+    lp = DictLP(g["lp"])
+    t = oracle.kkt_terms(lp, np.array(g["x"]), np.array(g["y"]))
+    assert t["pobj"] == pytest.approx(g["pobj"], abs=1e-14)
+    assert t["dobj"] == pytest.approx(g["dobj"], abs=1e-14)
+    assert t["rp"] == pytest.approx(g["rp_norm"], abs=1e-14)
+    assert t["rd"] == pytest.approx(g["rd_norm"], abs=1e-14)
+    assert t["q_norm"] ** 2 == pytest.approx(g["q_norm_sq"], rel=1e-14)
+    assert t["c_norm"] ** 2 == pytest.approx(g["c_norm_sq"], rel=1e-14)
+    k = oracle.kkt_omega(lp, np.array(g["x"]), np.array(g["y"]), g["omega"])
+    assert k * k == pytest.approx(g["kkt_omega_sq"], rel=1e-14)
+
+
+def test_alg2_scalars(golden):
+    g = golden["alg2_scalars"]
+    for c in g["cases"]:
+        want = math.inf if c["eta_bar"] == "inf" else c["eta_bar"]
+        assert oracle.eta_bar(c["dx2"], c["dy2"], c["cross"], c["omega"]) == want
+    for c in g["eta_next"]:
+        assert oracle.eta_next(c["eta"], c["eta_bar"], c["k"]) == pytest.approx(c["expect"], rel=1e-15)
+    # eta_bar = inf -> the growth branch: (1 + (k+2)^-0.6) eta
+    assert oracle.eta_next(2.0, math.inf, 0) == pytest.approx(2.0 * (1 + 2 ** -0.6), rel=1e-15)
+
+
+def test_primal_weight(golden):
+    g = golden["primal_weight"]
+    for c in g["init"]:
+        assert oracle.primal_weight_init(c["c_norm"], c["q_norm"]) == pytest.approx(c["expect"], rel=1e-15)
+    for c in g["update"]:
+        got = oracle.primal_weight_update(c["dx"], c["dy"], c["omega"], c["theta"])
+        assert got == pytest.approx(c["expect"], rel=1e-14)
+    # theta = 1 keeps only the new ratio, theta = 0 keeps the old weight
+    assert oracle.primal_weight_update(2.0, 6.0, 5.0, 1.0) == pytest.approx(3.0, rel=1e-14)
+    assert oracle.primal_weight_update(2.0, 6.0, 5.0, 0.0) == pytest.approx(5.0, rel=1e-14)
+
+
+def test_restart_mask_truth_table():
+    # Sec. 3.4: (i) cand <= 0.2 start; (ii) cand <= 0.8 start and cand > prev; (iii) t >= 0.36 k
+    assert oracle.restart_mask(0.19, 1.0, 0.3, 1, 100) == 1
+    assert oracle.restart_mask(0.2, 1.0, 0.3, 1, 100) == 1  # boundary: <= ; not > prev
+    assert oracle.restart_mask(0.5, 1.0, 0.4, 1, 100) == 2  # necessary decay + no local progress
+    assert oracle.restart_mask(0.5, 1.0, 0.6, 1, 100) == 0  # still progressing
+    assert oracle.restart_mask(0.81, 1.0, 0.1, 1, 100) == 0  # not enough decay
+    assert oracle.restart_mask(0.9, 1.0, 0.1, 36, 100) == 4  # long inner loop, boundary t = 0.36 k
+    assert oracle.restart_mask(0.9, 1.0, 0.1, 35, 100) == 0
+    assert oracle.restart_mask(0.1, 1.0, 0.05, 50, 100) == 1 | 2 | 4
+
+
+# ---------------------------------------------------------------- closed forms
+
+
+def _lp_from_dense(K, c, q, l, u, n_eq):
+    S = sp.csr_matrix(np.asarray(K, dtype=float).reshape(len(q), len(c)))
+    return lpgen.LP(m=len(q), n=len(c), n_eq=n_eq, c=np.asarray(c, float), row_ptr=S.indptr.astype(np.int32),
+                    col_idx=S.indices.astype(np.int32), val=S.data.astype(float), q=np.asarray(q, float),
+                    l=np.asarray(l, float), u=np.asarray(u, float))
+
+
+def test_closed_form_no_constraints():
+    # m = 0: x_j = l_j if c_j > 0, u_j if c_j < 0
+    rng = np.random.default_rng(3)
+    n = 40
+    c = rng.standard_normal(n)
+    l = rng.uniform(-3, 0, n)
+    u = rng.uniform(0, 3, n)
+    lp = lpgen.LP(m=0, n=n, n_eq=0, c=c, row_ptr=np.zeros(1, np.int32), col_idx=np.zeros(0, np.int32),
+                  val=np.zeros(0), q=np.zeros(0), l=l, u=u)
+    r = oracle.solve(lp, tol=1e-10, max_iter=20000)
+    assert r.status == oracle.OPTIMAL
+    x_exp = np.where(c > 0, l, u)
+    np.testing.assert_allclose(r.x, x_exp, atol=1e-9)
+    assert r.pobj == pytest.approx(float(c @ x_exp), rel=1e-10)
+
+
+def test_closed_form_fractional_knapsack():
+    # max v'x s.t. w'x <= W, 0 <= x <= 1  ==  min -v'x s.t. -w'x >= -W
+    rng = np.random.default_rng(5)
+    n = 12
+    v = rng.uniform(1, 5, n)
+    w = rng.uniform(1, 3, n)
+    W = 0.4 * w.sum()
+    order = np.argsort(-v / w)
+    x = np.zeros(n)
+    cap = W
+    for j in order:
+        take = min(1.0, cap / w[j])
+        x[j] = take
+        cap -= take * w[j]
+        if cap <= 0:
+            break
+    opt = -float(v @ x)
+    lp = _lp_from_dense([-w], -v, [-W], np.zeros(n), np.ones(n), n_eq=0)
+    r = oracle.solve(lp, tol=1e-10, max_iter=200000)
+    assert r.status == oracle.OPTIMAL
+    assert r.pobj == pytest.approx(opt, rel=1e-8)
+
+
+# ---------------------------------------------------------------- brute force
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_vertex_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 6))
+    m_eq = int(rng.integers(0, 3))
+    m_in = int(rng.integers(0, 3))
+    lp = lpgen.random_boxed_lp(seed, m_eq, m_in, n, density=0.7, planted=bool(seed % 2))
+    best, _ = vertex_enum(lp)
+    assert np.isfinite(best)
+    r = oracle.solve(lp, tol=1e-10, max_iter=500000)
+    assert r.status == oracle.OPTIMAL
+    assert r.pobj == pytest.approx(best, abs=1e-7 * (1 + abs(best)))
+    if lp.obj_star is not None:
+        assert best == pytest.approx(lp.obj_star, abs=1e-9 * (1 + abs(best)))
+
+
+# ---------------------------------------------------------------- planted optima
+
+
+def test_planted_pair_has_zero_kkt():
+    for lp in (lpgen.tiny_lp(0), lpgen.large_lp(1, m=3000, n=6000, nnz=60000)):
+        t = oracle.kkt_terms(lp, lp.x_star, lp.y_star)
+        scale = 1 + abs(t["pobj"])
+        assert abs(t["dobj"] - t["pobj"]) <= 1e-12 * scale
+        assert t["rp"] <= 1e-11 * (1 + t["q_norm"])
+        assert t["rd"] <= 1e-11 * (1 + t["c_norm"])
+        assert t["pobj"] == pytest.approx(lp.obj_star, rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_planted_tiny_objective(seed):
+    lp = lpgen.tiny_lp(seed)
+    r = oracle.solve(lp, tol=1e-8)
+    assert r.status == oracle.OPTIMAL
+    assert abs(r.pobj - lp.obj_star) <= 1e-6 * abs(lp.obj_star)
+    assert oracle.passes(lp, r.x, r.y, 1e-8)
+    assert np.all(r.x >= lp.l) and np.all(r.x <= lp.u)
+    assert np.all(r.y[lp.n_eq:] >= 0)
+
+
+def test_warm_start_at_optimum_is_a_fixed_point():
+    lp = lpgen.tiny_lp(4)
+    r = oracle.solve(lp, tol=1e-12, x0=lp.x_star, y0=lp.y_star, check_period=8)
+    assert r.status == oracle.OPTIMAL and r.iters == 8
+    assert oracle.relative_kkt(lp, r.x, r.y) < 1e-12
+
+
+# ---------------------------------------------------------------- independent solver
+
+
+def _highs(lp):
+    from scipy.optimize import linprog
+
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+    A_eq = K[: lp.n_eq] if lp.n_eq else None
+    b_eq = lp.q[: lp.n_eq] if lp.n_eq else None
+    A_ub = -K[lp.n_eq:] if lp.m > lp.n_eq else None
+    b_ub = -lp.q[lp.n_eq:] if lp.m > lp.n_eq else None
+    bounds = [(None if not np.isfinite(a) else a, None if not np.isfinite(b) else b) for a, b in zip(lp.l, lp.u)]
+    res = linprog(lp.c, A_ub=A_ub, b_ub=b_ub, A_eq=A_eq, b_eq=b_eq, bounds=bounds, method="highs")
+    assert res.status == 0
+    return res.fun
+
+
+@pytest.mark.parametrize("case", ["tiny-mixed", "all-eq", "all-ineq", "power-law"])
+def test_against_highs(case):
+    if case == "tiny-mixed":
+        lp = lpgen.tiny_lp(7)
+    elif case == "all-eq":
+        lp = lpgen.tiny_lp(8, m_eq=120, m_ineq=0, n=300)
+    elif case == "all-ineq":
+        lp = lpgen.tiny_lp(9, m_eq=0, m_ineq=150, n=300)
+    else:
+        lp = lpgen.large_lp(2, m=600, n=1200, nnz=12000)
+    ref = _highs(lp)
+    r = oracle.solve(lp, tol=1e-8, max_iter=400000)
+    assert r.status == oracle.OPTIMAL
+    assert abs(r.pobj - ref) <= 1e-6 * (1 + abs(ref))
+
+
+# ---------------------------------------------------------------- preconditioning
+
+
+def test_ruiz_equilibrates_and_scaling_identity():
+    lp = lpgen.large_lp(3, m=2000, n=4000, nnz=40000)
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+    sv, D1, D2 = oracle.precondition(lp, ruiz_iters=10, pc_alpha=-1.0)
+    Kt = sp.csr_matrix((sv, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+    # identity K~ = D1 K D2 (Sec. 2.2)
+    ref = (sp.diags(D1) @ K @ sp.diags(D2)).tocsr()
+    ref.sort_indices()
+    np.testing.assert_allclose(sv, ref.data, rtol=1e-13)
+    assert np.all(D1 > 0) and np.all(D2 > 0)
+
+    # l_inf equilibration (Ruiz): every nonempty row / column max tends to 1,
+    # the deviation shrinking geometrically with the number of passes
+    def dev(passes):
+        v, _, _ = oracle.precondition(lp, ruiz_iters=passes, pc_alpha=-1.0)
+        A = abs(sp.csr_matrix((v, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)))
+        r = A.max(axis=1).toarray().ravel()
+        c = A.max(axis=0).toarray().ravel()
+        return max(np.abs(r[r > 0] - 1).max(), np.abs(c[c > 0] - 1).max())
+
+    d = [dev(p) for p in (5, 10, 20, 40)]
+    assert d[1] < 5e-2 and d[2] < 1e-4 and d[3] < 1e-9
+    assert d[0] > d[1] > d[2] > d[3]
+
+
+def test_pock_chambolle_single_pass_closed_form():
+    lp = lpgen.tiny_lp(2)
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n))
+    sv, D1, D2 = oracle.precondition(lp, ruiz_iters=0, pc_alpha=1.0)
+    rs = np.asarray(abs(K).sum(axis=1)).ravel()
+    cs = np.asarray(abs(K).sum(axis=0)).ravel()
+    np.testing.assert_allclose(D1, 1 / np.sqrt(np.where(rs > 0, rs, 1)), rtol=1e-14)
+    np.testing.assert_allclose(D2, 1 / np.sqrt(np.where(cs > 0, cs, 1)), rtol=1e-14)
+
+
+def test_scaling_does_not_change_solution():
+    lp = lpgen.tiny_lp(11)
+    a = oracle.solve(lp, tol=1e-8)
+    b = oracle.solve(lp, tol=1e-8, ruiz_iters=0, pc_alpha=-1.0, max_iter=400000)
+    assert a.status == b.status == oracle.OPTIMAL
+    assert a.pobj == pytest.approx(b.pobj, rel=1e-6)
+
+
+# ---------------------------------------------------------------- Algorithm 3 (App. A)
+
+
+def test_alg3_restart_decay_and_bounded_length():
+    rng = np.random.default_rng(1)
+    m, n = 6, 14
+    A = rng.standard_normal((m, n))
+    xs = np.abs(rng.standard_normal(n))
+    xs[:6] = 0
+    ys = rng.standard_normal(m)
+    lam = np.zeros(n)
+    lam[:6] = rng.uniform(0.1, 1, 6)
+    c = A.T @ ys + lam
+    b = A @ xs
+    S = sp.csr_matrix(A)
+    s = 1 / (2 * np.linalg.norm(A, 2))  # Theorem: s <= 1 / (2 ||A||_2)
+    beta = 0.5
+    x, y, kr, lr = oracle.alg3(S.indptr, S.indices, S.data, b, c, m, n, s, beta, 200000)
+    assert len(lr) >= 20
+    # restart rule: KKT(z^{n+1,0}) <= beta KKT(z^{n,0}), so KKT(z^{n,0}) <= beta^n KKT(z^{0,0})
+    assert np.all(kr[1:] <= beta * kr[:-1] * (1 + 1e-12))
+    assert np.all(kr <= beta ** np.arange(len(kr)) * kr[0] * (1 + 1e-9))
+    # Theorem (ii): restart lengths stay bounded (no growth) while the KKT
+    # error is above the rounding floor of FP64
+    above = kr[: len(lr)] > 1e-10 * kr[0]
+    assert above.sum() >= 20
+    assert lr[above].max() <= 4 * np.median(lr[above])
+    # the KKT error of Appendix A vanishes at the limit: optimal objective
+    assert float(c @ x) == pytest.approx(float(c @ xs), abs=1e-9)
+    # the Appendix A KKT function is zero at the planted optimum
+    assert oracle.kkt_standard(S.indptr, S.indices, S.data, b, c, xs, ys, m, n) < 1e-12
+
+
+# ---------------------------------------------------------------- driver behaviour
+
+
+def test_iteration_limit_and_trace():
+    lp = lpgen.tiny_lp(1)
+    r = oracle.solve(lp, tol=1e-12, max_iter=200, check_period=16)
+    assert r.status == oracle.ITER_LIMIT and r.iters == 200
+    ks = r.trace["k"]
+    assert np.all(ks % 16 == 0) and np.all(np.diff(ks) == 16)
+    assert np.all(r.trace["eta_hat"] > 0) and np.all(r.trace["omega"] > 0)
+    # the first check of the run is in epoch 0 where t == k: criterion (iii) fires
+    assert r.trace["restart"][0] & 4
+
+
+def test_invalid_inputs_rejected():
+    lp = lpgen.tiny_lp(0)
+    bad = lpgen.tiny_lp(0)
+    bad.col_idx = bad.col_idx.copy()
+    bad.col_idx[3] = lp.n  # out of range
+    with pytest.raises(ValueError):
+        oracle.solve(bad)
+    bad = lpgen.tiny_lp(0)
+    bad.l = bad.l.copy()
+    bad.l[0] = 20.0  # l > u
+    with pytest.raises(ValueError):
+        oracle.solve(bad)
+    bad = lpgen.tiny_lp(0)
+    bad.c = bad.c.copy()
+    bad.c[0] = np.nan
+    with pytest.raises(ValueError):
+        oracle.solve(bad)
+
+
+def test_dense_helper_matches_csr():
+    lp = lpgen.tiny_lp(0)
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)).toarray()
+    np.testing.assert_array_equal(dense(lp), K)
+
+
+def test_first_solve_step_is_eq_pdhg(golden):
+    """The solver's inner step itself (not the separate helper): without
+    scaling, one accepted step from (x0, y0) is eq. (pdhg) with
+    tau = eta/omega, sigma = eta*omega, eta = 1/max|K_ij| (Alg. 1 init) and
+    omega = ||c|| / ||q|| (InitializePrimalWeight), computed here in numpy."""
+    g = golden["pdhg_step"]
+    lp = DictLP(g["lp"])
+    x0, y0 = np.array(g["x"]), np.array(g["y"])
+    r = oracle.solve(lp, tol=0.0, max_iter=1, check_period=1, ruiz_iters=0, pc_alpha=-1.0, x0=x0, y0=y0)
+    assert r.status == oracle.ITER_LIMIT and r.iters == 1 and r.attempts == 1
+    K = dense(lp)
+    eta = 1.0 / np.abs(lp.val).max()
+    omega = np.linalg.norm(lp.c) / np.linalg.norm(lp.q)
+    tau, sigma = eta / omega, eta * omega
+    x1 = np.clip(x0 - tau * (lp.c - K.T @ y0), lp.l, lp.u)
+    y1 = y0 + sigma * (lp.q - K @ (2 * x1 - x0))
+    y1[lp.n_eq:] = np.maximum(y1[lp.n_eq:], 0)
+    np.testing.assert_allclose(r.x, x1, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(r.y, y1, rtol=1e-14, atol=1e-15)
