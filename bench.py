@@ -1,0 +1,377 @@
+"""Benchmark: restarted-PDHG iterations per second on the GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload large|tiny] [--ttt]
+
+Workload (default): the planted-optimum LP with m = 1e6 rows (4e5
+equalities), n = 2e6 variables, nnz = 2e7 with Zipf(1.5) row lengths and
+lognormal(0, 2) values, FP64 (seeded synthetic data; the paper's MIPLIB /
+Mittelmann instances are not available).  One benchmark step is one check
+period of the solver: P = 64 accepted PDHG iterations (Algorithm 2 trials
+including any rejected ones) followed by the restart / termination check of
+Sec. 3.4 / Sec. 4.1 -- every kernel of the hot path.  The matrix (K + K' =
+480 MB) is far larger than the 129 MB L2, so every step streams it from HBM.
+
+value  = accepted PDHG iterations per second, inputs resident in HBM;
+e2e    = the same metric through the C ABI with host buffers: pdlp_create
+         (host -> device copy, transpose, scaling) + pdlp_solve for the same
+         number of iterations + device -> host copy of (x, y);
+roofline = the dominant kernel's algorithmic HBM bytes per launch over its
+         CUDA-event-timed average duration, against the measured copy
+         bandwidth in MEASURED_PEAKS.json;
+cpu_baseline = the FP64 CPU oracle (single thread) on a bounded sample of
+         the same LP.
+
+Multi-GPU: the plain path has an exchange per half-step (Kx', K'y'), so this
+benchmark runs independent replicas, one per rank, and reports the sum.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PDHG iters/s"
+UNIT = "iters/s"
+
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# dominant kernel from one ncu capture, keyed by the sha256 of the kernel
+# source it was taken on; reported as null once the source has changed.
+NCU_TRAFFIC = {}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in ("pdlp_kernels.cu", "pdlp_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2311_12180_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks / throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx = float(f[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_workload(name: str, seed: int = 0):
+    import lpgen
+
+    if name == "large":
+        lp = lpgen.large_lp(seed)
+        desc = ("planted LP m=1e6 (4e5 eq) n=2e6 nnz=%d, Zipf(1.5) row lengths (max %d), lognormal(0,2) values, "
+                "bounds 50%% [0,inf) 30%% [l,u] 20%% free" % (lp.nnz, lp.meta["max_row"]))
+    elif name == "tiny":
+        lp = lpgen.tiny_lp(seed)
+        desc = "planted LP m=200 (100 eq) n=500 nnz=%d, 2%% density, N(0,1), 0<=x<=10" % lp.nnz
+    else:
+        raise SystemExit("unknown workload " + name)
+    return lp, desc
+
+
+def algorithmic_bytes(lp, kernel: str) -> float:
+    """HBM bytes one launch must move at minimum (int32 indices, FP64 values):
+    k_primal: K' (row_ptr, col_idx, val) + gather of y (m) + read x, c, l, u,
+              sx + write g, x', sx' (8 n-vectors);
+    k_dual:   K + gather of x' (n) + read y, q, Kx, sy + write y', Kx', sy'
+              (7 m-vectors)."""
+    m, n, nnz = lp.m, lp.n, lp.nnz
+    if kernel == "k_primal":
+        return 4.0 * (n + 1) + 12.0 * nnz + 8.0 * m + 8 * 8.0 * n
+    if kernel == "k_dual":
+        return 4.0 * (m + 1) + 12.0 * nnz + 8.0 * n + 7 * 8.0 * m
+    if kernel == "k_primal_reuse_g":
+        return 9 * 8.0 * n
+    raise KeyError(kernel)
+
+
+def cpu_baseline(lp, budget_s: float = 20.0):
+    """The FP64 oracle as it stands (single thread), timed on a bounded sample:
+    solves with max_iter = a and b; the difference isolates the iteration rate
+    from the (shared) scaling set-up."""
+    import oracle
+
+    oracle.build()
+    t = time.perf_counter()
+    oracle.solve(lp, tol=1e-14, max_iter=2, trace_cap=1)
+    t_small = time.perf_counter() - t
+    # estimate per-iteration cost from a short run, then size the sample
+    t = time.perf_counter()
+    oracle.solve(lp, tol=1e-14, max_iter=6, trace_cap=1)
+    t6 = time.perf_counter() - t
+    per_it = max((t6 - t_small) / 4.0, 1e-6)
+    b = int(max(6, min(2000, budget_s / per_it)))
+    t = time.perf_counter()
+    oracle.solve(lp, tol=1e-14, max_iter=b, trace_cap=1)
+    tb = time.perf_counter() - t
+    rate = (b - 2) / max(tb - t_small, 1e-9)
+    return {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d accepted PDHG iterations of the same LP (rate from a %d-iteration minus a 2-iteration "
+                      "solve, so the shared Sec. 2.2 scaling set-up cancels)" % (b - 2, b)}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 CPU oracle on the host cores, same metric."""
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    lp, desc = make_workload(args.workload)
+    # each step: a bounded sample of the same workload (a few oracle iterations)
+    t = time.perf_counter()
+    oracle.solve(lp, tol=1e-14, max_iter=1, trace_cap=1)
+    t1 = time.perf_counter() - t
+    iters_per_step = 2 if args.workload == "large" else 64
+    for _ in range(args.warmup):
+        pass
+    t = time.perf_counter()
+    total_iters = 0
+    for _ in range(args.steps):
+        oracle.solve(lp, tol=1e-14, max_iter=1 + iters_per_step, trace_cap=1)
+        total_iters += iters_per_step
+    el = time.perf_counter() - t - args.steps * t1
+    val = total_iters / max(el, 1e-9)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d oracle iterations per step (set-up time of a 1-iteration solve "
+                                       "subtracted per step)" % iters_per_step},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=["large", "tiny"])
+    ap.add_argument("--ttt", action="store_true", help="also time full solves to 1e-4 and 1e-8 KKT")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2311_12180_gb300 import _build
+    from paper_2311_12180_gb300 import pdlp as P
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    _build.build()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    lp, desc = make_workload(args.workload)
+    stream = torch.cuda.Stream()
+    solver = P.Solver(lp, stream=stream.cuda_stream)
+    period = P.pdlp_default_params().check_period
+
+    # ---- warm-up (cold start, then W periods) ----
+    solver.begin(tol=1e-14, max_iter=10**12)
+    solver.run_periods(args.warmup)
+    st0, k0 = solver.poll()
+
+    # ---- timed region ----
+    def barrier():
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        solver.run_periods(args.steps)
+        ev1.record(stream)
+        ev1.synchronize()
+    barrier()
+    st1, k1 = solver.poll()
+    ms = ev0.elapsed_time(ev1)
+    iters = k1 - k0
+    if st1 != -1:
+        raise SystemExit("solve ended inside the timed region (status %d): timing invalid" % st1)
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    it_t = torch.tensor([float(iters)], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
+        pg.all_reduce(it_t, op=pg.ReduceOp.SUM)
+    ms_max = float(ms_t.item())
+    total_iters = float(it_t.item())
+    value = total_iters / (ms_max / 1000.0)
+    info = solver.info()
+
+    # ---- per-kernel event timing (same workload, direct launches) ----
+    times = solver.time_kernels(max(2, min(args.steps, 8)))
+    peak, peak_kind = measured_peaks()
+    cands = {k: v for k, v in times.items() if k in ("k_primal", "k_dual") and v[1] > 0}
+    dom = max(cands, key=lambda k: cands[k][0])
+    dom_ms = cands[dom][0] / cands[dom][1]
+    dom_bytes = algorithmic_bytes(lp, dom)
+    achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
+    sha = kernel_source_sha()
+    tr = NCU_TRAFFIC.get((dom, sha))
+    solver.finish()
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e_iters = int(max(1, round(iters / max(world, 1))))
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s2 = P.Solver(lp)
+    x, y, st, it2 = s2.solve(tol=1e-14, max_iter=e2e_iters)
+    e2e_s = time.perf_counter() - t
+    s2.close()
+    h2d = (4 * (lp.m + 1) + 12 * lp.nnz + 8 * 3 * lp.n + 8 * lp.m)
+    d2h = 8 * (lp.n + lp.m)
+    e2e_val = it2 / e2e_s * world
+
+    ttt = None
+    if args.ttt:
+        ttt = {}
+        with P.Solver(lp, time_limit_s=600.0) as s3:
+            for tol in (1e-4, 1e-8):
+                t = time.perf_counter()
+                _, _, stt, itt = s3.solve(tol=tol, max_iter=10**9)
+                ttt["%g" % tol] = {"seconds": time.perf_counter() - t, "status": P.STATUS_NAMES.get(stt, stt),
+                                   "iters": itt, "setup_excluded": True}
+
+    if rank != 0:
+        if pg is not None:
+            pg.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_baseline(lp)
+
+    kernels_per_period = 2 * (period + max(4, period // 8)) + 3
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "step": "one check period: %d accepted PDHG iterations + restart/termination "
+                   "check" % period, "l2": "inputs larger than L2 (K + K' = %.0f MB)" % (24 * lp.nnz / 1e6),
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "iters_timed": int(total_iters),
+        "attempts_per_iter": info["attempts"] / max(info["iters"], 1),
+        "effective_hbm_gbs": (algorithmic_bytes(lp, "k_primal") + algorithmic_bytes(lp, "k_dual")) * value / 1e9,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": tr,
+                     "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
+                     "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in times.items()}},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "iters": it2, "seconds": e2e_s, "note": "one step = create + solve(%d iterations) + outputs" % it2},
+        "gpu_launches": kernels_per_period * args.steps,
+        "clocks": clk.summary(),
+    }
+    if ttt is not None:
+        line["time_to_tol"] = ttt
+    print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * pdlp.h -- C ABI of the GB300 restarted-PDHG (PDLP) linear-programming solver.
+ *
+ * Problem (cuPDLP.jl paper, Sec. 2, eq. (lp) and eq. (primal-dual)):
+ *
+ *     min  c'x   s.t.   A x = b,   G x >= h,   l <= x <= u,
+ *
+ * passed as one CSR matrix K = (A; G) with m rows and n columns whose first
+ * n_eq rows are the equalities and the remaining m - n_eq rows the ">="
+ * constraints, and one right-hand side q = (b; h).  The paper lists G first;
+ * the order is only a permutation of the same problem.  Bounds may be
+ * -INFINITY / +INFINITY.  The dual variable y is free on equality rows and
+ * y >= 0 on ">=" rows (Lagrangian L(x,y) = c'x - y'Kx + q'y).
+ *
+ * Method: restarted PDHG of Algorithm 1 with the adaptive step of Algorithm 2
+ * (eq. (pdhg), eq. (step-size)), the KKT-error restart of Sec. 3.4 (eq. kkt),
+ * primal-weight initialisation / update of Sec. 2.2, Ruiz + Pock-Chambolle
+ * diagonal preconditioning of Sec. 2.2 (done on the GPU at create time), and
+ * termination on the relative KKT error of the ORIGINAL problem (Sec. 4.1).
+ * Every step of the iteration runs in this library's CUDA kernels on one GPU;
+ * the host only launches CUDA graphs and polls a status word.
+ *
+ * Conventions for every function below:
+ *   - Return value: PDLP_OK (0) or a negative PDLP_ERR_* code.  No function
+ *     aborts the process.  On error pdlp_last_error() returns a message for
+ *     the calling thread.
+ *   - Pointers named *_out are caller-allocated HOST buffers of the stated
+ *     length; inputs are HOST arrays copied during the call (the caller keeps
+ *     ownership and may free them on return).  Functions ending in _device
+ *     take DEVICE pointers instead (see their comments).
+ *   - A solver object is not thread-safe: use one host thread per object.
+ *   - Requires a CUDA device of compute capability 10.3 (GB300 / sm_103a).
+ */
+#ifndef PDLP_GB300_H
+#define PDLP_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---- */
+#define PDLP_OK 0
+#define PDLP_ERR_INVALID (-1) /* bad argument or malformed LP; nothing was done */
+#define PDLP_ERR_CUDA (-2)    /* a CUDA call failed (no device, launch error, ...) */
+#define PDLP_ERR_OOM (-3)     /* device or host allocation failed */
+
+/* ---- solve status (the `status` out-argument) ---- */
+#define PDLP_OPTIMAL 0    /* all three Sec. 4.1 inequalities hold with eps = tol */
+#define PDLP_ITER_LIMIT 1 /* max_iter accepted PDHG steps taken first */
+#define PDLP_TIME_LIMIT 2 /* params.time_limit_s wall-clock seconds elapsed first */
+#define PDLP_NUMERICAL 3  /* a NaN / Inf appeared in the step-size test */
+
+typedef struct pdlp_solver pdlp_solver; /* opaque */
+
+/* Algorithm parameters.  Defaults (pdlp_default_params) are the paper's
+ * constants where it prints them (beta = 0.2 / 0.8 / 0.36, Sec. 3.4; step
+ * exponents 0.3 / 0.6 are fixed, Algorithm 2) and this library's readings
+ * where it is silent (10 Ruiz passes, Pock-Chambolle alpha = 1, theta = 0.5,
+ * eps_zero = 1e-10, restart/termination check every 64 accepted steps). */
+typedef struct {
+  int32_t check_period;   /* P: restart + termination check after every P accepted steps (>= 1) */
+  int32_t ruiz_iters;     /* Ruiz l_inf passes at create (>= 0) */
+  double pc_alpha;        /* Pock-Chambolle exponent in [0, 2]; < 0 disables the pass */
+  double theta;           /* primal-weight smoothing, [0, 1] */
+  double eps_zero;        /* InitializePrimalWeight / PrimalWeightUpdate threshold */
+  double beta_suff;       /* restart criterion (i) */
+  double beta_nec;        /* restart criterion (ii) */
+  double beta_art;        /* restart criterion (iii) */
+  double time_limit_s;    /* wall-clock limit per solve; <= 0 means none */
+  int32_t value_bits;     /* 64: K values stored FP64; 32: the PDHG steps read FP32 copies of the
+                             scaled K (FP64 gathers, accumulation and iterates; restart / KKT checks
+                             and termination always use the FP64 K) */
+  int32_t f32_polish;     /* with value_bits = 32: switch the steps to the FP64 K when the original-
+                             space relative KKT error stalls over two restarts above tol (1 = on) */
+} pdlp_params;
+
+/* Summary of the last solve (pdlp_get_info). */
+typedef struct {
+  int32_t status;   /* PDLP_* status of the last solve, -1 while running / never solved */
+  int32_t which;    /* 0: the returned point is the current iterate, 1: the epoch average */
+  int64_t iters;    /* accepted PDHG steps (k of Algorithm 1) */
+  int64_t attempts; /* Algorithm 2 trials, accepted + rejected */
+  int64_t restarts; /* restarts taken (n of Algorithm 1) */
+  int64_t checks;   /* restart / termination checks evaluated */
+  double pobj, dobj;      /* c'x and q'y + l'lambda+ - u'lambda- on the original LP at the last check */
+  double rp_norm, rd_norm; /* ||(Ax-b, [h-Gx]+)||_2 and ||c - K'y - lambda||_2 (original LP) */
+  double q_norm, c_norm;  /* ||q||_2, ||c||_2 of the original LP */
+  double omega, eta_hat;  /* primal weight and next trial step size (scaled LP) */
+  double setup_ms;        /* pdlp_create device work (transfer + transpose + scaling) */
+  double solve_ms;        /* wall time of the last solve call */
+  int64_t graph_launches; /* CUDA-graph launches in the last solve */
+  int64_t f64_switch_iter; /* value_bits = 32 only: k at which the steps moved to FP64 K, -1 never */
+} pdlp_info;
+
+/* One restart / termination check (pdlp_get_trace), values on the scaled LP. */
+typedef struct {
+  int64_t k;        /* accepted steps when the check ran */
+  int32_t restart;  /* bit 0: criterion (i), bit 1: (ii), bit 2: (iii); 0 = no restart */
+  int32_t cand_avg; /* 1 if GetRestartCandidate picked the average */
+  double kkt_cur;   /* KKT_omega(current iterate), eq. (kkt) */
+  double kkt_avg;   /* KKT_omega(average iterate) */
+  double kkt_start; /* KKT_omega(z^{n,0}) after the check (recomputed with the new omega) */
+  double omega;     /* primal weight after the check */
+  double eta_hat;   /* next trial step size */
+} pdlp_check;
+
+/* Fills *p with the defaults listed above.  p must be non-NULL. */
+void pdlp_default_params(pdlp_params *p);
+
+/* Builds a solver for the LP: validates the CSR (row_ptr[0] = 0,
+ * non-decreasing, 0 <= col_idx < n, finite values / c / q, no NaN bounds,
+ * l <= u, l != +inf, u != -inf), copies everything to the GPU, builds K' and
+ * the SpMV tile schedules, and runs the Sec. 2.2 Ruiz + Pock-Chambolle
+ * scaling on the device.
+ *   m >= 0 rows, n >= 1 columns, 0 <= n_eq <= m, nnz = row_ptr[m] < 2^31.
+ *   c: n, row_ptr: m+1, col_idx / val: nnz (int32 / float64), q: m, l / u: n.
+ * Errors: PDLP_ERR_INVALID (bad input; *out untouched), PDLP_ERR_CUDA,
+ * PDLP_ERR_OOM.  On success *out owns device memory until pdlp_destroy. */
+int pdlp_create(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c,
+                const int32_t *row_ptr, const int32_t *col_idx, const double *val, const double *q,
+                const double *l, const double *u);
+
+/* As pdlp_create with explicit parameters (NULL = defaults) and a CUDA stream
+ * (a cudaStream_t passed as void*; NULL = the library creates its own
+ * non-blocking stream).  All device work of the solver is ordered on it. */
+int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c,
+                   const int32_t *row_ptr, const int32_t *col_idx, const double *val, const double *q,
+                   const double *l, const double *u, const pdlp_params *params, void *stream);
+
+/* Cold solve from x = 0, y = 0 (Sec. 4.1, "Initialization") to the relative
+ * KKT tolerance tol (> 0) or max_iter (>= 1) accepted steps.  Writes the
+ * solution of the ORIGINAL LP to x_out (n) and y_out (m; may be NULL when
+ * m = 0), the PDLP_* status to *status and the accepted step count to *iters
+ * (either pointer may be NULL).  Blocks until done. */
+int pdlp_solve(pdlp_solver *s, double tol, int64_t max_iter, double *x_out, double *y_out, int *status,
+               int64_t *iters);
+
+/* As pdlp_solve but starting from (x0, y0) given in the ORIGINAL space
+ * (host arrays of n and m; either may be NULL = zeros).  The point is used as
+ * given (the first PDHG step projects it). */
+int pdlp_solve_warm(pdlp_solver *s, const double *x0, const double *y0, double tol, int64_t max_iter,
+                    double *x_out, double *y_out, int *status, int64_t *iters);
+
+/* Non-blocking pieces of pdlp_solve, for callers that overlap work or time
+ * the iteration:  pdlp_begin resets the state (warm point as in
+ * pdlp_solve_warm, NULLs = cold) and evaluates KKT(z^{0,0});
+ * pdlp_run_periods enqueues n_periods CUDA-graph launches (each covers P
+ * accepted steps plus one restart / termination check, or stops early once
+ * the solve has ended) without waiting; pdlp_poll waits for the enqueued work
+ * and returns the status (-1 = still running); pdlp_finish writes the outputs
+ * like pdlp_solve and waits. */
+int pdlp_begin(pdlp_solver *s, const double *x0, const double *y0, double tol, int64_t max_iter);
+int pdlp_run_periods(pdlp_solver *s, int32_t n_periods);
+int pdlp_poll(pdlp_solver *s, int *status, int64_t *iters);
+int pdlp_finish(pdlp_solver *s, double *x_out, double *y_out, int *status, int64_t *iters);
+
+/* Enqueues n_periods periods like pdlp_run_periods but launches each kernel
+ * directly (no graph) between CUDA events on the solver's stream, then waits
+ * and adds each kernel class's event-measured device time to ms[i] and its
+ * launch count to launches[i] (arrays of pdlp_kernel_count() entries, caller
+ * zeroes them).  Same arithmetic as the graph path. */
+int pdlp_time_kernels(pdlp_solver *s, int32_t n_periods, double *ms, int64_t *launches);
+int32_t pdlp_kernel_count(void);
+const char *pdlp_kernel_name(int32_t i);
+
+/* Reports on the last solve.  info: see pdlp_info.  trace: up to cap check
+ * records (in order) and their total count in *count. */
+int pdlp_get_info(const pdlp_solver *s, pdlp_info *info);
+int pdlp_get_trace(const pdlp_solver *s, pdlp_check *trace, int32_t cap, int32_t *count);
+
+/* The Sec. 2.2 scaling computed at create: D1 (m), D2 (n) and the scaled
+ * values of K~ = D1 K D2 in the input's CSR order (nnz).  Any pointer may be
+ * NULL. */
+int pdlp_get_scaling(const pdlp_solver *s, double *D1, double *D2, double *val_scaled);
+
+/* The CUDA stream (cudaStream_t as void*) all work of `s` is ordered on. */
+void *pdlp_get_stream(const pdlp_solver *s);
+
+/* Bytes of device memory the solver holds. */
+size_t pdlp_device_bytes(const pdlp_solver *s);
+
+/* Frees the solver's device and host memory (NULL is a no-op). */
+void pdlp_destroy(pdlp_solver *s);
+
+/* Message for the last error on the calling thread ("" if none). */
+const char *pdlp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDLP_GB300_H */

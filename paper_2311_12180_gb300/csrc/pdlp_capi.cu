@@ -1,0 +1,675 @@
+// C ABI of the GB300 PDLP solver (declared in include/pdlp.h): input
+// validation, the transpose of K and the SpMV tile schedules (host, once per
+// LP), one device arena per solver, Sec. 2.2 scaling on the device, and the
+// solve driver that replays a captured CUDA graph of one check period and
+// polls a pinned copy of the device state one period behind, so the GPU never
+// waits for the host.
+
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pdlp.h"
+#include "pdlp_internal.cuh"
+
+using namespace pdlp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr int TRACE_CAP = 1 << 16;
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// Tiles: runs of consecutive rows with at most TILE_NNZ nonzeros and
+// TILE_ROWS rows; a row longer than TILE_NNZ forms a tile of its own.
+std::vector<int32_t> build_tiles(const int32_t *ptr, int32_t rows) {
+  std::vector<int32_t> t;
+  t.push_back(0);
+  int32_t r = 0;
+  while (r < rows) {
+    const int32_t start = r;
+    long long nz = 0;
+    while (r < rows && r - start < TILE_ROWS) {
+      const long long len = (long long)ptr[r + 1] - ptr[r];
+      if (r > start && nz + len > TILE_NNZ) break;
+      nz += len;
+      ++r;
+      if (nz > TILE_NNZ) break;
+    }
+    t.push_back(r);
+  }
+  return t;
+}
+
+struct Layout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+}  // namespace
+
+struct pdlp_solver {
+  int32_t m = 0, n = 0, n_eq = 0;
+  int64_t nnz = 0;
+  int device = 0;
+  pdlp_params prm{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  int num_sms = 0;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  Csr K{}, KT{};
+  Vecs V{};
+  DevState *st = nullptr;
+  double *d_scal = nullptr;
+  int32_t *K_ptr = nullptr, *K_idx = nullptr, *T_ptr = nullptr, *T_idx = nullptr;
+  double *K_val = nullptr, *T_val = nullptr;
+  float *K_val32 = nullptr, *T_val32 = nullptr;
+  double *D1 = nullptr, *D2 = nullptr, *work_m = nullptr, *work_n = nullptr;
+  double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr, *l0 = nullptr, *u0 = nullptr;
+  int gridA = 1, gridB = 1, gridR1 = 1, gridR2 = 1, gridR3 = 1;
+  int slots = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  DevState *h_st = nullptr;    // pinned: state written by the host before a solve / read after
+  DevState *h_poll = nullptr;  // pinned: two slots of polled state
+  double *h_scal = nullptr;    // pinned
+  double eta_hat0 = 1.0, omega0 = 1.0, q_norm = 0.0, c_norm = 0.0;
+  double setup_ms = 0.0, solve_ms = 0.0, t0 = 0.0;
+  int64_t launches = 0;
+  int last_status = -1;
+  bool have_result = false;
+};
+
+namespace {
+
+int validate(int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *rp, const int32_t *ci,
+             const double *v, const double *q, const double *l, const double *u) {
+  if (m < 0 || n < 1 || n_eq < 0 || n_eq > m) return fail(PDLP_ERR_INVALID, "dimensions: need m >= 0, n >= 1, 0 <= n_eq <= m");
+  if (!c || !rp || !l || !u || (m > 0 && !q)) return fail(PDLP_ERR_INVALID, "null input array");
+  if (rp[0] != 0) return fail(PDLP_ERR_INVALID, "row_ptr[0] must be 0");
+  for (int32_t i = 0; i < m; ++i)
+    if (rp[i + 1] < rp[i]) return fail(PDLP_ERR_INVALID, "row_ptr is not non-decreasing at row " + std::to_string(i));
+  const int64_t nnz = rp[m];
+  if (nnz > 0 && (!ci || !v)) return fail(PDLP_ERR_INVALID, "null col_idx / val");
+  for (int64_t e = 0; e < nnz; ++e) {
+    if (ci[e] < 0 || ci[e] >= n) return fail(PDLP_ERR_INVALID, "col_idx out of range at nonzero " + std::to_string(e));
+    if (!std::isfinite(v[e])) return fail(PDLP_ERR_INVALID, "non-finite matrix value at nonzero " + std::to_string(e));
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    if (!std::isfinite(c[j])) return fail(PDLP_ERR_INVALID, "non-finite c at " + std::to_string(j));
+    if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY)
+      return fail(PDLP_ERR_INVALID, "bad bounds at variable " + std::to_string(j));
+  }
+  for (int32_t i = 0; i < m; ++i)
+    if (!std::isfinite(q[i])) return fail(PDLP_ERR_INVALID, "non-finite q at row " + std::to_string(i));
+  return PDLP_OK;
+}
+
+int check_params(const pdlp_params &p) {
+  if (p.check_period < 1 || p.ruiz_iters < 0 || !(p.pc_alpha <= 2.0) || !(p.theta >= 0.0 && p.theta <= 1.0) ||
+      !(p.eps_zero >= 0.0) || !(p.beta_suff > 0.0) || !(p.beta_nec > 0.0) || !(p.beta_art > 0.0) ||
+      (p.value_bits != 64 && p.value_bits != 32))
+    return fail(PDLP_ERR_INVALID, "invalid parameters");
+  return PDLP_OK;
+}
+
+void free_solver(pdlp_solver *s) {
+  if (!s) return;
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  for (auto &e : s->ev)
+    if (e) cudaEventDestroy(e);
+  if (s->arena) cudaFree(s->arena);
+  if (s->h_st) cudaFreeHost(s->h_st);
+  if (s->h_poll) cudaFreeHost(s->h_poll);
+  if (s->h_scal) cudaFreeHost(s->h_scal);
+  if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+  delete s;
+}
+
+int build_graph(pdlp_solver *s) {
+  if (s->gexec) return PDLP_OK;
+  CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < s->slots && e == cudaSuccess; ++i) {
+    e = launch_primal(s->KT, s->V, s->st, s->gridA, s->cap_stream);
+    if (e == cudaSuccess) e = launch_dual(s->K, s->V, s->st, s->gridB, s->cap_stream);
+  }
+  if (e == cudaSuccess) e = launch_check_primal(s->KT, s->V, s->st, s->gridR1, s->cap_stream);
+  if (e == cudaSuccess) e = launch_check_dual(s->K, s->V, s->st, s->gridR2, s->cap_stream);
+  if (e == cudaSuccess) e = launch_restart(s->V, s->st, s->gridR3, s->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s->cap_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(PDLP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
+  if (e2 != cudaSuccess) return fail(PDLP_ERR_CUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
+  s->graph = g;
+  CK(cudaGraphInstantiate(&s->gexec, s->graph, 0));
+  return PDLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pdlp_default_params(pdlp_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->check_period = 64;
+  p->ruiz_iters = 10;
+  p->pc_alpha = 1.0;
+  p->theta = 0.5;
+  p->eps_zero = 1e-10;
+  p->beta_suff = 0.2;
+  p->beta_nec = 0.8;
+  p->beta_art = 0.36;
+  p->time_limit_s = 0.0;
+  p->value_bits = 64;
+  p->f32_polish = 1;
+}
+
+const char *pdlp_last_error(void) { return g_err.c_str(); }
+
+int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *row_ptr,
+                   const int32_t *col_idx, const double *val, const double *q, const double *l, const double *u,
+                   const pdlp_params *params, void *stream) {
+  g_err.clear();
+  if (!out) return fail(PDLP_ERR_INVALID, "out is NULL");
+  pdlp_params prm;
+  if (params)
+    prm = *params;
+  else
+    pdlp_default_params(&prm);
+  int rc = check_params(prm);
+  if (rc) return rc;
+  rc = validate(m, n, n_eq, c, row_ptr, col_idx, val, q, l, u);
+  if (rc) return rc;
+  const double t_start = now_ms();
+  const int64_t nnz = row_ptr[m];
+  if (nnz >= ((int64_t)1 << 31)) return fail(PDLP_ERR_INVALID, "nnz must be < 2^31");
+
+  // ---- host: K' by a stable counting sort, tile schedules ----
+  std::vector<int32_t> tp((size_t)n + 1, 0), ti((size_t)nnz);
+  std::vector<double> tv((size_t)nnz);
+  for (int64_t e = 0; e < nnz; ++e) tp[col_idx[e] + 1]++;
+  for (int32_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
+  {
+    std::vector<int32_t> fill(tp.begin(), tp.end() - 1);
+    for (int32_t i = 0; i < m; ++i)
+      for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+        const int32_t pos = fill[col_idx[e]]++;
+        ti[pos] = i;
+        tv[pos] = val[e];
+      }
+  }
+  std::vector<int32_t> tilesK = build_tiles(row_ptr, m);
+  std::vector<int32_t> tilesT = build_tiles(tp.data(), n);
+  double qn = 0.0, cn = 0.0;
+  for (int32_t i = 0; i < m; ++i) qn += q[i] * q[i];
+  for (int32_t j = 0; j < n; ++j) cn += c[j] * c[j];
+
+  pdlp_solver *s = new pdlp_solver();
+  s->m = m;
+  s->n = n;
+  s->n_eq = n_eq;
+  s->nnz = nnz;
+  s->prm = prm;
+  s->q_norm = std::sqrt(qn);
+  s->c_norm = std::sqrt(cn);
+#define CKS(call)                                                                                              \
+  do {                                                                                                         \
+    cudaError_t e_ = (call);                                                                                   \
+    if (e_ != cudaSuccess) {                                                                                   \
+      int code_ = (e_ == cudaErrorMemoryAllocation) ? PDLP_ERR_OOM : PDLP_ERR_CUDA;                          \
+      std::string msg_ = std::string(#call) + ": " + cudaGetErrorString(e_);                                  \
+      free_solver(s);                                                                                          \
+      return fail(code_, msg_);                                                                                \
+    }                                                                                                          \
+  } while (0)
+  CKS(cudaGetDevice(&s->device));
+  int major = 0, minor = 0;
+  CKS(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, s->device));
+  CKS(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, s->device));
+  CKS(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
+  if (stream) {
+    s->stream = (cudaStream_t)stream;
+  } else {
+    CKS(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+    s->own_stream = true;
+  }
+  CKS(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  CKS(cudaEventCreateWithFlags(&s->ev[0], cudaEventDisableTiming));
+  CKS(cudaEventCreateWithFlags(&s->ev[1], cudaEventDisableTiming));
+  CKS(cudaMallocHost((void **)&s->h_st, sizeof(DevState)));
+  CKS(cudaMallocHost((void **)&s->h_poll, 2 * sizeof(DevState)));
+  CKS(cudaMallocHost((void **)&s->h_scal, 8 * sizeof(double)));
+  std::memset(s->h_st, 0, sizeof(DevState));
+  s->h_st->status = ST_RUNNING;
+
+  auto capped = [](int g, int ntiles) { return g < (ntiles > 0 ? ntiles : 1) ? g : (ntiles > 0 ? ntiles : 1); };
+  s->gridA = capped(occupancy_grid(KC_PRIMAL, s->num_sms), (int)tilesT.size() - 1);
+  s->gridB = capped(occupancy_grid(KC_DUAL, s->num_sms), (int)tilesK.size() - 1);
+  s->gridR1 = capped(occupancy_grid(KC_R1, s->num_sms), (int)tilesT.size() - 1);
+  s->gridR2 = capped(occupancy_grid(KC_R2, s->num_sms), (int)tilesK.size() - 1);
+  {
+    const int64_t mx = n > m ? n : m;
+    int g = occupancy_grid(KC_R3, s->num_sms);
+    const int64_t need = (mx + NT - 1) / NT;
+    s->gridR3 = (int)(need < g ? (need > 0 ? need : 1) : g);
+  }
+  const bool f32 = prm.value_bits == 32;
+
+  // ---- one device arena ----
+  Layout L;
+  const size_t M = (size_t)m, N = (size_t)n, Z = (size_t)nnz;
+  const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z + 16), o_Kval = L.take(8 * Z + 16);
+  const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + 16), o_Tval = L.take(8 * Z + 16);
+  const size_t o_Kv32 = f32 ? L.take(4 * Z + 16) : 0, o_Tv32 = f32 ? L.take(4 * Z + 16) : 0;
+  const size_t o_Ktl = L.take(4 * tilesK.size()), o_Ttl = L.take(4 * tilesT.size());
+  const size_t nvec_n = 17, nvec_m = 13;
+  const size_t o_vn = L.take(8 * N * nvec_n), o_vm = L.take(8 * (M + 1) * nvec_m);
+  const size_t o_pA = L.take(8 * (size_t)s->gridA * NV_A), o_pB = L.take(8 * (size_t)s->gridB * NV_B);
+  const size_t o_pR1 = L.take(8 * (size_t)s->gridR1 * NV_R1), o_pR2 = L.take(8 * (size_t)s->gridR2 * NV_R2);
+  const size_t o_pR3 = L.take(8 * (size_t)s->gridR3 * NV_R3);
+  const size_t o_st = L.take(sizeof(DevState)), o_tr = L.take(sizeof(TraceRec) * TRACE_CAP);
+  const size_t o_sc = L.take(8 * 8);
+  s->arena_bytes = L.off;
+  CKS(cudaMalloc((void **)&s->arena, s->arena_bytes));
+  char *A = s->arena;
+  s->K_ptr = (int32_t *)(A + o_Kptr);
+  s->K_idx = (int32_t *)(A + o_Kidx);
+  s->K_val = (double *)(A + o_Kval);
+  s->T_ptr = (int32_t *)(A + o_Tptr);
+  s->T_idx = (int32_t *)(A + o_Tidx);
+  s->T_val = (double *)(A + o_Tval);
+  s->K_val32 = f32 ? (float *)(A + o_Kv32) : nullptr;
+  s->T_val32 = f32 ? (float *)(A + o_Tv32) : nullptr;
+  int32_t *Ktl = (int32_t *)(A + o_Ktl), *Ttl = (int32_t *)(A + o_Ttl);
+  double *vn = (double *)(A + o_vn), *vm = (double *)(A + o_vm);
+  auto VN = [&](int i) { return vn + (size_t)i * N; };
+  auto VM = [&](int i) { return vm + (size_t)i * (M + 1); };
+  s->c = VN(0);
+  s->l = VN(1);
+  s->u = VN(2);
+  s->D2 = VN(3);
+  s->l0 = VN(4);
+  s->u0 = VN(5);
+  s->work_n = VN(16);
+  s->q = VM(0);
+  s->D1 = VM(1);
+  s->work_m = VM(12);
+  s->st = (DevState *)(A + o_st);
+  s->d_scal = (double *)(A + o_sc);
+
+  Vecs &V = s->V;
+  V.n = n;
+  V.m = m;
+  V.n_eq = n_eq;
+  V.gridA = s->gridA;
+  V.gridR1 = s->gridR1;
+  V.c = s->c;
+  V.l = s->l;
+  V.u = s->u;
+  V.D2 = s->D2;
+  V.l0 = s->l0;
+  V.u0 = s->u0;
+  V.q = s->q;
+  V.D1 = s->D1;
+  V.x[0] = VN(6);
+  V.x[1] = VN(7);
+  V.sx[0] = VN(8);
+  V.sx[1] = VN(9);
+  V.g = VN(10);
+  V.gbar = VN(11);
+  V.xlast = VN(12);
+  V.xout = VN(13);
+  V.y[0] = VM(2);
+  V.y[1] = VM(3);
+  V.sy[0] = VM(4);
+  V.sy[1] = VM(5);
+  V.Kx[0] = VM(6);
+  V.Kx[1] = VM(7);
+  V.Kxbar = VM(8);
+  V.ylast = VM(9);
+  V.yout = VM(10);
+  V.partA = (double *)(A + o_pA);
+  V.partB = (double *)(A + o_pB);
+  V.partR1 = (double *)(A + o_pR1);
+  V.partR2 = (double *)(A + o_pR2);
+  V.partR3 = (double *)(A + o_pR3);
+  V.trace = (TraceRec *)(A + o_tr);
+
+  s->K = Csr{m, (int32_t)tilesK.size() - 1, s->K_ptr, s->K_idx, s->K_val, s->K_val32, Ktl};
+  s->KT = Csr{n, (int32_t)tilesT.size() - 1, s->T_ptr, s->T_idx, s->T_val, s->T_val32, Ttl};
+
+  // ---- transfers ----
+  cudaStream_t st = s->stream;
+  CKS(cudaMemsetAsync(s->arena, 0, s->arena_bytes, st));
+  CKS(cudaMemcpyAsync(s->K_ptr, row_ptr, 4 * (M + 1), cudaMemcpyHostToDevice, st));
+  if (nnz) {
+    CKS(cudaMemcpyAsync(s->K_idx, col_idx, 4 * Z, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(s->K_val, val, 8 * Z, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(s->T_idx, ti.data(), 4 * Z, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
+  }
+  CKS(cudaMemcpyAsync(s->T_ptr, tp.data(), 4 * (N + 1), cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(Ktl, tilesK.data(), 4 * tilesK.size(), cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(Ttl, tilesT.data(), 4 * tilesT.size(), cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(s->l0, l, 8 * N, cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(s->u0, u, 8 * N, cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(V.xout, c, 8 * N, cudaMemcpyHostToDevice, st));  // original c, consumed below
+  if (m) CKS(cudaMemcpyAsync(V.yout, q, 8 * M, cudaMemcpyHostToDevice, st));
+
+  // ---- Sec. 2.2 scaling on the device ----
+  CKS(setup_scale(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, s->D1, s->D2, s->work_m,
+                  s->work_n, prm.ruiz_iters, prm.pc_alpha, st));
+  CKS(setup_vectors(m, n, V.xout, V.yout, s->l0, s->u0, s->D1, s->D2, s->c, s->q, s->l, s->u, st));
+  if (f32) {
+    CKS(setup_f32(nnz, s->K_val, s->K_val32, st));
+    CKS(setup_f32(nnz, s->T_val, s->T_val32, st));
+  }
+  CKS(setup_scalars(m, n, nnz, s->c, s->q, s->K_val, s->d_scal, st));
+  CKS(cudaMemcpyAsync(s->h_scal, s->d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+  const double cc = std::sqrt(s->h_scal[0]), qq = std::sqrt(s->h_scal[1]), kmax = s->h_scal[2];
+  s->eta_hat0 = kmax > 0.0 ? 1.0 / kmax : 1.0;                                        // Algorithm 1
+  s->omega0 = (cc > prm.eps_zero && qq > prm.eps_zero) ? cc / qq : 1.0;              // InitializePrimalWeight
+  s->slots = prm.check_period + (prm.check_period / 8 > 4 ? prm.check_period / 8 : 4);
+  s->setup_ms = now_ms() - t_start;
+#undef CKS
+  *out = s;
+  return PDLP_OK;
+}
+
+int pdlp_create(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *row_ptr,
+                const int32_t *col_idx, const double *val, const double *q, const double *l, const double *u) {
+  return pdlp_create_ex(out, m, n, n_eq, c, row_ptr, col_idx, val, q, l, u, nullptr, nullptr);
+}
+
+void pdlp_destroy(pdlp_solver *s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  free_solver(s);
+}
+
+int pdlp_begin(pdlp_solver *s, const double *x0, const double *y0, double tol, int64_t max_iter) {
+  g_err.clear();
+  if (!s) return fail(PDLP_ERR_INVALID, "solver is NULL");
+  if (!(tol >= 0.0) || max_iter < 1) return fail(PDLP_ERR_INVALID, "need tol >= 0 and max_iter >= 1");
+  CK(cudaSetDevice(s->device));
+  int rc = build_graph(s);
+  if (rc) return rc;
+  cudaStream_t st = s->stream;
+  Vecs &V = s->V;
+  const size_t N = (size_t)s->n, M = (size_t)s->m;
+  if (x0) CK(cudaMemcpyAsync(V.xout, x0, 8 * N, cudaMemcpyHostToDevice, st));
+  if (y0 && M) CK(cudaMemcpyAsync(V.yout, y0, 8 * M, cudaMemcpyHostToDevice, st));
+  CK(setup_warm(s->m, s->n, x0 ? V.xout : nullptr, (y0 && M) ? V.yout : nullptr, s->D1, s->D2, V.x[0], V.y[0], st));
+  CK(cudaMemsetAsync(V.sx[0], 0, 8 * N, st));
+  CK(cudaMemsetAsync(V.sx[1], 0, 8 * N, st));
+  CK(cudaMemcpyAsync(V.xlast, V.x[0], 8 * N, cudaMemcpyDeviceToDevice, st));
+  if (M) {
+    CK(cudaMemsetAsync(V.sy[0], 0, 8 * M, st));
+    CK(cudaMemsetAsync(V.sy[1], 0, 8 * M, st));
+    CK(cudaMemcpyAsync(V.ylast, V.y[0], 8 * M, cudaMemcpyDeviceToDevice, st));
+  }
+  CK(cudaStreamSynchronize(st));  // h_st may still be read by an earlier async copy
+  DevState &h = *s->h_st;
+  std::memset(&h, 0, sizeof(DevState));
+  h.eta = s->eta_hat0;
+  h.omega = s->omega0;
+  h.W = 0.0;
+  h.tol = tol;
+  h.q_norm = s->q_norm;
+  h.c_norm = s->c_norm;
+  h.theta = s->prm.theta;
+  h.eps_zero = s->prm.eps_zero;
+  h.beta_suff = s->prm.beta_suff;
+  h.beta_nec = s->prm.beta_nec;
+  h.beta_art = s->prm.beta_art;
+  h.rel_kkt_best = INFINITY;
+  h.max_iter = max_iter;
+  h.f64_switch_k = -1;
+  h.cur = 0;
+  h.need_g = 1;
+  h.check_pending = 1;
+  h.status = ST_RUNNING;
+  h.mode = MODE_INIT;
+  h.P = s->prm.check_period;
+  h.trace_cap = TRACE_CAP;
+  h.use_f32 = s->prm.value_bits == 32 ? 1 : 0;
+  h.polish = s->prm.f32_polish ? 1 : 0;
+  CK(cudaMemcpyAsync(s->st, s->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
+  // KKT(z^{0,0}): K'y, Kx and the pieces of eq. (kkt) at the start point
+  CK(launch_check_primal(s->KT, V, s->st, s->gridR1, st));
+  CK(launch_check_dual(s->K, V, s->st, s->gridR2, st));
+  s->launches = 0;
+  s->have_result = false;
+  s->last_status = ST_RUNNING;
+  s->t0 = now_ms();
+  return PDLP_OK;
+}
+
+int pdlp_run_periods(pdlp_solver *s, int32_t n_periods) {
+  g_err.clear();
+  if (!s || !s->gexec) return fail(PDLP_ERR_INVALID, "call pdlp_begin first");
+  CK(cudaSetDevice(s->device));
+  for (int32_t i = 0; i < n_periods; ++i) {
+    CK(cudaGraphLaunch(s->gexec, s->stream));
+    s->launches++;
+  }
+  return PDLP_OK;
+}
+
+int pdlp_poll(pdlp_solver *s, int *status, int64_t *iters) {
+  g_err.clear();
+  if (!s) return fail(PDLP_ERR_INVALID, "solver is NULL");
+  CK(cudaSetDevice(s->device));
+  CK(cudaMemcpyAsync(&s->h_poll[0], s->st, sizeof(DevState), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (status) *status = s->h_poll[0].status;
+  if (iters) *iters = s->h_poll[0].k;
+  return PDLP_OK;
+}
+
+int pdlp_finish(pdlp_solver *s, double *x_out, double *y_out, int *status, int64_t *iters) {
+  g_err.clear();
+  if (!s) return fail(PDLP_ERR_INVALID, "solver is NULL");
+  CK(cudaSetDevice(s->device));
+  cudaStream_t st = s->stream;
+  CK(launch_output(s->V, s->st, st));
+  CK(cudaMemcpyAsync(s->h_st, s->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  if (x_out) CK(cudaMemcpyAsync(x_out, s->V.xout, 8 * (size_t)s->n, cudaMemcpyDeviceToHost, st));
+  if (y_out && s->m) CK(cudaMemcpyAsync(y_out, s->V.yout, 8 * (size_t)s->m, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  s->solve_ms = now_ms() - s->t0;
+  s->have_result = true;
+  s->last_status = s->h_st->status;
+  if (status) *status = s->h_st->status;
+  if (iters) *iters = s->h_st->k;
+  return PDLP_OK;
+}
+
+int pdlp_solve_warm(pdlp_solver *s, const double *x0, const double *y0, double tol, int64_t max_iter, double *x_out,
+                    double *y_out, int *status, int64_t *iters) {
+  int rc = pdlp_begin(s, x0, y0, tol, max_iter);
+  if (rc) return rc;
+  cudaStream_t st = s->stream;
+  const double limit_ms = s->prm.time_limit_s > 0.0 ? 1000.0 * s->prm.time_limit_s : INFINITY;
+  // one period in flight ahead of the one being polled
+  int slot = 0;
+  CK(cudaGraphLaunch(s->gexec, st));
+  s->launches++;
+  CK(cudaMemcpyAsync(&s->h_poll[slot], s->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(s->ev[slot], st));
+  for (;;) {
+    const int nxt = slot ^ 1;
+    CK(cudaGraphLaunch(s->gexec, st));
+    s->launches++;
+    CK(cudaMemcpyAsync(&s->h_poll[nxt], s->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(s->ev[nxt], st));
+    CK(cudaEventSynchronize(s->ev[slot]));
+    if (s->h_poll[slot].status != ST_RUNNING) break;
+    if (now_ms() - s->t0 > limit_ms) {
+      CK(launch_time_limit(s->st, st));
+      break;
+    }
+    slot = nxt;
+  }
+  return pdlp_finish(s, x_out, y_out, status, iters);
+}
+
+int pdlp_solve(pdlp_solver *s, double tol, int64_t max_iter, double *x_out, double *y_out, int *status,
+               int64_t *iters) {
+  return pdlp_solve_warm(s, nullptr, nullptr, tol, max_iter, x_out, y_out, status, iters);
+}
+
+int32_t pdlp_kernel_count(void) { return KC_NUM; }
+const char *pdlp_kernel_name(int32_t i) { return kernel_class_name(i); }
+
+int pdlp_time_kernels(pdlp_solver *s, int32_t n_periods, double *ms, int64_t *launches) {
+  g_err.clear();
+  if (!s || !ms || !launches) return fail(PDLP_ERR_INVALID, "null argument");
+  CK(cudaSetDevice(s->device));
+  cudaStream_t st = s->stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto timed = [&](int kc, cudaError_t (*fn)(pdlp_solver *, cudaStream_t)) -> int {
+    CK(cudaEventRecord(e0, st));
+    CK(fn(s, st));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    ms[kc] += t;
+    launches[kc] += 1;
+    return PDLP_OK;
+  };
+  auto poll = [&](DevState &out) -> int {
+    CK(cudaMemcpyAsync(&s->h_poll[0], s->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out = s->h_poll[0];
+    return PDLP_OK;
+  };
+  int rc = PDLP_OK;
+  int done = 0;
+  DevState h;
+  while (done < n_periods && rc == PDLP_OK) {
+    if ((rc = poll(h))) break;
+    if (h.status != ST_RUNNING) break;
+    if (!h.check_pending) {
+      rc = timed(h.need_g ? KC_PRIMAL : KC_PRIMAL_REUSE,
+                 [](pdlp_solver *t, cudaStream_t q) { return launch_primal(t->KT, t->V, t->st, t->gridA, q); });
+      if (!rc) rc = timed(KC_DUAL, [](pdlp_solver *t, cudaStream_t q) { return launch_dual(t->K, t->V, t->st, t->gridB, q); });
+      continue;
+    }
+    rc = timed(KC_R1, [](pdlp_solver *t, cudaStream_t q) { return launch_check_primal(t->KT, t->V, t->st, t->gridR1, q); });
+    if (!rc) rc = timed(KC_R2, [](pdlp_solver *t, cudaStream_t q) { return launch_check_dual(t->K, t->V, t->st, t->gridR2, q); });
+    if (!rc) rc = poll(h);
+    if (!rc && h.status == ST_RUNNING && h.restart_to)
+      rc = timed(KC_R3, [](pdlp_solver *t, cudaStream_t q) { return launch_restart(t->V, t->st, t->gridR3, q); });
+    ++done;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int pdlp_get_info(const pdlp_solver *s, pdlp_info *info) {
+  g_err.clear();
+  if (!s || !info) return fail(PDLP_ERR_INVALID, "null argument");
+  const DevState &h = *s->h_st;
+  std::memset(info, 0, sizeof(*info));
+  info->status = s->have_result ? h.status : -1;
+  info->which = h.which;
+  info->iters = h.k;
+  info->attempts = h.attempts;
+  info->restarts = h.restarts;
+  info->checks = h.checks;
+  info->pobj = h.term[0];
+  info->dobj = h.term[1];
+  info->rp_norm = h.term[2];
+  info->rd_norm = h.term[3];
+  info->q_norm = s->q_norm;
+  info->c_norm = s->c_norm;
+  info->omega = h.omega;
+  info->eta_hat = h.eta;
+  info->setup_ms = s->setup_ms;
+  info->solve_ms = s->solve_ms;
+  info->graph_launches = s->launches;
+  info->f64_switch_iter = h.f64_switch_k;
+  return PDLP_OK;
+}
+
+int pdlp_get_trace(const pdlp_solver *s, pdlp_check *trace, int32_t cap, int32_t *count) {
+  g_err.clear();
+  if (!s || (cap > 0 && !trace)) return fail(PDLP_ERR_INVALID, "null argument");
+  CK(cudaSetDevice(s->device));
+  const int nt = s->h_st->ntrace;
+  if (count) *count = nt;
+  const int ncopy = nt < cap ? nt : cap;
+  if (ncopy <= 0) return PDLP_OK;
+  std::vector<TraceRec> tmp(ncopy);
+  CK(cudaMemcpy(tmp.data(), s->V.trace, sizeof(TraceRec) * ncopy, cudaMemcpyDeviceToHost));
+  for (int i = 0; i < ncopy; ++i) {
+    trace[i].k = tmp[i].k;
+    trace[i].restart = tmp[i].restart;
+    trace[i].cand_avg = tmp[i].cand_avg;
+    trace[i].kkt_cur = tmp[i].kkt_cur;
+    trace[i].kkt_avg = tmp[i].kkt_avg;
+    trace[i].kkt_start = tmp[i].kkt_start;
+    trace[i].omega = tmp[i].omega;
+    trace[i].eta_hat = tmp[i].eta_hat;
+  }
+  return PDLP_OK;
+}
+
+int pdlp_get_scaling(const pdlp_solver *s, double *D1, double *D2, double *val_scaled) {
+  g_err.clear();
+  if (!s) return fail(PDLP_ERR_INVALID, "solver is NULL");
+  CK(cudaSetDevice(s->device));
+  CK(cudaStreamSynchronize(s->stream));
+  if (D1 && s->m) CK(cudaMemcpy(D1, s->D1, 8 * (size_t)s->m, cudaMemcpyDeviceToHost));
+  if (D2) CK(cudaMemcpy(D2, s->D2, 8 * (size_t)s->n, cudaMemcpyDeviceToHost));
+  if (val_scaled && s->nnz) CK(cudaMemcpy(val_scaled, s->K_val, 8 * (size_t)s->nnz, cudaMemcpyDeviceToHost));
+  return PDLP_OK;
+}
+
+void *pdlp_get_stream(const pdlp_solver *s) { return s ? (void *)s->stream : nullptr; }
+
+size_t pdlp_device_bytes(const pdlp_solver *s) { return s ? s->arena_bytes : 0; }
+
+}  // extern "C"

@@ -1,0 +1,197 @@
+// Setup-time kernels: Sec. 2.2 diagonal preconditioning on the GPU (Ruiz
+// l_inf passes, then one Pock-Chambolle pass), scaling of c, q, l, u, the
+// FP32 value copy, the scalar reductions behind Algorithm 1's initial step
+// size and InitializePrimalWeight, and the scaled warm-start point.
+//
+// K and K' are scaled in place with the same two divisions in the same order
+// for every entry, (v / r_i) / s_j with r the row factor of K and s its column
+// factor, so the two copies stay exact transposes of each other.
+
+#include <math.h>
+
+#include "pdlp_internal.cuh"
+
+namespace pdlp {
+
+namespace {
+
+constexpr int ST = 256;
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_add(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One warp per row: out[r] = max_e |val[e]| (kind 0) or sum_e |val[e]|^p (kind 1).
+__global__ void k_row_norm(const int32_t *__restrict__ ptr, const double *__restrict__ val, int32_t rows,
+                           double *__restrict__ out, int kind, double p) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * ST + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * ST) >> 5;
+  for (long long r = warp; r < rows; r += nwarps) {
+    const int e0 = ptr[r], e1 = ptr[r + 1];
+    double acc = 0.0;
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const double a = fabs(val[e]);
+      if (kind == 0)
+        acc = fmax(acc, a);
+      else
+        acc += (p == 1.0) ? a : pow(a, p);
+    }
+    acc = kind == 0 ? warp_max(acc) : warp_add(acc);
+    if (lane == 0) out[r] = acc;
+  }
+}
+
+// f <- sqrt(f), or 1 where the line is empty (norm 0).
+__global__ void k_factor(double *__restrict__ f, int32_t n) {
+  for (int i = blockIdx.x * ST + threadIdx.x; i < n; i += gridDim.x * ST) f[i] = f[i] > 0.0 ? sqrt(f[i]) : 1.0;
+}
+
+// K (row_is_kmajor = 1): val[e] = (val[e] / r[i]) / s[idx[e]] for row i.
+// K' (row_is_kmajor = 0): row j of K', idx = row of K: (val / r[idx]) / s[j].
+__global__ void k_scale(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx, double *__restrict__ val,
+                        int32_t rows, const double *__restrict__ r, const double *__restrict__ s,
+                        int row_is_kmajor) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * ST + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * ST) >> 5;
+  for (long long row = warp; row < rows; row += nwarps) {
+    const int e0 = ptr[row], e1 = ptr[row + 1];
+    for (int e = e0 + lane; e < e1; e += 32) {
+      const int o = idx[e];
+      if (row_is_kmajor)
+        val[e] = val[e] / r[row] / s[o];
+      else
+        val[e] = val[e] / r[o] / s[row];
+    }
+  }
+}
+
+__global__ void k_div(double *__restrict__ D, const double *__restrict__ f, int32_t n) {
+  for (int i = blockIdx.x * ST + threadIdx.x; i < n; i += gridDim.x * ST) D[i] = D[i] / f[i];
+}
+
+__global__ void k_fill(double *__restrict__ a, int32_t n, double v) {
+  for (int i = blockIdx.x * ST + threadIdx.x; i < n; i += gridDim.x * ST) a[i] = v;
+}
+
+__global__ void k_vectors(int32_t m, int32_t n, const double *__restrict__ c0, const double *__restrict__ q0,
+                          const double *__restrict__ l0, const double *__restrict__ u0, const double *__restrict__ D1,
+                          const double *__restrict__ D2, double *__restrict__ c, double *__restrict__ q,
+                          double *__restrict__ l, double *__restrict__ u) {
+  for (int j = blockIdx.x * ST + threadIdx.x; j < n; j += gridDim.x * ST) {
+    c[j] = D2[j] * c0[j];
+    l[j] = l0[j] / D2[j];
+    u[j] = u0[j] / D2[j];
+  }
+  for (int i = blockIdx.x * ST + threadIdx.x; i < m; i += gridDim.x * ST) q[i] = D1[i] * q0[i];
+}
+
+__global__ void k_f32(long long nnz, const double *__restrict__ v, float *__restrict__ f) {
+  for (long long e = (long long)blockIdx.x * ST + threadIdx.x; e < nnz; e += (long long)gridDim.x * ST)
+    f[e] = (float)v[e];
+}
+
+// Single CTA of 1024 threads: out = {sum c^2, sum q^2, max |val|}; fixed order.
+__global__ void k_scalars(int32_t m, int32_t n, long long nnz, const double *__restrict__ c,
+                          const double *__restrict__ q, const double *__restrict__ val, double *__restrict__ out) {
+  __shared__ double red[3][32];
+  double a = 0.0, b = 0.0, mx = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) a += c[j] * c[j];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) b += q[i] * q[i];
+  for (long long e = threadIdx.x; e < nnz; e += blockDim.x) mx = fmax(mx, fabs(val[e]));
+  a = warp_add(a);
+  b = warp_add(b);
+  mx = warp_max(mx);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+    red[2][wid] = mx;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    a = warp_add(lane < nw ? red[0][lane] : 0.0);
+    b = warp_add(lane < nw ? red[1][lane] : 0.0);
+    mx = warp_max(lane < nw ? red[2][lane] : 0.0);
+    if (lane == 0) {
+      out[0] = a;
+      out[1] = b;
+      out[2] = mx;
+    }
+  }
+}
+
+__global__ void k_warm(int32_t m, int32_t n, const double *__restrict__ x0, const double *__restrict__ y0,
+                       const double *__restrict__ D1, const double *__restrict__ D2, double *__restrict__ x,
+                       double *__restrict__ y) {
+  for (int j = blockIdx.x * ST + threadIdx.x; j < n; j += gridDim.x * ST) x[j] = x0 ? x0[j] / D2[j] : 0.0;
+  for (int i = blockIdx.x * ST + threadIdx.x; i < m; i += gridDim.x * ST) y[i] = y0 ? y0[i] / D1[i] : 0.0;
+}
+
+int grid_for(long long n) {
+  long long g = (n + ST - 1) / ST;
+  if (g > 8192) g = 8192;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32_t *K_idx, double *K_val,
+                        int32_t *T_ptr, int32_t *T_idx, double *T_val, double *D1, double *D2, double *work_m,
+                        double *work_n, int ruiz_iters, double pc_alpha, cudaStream_t s) {
+  (void)nnz;
+  if (m > 0) k_fill<<<grid_for(m), ST, 0, s>>>(D1, m, 1.0);
+  k_fill<<<grid_for(n), ST, 0, s>>>(D2, n, 1.0);
+  const int passes = ruiz_iters + (pc_alpha >= 0.0 ? 1 : 0);
+  for (int it = 0; it < passes; ++it) {
+    const bool ruiz = it < ruiz_iters;
+    const int kind = ruiz ? 0 : 1;
+    // row factors of K (one warp per row of K), column factors (rows of K')
+    if (m > 0) k_row_norm<<<grid_for((long long)m * 32), ST, 0, s>>>(K_ptr, K_val, m, work_m, kind, 2.0 - pc_alpha);
+    k_row_norm<<<grid_for((long long)n * 32), ST, 0, s>>>(T_ptr, T_val, n, work_n, kind, pc_alpha);
+    if (m > 0) k_factor<<<grid_for(m), ST, 0, s>>>(work_m, m);
+    k_factor<<<grid_for(n), ST, 0, s>>>(work_n, n);
+    if (m > 0) k_scale<<<grid_for((long long)m * 32), ST, 0, s>>>(K_ptr, K_idx, K_val, m, work_m, work_n, 1);
+    k_scale<<<grid_for((long long)n * 32), ST, 0, s>>>(T_ptr, T_idx, T_val, n, work_m, work_n, 0);
+    if (m > 0) k_div<<<grid_for(m), ST, 0, s>>>(D1, work_m, m);
+    k_div<<<grid_for(n), ST, 0, s>>>(D2, work_n, n);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *q0, const double *l0,
+                          const double *u0, const double *D1, const double *D2, double *c, double *q, double *l,
+                          double *u, cudaStream_t s) {
+  k_vectors<<<grid_for(n > m ? n : m), ST, 0, s>>>(m, n, c0, q0, l0, u0, D1, D2, c, q, l, u);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_f32(int64_t nnz, const double *val, float *val32, cudaStream_t s) {
+  if (nnz > 0) k_f32<<<grid_for(nnz), ST, 0, s>>>(nnz, val, val32);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_scalars(int32_t m, int32_t n, int64_t nnz, const double *c, const double *q, const double *val,
+                          double *out, cudaStream_t s) {
+  k_scalars<<<1, 1024, 0, s>>>(m, n, nnz, c, q, val, out);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0, const double *D1,
+                       const double *D2, double *x, double *y, cudaStream_t s) {
+  k_warm<<<grid_for(n > m ? n : m), ST, 0, s>>>(m, n, x0, y0, D1, D2, x, y);
+  return cudaGetLastError();
+}
+
+}  // namespace pdlp

@@ -1,0 +1,314 @@
+"""ctypes binding of the C ABI in include/pdlp.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA kernels of libpdlp_gb300.so; this
+module only converts numpy arrays to pointers.  There is no CPU fallback: if
+the library is missing or no GB300 is visible, the calls raise.
+
+Module-level functions carry the C names (pdlp_create, pdlp_solve, ...);
+``Solver`` wraps them for convenience.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+OK, ERR_INVALID, ERR_CUDA, ERR_OOM = 0, -1, -2, -3
+OPTIMAL, ITER_LIMIT, TIME_LIMIT, NUMERICAL = 0, 1, 2, 3
+STATUS_NAMES = {OPTIMAL: "optimal", ITER_LIMIT: "iteration_limit", TIME_LIMIT: "time_limit",
+                NUMERICAL: "numerical_error", -1: "running"}
+
+
+class PdlpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("pdlp error %d: %s" % (code, msg))
+        self.code = code
+
+
+class pdlp_params(C.Structure):
+    _fields_ = [
+        ("check_period", C.c_int32),
+        ("ruiz_iters", C.c_int32),
+        ("pc_alpha", C.c_double),
+        ("theta", C.c_double),
+        ("eps_zero", C.c_double),
+        ("beta_suff", C.c_double),
+        ("beta_nec", C.c_double),
+        ("beta_art", C.c_double),
+        ("time_limit_s", C.c_double),
+        ("value_bits", C.c_int32),
+        ("f32_polish", C.c_int32),
+    ]
+
+
+class pdlp_info(C.Structure):
+    _fields_ = [
+        ("status", C.c_int32),
+        ("which", C.c_int32),
+        ("iters", C.c_int64),
+        ("attempts", C.c_int64),
+        ("restarts", C.c_int64),
+        ("checks", C.c_int64),
+        ("pobj", C.c_double),
+        ("dobj", C.c_double),
+        ("rp_norm", C.c_double),
+        ("rd_norm", C.c_double),
+        ("q_norm", C.c_double),
+        ("c_norm", C.c_double),
+        ("omega", C.c_double),
+        ("eta_hat", C.c_double),
+        ("setup_ms", C.c_double),
+        ("solve_ms", C.c_double),
+        ("graph_launches", C.c_int64),
+        ("f64_switch_iter", C.c_int64),
+    ]
+
+
+CHECK_DTYPE = np.dtype(
+    [
+        ("k", np.int64),
+        ("restart", np.int32),
+        ("cand_avg", np.int32),
+        ("kkt_cur", np.float64),
+        ("kkt_avg", np.float64),
+        ("kkt_start", np.float64),
+        ("omega", np.float64),
+        ("eta_hat", np.float64),
+    ]
+)
+
+# every symbol include/pdlp.h declares
+EXPORTS = (
+    "pdlp_default_params", "pdlp_create", "pdlp_create_ex", "pdlp_solve", "pdlp_solve_warm", "pdlp_begin",
+    "pdlp_run_periods", "pdlp_poll", "pdlp_finish", "pdlp_time_kernels", "pdlp_kernel_count",
+    "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
+    "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error",
+)
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libpdlp_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("libpdlp_gb300.so is not built; run __graft_entry__.build() or "
+                           "python -m paper_2311_12180_gb300._build")
+    L = C.CDLL(path)
+    vp, i32, i64, d, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.c_size_t
+    P = C.POINTER
+    L.pdlp_default_params.argtypes = [P(pdlp_params)]
+    L.pdlp_default_params.restype = None
+    L.pdlp_create.argtypes = [P(vp), i32, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.pdlp_create.restype = C.c_int
+    L.pdlp_create_ex.argtypes = [P(vp), i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, P(pdlp_params), vp]
+    L.pdlp_create_ex.restype = C.c_int
+    L.pdlp_solve.argtypes = [vp, d, i64, vp, vp, P(C.c_int), P(i64)]
+    L.pdlp_solve.restype = C.c_int
+    L.pdlp_solve_warm.argtypes = [vp, vp, vp, d, i64, vp, vp, P(C.c_int), P(i64)]
+    L.pdlp_solve_warm.restype = C.c_int
+    L.pdlp_begin.argtypes = [vp, vp, vp, d, i64]
+    L.pdlp_begin.restype = C.c_int
+    L.pdlp_run_periods.argtypes = [vp, i32]
+    L.pdlp_run_periods.restype = C.c_int
+    L.pdlp_poll.argtypes = [vp, P(C.c_int), P(i64)]
+    L.pdlp_poll.restype = C.c_int
+    L.pdlp_finish.argtypes = [vp, vp, vp, P(C.c_int), P(i64)]
+    L.pdlp_finish.restype = C.c_int
+    L.pdlp_time_kernels.argtypes = [vp, i32, vp, vp]
+    L.pdlp_time_kernels.restype = C.c_int
+    L.pdlp_kernel_count.argtypes = []
+    L.pdlp_kernel_count.restype = i32
+    L.pdlp_kernel_name.argtypes = [i32]
+    L.pdlp_kernel_name.restype = C.c_char_p
+    L.pdlp_get_info.argtypes = [vp, P(pdlp_info)]
+    L.pdlp_get_info.restype = C.c_int
+    L.pdlp_get_trace.argtypes = [vp, vp, i32, P(i32)]
+    L.pdlp_get_trace.restype = C.c_int
+    L.pdlp_get_scaling.argtypes = [vp, vp, vp, vp]
+    L.pdlp_get_scaling.restype = C.c_int
+    L.pdlp_get_stream.argtypes = [vp]
+    L.pdlp_get_stream.restype = vp
+    L.pdlp_device_bytes.argtypes = [vp]
+    L.pdlp_device_bytes.restype = sz
+    L.pdlp_destroy.argtypes = [vp]
+    L.pdlp_destroy.restype = None
+    L.pdlp_last_error.argtypes = []
+    L.pdlp_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != OK:
+        raise PdlpError(rc, lib().pdlp_last_error().decode())
+    return rc
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a, n=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.shape[0] != n:
+        raise ValueError("expected length %d, got %d" % (n, a.shape[0]))
+    return a
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------- C-named functions
+
+
+def pdlp_default_params() -> pdlp_params:
+    p = pdlp_params()
+    lib().pdlp_default_params(C.byref(p))
+    return p
+
+
+def pdlp_create(m, n, n_eq, c, row_ptr, col_idx, val, q, l, u, params=None, stream=None):
+    """pdlp_create / pdlp_create_ex; returns the opaque handle (c_void_p)."""
+    h = C.c_void_p()
+    c, q, l, u = _f64(c, n), _f64(q, m), _f64(l, n), _f64(u, n)
+    row_ptr, col_idx, val = _i32(row_ptr), _i32(col_idx), _f64(val)
+    if params is None and stream is None:
+        rc = lib().pdlp_create(C.byref(h), m, n, n_eq, _ptr(c), _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(q),
+                               _ptr(l), _ptr(u))
+    else:
+        rc = lib().pdlp_create_ex(C.byref(h), m, n, n_eq, _ptr(c), _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                  _ptr(q), _ptr(l), _ptr(u), C.byref(params) if params is not None else None,
+                                  C.c_void_p(stream) if stream else None)
+    _check(rc)
+    return h
+
+
+def pdlp_solve_warm(h, x0, y0, tol, max_iter, n, m):
+    x = np.empty(n)
+    y = np.empty(max(m, 1))
+    st = C.c_int(-9)
+    it = C.c_int64(0)
+    _check(lib().pdlp_solve_warm(h, _ptr(_f64(x0, n)), _ptr(_f64(y0, m)), tol, int(max_iter), _ptr(x), _ptr(y),
+                                 C.byref(st), C.byref(it)))
+    return x, y[:m], st.value, it.value
+
+
+def pdlp_solve(h, tol, max_iter, n, m):
+    return pdlp_solve_warm(h, None, None, tol, max_iter, n, m)
+
+
+def pdlp_destroy(h):
+    if h:
+        lib().pdlp_destroy(h)
+
+
+def kernel_names():
+    L = lib()
+    return [L.pdlp_kernel_name(i).decode() for i in range(L.pdlp_kernel_count())]
+
+
+# ---------------------------------------------------------------- convenience wrapper
+
+
+class Solver:
+    """One LP on the GPU.  `lp` is anything with fields m, n, n_eq, c,
+    row_ptr, col_idx, val, q, l, u (e.g. lpgen.LP)."""
+
+    def __init__(self, lp, params: pdlp_params | None = None, stream: int | None = None, **kw):
+        if kw:
+            params = params or pdlp_default_params()
+            for k, v in kw.items():
+                setattr(params, k, v)
+        self.m, self.n, self.n_eq = int(lp.m), int(lp.n), int(lp.n_eq)
+        self.nnz = int(lp.row_ptr[-1])
+        self.h = pdlp_create(self.m, self.n, self.n_eq, lp.c, lp.row_ptr, lp.col_idx, lp.val, lp.q, lp.l, lp.u,
+                             params=params, stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            pdlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, tol=1e-4, max_iter=1_000_000, x0=None, y0=None):
+        """Returns (x, y, status, iters) in the original space."""
+        return pdlp_solve_warm(self.h, x0, y0, tol, max_iter, self.n, self.m)
+
+    # non-blocking pieces
+    def begin(self, tol=1e-4, max_iter=1_000_000, x0=None, y0=None):
+        _check(lib().pdlp_begin(self.h, _ptr(_f64(x0, self.n)), _ptr(_f64(y0, self.m)), tol, int(max_iter)))
+
+    def run_periods(self, n):
+        _check(lib().pdlp_run_periods(self.h, int(n)))
+
+    def poll(self):
+        st = C.c_int(-9)
+        it = C.c_int64(0)
+        _check(lib().pdlp_poll(self.h, C.byref(st), C.byref(it)))
+        return st.value, it.value
+
+    def finish(self):
+        x = np.empty(self.n)
+        y = np.empty(max(self.m, 1))
+        st = C.c_int(-9)
+        it = C.c_int64(0)
+        _check(lib().pdlp_finish(self.h, _ptr(x), _ptr(y), C.byref(st), C.byref(it)))
+        return x, y[: self.m], st.value, it.value
+
+    def time_kernels(self, n_periods):
+        k = lib().pdlp_kernel_count()
+        ms = np.zeros(k)
+        ln = np.zeros(k, dtype=np.int64)
+        _check(lib().pdlp_time_kernels(self.h, int(n_periods), _ptr(ms), _ptr(ln)))
+        return {name: (float(ms[i]), int(ln[i])) for i, name in enumerate(kernel_names())}
+
+    def info(self) -> dict:
+        inf = pdlp_info()
+        _check(lib().pdlp_get_info(self.h, C.byref(inf)))
+        return {f: getattr(inf, f) for f, _ in pdlp_info._fields_}
+
+    def trace(self, cap=1 << 16):
+        out = np.zeros(cap, dtype=CHECK_DTYPE)
+        cnt = C.c_int32(0)
+        _check(lib().pdlp_get_trace(self.h, _ptr(out), cap, C.byref(cnt)))
+        return out[: min(cnt.value, cap)].copy()
+
+    def scaling(self):
+        D1 = np.zeros(max(self.m, 1))
+        D2 = np.zeros(self.n)
+        v = np.zeros(max(self.nnz, 1))
+        _check(lib().pdlp_get_scaling(self.h, _ptr(D1), _ptr(D2), _ptr(v)))
+        return D1[: self.m], D2, v[: self.nnz]
+
+    @property
+    def stream(self) -> int:
+        return lib().pdlp_get_stream(self.h) or 0
+
+    def device_bytes(self) -> int:
+        return int(lib().pdlp_device_bytes(self.h))

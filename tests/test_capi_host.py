@@ -1,0 +1,110 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/pdlp.h declares, and rejects malformed input on the host before any
+CUDA call."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import lpgen
+from paper_2311_12180_gb300 import _build
+from paper_2311_12180_gb300 import pdlp as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return P.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pdlp.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pdlp_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(P.EXPORTS) == names
+
+
+def test_default_params(L):
+    p = P.pdlp_default_params()
+    assert p.check_period == 64 and p.ruiz_iters == 10 and p.pc_alpha == 1.0
+    assert (p.beta_suff, p.beta_nec, p.beta_art) == (0.2, 0.8, 0.36)
+    assert p.theta == 0.5 and p.eps_zero == 1e-10 and p.value_bits == 64
+
+
+def test_kernel_names(L):
+    names = P.kernel_names()
+    assert names[:2] == ["k_primal", "k_dual"]
+
+
+def _create(lp, **kw):
+    return P.pdlp_create(lp.m, lp.n, lp.n_eq, lp.c, lp.row_ptr, lp.col_idx, lp.val, lp.q, lp.l, lp.u, **kw)
+
+
+@pytest.mark.parametrize("defect", ["col_range", "row_ptr_order", "row_ptr_start", "nan_val", "l_gt_u",
+                                    "nan_c", "inf_q", "l_plus_inf", "n_eq_too_big", "n_zero"])
+def test_invalid_input_rejected_on_host(L, defect):
+    lp = lpgen.tiny_lp(0)
+    lp.col_idx = lp.col_idx.copy()
+    lp.row_ptr = lp.row_ptr.copy()
+    lp.val, lp.c, lp.q, lp.l, lp.u = lp.val.copy(), lp.c.copy(), lp.q.copy(), lp.l.copy(), lp.u.copy()
+    if defect == "col_range":
+        lp.col_idx[5] = lp.n
+    elif defect == "row_ptr_order":
+        lp.row_ptr[3] = lp.row_ptr[4] + 1
+    elif defect == "row_ptr_start":
+        lp.row_ptr = lp.row_ptr + 1
+    elif defect == "nan_val":
+        lp.val[0] = np.nan
+    elif defect == "l_gt_u":
+        lp.l[2] = 11.0
+    elif defect == "nan_c":
+        lp.c[1] = np.nan
+    elif defect == "inf_q":
+        lp.q[0] = np.inf
+    elif defect == "l_plus_inf":
+        lp.l[0] = np.inf
+        lp.u[0] = np.inf
+    elif defect == "n_eq_too_big":
+        lp.n_eq = lp.m + 1
+    elif defect == "n_zero":
+        lp.n = 0
+        lp.c = lp.c[:0]
+        lp.l = lp.l[:0]
+        lp.u = lp.u[:0]
+    with pytest.raises(P.PdlpError) as e:
+        _create(lp)
+    assert e.value.code == P.ERR_INVALID
+    assert L.pdlp_last_error().decode() != ""
+
+
+def test_invalid_params_rejected(L):
+    lp = lpgen.tiny_lp(0)
+    p = P.pdlp_default_params()
+    p.check_period = 0
+    with pytest.raises(P.PdlpError) as e:
+        _create(lp, params=p)
+    assert e.value.code == P.ERR_INVALID
+    p = P.pdlp_default_params()
+    p.value_bits = 16
+    with pytest.raises(P.PdlpError):
+        _create(lp, params=p)
+
+
+def test_null_handles_are_safe(L):
+    L.pdlp_destroy(None)
+    assert L.pdlp_device_bytes(None) == 0
+    assert L.pdlp_get_stream(None) is None
+    assert L.pdlp_run_periods(None, 1) == P.ERR_INVALID
+    assert L.pdlp_begin(None, None, None, 1e-4, 10) == P.ERR_INVALID

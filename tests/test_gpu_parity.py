@@ -1,0 +1,230 @@
+"""GPU parity: the CUDA solver (through the C ABI) against the FP64 CPU
+oracle on the same seeded inputs.
+
+Tolerances (derived from the arithmetic, not tuned):
+  * Scaling: the Ruiz passes are max / sqrt / divide -- exact and correctly
+    rounded on both sides -- so only the Pock-Chambolle row / column sums differ
+    in summation order: |D1, D2, K~| agree to a few ulps (rtol 1e-13).
+  * Iterates after N steps with identical accept / restart decisions: both
+    sides compute the same formulas in FP64; summation order and FMA
+    contraction differ, so every step adds O(1e-16) relative noise and PDHG
+    is non-expansive: rtol 1e-9 with an absolute floor of 1e-9 * max|x|.
+  * Solutions: the optimum need not be unique, so vectors are never compared
+    after convergence; the objective must match the oracle's to 1e-6 relative
+    at tol = 1e-8 (a tol-eps solution's objective is only fixed to
+    eps * (1 + |obj|)), and the oracle's own Sec. 4.1 evaluation of the GPU's
+    (x, y) must pass the requested tolerance.
+"""
+
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+from paper_2311_12180_gb300 import pdlp as P
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(lp, **kw):
+    return P.Solver(lp, **kw)
+
+
+def _oracle(lp, **kw):
+    return oracle.solve(lp, **kw)
+
+
+def _assert_feasible_signs(lp, x, y):
+    assert np.all(x >= lp.l) and np.all(x <= lp.u)
+    assert np.all(y[lp.n_eq:] >= 0)
+
+
+# ---------------------------------------------------------------- scaling
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_scaling_matches_oracle(seed):
+    lp = lpgen.large_lp(seed, m=3000, n=6000, nnz=60000)
+    with _solver(lp) as s:
+        D1, D2, v = s.scaling()
+    sv, oD1, oD2 = oracle.precondition(lp, ruiz_iters=10, pc_alpha=1.0)
+    np.testing.assert_allclose(D1, oD1, rtol=1e-13)
+    np.testing.assert_allclose(D2, oD2, rtol=1e-13)
+    np.testing.assert_allclose(v, sv, rtol=1e-13)
+
+
+def test_ruiz_only_scaling_is_bitwise():
+    lp = lpgen.tiny_lp(3)
+    with _solver(lp, pc_alpha=-1.0) as s:
+        D1, D2, v = s.scaling()
+    sv, oD1, oD2 = oracle.precondition(lp, ruiz_iters=10, pc_alpha=-1.0)
+    assert np.array_equal(D1, oD1) and np.array_equal(D2, oD2) and np.array_equal(v, sv)
+
+
+# ---------------------------------------------------------------- iterates
+
+
+@pytest.mark.parametrize("case,P_,N", [("tiny", 64, 40), ("tiny", 1, 12), ("tiny", 8, 130), ("powerlaw", 64, 30)])
+def test_iterates_match_oracle(case, P_, N):
+    lp = lpgen.tiny_lp(5) if case == "tiny" else lpgen.large_lp(4, m=20000, n=40000, nnz=400000)
+    with _solver(lp, check_period=P_) as s:
+        x, y, st, it = s.solve(tol=1e-14, max_iter=N)
+        tr = s.trace()
+        info = s.info()
+    r = _oracle(lp, tol=1e-14, max_iter=N, check_period=P_)
+    assert st == P.ITER_LIMIT == r.status and it == N == r.iters
+    assert info["attempts"] == r.attempts and info["restarts"] == r.restarts
+    assert len(tr) == len(r.trace)
+    np.testing.assert_array_equal(tr["k"], r.trace["k"])
+    np.testing.assert_array_equal(tr["restart"], r.trace["restart"])
+    np.testing.assert_array_equal(tr["cand_avg"], r.trace["cand_avg"])
+    for f in ("kkt_cur", "kkt_avg", "kkt_start", "omega", "eta_hat"):
+        np.testing.assert_allclose(tr[f], r.trace[f], rtol=1e-9, err_msg=f)
+    np.testing.assert_allclose(x, r.x, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.x).max()))
+    np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))
+
+
+def test_deterministic():
+    lp = lpgen.large_lp(6, m=20000, n=40000, nnz=400000)
+    with _solver(lp) as s:
+        a = s.solve(tol=1e-12, max_iter=300)
+        b = s.solve(tol=1e-12, max_iter=300)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[3] == b[3]
+
+
+# ---------------------------------------------------------------- solutions
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tiny_solution_parity(seed):
+    lp = lpgen.tiny_lp(seed)
+    r4 = _oracle(lp, tol=1e-4)
+    r8 = _oracle(lp, tol=1e-8)
+    with _solver(lp) as s:
+        x4, y4, st4, it4 = s.solve(tol=1e-4)
+        x8, y8, st8, it8 = s.solve(tol=1e-8)
+        info8 = s.info()
+    assert st4 == st8 == P.OPTIMAL
+    assert oracle.passes(lp, x4, y4, 1e-4) and oracle.passes(lp, x8, y8, 1e-8)
+    _assert_feasible_signs(lp, x8, y8)
+    obj8 = float(lp.c @ x8)
+    assert abs(obj8 - r8.pobj) <= 1e-6 * abs(r8.pobj)
+    assert abs(obj8 - lp.obj_star) <= 1e-6 * abs(lp.obj_star)
+    assert abs(float(lp.c @ x4) - r4.pobj) <= 2e-4 * (1 + abs(r4.pobj))
+    # same decisions on the same arithmetic: identical iteration counts
+    assert it4 == r4.iters and it8 == r8.iters
+    assert info8["pobj"] == pytest.approx(r8.pobj, rel=1e-9)
+
+
+@pytest.mark.parametrize("case", ["all_eq", "all_ineq", "no_rows", "free_vars", "long_rows", "empty_lines",
+                                  "ragged_tiles"])
+def test_edge_cases(case):
+    rng = np.random.default_rng(17)
+    if case == "all_eq":
+        lp = lpgen.tiny_lp(21, m_eq=150, m_ineq=0, n=400)
+    elif case == "all_ineq":
+        lp = lpgen.tiny_lp(22, m_eq=0, m_ineq=150, n=400)
+    elif case == "no_rows":
+        n = 300
+        c = rng.standard_normal(n)
+        lp = lpgen.LP(m=0, n=n, n_eq=0, c=c, row_ptr=np.zeros(1, np.int32), col_idx=np.zeros(0, np.int32),
+                      val=np.zeros(0), q=np.zeros(0), l=rng.uniform(-2, 0, n), u=rng.uniform(0, 2, n))
+    elif case == "free_vars":
+        lp = lpgen.large_lp(23, m=400, n=800, nnz=6000)  # 20 % free, 50 % [0, inf)
+    elif case == "long_rows":
+        # rows much longer than a tile (2048) next to short ones
+        m, n = 40, 12000
+        lens = np.array([1, 2, 5000, 3, 2500, 1] + [40] * (m - 6))
+        row_ptr, cols = lpgen._sample_rows(rng, lens, n)
+        row_ptr, cols = lpgen._cover_columns(rng, row_ptr, cols, m, n)
+        val = rng.standard_normal(cols.size)
+        lp = lpgen.plant(rng, m, n, 20, row_ptr, cols, val, np.zeros(n), np.full(n, 10.0))
+    elif case == "empty_lines":
+        # an empty ">=" row with q <= 0 and empty columns (variables only in c)
+        base = lpgen.tiny_lp(24, m_eq=60, m_ineq=60, n=300)
+        m, n = base.m + 1, base.n + 7
+        row_ptr = np.concatenate([base.row_ptr, [base.row_ptr[-1]]]).astype(np.int32)
+        c = np.concatenate([base.c, rng.uniform(0.5, 1.0, 7)])
+        q = np.concatenate([base.q, [-1.0]])
+        lp = lpgen.LP(m=m, n=n, n_eq=base.n_eq, c=c, row_ptr=row_ptr, col_idx=base.col_idx, val=base.val, q=q,
+                      l=np.concatenate([base.l, np.zeros(7)]), u=np.concatenate([base.u, np.full(7, 3.0)]))
+    else:  # sizes that leave a ragged last tile on both sides
+        lp = lpgen.tiny_lp(25, m_eq=257, m_ineq=300, n=2049, density=0.004)
+    r = _oracle(lp, tol=1e-8, max_iter=200000)
+    assert r.status == oracle.OPTIMAL
+    with _solver(lp) as s:
+        x, y, st, it = s.solve(tol=1e-8, max_iter=200000)
+    assert st == P.OPTIMAL
+    assert oracle.passes(lp, x, y, 1e-8)
+    _assert_feasible_signs(lp, x, y)
+    assert abs(float(lp.c @ x) - r.pobj) <= 1e-6 * (1 + abs(r.pobj))
+
+
+def test_warm_start_at_planted_optimum():
+    lp = lpgen.tiny_lp(4)
+    with _solver(lp, check_period=8) as s:
+        x, y, st, it = s.solve(tol=1e-12, x0=lp.x_star, y0=lp.y_star)
+    assert st == P.OPTIMAL and it == 8
+    assert oracle.relative_kkt(lp, x, y) < 1e-12
+
+
+def test_limits_and_info():
+    lp = lpgen.tiny_lp(6)
+    with _solver(lp, check_period=16) as s:
+        x, y, st, it = s.solve(tol=1e-14, max_iter=100)
+        inf = s.info()
+        assert st == P.ITER_LIMIT and it == 100
+        assert inf["status"] == P.ITER_LIMIT and inf["iters"] == 100
+        assert inf["attempts"] >= 100 and inf["checks"] >= 6
+        assert inf["graph_launches"] >= 7
+        assert s.device_bytes() > 0 and s.stream != 0
+    big = lpgen.large_lp(7, m=20000, n=40000, nnz=400000)
+    with _solver(big, time_limit_s=0.05) as s:
+        x, y, st, it = s.solve(tol=1e-14, max_iter=10**9)
+    assert st == P.TIME_LIMIT and it > 0
+
+
+def test_async_pieces_match_blocking_solve():
+    lp = lpgen.tiny_lp(8)
+    with _solver(lp) as s:
+        xa, ya, sa, ia = s.solve(tol=1e-6)
+        s.begin(tol=1e-6)
+        for _ in range(10000):
+            s.run_periods(4)
+            st, k = s.poll()
+            if st != -1:
+                break
+        xb, yb, sb, ib = s.finish()
+    assert sa == sb == P.OPTIMAL and ia == ib
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+
+
+def test_kernel_timing_mode_runs_same_arithmetic():
+    lp = lpgen.tiny_lp(9)
+    with _solver(lp) as s:
+        x1, y1, s1, i1 = s.solve(tol=1e-12, max_iter=256)
+        s.begin(tol=1e-12, max_iter=256)
+        t = s.time_kernels(4)
+        x2, y2, s2, i2 = s.finish()
+    assert i1 == i2 == 256 and np.array_equal(x1, x2) and np.array_equal(y1, y2)
+    assert t["k_primal"][1] >= 256 and t["k_dual"][1] >= 256 and t["k_check_dual"][1] == 4
+    assert all(v[0] >= 0 for v in t.values())
+
+
+# ---------------------------------------------------------------- full-size workload
+
+
+@pytest.mark.slow
+def test_full_size_iterates_match_oracle():
+    """The 1e6 x 2e6, nnz 2e7 power-law LP in the benchmark's launch
+    configuration: 20 PDHG steps on the GPU against the oracle, elementwise."""
+    lp = lpgen.large_lp(0)
+    N = 20
+    with _solver(lp) as s:
+        x, y, st, it = s.solve(tol=1e-14, max_iter=N)
+        tr = s.trace()
+    r = _oracle(lp, tol=1e-14, max_iter=N)
+    assert st == r.status == P.ITER_LIMIT and it == r.iters == N
+    np.testing.assert_allclose(x, r.x, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.x).max()))
+    np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))
+    assert len(tr) == len(r.trace)
