@@ -42,13 +42,14 @@ double now_ms() {
 }
 
 // Tiles: runs of consecutive rows with at most TILE_NNZ nonzeros and
-// TILE_ROWS rows; a row longer than TILE_NNZ forms a tile of its own.
-std::vector<int32_t> build_tiles(const int32_t *ptr, int32_t rows) {
-  std::vector<int32_t> t;
-  t.push_back(0);
+// TILE_ROWS rows; a row longer than TILE_NNZ forms a tile of its own.  Each
+// entry is {first row, first nonzero}; a final entry {rows, nnz} closes the list.
+std::vector<int2> build_tiles(const int32_t *ptr, int32_t rows) {
+  std::vector<int2> t;
   int32_t r = 0;
   while (r < rows) {
     const int32_t start = r;
+    t.push_back(make_int2(start, ptr[start]));
     long long nz = 0;
     while (r < rows && r - start < TILE_ROWS) {
       const long long len = (long long)ptr[r + 1] - ptr[r];
@@ -57,8 +58,8 @@ std::vector<int32_t> build_tiles(const int32_t *ptr, int32_t rows) {
       ++r;
       if (nz > TILE_NNZ) break;
     }
-    t.push_back(r);
   }
+  t.push_back(make_int2(rows, ptr[rows]));
   return t;
 }
 
@@ -233,8 +234,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
         tv[pos] = val[e];
       }
   }
-  std::vector<int32_t> tilesK = build_tiles(row_ptr, m);
-  std::vector<int32_t> tilesT = build_tiles(tp.data(), n);
+  std::vector<int2> tilesK = build_tiles(row_ptr, m);
+  std::vector<int2> tilesT = build_tiles(tp.data(), n);
   double qn = 0.0, cn = 0.0;
   for (int32_t i = 0; i < m; ++i) qn += q[i] * q[i];
   for (int32_t j = 0; j < n; ++j) cn += c[j] * c[j];
@@ -262,6 +263,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   CKS(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, s->device));
   CKS(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, s->device));
   CKS(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
+  CKS(kernels_init());
   if (stream) {
     s->stream = (cudaStream_t)stream;
   } else {
@@ -296,7 +298,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z + 16), o_Kval = L.take(8 * Z + 16);
   const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + 16), o_Tval = L.take(8 * Z + 16);
   const size_t o_Kv32 = f32 ? L.take(4 * Z + 16) : 0, o_Tv32 = f32 ? L.take(4 * Z + 16) : 0;
-  const size_t o_Ktl = L.take(4 * tilesK.size()), o_Ttl = L.take(4 * tilesT.size());
+  const size_t o_Ktl = L.take(sizeof(int2) * tilesK.size()), o_Ttl = L.take(sizeof(int2) * tilesT.size());
   const size_t nvec_n = 17, nvec_m = 13;
   const size_t o_vn = L.take(8 * N * nvec_n), o_vm = L.take(8 * (M + 1) * nvec_m);
   const size_t o_pA = L.take(8 * (size_t)s->gridA * NV_A), o_pB = L.take(8 * (size_t)s->gridB * NV_B);
@@ -315,7 +317,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   s->T_val = (double *)(A + o_Tval);
   s->K_val32 = f32 ? (float *)(A + o_Kv32) : nullptr;
   s->T_val32 = f32 ? (float *)(A + o_Tv32) : nullptr;
-  int32_t *Ktl = (int32_t *)(A + o_Ktl), *Ttl = (int32_t *)(A + o_Ttl);
+  int2 *Ktl = (int2 *)(A + o_Ktl), *Ttl = (int2 *)(A + o_Ttl);
   double *vn = (double *)(A + o_vn), *vm = (double *)(A + o_vm);
   auto VN = [&](int i) { return vn + (size_t)i * N; };
   auto VM = [&](int i) { return vm + (size_t)i * (M + 1); };
@@ -384,8 +386,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
     CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
   }
   CKS(cudaMemcpyAsync(s->T_ptr, tp.data(), 4 * (N + 1), cudaMemcpyHostToDevice, st));
-  CKS(cudaMemcpyAsync(Ktl, tilesK.data(), 4 * tilesK.size(), cudaMemcpyHostToDevice, st));
-  CKS(cudaMemcpyAsync(Ttl, tilesT.data(), 4 * tilesT.size(), cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(Ktl, tilesK.data(), sizeof(int2) * tilesK.size(), cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(Ttl, tilesT.data(), sizeof(int2) * tilesT.size(), cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(s->l0, l, 8 * N, cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(s->u0, u, 8 * N, cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(V.xout, c, 8 * N, cudaMemcpyHostToDevice, st));  // original c, consumed below

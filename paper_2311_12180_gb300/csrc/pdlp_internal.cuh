@@ -12,7 +12,7 @@ namespace pdlp {
 // time, one row per thread in the epilogue.
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
-constexpr int TILE_NNZ = 2048;
+constexpr int TILE_NNZ = 1024;
 constexpr int TILE_ROWS = 256;
 constexpr int SERIAL_MAX = 32;  // rows up to this length are summed by one thread
 
@@ -42,7 +42,7 @@ struct Csr {
   const int32_t *idx;    // nnz
   const double *val;     // nnz, FP64 (scaled)
   const float *val32;    // nnz, FP32 copy of val (or null)
-  const int32_t *tiles;  // ntiles + 1 row starts
+  const int2 *tmeta;     // ntiles + 1: {first row, first nonzero} of each tile; last = {rows, nnz}
 };
 
 // Device-resident solver state: read by every kernel at entry, written only
@@ -115,6 +115,7 @@ cudaError_t launch_restart(const Vecs &V, DevState *st, int grid, cudaStream_t s
 cudaError_t launch_output(const Vecs &V, DevState *st, cudaStream_t s);
 cudaError_t launch_time_limit(DevState *st, cudaStream_t s);
 int occupancy_grid(int kc, int num_sms);
+cudaError_t kernels_init();  // one-time function attributes (dynamic shared memory)
 
 // ---- setup kernels (pdlp_setup.cu) ----
 cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32_t *K_idx, double *K_val,

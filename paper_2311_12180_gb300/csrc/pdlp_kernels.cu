@@ -25,15 +25,18 @@
 // check kernels advances the solve by exactly one check period.
 //
 // SpMV: a tile is a run of consecutive rows with <= TILE_NNZ nonzeros and
-// <= TILE_ROWS rows (or one longer row).  The CTA loads the tile's column
-// indices and values with coalesced streaming loads (evict-first, they are
-// read once per SpMV), gathers the vector entries (L2-resident: 8-16 MB for
-// the 1e6 x 2e6 LP against a 129 MB L2) and stages value / entry pairs in
-// shared memory; rows of up to SERIAL_MAX entries are then summed by one
-// thread each with FMA, longer rows by a warp, and a row longer than the tile
-// by the whole CTA.  The epilogue runs one row per thread on the row sums
-// still in registers, so x', y', the averages and the partial norms never
-// make an extra pass over HBM.  Reductions are deterministic: fixed per-thread
+// <= TILE_ROWS rows (or one longer row).  The random 8-byte gathers of x / y
+// are the binding resource on GB300 (each is a distinct cache line for the
+// SM's L1TEX tag stage, ~0.9 lines per clock per SM), so the two hot kernels
+// run a persistent per-CTA software pipeline of cp.async copies: while tile k
+// is reduced, the gathers of tile k+1 and the index / value / row-pointer
+// copies of tile k+2 are in flight, landing directly in shared memory.  The
+// reduction keeps every lane busy (GB300 issues FP64 at ~1.6 DFMA per clock
+// per SM and a warp-wide FP64 instruction costs the same however many lanes
+// are active): thread t sums EPT consecutive entries with FMA, and rows that
+// cross thread boundaries are completed from per-thread carries.  The
+// epilogue runs one row per thread on operands prefetched into registers
+// before the reduction.  Reductions are deterministic: fixed per-thread
 // order, fixed shuffle trees, fixed block order in the last CTA.  No atomics
 // touch floating point.
 
@@ -124,12 +127,34 @@ __device__ __forceinline__ void sum_partials(const double *part, int count, doub
 
 // ---------------------------------------------------------------- tile SpMV
 
-// Shared memory of one tile.  With one gathered vector, a[] holds the values
-// and b[] the gathered entries (summed with FMA); with two vectors, a[] and
-// b[] hold the two products.  Either way 2 * TILE_NNZ doubles.
+// Balanced tile SpMV.  GB300 issues FP64 at ~1.6 DFMA per clock per SM, and
+// a warp-wide FP64 instruction costs the same issue slots however many lanes
+// are active, so the reduction must keep every lane busy:
+//   phase A  coalesced streaming loads of the tile's indices and values, the
+//            gathers, and staging of (value, entry) pairs in shared memory;
+//   phase B  thread t sums the EPT consecutive entries [EPT t, EPT t + EPT)
+//            with full-lane FMAs, writing rows that start and end in its range
+//            directly, keeping the partial of the row it enters ("head") and
+//            of the row it leaves open ("carry");
+//   phase C  the thread holding a row's last entry adds the carries of the
+//            threads the row crossed: serially for up to CHAIN_MAX of them,
+//            otherwise with a warp-strided sum.
+// The staging arrays are padded by one slot per EPT entries so phase B reads
+// (stride EPT + 1 = 5 doubles across lanes) are free of bank conflicts.
+constexpr int EPT = TILE_NNZ / NT;  // 4
+static_assert(EPT >= 2 && (EPT & (EPT - 1)) == 0, "EPT must be a power of two");
+constexpr int PADDED = TILE_NNZ + TILE_NNZ / EPT;
+constexpr int CHAIN_MAX = 8;
+__device__ __forceinline__ int pidx(int o) { return o + o / EPT; }
+
+// With one gathered vector a[] holds values and b[] gathered entries (summed
+// with FMA); with two vectors a[] and b[] hold the two products.
+template <int NVS>
 struct TileSmem {
-  double a[TILE_NNZ];
-  double b[TILE_NNZ];
+  double a[PADDED];
+  double b[PADDED];
+  double rowsum[NVS][TILE_ROWS];
+  double carry[NVS][NT];
   int off[TILE_ROWS + 1];
   double red[16 * NW];
   int flag;
@@ -141,12 +166,13 @@ __device__ __forceinline__ double ld_val(const float *p) { return (double)__ldcs
 // Row sums of one tile against NV (1 or 2) gathered vectors: out[a] of thread
 // t holds the sum for row r0 + t (t < r1 - r0).  With SCALED, vector a is
 // multiplied by sc[a] entry by entry before use (the epoch average 1/W * sum).
-template <typename VT, int NV, bool SCALED>
+template <typename VT, int NV, bool SCALED, int NVS>
 __device__ __forceinline__ void tile_spmv(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
                                           const VT *__restrict__ val, const double *const (&xs)[NV],
-                                          const double (&sc)[NV], int r0, int r1, TileSmem &sm,
+                                          const double (&sc)[NV], int r0, int r1, TileSmem<NVS> &sm,
                                           double (&out)[NV]) {
   static_assert(NV == 1 || NV == 2, "one or two gathered vectors");
+  static_assert(NV <= NVS, "tile shared memory too small");
   const int tid = threadIdx.x;
   const int e0 = ptr[r0], e1 = ptr[r1];
   const int nz = e1 - e0, nrows = r1 - r0;
@@ -172,162 +198,447 @@ __device__ __forceinline__ void tile_spmv(const int32_t *__restrict__ ptr, const
     }
     return;
   }
-  constexpr int PER = TILE_NNZ / NT;
-  int cols[PER];
-  double vals[PER];
+  // ---- phase A ----
+  int cols[EPT];
+  double vals[EPT];
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
+  for (int k = 0; k < EPT; ++k) {
     const int o = tid + k * NT;
     cols[k] = o < nz ? __ldcs(idx + e0 + o) : 0;
     vals[k] = o < nz ? ld_val(val + e0 + o) : 0.0;
   }
 #pragma unroll
-  for (int k = 0; k < PER; ++k) {
+  for (int k = 0; k < EPT; ++k) {
     const int o = tid + k * NT;
     if (o < nz) {
+      const int p = pidx(o);
       const double x0 = __ldg(xs[0] + cols[k]);
       if (NV == 1) {
-        sm.a[o] = vals[k];
-        sm.b[o] = SCALED ? sc[0] * x0 : x0;
+        sm.a[p] = vals[k];
+        sm.b[p] = SCALED ? sc[0] * x0 : x0;
       } else {
         const double x1 = __ldg(xs[NV - 1] + cols[k]);
-        sm.a[o] = vals[k] * (SCALED ? sc[0] * x0 : x0);
-        sm.b[o] = vals[k] * (SCALED ? sc[NV - 1] * x1 : x1);
+        sm.a[p] = vals[k] * (SCALED ? sc[0] * x0 : x0);
+        sm.b[p] = vals[k] * (SCALED ? sc[NV - 1] * x1 : x1);
       }
     }
   }
-  if (tid < nrows) sm.off[tid] = ptr[r0 + tid] - e0;
+  if (tid < nrows) {
+    sm.off[tid] = ptr[r0 + tid] - e0;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) sm.rowsum[a][tid] = 0.0;
+  }
   if (tid == 0) sm.off[nrows] = nz;
   __syncthreads();
-  bool longrow = false;
-  if (tid < nrows) {
-    const int a0 = sm.off[tid], a1 = sm.off[tid + 1];
-    if (a1 - a0 <= SERIAL_MAX) {
-      for (int e = a0; e < a1; ++e) {
+  // ---- phase B ----
+  const int s0 = tid * EPT;
+  double acc[NV], carry[NV], head[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) acc[a] = carry[a] = head[a] = 0.0;
+  bool has_head = false;
+  int head_row = 0;
+  if (s0 < nz) {
+    int lo = 0, hi = nrows;  // largest row with off[row] <= s0 (a nonempty row holding entry s0)
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (sm.off[mid] <= s0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    int r = lo, rstart = sm.off[lo], rend = sm.off[lo + 1];
+    const int s1 = min(s0 + EPT, nz);
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = s0 + i;
+      if (e < s1) {
+        const int p = pidx(e);
         if (NV == 1) {
-          out[0] = fma(sm.a[e], sm.b[e], out[0]);
+          acc[0] = fma(sm.a[p], sm.b[p], acc[0]);
         } else {
-          out[0] += sm.a[e];
-          out[NV - 1] += sm.b[e];
+          acc[0] += sm.a[p];
+          acc[NV - 1] += sm.b[p];
+        }
+        if (e + 1 == rend) {
+          if (rstart >= s0) {
+#pragma unroll
+            for (int a = 0; a < NV; ++a) sm.rowsum[a][r] = acc[a];
+          } else {
+            has_head = true;
+            head_row = r;
+#pragma unroll
+            for (int a = 0; a < NV; ++a) head[a] = acc[a];
+          }
+#pragma unroll
+          for (int a = 0; a < NV; ++a) acc[a] = 0.0;
+          if (e + 1 < nz) {
+            do {
+              ++r;
+            } while (sm.off[r + 1] == e + 1);
+            rstart = e + 1;
+            rend = sm.off[r + 1];
+          }
         }
       }
+    }
+    if (rend > s1) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) carry[a] = acc[a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) sm.carry[a][tid] = carry[a];
+  __syncthreads();
+  // ---- phase C ----
+  bool longchain = false;
+  int ts = 0;
+  if (has_head) {
+    ts = sm.off[head_row] / EPT;  // thread holding the row's first entry
+    if (tid - ts <= CHAIN_MAX) {
+      double s[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s[a] = head[a];
+      for (int t2 = tid - 1; t2 >= ts; --t2) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) s[a] += sm.carry[a][t2];
+      }
+#pragma unroll
+      for (int a = 0; a < NV; ++a) sm.rowsum[a][head_row] = s[a];
     } else {
-      longrow = true;
+      longchain = true;
     }
   }
   const int lane = tid & 31;
-  unsigned int msk = __ballot_sync(0xffffffffu, longrow);
+  unsigned int msk = __ballot_sync(0xffffffffu, longchain);
   while (msk) {
     const int src = __ffs(msk) - 1;
     msk &= msk - 1;
-    const int row = (tid & ~31) + src;
-    const int a0 = sm.off[row], a1 = sm.off[row + 1];
-    double acc[NV];
+    const int row = __shfl_sync(0xffffffffu, head_row, src);
+    const int t0 = __shfl_sync(0xffffffffu, ts, src);
+    const int tend = (tid & ~31) + src;
+    double s[NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-    for (int e = a0 + lane; e < a1; e += 32) {
-      if (NV == 1) {
-        acc[0] = fma(sm.a[e], sm.b[e], acc[0]);
-      } else {
-        acc[0] += sm.a[e];
-        acc[NV - 1] += sm.b[e];
-      }
+    for (int a = 0; a < NV; ++a) s[a] = 0.0;
+    for (int t2 = t0 + lane; t2 < tend; t2 += 32) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s[a] += sm.carry[a][t2];
     }
 #pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] = warp_sum(acc[a]);
+    for (int a = 0; a < NV; ++a) s[a] = warp_sum(s[a]);
     if (lane == src) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) out[a] = acc[a];
+      for (int a = 0; a < NV; ++a) sm.rowsum[a][row] = s[a] + head[a];
     }
+  }
+  __syncthreads();
+  if (tid < nrows) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) out[a] = sm.rowsum[a][tid];
   }
   __syncthreads();
 }
 
 // ---------------------------------------------------------------- primal step
 
-template <typename VT>
-__device__ __forceinline__ void primal_tiles(const Csr &KT, const VT *__restrict__ tval, const Vecs &V, int cur,
-                                             int need_g, double eta, double tau, double &dx2, TileSmem &sm) {
-  const int nxt = cur ^ 1;
-  const double *__restrict__ x = V.x[cur];
-  const double *__restrict__ sx = V.sx[cur];
-  double *__restrict__ xn = V.x[nxt];
-  double *__restrict__ sxn = V.sx[nxt];
-  const double *const xs[1] = {V.y[cur]};
-  const double sc[1] = {1.0};
-  for (int t = blockIdx.x; t < KT.ntiles; t += gridDim.x) {
-    const int r0 = KT.tiles[t], r1 = KT.tiles[t + 1];
-    double gs[1];
-    if (need_g) tile_spmv<VT, 1, false>(KT.ptr, KT.idx, tval, xs, sc, r0, r1, sm, gs);
-    if ((int)threadIdx.x < r1 - r0) {
-      const int j = r0 + threadIdx.x;
-      double g;
-      if (need_g) {
-        g = gs[0];
-        V.g[j] = g;
-      } else {
-        g = V.g[j];
-      }
-      const double xj = x[j];
-      double v = xj - tau * (V.c[j] - g);
-      const double lj = V.l[j], uj = V.u[j];
-      if (v < lj) v = lj;
-      if (v > uj) v = uj;
-      xn[j] = v;
-      sxn[j] = sx[j] + eta * v;
-      const double d = v - xj;
-      dx2 = fma(d, d, dx2);
-    }
-  }
+// Order-preserving integer key of an IEEE double (sign-magnitude -> two's
+// complement): a < b  <=>  key(a) < key(b) for non-NaN values (with -0 < +0).
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
 
-__global__ void __launch_bounds__(NT) k_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem sm;
-  if (st->status != ST_RUNNING || st->check_pending) return;
-  const int cur = st->cur, need_g = st->need_g, f32 = st->use_f32;
-  const double eta = st->eta, omega = st->omega;
-  const double tau = eta / omega;
+// proj onto [l, u] with integer compares, keeping the clamp off the FP64 pipe.
+// A NaN input maps to u (positive NaN) or l (negative NaN); with infinite
+// bounds it becomes +-inf and the step test flags it.
+__device__ __forceinline__ double clamp_bits(double v, double l, double u) {
+  const long long kv = dkey(v);
+  double r = v;
+  if (kv < dkey(l)) r = l;
+  if (kv > dkey(u)) r = u;
+  return r;
+}
+
+// ---------------------------------------------------------------- pipelined tile SpMV (hot kernels)
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_val(double *dst, const double *src) { cp8(dst, src); }
+__device__ __forceinline__ void cp_val(float *dst, const float *src) { cp4(dst, src); }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Three copy stages (tile k being reduced, k+1 being gathered, k+2 loading)
+// and two gather buffers.  Values are stored in the padded layout of pidx()
+// (as VT; a float stage uses the first half of its slot).
+struct PipeSmem {
+  int cols[3][TILE_NNZ];
+  double vals[3][PADDED];
+  int ptr[3][TILE_ROWS + 1];
+  double xg[2][PADDED];
+  double rowsum[TILE_ROWS];
+  double carry[NT];
+  double red[16 * NW];
+  int flag;
+};
+
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return (double)v; }
+
+template <typename VT>
+__device__ __forceinline__ void stage_load(const Csr &A, const VT *__restrict__ val, int2 m0, int2 m1, int s,
+                                           PipeSmem &sm) {
+  const int nz = m1.y - m0.y, nrows = m1.x - m0.x;
+  if (nz > TILE_NNZ) return;  // a long row is streamed directly by tile_long
+  VT *sv = reinterpret_cast<VT *>(sm.vals[s]);
+  for (int o = threadIdx.x; o < nz; o += NT) {
+    cp4(&sm.cols[s][o], A.idx + m0.y + o);
+    cp_val(sv + pidx(o), val + m0.y + o);
+  }
+  for (int r = threadIdx.x; r <= nrows; r += NT) cp4(&sm.ptr[s][r], A.ptr + m0.x + r);
+}
+
+__device__ __forceinline__ void gather_issue(const double *__restrict__ xg, int2 m0, int2 m1, int s, int bb,
+                                             PipeSmem &sm) {
+  const int nz = m1.y - m0.y;
+  if (nz > TILE_NNZ) return;
+  for (int o = threadIdx.x; o < nz; o += NT) cp8(&sm.xg[bb][pidx(o)], xg + sm.cols[s][o]);
+}
+
+// Reduce one staged tile (phases B and C of the balanced scheme) and run the
+// epilogue for row r0 + threadIdx.x.
+template <typename VT, class Epi>
+__device__ __forceinline__ void tile_compute(int2 m0, int2 m1, int s, int bb, PipeSmem &sm, Epi &ep) {
+  const int tid = threadIdx.x;
+  const int r0 = m0.x, e0 = m0.y;
+  const int nrows = m1.x - m0.x, nz = m1.y - m0.y;
+  const bool has_row = tid < nrows;
+  if (has_row) ep.prefetch(r0 + tid);
+  const VT *__restrict__ sv = reinterpret_cast<const VT *>(sm.vals[s]);
+  const double *__restrict__ sx = sm.xg[bb];
+  const int *__restrict__ sp = sm.ptr[s];  // raw row pointers; local offset = sp[r] - e0
+  const int s0 = tid * EPT;
+  double acc = 0.0, carry = 0.0, head = 0.0;
+  bool has_head = false;
+  int head_row = 0;
+  if (s0 < nz) {
+    int lo = 0, hi = nrows;  // largest row with offset <= s0: the nonempty row holding entry s0
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (sp[mid] - e0 <= s0)
+        lo = mid;
+      else
+        hi = mid;
+    }
+    int r = lo, rstart = sp[lo] - e0, rend = sp[lo + 1] - e0;
+    const int s1 = min(s0 + EPT, nz);
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = s0 + i;
+      if (e < s1) {
+        const int p = pidx(e);
+        acc = fma(to_f64(sv[p]), sx[p], acc);
+        if (e + 1 == rend) {
+          if (rstart >= s0) {
+            sm.rowsum[r] = acc;
+          } else {
+            has_head = true;
+            head_row = r;
+            head = acc;
+          }
+          acc = 0.0;
+          if (e + 1 < nz) {
+            do {
+              ++r;
+            } while (sp[r + 1] - e0 == e + 1);
+            rstart = e + 1;
+            rend = sp[r + 1] - e0;
+          }
+        }
+      }
+    }
+    if (rend > s1) carry = acc;
+  }
+  sm.carry[tid] = carry;
+  __syncthreads();
+  bool longchain = false;
+  int ts = 0;
+  if (has_head) {
+    ts = (sp[head_row] - e0) / EPT;  // thread holding the row's first entry
+    if (tid - ts <= CHAIN_MAX) {
+      double sum = head;
+      for (int t2 = tid - 1; t2 >= ts; --t2) sum += sm.carry[t2];
+      sm.rowsum[head_row] = sum;
+    } else {
+      longchain = true;
+    }
+  }
+  const int lane = tid & 31;
+  unsigned int msk = __ballot_sync(0xffffffffu, longchain);
+  while (msk) {
+    const int src = __ffs(msk) - 1;
+    msk &= msk - 1;
+    const int row = __shfl_sync(0xffffffffu, head_row, src);
+    const int t0 = __shfl_sync(0xffffffffu, ts, src);
+    const int tend = (tid & ~31) + src;
+    double sum = 0.0;
+    for (int t2 = t0 + lane; t2 < tend; t2 += 32) sum += sm.carry[t2];
+    sum = warp_sum(sum);
+    if (lane == src) sm.rowsum[row] = sum + head;
+  }
+  __syncthreads();
+  if (has_row) ep.finish(r0 + tid, sp[tid] == sp[tid + 1] ? 0.0 : sm.rowsum[tid]);
+}
+
+// A single row longer than a tile: the whole CTA streams it directly.
+template <typename VT, class Epi>
+__device__ __forceinline__ void tile_long(const Csr &A, const VT *__restrict__ val, const double *__restrict__ xg,
+                                          int2 m0, int2 m1, PipeSmem &sm, Epi &ep) {
+  if (threadIdx.x == 0) ep.prefetch(m0.x);
   double acc[1] = {0.0};
-  if (f32)
-    primal_tiles<float>(KT, KT.val32, V, cur, need_g, eta, tau, acc[0], sm);
-  else
-    primal_tiles<double>(KT, KT.val, V, cur, need_g, eta, tau, acc[0], sm);
+  for (int e = m0.y + threadIdx.x; e < m1.y; e += NT) acc[0] = fma(ld_val(val + e), __ldg(xg + __ldcs(A.idx + e)), acc[0]);
+  block_sum<1>(acc, sm.red);
+  if (threadIdx.x == 0) ep.finish(m0.x, acc[0]);
+}
+
+// Persistent loop over tiles blockIdx.x + k * gridDim.x with the copy
+// pipeline described at the top of the file.
+template <typename VT, class Epi>
+__device__ __forceinline__ void spmv_pipeline(const Csr &A, const VT *__restrict__ val, const double *__restrict__ xg,
+                                              PipeSmem &sm, Epi &ep) {
+  const int G = gridDim.x, T = A.ntiles;
+  int t = blockIdx.x;
+  if (t >= T) return;
+  int2 a0 = A.tmeta[t], a1 = A.tmeta[t + 1];  // tile k
+  int2 b0 = make_int2(0, 0), b1 = b0;         // tile k+1
+  if (t + G < T) {
+    b0 = A.tmeta[t + G];
+    b1 = A.tmeta[t + G + 1];
+  }
+  stage_load<VT>(A, val, a0, a1, 0, sm);
+  cp_commit();
+  if (t + G < T) stage_load<VT>(A, val, b0, b1, 1, sm);
+  cp_commit();
+  cp_wait_all_but_one();
+  __syncthreads();
+  gather_issue(xg, a0, a1, 0, 0, sm);
+  cp_commit();
+  for (int k = 0; t < T; ++k, t += G) {
+    int2 c0 = make_int2(0, 0), c1 = c0;  // tile k+2
+    const bool has1 = t + G < T, has2 = t + 2 * G < T;
+    if (has2) {
+      c0 = A.tmeta[t + 2 * G];
+      c1 = A.tmeta[t + 2 * G + 1];
+    }
+    cp_wait_all();
+    __syncthreads();  // stage of tile k+1 and the gathers of tile k have landed
+    if (has1) gather_issue(xg, b0, b1, (k + 1) % 3, (k + 1) & 1, sm);
+    cp_commit();
+    if (has2) stage_load<VT>(A, val, c0, c1, (k + 2) % 3, sm);
+    cp_commit();
+    if (a1.y - a0.y > TILE_NNZ)
+      tile_long<VT>(A, val, xg, a0, a1, sm, ep);
+    else
+      tile_compute<VT>(a0, a1, k % 3, k & 1, sm, ep);
+    a0 = b0;
+    a1 = b1;
+    b0 = c0;
+    b1 = c1;
+  }
+  cp_wait_all();
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- primal step
+
+struct PrimalEpi {
+  const double *__restrict__ c, *__restrict__ l, *__restrict__ u, *__restrict__ x, *__restrict__ sx;
+  double *__restrict__ g, *__restrict__ xn, *__restrict__ sxn;
+  double tau, eta, dx2;
+  double pc, pl, pu, px, psx;
+  __device__ __forceinline__ void prefetch(int j) {
+    pc = c[j];
+    pl = l[j];
+    pu = u[j];
+    px = x[j];
+    psx = sx[j];
+  }
+  __device__ __forceinline__ void finish(int j, double gj) {
+    g[j] = gj;
+    const double v = clamp_bits(fma(-tau, pc - gj, px), pl, pu);
+    xn[j] = v;
+    sxn[j] = fma(eta, v, psx);
+    const double d = v - px;
+    dx2 = fma(d, d, dx2);
+  }
+};
+
+extern __shared__ __align__(16) unsigned char g_dsmem[];
+
+__global__ void __launch_bounds__(NT) k_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
+  PipeSmem &sm = *reinterpret_cast<PipeSmem *>(g_dsmem);
+  if (st->status != ST_RUNNING || st->check_pending) return;
+  const int cur = st->cur, nxt = cur ^ 1, need_g = st->need_g, f32 = st->use_f32;
+  const double eta = st->eta, omega = st->omega;
+  PrimalEpi ep;
+  ep.c = V.c;
+  ep.l = V.l;
+  ep.u = V.u;
+  ep.x = V.x[cur];
+  ep.sx = V.sx[cur];
+  ep.g = V.g;
+  ep.xn = V.x[nxt];
+  ep.sxn = V.sx[nxt];
+  ep.tau = eta / omega;
+  ep.eta = eta;
+  ep.dx2 = 0.0;
+  if (need_g) {
+    if (f32)
+      spmv_pipeline<float>(KT, KT.val32, V.y[cur], sm, ep);
+    else
+      spmv_pipeline<double>(KT, KT.val, V.y[cur], sm, ep);
+  } else {
+    // rejected trial: g = K'y is unchanged, only the projection reruns
+    for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += gridDim.x * NT) {
+      ep.prefetch(j);
+      ep.finish(j, V.g[j]);
+    }
+  }
+  double acc[1] = {ep.dx2};
   block_sum<1>(acc, sm.red);
   if (threadIdx.x == 0) V.partA[blockIdx.x] = acc[0];
 }
 
 // ---------------------------------------------------------------- dual step + Algorithm 2 test
 
-template <typename VT>
-__device__ __forceinline__ void dual_tiles(const Csr &K, const VT *__restrict__ kval, const Vecs &V, int cur,
-                                           double eta, double sigma, double (&acc)[2], TileSmem &sm) {
-  const int nxt = cur ^ 1;
-  const double *const xs[1] = {V.x[nxt]};
-  const double sc[1] = {1.0};
-  const double *__restrict__ y = V.y[cur];
-  const double *__restrict__ sy = V.sy[cur];
-  const double *__restrict__ kx = V.Kx[cur];
-  double *__restrict__ yn = V.y[nxt];
-  double *__restrict__ syn = V.sy[nxt];
-  double *__restrict__ kxn = V.Kx[nxt];
-  for (int t = blockIdx.x; t < K.ntiles; t += gridDim.x) {
-    const int r0 = K.tiles[t], r1 = K.tiles[t + 1];
-    double ks[1];
-    tile_spmv<VT, 1, false>(K.ptr, K.idx, kval, xs, sc, r0, r1, sm, ks);
-    if ((int)threadIdx.x < r1 - r0) {
-      const int i = r0 + threadIdx.x;
-      const double kxi = kx[i], yi = y[i], kn = ks[0];
-      double v = yi + sigma * (V.q[i] - (2.0 * kn - kxi));
-      if (i >= V.n_eq && v < 0.0) v = 0.0;
-      yn[i] = v;
-      kxn[i] = kn;
-      syn[i] = sy[i] + eta * v;
-      const double d = v - yi;
-      acc[0] = fma(d, d, acc[0]);
-      acc[1] = fma(d, kn - kxi, acc[1]);
-    }
+struct DualEpi {
+  const double *__restrict__ q, *__restrict__ y, *__restrict__ kx, *__restrict__ sy;
+  double *__restrict__ yn, *__restrict__ kxn, *__restrict__ syn;
+  double sigma, eta, dy2, cross;
+  int n_eq;
+  double pq, py, pkx, psy;
+  __device__ __forceinline__ void prefetch(int i) {
+    pq = q[i];
+    py = y[i];
+    pkx = kx[i];
+    psy = sy[i];
   }
-}
+  __device__ __forceinline__ void finish(int i, double kn) {
+    double v = fma(sigma, pq - fma(2.0, kn, -pkx), py);
+    if (i >= n_eq && __double_as_longlong(v) < 0) v = 0.0;  // proj_Y: sign bit test
+    yn[i] = v;
+    kxn[i] = kn;
+    syn[i] = fma(eta, v, psy);
+    const double d = v - py;
+    dy2 = fma(d, d, dy2);
+    cross = fma(d, kn - pkx, cross);
+  }
+};
 
 // Algorithm 2 acceptance test (one thread).  eq. (step-size) with the
 // interaction taken in absolute value; the exponent base counts the step
@@ -360,16 +671,28 @@ __device__ void step_test(DevState *st, double dx2, double dy2, double cross) {
 }
 
 __global__ void __launch_bounds__(NT) k_dual(Csr K, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem sm;
+  PipeSmem &sm = *reinterpret_cast<PipeSmem *>(g_dsmem);
   if (st->status != ST_RUNNING || st->check_pending) return;
-  const int cur = st->cur, f32 = st->use_f32;
+  const int cur = st->cur, nxt = cur ^ 1, f32 = st->use_f32;
   const double eta = st->eta, omega = st->omega;
-  const double sigma = eta * omega;
-  double acc[2] = {0.0, 0.0};
+  DualEpi ep;
+  ep.q = V.q;
+  ep.y = V.y[cur];
+  ep.kx = V.Kx[cur];
+  ep.sy = V.sy[cur];
+  ep.yn = V.y[nxt];
+  ep.kxn = V.Kx[nxt];
+  ep.syn = V.sy[nxt];
+  ep.sigma = eta * omega;
+  ep.eta = eta;
+  ep.dy2 = 0.0;
+  ep.cross = 0.0;
+  ep.n_eq = V.n_eq;
   if (f32)
-    dual_tiles<float>(K, K.val32, V, cur, eta, sigma, acc, sm);
+    spmv_pipeline<float>(K, K.val32, V.x[nxt], sm, ep);
   else
-    dual_tiles<double>(K, K.val, V, cur, eta, sigma, acc, sm);
+    spmv_pipeline<double>(K, K.val, V.x[nxt], sm, ep);
+  double acc[2] = {ep.dy2, ep.cross};
   double tot[2];
   if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], sm.red, &sm.flag, tot)) return;
   double dx[1];
@@ -402,7 +725,7 @@ __device__ __forceinline__ void dual_piece(double c, double g, double l, double 
 }
 
 __global__ void __launch_bounds__(NT) k_check_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem sm;
+  __shared__ TileSmem<2> sm;
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur, need_g = st->need_g;
   const bool check = mode == MODE_CHECK;
@@ -413,7 +736,7 @@ __global__ void __launch_bounds__(NT) k_check_primal(Csr KT, Vecs V, DevState *_
 #pragma unroll
   for (int a = 0; a < NV_R1; ++a) acc[a] = 0.0;
   for (int t = blockIdx.x; t < KT.ntiles; t += gridDim.x) {
-    const int r0 = KT.tiles[t], r1 = KT.tiles[t + 1];
+    const int r0 = KT.tmeta[t].x, r1 = KT.tmeta[t + 1].x;
     double g = 0.0, gb = 0.0;
     double s2[2];
     double s1[1];
@@ -578,7 +901,7 @@ __device__ void check_decide(DevState *st, TraceRec *trace, const double *p, con
 }
 
 __global__ void __launch_bounds__(NT) k_check_dual(Csr K, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem sm;
+  __shared__ TileSmem<1> sm;
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur;
   const bool check = mode == MODE_CHECK;
@@ -589,7 +912,7 @@ __global__ void __launch_bounds__(NT) k_check_dual(Csr K, Vecs V, DevState *__re
 #pragma unroll
   for (int a = 0; a < NV_R2; ++a) acc[a] = 0.0;
   for (int t = blockIdx.x; t < K.ntiles; t += gridDim.x) {
-    const int r0 = K.tiles[t], r1 = K.tiles[t + 1];
+    const int r0 = K.tmeta[t].x, r1 = K.tmeta[t + 1].x;
     double s1[1];
     if (!check) {
       const double *const xs[1] = {V.x[cur]};
@@ -727,8 +1050,8 @@ const char *kernel_class_name(int kc) {
 int occupancy_grid(int kc, int num_sms) {
   int nb = 1;
   switch (kc) {
-    case KC_PRIMAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_primal, NT, 0); break;
-    case KC_DUAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dual, NT, 0); break;
+    case KC_PRIMAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_primal, NT, sizeof(PipeSmem)); break;
+    case KC_DUAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dual, NT, sizeof(PipeSmem)); break;
     case KC_R1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_primal, NT, 0); break;
     case KC_R2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_dual, NT, 0); break;
     case KC_R3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_restart, NT, 0); break;
@@ -738,12 +1061,18 @@ int occupancy_grid(int kc, int num_sms) {
   return nb * num_sms;
 }
 
+cudaError_t kernels_init() {
+  cudaError_t e = cudaFuncSetAttribute(k_primal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem));
+  return e;
+}
 cudaError_t launch_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
-  k_primal<<<grid, NT, 0, s>>>(KT, V, st);
+  k_primal<<<grid, NT, sizeof(PipeSmem), s>>>(KT, V, st);
   return cudaGetLastError();
 }
 cudaError_t launch_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
-  k_dual<<<grid, NT, 0, s>>>(K, V, st);
+  k_dual<<<grid, NT, sizeof(PipeSmem), s>>>(K, V, st);
   return cudaGetLastError();
 }
 cudaError_t launch_check_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
