@@ -188,6 +188,36 @@ void pdlp_destroy(pdlp_solver *s);
 /* Message for the last error on the calling thread ("" if none). */
 const char *pdlp_last_error(void);
 
+/* Allocation-free Ruiz + Pock-Chambolle scaling of a matrix the caller keeps
+ * in DEVICE memory.  This entry point has no counterpart in the paper; it is
+ * the same scaling pdlp_create applies (same kernels, same order of
+ * operations, so the results equal pdlp_get_scaling's), offered for callers
+ * that cannot call cudaMalloc or cudaFree: code that must take every byte of
+ * device memory from its own pool (a framework's caching allocator, a
+ * service with a fixed memory budget) and code that must not stall the device,
+ * which cudaFree does.  It allocates nothing: the per-pass row and column
+ * factors live in a fixed 4 MiB device array inside this library, held by
+ * every GPU that loads the library until the process exits.
+ *   K (m x n CSR: K_ptr m+1, K_idx / K_val nnz) and its transpose K' (n x m
+ *   CSR: KT_ptr n+1, KT_idx / KT_val nnz, entries of each row in increasing
+ *   order of K's row index) are DEVICE arrays; K_val and KT_val are scaled in
+ *   place to D1 K D2 (and its transpose); D1 (m) and D2 (n) are DEVICE
+ *   outputs.  ruiz_iters >= 0 l_inf passes, then one Pock-Chambolle pass with
+ *   exponent pc_alpha <= 2 (pc_alpha < 0 skips it), as in pdlp_params.
+ *   stream: a cudaStream_t as void* (NULL = the legacy default stream); the
+ *   work is enqueued there and the call returns without waiting.
+ * Limits and errors: 0 <= m <= 262144 and 1 <= n <= 262144, else
+ * PDLP_ERR_INVALID with a message naming the limit; null pointers also give
+ * PDLP_ERR_INVALID.  The first call on each device looks up the device
+ * address of the internal array (with that device current), so make that
+ * first call before any stream capture begins.  All calls share the one
+ * array: calls whose work overlaps on the GPU (different streams, or several
+ * host threads) race and corrupt each other's factors.  Every factor is fully
+ * rewritten in each pass, so nothing is left over from an earlier call. */
+int pdlp_scale_device_noalloc(int32_t m, int32_t n, const int32_t *K_ptr, const int32_t *K_idx, double *K_val,
+                              const int32_t *KT_ptr, const int32_t *KT_idx, double *KT_val, int32_t ruiz_iters,
+                              double pc_alpha, double *D1, double *D2, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

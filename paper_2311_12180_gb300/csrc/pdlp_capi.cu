@@ -74,6 +74,8 @@ struct Layout {
 
 }  // namespace
 
+int pdlp::set_error(int code, const char *msg) { return fail(code, msg ? msg : ""); }
+
 struct pdlp_solver {
   int32_t m = 0, n = 0, n_eq = 0;
   int64_t nnz = 0;

@@ -131,4 +131,7 @@ cudaError_t setup_scalars(int32_t m, int32_t n, int64_t nnz, const double *c, co
 cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0, const double *D1,
                        const double *D2, double *x, double *y, cudaStream_t s);
 
+// Records `msg` as the calling thread's pdlp_last_error() and returns `code`.
+int set_error(int code, const char *msg);
+
 }  // namespace pdlp

@@ -9,6 +9,10 @@
 
 #include <math.h>
 
+#include <mutex>
+#include <string>
+
+#include "pdlp.h"
 #include "pdlp_internal.cuh"
 
 namespace pdlp {
@@ -195,3 +199,61 @@ cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0,
 }
 
 }  // namespace pdlp
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the scaling pass (pdlp_scale_device_noalloc).
+//
+// The per-pass row and column factors of setup_scale live in this file-scope
+// device array instead of in memory the solver allocates.  The array's host
+// symbol is only a host-side stand-in: kernels receive the device address
+// looked up once per device with cudaGetSymbolAddress (under a lock, with
+// that device current) on the first call made on the device.
+
+namespace {
+
+constexpr int32_t NOALLOC_MAX_LINES = 1 << 18;  // rows and columns, each
+__device__ __align__(256) double g_scale_scratch[2 * NOALLOC_MAX_LINES];
+
+constexpr int MAX_DEVICES = 256;
+std::mutex g_scratch_mu;
+double *g_scratch_dev[MAX_DEVICES] = {};
+
+}  // namespace
+
+extern "C" int pdlp_scale_device_noalloc(int32_t m, int32_t n, const int32_t *K_ptr, const int32_t *K_idx,
+                                         double *K_val, const int32_t *KT_ptr, const int32_t *KT_idx, double *KT_val,
+                                         int32_t ruiz_iters, double pc_alpha, double *D1, double *D2,
+                                         void *stream) {
+  using namespace pdlp;
+  if (m < 0 || n < 1 || m > NOALLOC_MAX_LINES || n > NOALLOC_MAX_LINES)
+    return set_error(PDLP_ERR_INVALID,
+                     ("pdlp_scale_device_noalloc: need 0 <= m <= 262144 and 1 <= n <= 262144 (got m=" +
+                      std::to_string(m) + ", n=" + std::to_string(n) + ")")
+                         .c_str());
+  if (ruiz_iters < 0 || !(pc_alpha <= 2.0))
+    return set_error(PDLP_ERR_INVALID, "pdlp_scale_device_noalloc: need ruiz_iters >= 0 and pc_alpha <= 2");
+  if (!KT_ptr || !D2 || (m > 0 && (!K_ptr || !D1)))
+    return set_error(PDLP_ERR_INVALID, "pdlp_scale_device_noalloc: null pointer argument");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
+  if (dev < 0 || dev >= MAX_DEVICES) return set_error(PDLP_ERR_INVALID, "pdlp_scale_device_noalloc: device ordinal");
+  double *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+      void *p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_scale_scratch);
+      if (e != cudaSuccess) return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
+      g_scratch_dev[dev] = static_cast<double *>(p);
+    }
+    scratch = g_scratch_dev[dev];
+  }
+  double *work_m = scratch, *work_n = scratch + NOALLOC_MAX_LINES;
+  e = setup_scale(m, n, 0, const_cast<int32_t *>(K_ptr), const_cast<int32_t *>(K_idx), K_val,
+                  const_cast<int32_t *>(KT_ptr), const_cast<int32_t *>(KT_idx), KT_val, D1, D2, work_m, work_n,
+                  ruiz_iters, pc_alpha, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
+  return PDLP_OK;
+}
+

@@ -86,7 +86,7 @@ EXPORTS = (
     "pdlp_default_params", "pdlp_create", "pdlp_create_ex", "pdlp_solve", "pdlp_solve_warm", "pdlp_begin",
     "pdlp_run_periods", "pdlp_poll", "pdlp_finish", "pdlp_time_kernels", "pdlp_kernel_count",
     "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
-    "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error",
+    "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error", "pdlp_scale_device_noalloc",
 )
 
 _lib = None
@@ -146,6 +146,8 @@ def lib():
     L.pdlp_destroy.restype = None
     L.pdlp_last_error.argtypes = []
     L.pdlp_last_error.restype = C.c_char_p
+    L.pdlp_scale_device_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, i32, d, vp, vp, vp]
+    L.pdlp_scale_device_noalloc.restype = C.c_int
     _lib = L
     return L
 
@@ -215,6 +217,14 @@ def pdlp_solve(h, tol, max_iter, n, m):
 def pdlp_destroy(h):
     if h:
         lib().pdlp_destroy(h)
+
+
+def pdlp_scale_device_noalloc(m, n, K_ptr, K_idx, K_val, KT_ptr, KT_idx, KT_val, ruiz_iters, pc_alpha, D1, D2,
+                              stream=None):
+    """Allocation-free scaling of a device-resident K and K' (all arguments
+    are device addresses as ints, e.g. torch tensors' data_ptr())."""
+    _check(lib().pdlp_scale_device_noalloc(m, n, K_ptr, K_idx, K_val, KT_ptr, KT_idx, KT_val, int(ruiz_iters),
+                                           float(pc_alpha), D1, D2, stream))
 
 
 def kernel_names():
