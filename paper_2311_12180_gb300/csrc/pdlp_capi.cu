@@ -297,9 +297,12 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   // ---- one device arena ----
   Layout L;
   const size_t M = (size_t)m, N = (size_t)n, Z = (size_t)nnz;
-  const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z + 16), o_Kval = L.take(8 * Z + 16);
-  const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + 16), o_Tval = L.take(8 * Z + 16);
-  const size_t o_Kv32 = f32 ? L.take(4 * Z + 16) : 0, o_Tv32 = f32 ? L.take(4 * Z + 16) : 0;
+  // matrix arrays are padded: the SpMV's 8-entry vector loads may read up to
+  // EPT - 1 entries past the last nonzero (masked, never used)
+  const size_t PADB = 256;
+  const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z + PADB), o_Kval = L.take(8 * Z + PADB);
+  const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + PADB), o_Tval = L.take(8 * Z + PADB);
+  const size_t o_Kv32 = f32 ? L.take(4 * Z + PADB) : 0, o_Tv32 = f32 ? L.take(4 * Z + PADB) : 0;
   const size_t o_Ktl = L.take(sizeof(int2) * tilesK.size()), o_Ttl = L.take(sizeof(int2) * tilesT.size());
   const size_t nvec_n = 17, nvec_m = 13;
   const size_t o_vn = L.take(8 * N * nvec_n), o_vm = L.take(8 * (M + 1) * nvec_m);

@@ -12,9 +12,9 @@ namespace pdlp {
 // time, one row per thread in the epilogue.
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
-constexpr int TILE_NNZ = 1024;
+constexpr int EPT = 8;                   // consecutive entries per thread
+constexpr int TILE_NNZ = NT * EPT - EPT;  // 2040: the EPT-aligned span of a tile fits NT * EPT
 constexpr int TILE_ROWS = 256;
-constexpr int SERIAL_MAX = 32;  // rows up to this length are summed by one thread
 
 constexpr int ST_RUNNING = -1;
 constexpr int ST_OPTIMAL = 0;

@@ -24,21 +24,26 @@
 // has nothing to do, so a fixed CUDA graph of P + E trial slots followed by the
 // check kernels advances the solve by exactly one check period.
 //
-// SpMV: a tile is a run of consecutive rows with <= TILE_NNZ nonzeros and
-// <= TILE_ROWS rows (or one longer row).  The random 8-byte gathers of x / y
-// are the binding resource on GB300 (each is a distinct cache line for the
-// SM's L1TEX tag stage, ~0.9 lines per clock per SM), so the two hot kernels
-// run a persistent per-CTA software pipeline of cp.async copies: while tile k
-// is reduced, the gathers of tile k+1 and the index / value / row-pointer
-// copies of tile k+2 are in flight, landing directly in shared memory.  The
-// reduction keeps every lane busy (GB300 issues FP64 at ~1.6 DFMA per clock
-// per SM and a warp-wide FP64 instruction costs the same however many lanes
-// are active): thread t sums EPT consecutive entries with FMA, and rows that
-// cross thread boundaries are completed from per-thread carries.  The
-// epilogue runs one row per thread on operands prefetched into registers
-// before the reduction.  Reductions are deterministic: fixed per-thread
-// order, fixed shuffle trees, fixed block order in the last CTA.  No atomics
-// touch floating point.
+// SpMV ("tile_direct"): a tile is a run of consecutive rows with <= TILE_NNZ
+// nonzeros and <= TILE_ROWS rows (or one longer row).  Thread t of the CTA
+// owns the EPT consecutive entries starting at a + EPT t, where a is the
+// tile's first nonzero rounded down to a multiple of EPT; it loads their
+// column indices and values with 16-byte streaming vector loads (coalesced
+// across the warp, evict-first: read once per SpMV), masks entries outside
+// the tile, and issues its EPT random gathers of x / y at once into
+// registers.  The random gathers are the binding resource on GB300 (each is
+// a distinct cache line for the SM's L1TEX tag stage, ~0.9 lines per clock
+// per SM measured), so the kernel keeps per-entry instruction counts low and
+// relies on occupancy (no matrix staging in shared memory) for many gathers
+// in flight.  The reduction keeps every lane busy -- GB300 issues FP64 at
+// ~1.6 DFMA per clock per SM and a warp-wide FP64 instruction costs the same
+// however many lanes are active: each thread sums its entries with FMA,
+// writing rows that start and end in its range directly, and rows that cross
+// thread boundaries are completed from per-thread carries (serially for up to
+// CHAIN_MAX threads, else by a warp-strided sum).  The epilogue runs one row
+// per thread on operands prefetched into registers before the reduction.
+// Reductions are deterministic: fixed per-thread order, fixed shuffle trees,
+// fixed block order in the last CTA.  No atomics touch floating point.
 
 #include <math.h>
 #include <math_constants.h>
@@ -125,220 +130,7 @@ __device__ __forceinline__ void sum_partials(const double *part, int count, doub
   block_sum<NV>(tot, s_red);
 }
 
-// ---------------------------------------------------------------- tile SpMV
-
-// Balanced tile SpMV.  GB300 issues FP64 at ~1.6 DFMA per clock per SM, and
-// a warp-wide FP64 instruction costs the same issue slots however many lanes
-// are active, so the reduction must keep every lane busy:
-//   phase A  coalesced streaming loads of the tile's indices and values, the
-//            gathers, and staging of (value, entry) pairs in shared memory;
-//   phase B  thread t sums the EPT consecutive entries [EPT t, EPT t + EPT)
-//            with full-lane FMAs, writing rows that start and end in its range
-//            directly, keeping the partial of the row it enters ("head") and
-//            of the row it leaves open ("carry");
-//   phase C  the thread holding a row's last entry adds the carries of the
-//            threads the row crossed: serially for up to CHAIN_MAX of them,
-//            otherwise with a warp-strided sum.
-// The staging arrays are padded by one slot per EPT entries so phase B reads
-// (stride EPT + 1 = 5 doubles across lanes) are free of bank conflicts.
-constexpr int EPT = TILE_NNZ / NT;  // 4
-static_assert(EPT >= 2 && (EPT & (EPT - 1)) == 0, "EPT must be a power of two");
-constexpr int PADDED = TILE_NNZ + TILE_NNZ / EPT;
-constexpr int CHAIN_MAX = 8;
-__device__ __forceinline__ int pidx(int o) { return o + o / EPT; }
-
-// With one gathered vector a[] holds values and b[] gathered entries (summed
-// with FMA); with two vectors a[] and b[] hold the two products.
-template <int NVS>
-struct TileSmem {
-  double a[PADDED];
-  double b[PADDED];
-  double rowsum[NVS][TILE_ROWS];
-  double carry[NVS][NT];
-  int off[TILE_ROWS + 1];
-  double red[16 * NW];
-  int flag;
-};
-
-__device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
-__device__ __forceinline__ double ld_val(const float *p) { return (double)__ldcs(p); }
-
-// Row sums of one tile against NV (1 or 2) gathered vectors: out[a] of thread
-// t holds the sum for row r0 + t (t < r1 - r0).  With SCALED, vector a is
-// multiplied by sc[a] entry by entry before use (the epoch average 1/W * sum).
-template <typename VT, int NV, bool SCALED, int NVS>
-__device__ __forceinline__ void tile_spmv(const int32_t *__restrict__ ptr, const int32_t *__restrict__ idx,
-                                          const VT *__restrict__ val, const double *const (&xs)[NV],
-                                          const double (&sc)[NV], int r0, int r1, TileSmem<NVS> &sm,
-                                          double (&out)[NV]) {
-  static_assert(NV == 1 || NV == 2, "one or two gathered vectors");
-  static_assert(NV <= NVS, "tile shared memory too small");
-  const int tid = threadIdx.x;
-  const int e0 = ptr[r0], e1 = ptr[r1];
-  const int nz = e1 - e0, nrows = r1 - r0;
-#pragma unroll
-  for (int a = 0; a < NV; ++a) out[a] = 0.0;
-  if (nz > TILE_NNZ) {  // one row longer than a tile: the whole CTA strides over it
-    double acc[NV];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-    for (int e = e0 + tid; e < e1; e += NT) {
-      const int col = __ldcs(idx + e);
-      const double v = ld_val(val + e);
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        const double xv = __ldg(xs[a] + col);
-        acc[a] = fma(v, SCALED ? sc[a] * xv : xv, acc[a]);
-      }
-    }
-    block_sum<NV>(acc, sm.red);
-    if (tid == 0) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) out[a] = acc[a];
-    }
-    return;
-  }
-  // ---- phase A ----
-  int cols[EPT];
-  double vals[EPT];
-#pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int o = tid + k * NT;
-    cols[k] = o < nz ? __ldcs(idx + e0 + o) : 0;
-    vals[k] = o < nz ? ld_val(val + e0 + o) : 0.0;
-  }
-#pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int o = tid + k * NT;
-    if (o < nz) {
-      const int p = pidx(o);
-      const double x0 = __ldg(xs[0] + cols[k]);
-      if (NV == 1) {
-        sm.a[p] = vals[k];
-        sm.b[p] = SCALED ? sc[0] * x0 : x0;
-      } else {
-        const double x1 = __ldg(xs[NV - 1] + cols[k]);
-        sm.a[p] = vals[k] * (SCALED ? sc[0] * x0 : x0);
-        sm.b[p] = vals[k] * (SCALED ? sc[NV - 1] * x1 : x1);
-      }
-    }
-  }
-  if (tid < nrows) {
-    sm.off[tid] = ptr[r0 + tid] - e0;
-#pragma unroll
-    for (int a = 0; a < NV; ++a) sm.rowsum[a][tid] = 0.0;
-  }
-  if (tid == 0) sm.off[nrows] = nz;
-  __syncthreads();
-  // ---- phase B ----
-  const int s0 = tid * EPT;
-  double acc[NV], carry[NV], head[NV];
-#pragma unroll
-  for (int a = 0; a < NV; ++a) acc[a] = carry[a] = head[a] = 0.0;
-  bool has_head = false;
-  int head_row = 0;
-  if (s0 < nz) {
-    int lo = 0, hi = nrows;  // largest row with off[row] <= s0 (a nonempty row holding entry s0)
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (sm.off[mid] <= s0)
-        lo = mid;
-      else
-        hi = mid;
-    }
-    int r = lo, rstart = sm.off[lo], rend = sm.off[lo + 1];
-    const int s1 = min(s0 + EPT, nz);
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = s0 + i;
-      if (e < s1) {
-        const int p = pidx(e);
-        if (NV == 1) {
-          acc[0] = fma(sm.a[p], sm.b[p], acc[0]);
-        } else {
-          acc[0] += sm.a[p];
-          acc[NV - 1] += sm.b[p];
-        }
-        if (e + 1 == rend) {
-          if (rstart >= s0) {
-#pragma unroll
-            for (int a = 0; a < NV; ++a) sm.rowsum[a][r] = acc[a];
-          } else {
-            has_head = true;
-            head_row = r;
-#pragma unroll
-            for (int a = 0; a < NV; ++a) head[a] = acc[a];
-          }
-#pragma unroll
-          for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-          if (e + 1 < nz) {
-            do {
-              ++r;
-            } while (sm.off[r + 1] == e + 1);
-            rstart = e + 1;
-            rend = sm.off[r + 1];
-          }
-        }
-      }
-    }
-    if (rend > s1) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) carry[a] = acc[a];
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < NV; ++a) sm.carry[a][tid] = carry[a];
-  __syncthreads();
-  // ---- phase C ----
-  bool longchain = false;
-  int ts = 0;
-  if (has_head) {
-    ts = sm.off[head_row] / EPT;  // thread holding the row's first entry
-    if (tid - ts <= CHAIN_MAX) {
-      double s[NV];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) s[a] = head[a];
-      for (int t2 = tid - 1; t2 >= ts; --t2) {
-#pragma unroll
-        for (int a = 0; a < NV; ++a) s[a] += sm.carry[a][t2];
-      }
-#pragma unroll
-      for (int a = 0; a < NV; ++a) sm.rowsum[a][head_row] = s[a];
-    } else {
-      longchain = true;
-    }
-  }
-  const int lane = tid & 31;
-  unsigned int msk = __ballot_sync(0xffffffffu, longchain);
-  while (msk) {
-    const int src = __ffs(msk) - 1;
-    msk &= msk - 1;
-    const int row = __shfl_sync(0xffffffffu, head_row, src);
-    const int t0 = __shfl_sync(0xffffffffu, ts, src);
-    const int tend = (tid & ~31) + src;
-    double s[NV];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) s[a] = 0.0;
-    for (int t2 = t0 + lane; t2 < tend; t2 += 32) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) s[a] += sm.carry[a][t2];
-    }
-#pragma unroll
-    for (int a = 0; a < NV; ++a) s[a] = warp_sum(s[a]);
-    if (lane == src) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) sm.rowsum[a][row] = s[a] + head[a];
-    }
-  }
-  __syncthreads();
-  if (tid < nrows) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) out[a] = sm.rowsum[a][tid];
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------- primal step
+// ---------------------------------------------------------------- IEEE-bit helpers
 
 // Order-preserving integer key of an IEEE double (sign-magnitude -> two's
 // complement): a < b  <=>  key(a) < key(b) for non-NaN values (with -0 < +0).
@@ -358,122 +150,178 @@ __device__ __forceinline__ double clamp_bits(double v, double l, double u) {
   return r;
 }
 
-// ---------------------------------------------------------------- pipelined tile SpMV (hot kernels)
+// ---------------------------------------------------------------- tile SpMV
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void cp4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp8(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_val(double *dst, const double *src) { cp8(dst, src); }
-__device__ __forceinline__ void cp_val(float *dst, const float *src) { cp4(dst, src); }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+constexpr int CHAIN_MAX = 8;
+static_assert(EPT == 8, "load_chunk() loads 8 entries");
 
-// Three copy stages (tile k being reduced, k+1 being gathered, k+2 loading)
-// and two gather buffers.  Values are stored in the padded layout of pidx()
-// (as VT; a float stage uses the first half of its slot).
-struct PipeSmem {
-  int cols[3][TILE_NNZ];
-  double vals[3][PADDED];
-  int ptr[3][TILE_ROWS + 1];
-  double xg[2][PADDED];
-  double rowsum[TILE_ROWS];
-  double carry[NT];
+template <int NV>
+struct TileSmem {
+  int off[TILE_ROWS + 1];  // row starts relative to the tile's aligned base
+  double rowsum[NV][TILE_ROWS];
+  double carry[NV][NT];
   double red[16 * NW];
   int flag;
 };
 
-__device__ __forceinline__ double to_f64(double v) { return v; }
-__device__ __forceinline__ double to_f64(float v) { return (double)v; }
-
-template <typename VT>
-__device__ __forceinline__ void stage_load(const Csr &A, const VT *__restrict__ val, int2 m0, int2 m1, int s,
-                                           PipeSmem &sm) {
-  const int nz = m1.y - m0.y, nrows = m1.x - m0.x;
-  if (nz > TILE_NNZ) return;  // a long row is streamed directly by tile_long
-  VT *sv = reinterpret_cast<VT *>(sm.vals[s]);
-  for (int o = threadIdx.x; o < nz; o += NT) {
-    cp4(&sm.cols[s][o], A.idx + m0.y + o);
-    cp_val(sv + pidx(o), val + m0.y + o);
+__device__ __forceinline__ void load_chunk(const int32_t *p, int (&c)[EPT]) {
+  const int4 a = __ldcs(reinterpret_cast<const int4 *>(p));
+  const int4 b = __ldcs(reinterpret_cast<const int4 *>(p) + 1);
+  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
+  c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
+}
+__device__ __forceinline__ void load_chunk(const double *p, double (&v)[EPT]) {
+#pragma unroll
+  for (int k = 0; k < EPT / 2; ++k) {
+    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p) + k);
+    v[2 * k] = a.x;
+    v[2 * k + 1] = a.y;
   }
-  for (int r = threadIdx.x; r <= nrows; r += NT) cp4(&sm.ptr[s][r], A.ptr + m0.x + r);
 }
-
-__device__ __forceinline__ void gather_issue(const double *__restrict__ xg, int2 m0, int2 m1, int s, int bb,
-                                             PipeSmem &sm) {
-  const int nz = m1.y - m0.y;
-  if (nz > TILE_NNZ) return;
-  for (int o = threadIdx.x; o < nz; o += NT) cp8(&sm.xg[bb][pidx(o)], xg + sm.cols[s][o]);
+__device__ __forceinline__ void load_chunk(const float *p, double (&v)[EPT]) {
+#pragma unroll
+  for (int k = 0; k < EPT / 4; ++k) {
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p) + k);
+    v[4 * k] = a.x;
+    v[4 * k + 1] = a.y;
+    v[4 * k + 2] = a.z;
+    v[4 * k + 3] = a.w;
+  }
 }
+__device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_val(const float *p) { return (double)__ldcs(p); }
 
-// Reduce one staged tile (phases B and C of the balanced scheme) and run the
-// epilogue for row r0 + threadIdx.x.
-template <typename VT, class Epi>
-__device__ __forceinline__ void tile_compute(int2 m0, int2 m1, int s, int bb, PipeSmem &sm, Epi &ep) {
+// One tile of y = A x for NV (1 or 2) gathered vectors, followed by the
+// epilogue ep.finish(row, sums) for row r0 + threadIdx.x.  With SCALED,
+// vector a is multiplied by sc[a] entry by entry (the epoch average 1/W sum).
+template <typename VT, int NV, bool SCALED, int NVS, class Epi>
+__device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__ val,
+                                            const double *const (&xs)[NV], const double (&sc)[NV], int2 m0, int2 m1,
+                                            TileSmem<NVS> &sm, Epi &ep) {
+  static_assert(NV == 1 || NV == 2, "one or two gathered vectors");
+  static_assert(NV <= NVS, "tile shared memory holds fewer vectors");
   const int tid = threadIdx.x;
-  const int r0 = m0.x, e0 = m0.y;
-  const int nrows = m1.x - m0.x, nz = m1.y - m0.y;
-  const bool has_row = tid < nrows;
-  if (has_row) ep.prefetch(r0 + tid);
-  const VT *__restrict__ sv = reinterpret_cast<const VT *>(sm.vals[s]);
-  const double *__restrict__ sx = sm.xg[bb];
-  const int *__restrict__ sp = sm.ptr[s];  // raw row pointers; local offset = sp[r] - e0
-  const int s0 = tid * EPT;
-  double acc = 0.0, carry = 0.0, head = 0.0;
-  bool has_head = false;
-  int head_row = 0;
-  if (s0 < nz) {
-    int lo = 0, hi = nrows;  // largest row with offset <= s0: the nonempty row holding entry s0
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (sp[mid] - e0 <= s0)
-        lo = mid;
-      else
-        hi = mid;
+  const int r0 = m0.x, e0 = m0.y, e1 = m1.y;
+  const int nrows = m1.x - m0.x;
+  if (e1 - e0 > TILE_NNZ) {  // one row longer than a tile: the whole CTA strides over it
+    if (tid == 0) ep.prefetch(r0);
+    double acc[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
+    for (int e = e0 + tid; e < e1; e += NT) {
+      const int col = __ldcs(A.idx + e);
+      const double v = ld_val(val + e);
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const double xv = __ldg(xs[a] + col);
+        acc[a] = fma(v, SCALED ? sc[a] * xv : xv, acc[a]);
+      }
     }
-    int r = lo, rstart = sp[lo] - e0, rend = sp[lo + 1] - e0;
-    const int s1 = min(s0 + EPT, nz);
+    block_sum<NV>(acc, sm.red);
+    if (tid == 0) ep.finish(r0, acc);
+    return;
+  }
+  // ---- loads and gathers (registers) ----
+  const int base = e0 & ~(EPT - 1);
+  const int c0 = EPT * tid;  // this thread's chunk, relative to base
+  int col[EPT];
+  double v[EPT];
+  double xv[NV][EPT];
+  if (base + c0 < e1) {
+    load_chunk(A.idx + base + c0, col);
+    load_chunk(val + base + c0, v);
+  } else {
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
-      const int e = s0 + i;
-      if (e < s1) {
-        const int p = pidx(e);
-        acc = fma(to_f64(sv[p]), sx[p], acc);
+      col[i] = 0;
+      v[i] = 0.0;
+    }
+  }
+  const int lo = e0 - base, hi = e1 - base;  // tile entries, relative to base
+#pragma unroll
+  for (int i = 0; i < EPT; ++i) {
+    const bool in = c0 + i >= lo && c0 + i < hi;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      double g = 0.0;
+      if (in) g = __ldg(xs[a] + col[i]);
+      xv[a][i] = SCALED ? sc[a] * g : g;
+    }
+  }
+  if (tid < nrows) {
+    ep.prefetch(r0 + tid);
+    sm.off[tid] = A.ptr[r0 + tid] - base;
+  }
+  if (tid == 0) sm.off[nrows] = hi;
+  __syncthreads();
+  // ---- per-thread consecutive sums ----
+  const int s0 = max(c0, lo), s1 = min(c0 + EPT, hi);
+  double acc[NV], carry[NV], head[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) acc[a] = carry[a] = head[a] = 0.0;
+  bool has_head = false;
+  int head_row = 0;
+  if (s0 < s1) {
+    int lo_r = 0, hi_r = nrows;  // largest row with start <= s0: the nonempty row holding entry s0
+    while (hi_r - lo_r > 1) {
+      const int mid = (lo_r + hi_r) >> 1;
+      if (sm.off[mid] <= s0)
+        lo_r = mid;
+      else
+        hi_r = mid;
+    }
+    int r = lo_r, rstart = sm.off[lo_r], rend = sm.off[lo_r + 1];
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      const int e = c0 + i;
+      if (e >= s0 && e < s1) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) acc[a] = fma(v[i], xv[a][i], acc[a]);
         if (e + 1 == rend) {
           if (rstart >= s0) {
-            sm.rowsum[r] = acc;
+#pragma unroll
+            for (int a = 0; a < NV; ++a) sm.rowsum[a][r] = acc[a];
           } else {
             has_head = true;
             head_row = r;
-            head = acc;
+#pragma unroll
+            for (int a = 0; a < NV; ++a) head[a] = acc[a];
           }
-          acc = 0.0;
-          if (e + 1 < nz) {
+#pragma unroll
+          for (int a = 0; a < NV; ++a) acc[a] = 0.0;
+          if (e + 1 < hi) {
             do {
               ++r;
-            } while (sp[r + 1] - e0 == e + 1);
+            } while (sm.off[r + 1] == e + 1);
             rstart = e + 1;
-            rend = sp[r + 1] - e0;
+            rend = sm.off[r + 1];
           }
         }
       }
     }
-    if (rend > s1) carry = acc;
+    if (rend > s1) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) carry[a] = acc[a];
+    }
   }
-  sm.carry[tid] = carry;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) sm.carry[a][tid] = carry[a];
   __syncthreads();
+  // ---- rows that crossed thread boundaries ----
   bool longchain = false;
   int ts = 0;
   if (has_head) {
-    ts = (sp[head_row] - e0) / EPT;  // thread holding the row's first entry
+    ts = sm.off[head_row] / EPT;  // thread holding the row's first entry
     if (tid - ts <= CHAIN_MAX) {
-      double sum = head;
-      for (int t2 = tid - 1; t2 >= ts; --t2) sum += sm.carry[t2];
-      sm.rowsum[head_row] = sum;
+      double sum[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) sum[a] = head[a];
+      for (int t2 = tid - 1; t2 >= ts; --t2) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) sum[a] += sm.carry[a][t2];
+      }
+#pragma unroll
+      for (int a = 0; a < NV; ++a) sm.rowsum[a][head_row] = sum[a];
     } else {
       longchain = true;
     }
@@ -486,72 +334,38 @@ __device__ __forceinline__ void tile_compute(int2 m0, int2 m1, int s, int bb, Pi
     const int row = __shfl_sync(0xffffffffu, head_row, src);
     const int t0 = __shfl_sync(0xffffffffu, ts, src);
     const int tend = (tid & ~31) + src;
-    double sum = 0.0;
-    for (int t2 = t0 + lane; t2 < tend; t2 += 32) sum += sm.carry[t2];
-    sum = warp_sum(sum);
-    if (lane == src) sm.rowsum[row] = sum + head;
-  }
-  __syncthreads();
-  if (has_row) ep.finish(r0 + tid, sp[tid] == sp[tid + 1] ? 0.0 : sm.rowsum[tid]);
-}
-
-// A single row longer than a tile: the whole CTA streams it directly.
-template <typename VT, class Epi>
-__device__ __forceinline__ void tile_long(const Csr &A, const VT *__restrict__ val, const double *__restrict__ xg,
-                                          int2 m0, int2 m1, PipeSmem &sm, Epi &ep) {
-  if (threadIdx.x == 0) ep.prefetch(m0.x);
-  double acc[1] = {0.0};
-  for (int e = m0.y + threadIdx.x; e < m1.y; e += NT) acc[0] = fma(ld_val(val + e), __ldg(xg + __ldcs(A.idx + e)), acc[0]);
-  block_sum<1>(acc, sm.red);
-  if (threadIdx.x == 0) ep.finish(m0.x, acc[0]);
-}
-
-// Persistent loop over tiles blockIdx.x + k * gridDim.x with the copy
-// pipeline described at the top of the file.
-template <typename VT, class Epi>
-__device__ __forceinline__ void spmv_pipeline(const Csr &A, const VT *__restrict__ val, const double *__restrict__ xg,
-                                              PipeSmem &sm, Epi &ep) {
-  const int G = gridDim.x, T = A.ntiles;
-  int t = blockIdx.x;
-  if (t >= T) return;
-  int2 a0 = A.tmeta[t], a1 = A.tmeta[t + 1];  // tile k
-  int2 b0 = make_int2(0, 0), b1 = b0;         // tile k+1
-  if (t + G < T) {
-    b0 = A.tmeta[t + G];
-    b1 = A.tmeta[t + G + 1];
-  }
-  stage_load<VT>(A, val, a0, a1, 0, sm);
-  cp_commit();
-  if (t + G < T) stage_load<VT>(A, val, b0, b1, 1, sm);
-  cp_commit();
-  cp_wait_all_but_one();
-  __syncthreads();
-  gather_issue(xg, a0, a1, 0, 0, sm);
-  cp_commit();
-  for (int k = 0; t < T; ++k, t += G) {
-    int2 c0 = make_int2(0, 0), c1 = c0;  // tile k+2
-    const bool has1 = t + G < T, has2 = t + 2 * G < T;
-    if (has2) {
-      c0 = A.tmeta[t + 2 * G];
-      c1 = A.tmeta[t + 2 * G + 1];
+    double sum[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) sum[a] = 0.0;
+    for (int t2 = t0 + lane; t2 < tend; t2 += 32) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) sum[a] += sm.carry[a][t2];
     }
-    cp_wait_all();
-    __syncthreads();  // stage of tile k+1 and the gathers of tile k have landed
-    if (has1) gather_issue(xg, b0, b1, (k + 1) % 3, (k + 1) & 1, sm);
-    cp_commit();
-    if (has2) stage_load<VT>(A, val, c0, c1, (k + 2) % 3, sm);
-    cp_commit();
-    if (a1.y - a0.y > TILE_NNZ)
-      tile_long<VT>(A, val, xg, a0, a1, sm, ep);
-    else
-      tile_compute<VT>(a0, a1, k % 3, k & 1, sm, ep);
-    a0 = b0;
-    a1 = b1;
-    b0 = c0;
-    b1 = c1;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) sum[a] = warp_sum(sum[a]);
+    if (lane == src) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) sm.rowsum[a][row] = sum[a] + head[a];
+    }
   }
-  cp_wait_all();
   __syncthreads();
+  double out[NV];
+  const bool has_row = tid < nrows;
+  if (has_row) {
+    const bool empty = sm.off[tid] == sm.off[tid + 1];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) out[a] = empty ? 0.0 : sm.rowsum[a][tid];
+  }
+  __syncthreads();  // the next tile rewrites off / rowsum
+  if (has_row) ep.finish(r0 + tid, out);
+}
+
+// Persistent loop over this CTA's tiles.
+template <typename VT, int NV, bool SCALED, int NVS, class Epi>
+__device__ __forceinline__ void spmv_tiles(const Csr &A, const VT *__restrict__ val, const double *const (&xs)[NV],
+                                           const double (&sc)[NV], TileSmem<NVS> &sm, Epi &ep) {
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x)
+    tile_direct<VT, NV, SCALED>(A, val, xs, sc, A.tmeta[t], A.tmeta[t + 1], sm, ep);
 }
 
 // ---------------------------------------------------------------- primal step
@@ -568,8 +382,9 @@ struct PrimalEpi {
     px = x[j];
     psx = sx[j];
   }
-  __device__ __forceinline__ void finish(int j, double gj) {
-    g[j] = gj;
+  __device__ __forceinline__ void finish(int j, const double (&gs)[1]) { apply(j, gs[0], true); }
+  __device__ __forceinline__ void apply(int j, double gj, bool store_g) {
+    if (store_g) g[j] = gj;
     const double v = clamp_bits(fma(-tau, pc - gj, px), pl, pu);
     xn[j] = v;
     sxn[j] = fma(eta, v, psx);
@@ -578,10 +393,8 @@ struct PrimalEpi {
   }
 };
 
-extern __shared__ __align__(16) unsigned char g_dsmem[];
-
 __global__ void __launch_bounds__(NT) k_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
-  PipeSmem &sm = *reinterpret_cast<PipeSmem *>(g_dsmem);
+  __shared__ TileSmem<1> sm;
   if (st->status != ST_RUNNING || st->check_pending) return;
   const int cur = st->cur, nxt = cur ^ 1, need_g = st->need_g, f32 = st->use_f32;
   const double eta = st->eta, omega = st->omega;
@@ -598,15 +411,17 @@ __global__ void __launch_bounds__(NT) k_primal(Csr KT, Vecs V, DevState *__restr
   ep.eta = eta;
   ep.dx2 = 0.0;
   if (need_g) {
+    const double *const xs[1] = {V.y[cur]};
+    const double sc[1] = {1.0};
     if (f32)
-      spmv_pipeline<float>(KT, KT.val32, V.y[cur], sm, ep);
+      spmv_tiles<float, 1, false>(KT, KT.val32, xs, sc, sm, ep);
     else
-      spmv_pipeline<double>(KT, KT.val, V.y[cur], sm, ep);
+      spmv_tiles<double, 1, false>(KT, KT.val, xs, sc, sm, ep);
   } else {
     // rejected trial: g = K'y is unchanged, only the projection reruns
     for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += gridDim.x * NT) {
       ep.prefetch(j);
-      ep.finish(j, V.g[j]);
+      ep.apply(j, V.g[j], false);
     }
   }
   double acc[1] = {ep.dx2};
@@ -628,7 +443,8 @@ struct DualEpi {
     pkx = kx[i];
     psy = sy[i];
   }
-  __device__ __forceinline__ void finish(int i, double kn) {
+  __device__ __forceinline__ void finish(int i, const double (&ks)[1]) {
+    const double kn = ks[0];
     double v = fma(sigma, pq - fma(2.0, kn, -pkx), py);
     if (i >= n_eq && __double_as_longlong(v) < 0) v = 0.0;  // proj_Y: sign bit test
     yn[i] = v;
@@ -671,7 +487,7 @@ __device__ void step_test(DevState *st, double dx2, double dy2, double cross) {
 }
 
 __global__ void __launch_bounds__(NT) k_dual(Csr K, Vecs V, DevState *__restrict__ st) {
-  PipeSmem &sm = *reinterpret_cast<PipeSmem *>(g_dsmem);
+  __shared__ TileSmem<1> sm;
   if (st->status != ST_RUNNING || st->check_pending) return;
   const int cur = st->cur, nxt = cur ^ 1, f32 = st->use_f32;
   const double eta = st->eta, omega = st->omega;
@@ -688,10 +504,12 @@ __global__ void __launch_bounds__(NT) k_dual(Csr K, Vecs V, DevState *__restrict
   ep.dy2 = 0.0;
   ep.cross = 0.0;
   ep.n_eq = V.n_eq;
+  const double *const xs[1] = {V.x[nxt]};
+  const double sc[1] = {1.0};
   if (f32)
-    spmv_pipeline<float>(K, K.val32, V.x[nxt], sm, ep);
+    spmv_tiles<float, 1, false>(K, K.val32, xs, sc, sm, ep);
   else
-    spmv_pipeline<double>(K, K.val, V.x[nxt], sm, ep);
+    spmv_tiles<double, 1, false>(K, K.val, xs, sc, sm, ep);
   double acc[2] = {ep.dy2, ep.cross};
   double tot[2];
   if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], sm.red, &sm.flag, tot)) return;
@@ -724,57 +542,82 @@ __device__ __forceinline__ void dual_piece(double c, double g, double l, double 
   if (lam < 0.0) acc[3] = acc[3] - u * (-lam);
 }
 
+// Epilogue of the dual-side check pass.  kind 0: start point (sums = {K'y});
+// kind 1: check with stale g (sums = {K'y, K'ybar}); kind 2: check with g
+// current (sums = {K'ybar}, g loaded).
+struct CheckPrimalEpi {
+  const double *__restrict__ c, *__restrict__ l, *__restrict__ u, *__restrict__ d2, *__restrict__ x,
+      *__restrict__ sx;
+  double *__restrict__ g, *__restrict__ gbar;
+  double invW;
+  int kind;
+  double acc[NV_R1];
+  double pc, pl, pu, pd2, px, psx, pg;
+  __device__ __forceinline__ void prefetch(int j) {
+    pc = c[j];
+    pl = l[j];
+    pu = u[j];
+    pd2 = d2[j];
+    px = x[j];
+    psx = kind ? sx[j] : 0.0;
+    pg = kind == 2 ? g[j] : 0.0;
+  }
+  template <int NV>
+  __device__ __forceinline__ void finish(int j, const double (&s)[NV]) {
+    double gj = pg, gb = 0.0;
+    if (kind == 0) {
+      gj = s[0];
+      g[j] = gj;
+    } else if (kind == 1) {
+      gj = s[0];
+      gb = s[NV - 1];
+      g[j] = gj;
+    } else {
+      gb = s[0];
+    }
+    dual_piece(pc, gj, pl, pu, pd2, px, acc);
+    if (kind) {
+      gbar[j] = gb;
+      dual_piece(pc, gb, pl, pu, pd2, invW * psx, acc + 4);
+    }
+  }
+};
+
 __global__ void __launch_bounds__(NT) k_check_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
   __shared__ TileSmem<2> sm;
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur, need_g = st->need_g;
   const bool check = mode == MODE_CHECK;
-  const double invW = check ? 1.0 / st->W : 0.0;
-  const double *__restrict__ x = V.x[cur];
-  const double *__restrict__ sx = V.sx[cur];
-  double acc[NV_R1];
+  CheckPrimalEpi ep;
+  ep.c = V.c;
+  ep.l = V.l;
+  ep.u = V.u;
+  ep.d2 = V.D2;
+  ep.x = V.x[cur];
+  ep.sx = V.sx[cur];
+  ep.g = V.g;
+  ep.gbar = V.gbar;
+  ep.invW = check ? 1.0 / st->W : 0.0;
+  ep.kind = !check ? 0 : (need_g ? 1 : 2);
 #pragma unroll
-  for (int a = 0; a < NV_R1; ++a) acc[a] = 0.0;
-  for (int t = blockIdx.x; t < KT.ntiles; t += gridDim.x) {
-    const int r0 = KT.tmeta[t].x, r1 = KT.tmeta[t + 1].x;
-    double g = 0.0, gb = 0.0;
-    double s2[2];
-    double s1[1];
-    if (!check) {
-      const double *const xs[1] = {V.y[cur]};
-      const double sc[1] = {1.0};
-      tile_spmv<double, 1, false>(KT.ptr, KT.idx, KT.val, xs, sc, r0, r1, sm, s1);
-      g = s1[0];
-    } else if (need_g) {
-      const double *const xs[2] = {V.y[cur], V.sy[cur]};
-      const double sc[2] = {1.0, invW};
-      tile_spmv<double, 2, true>(KT.ptr, KT.idx, KT.val, xs, sc, r0, r1, sm, s2);
-      g = s2[0];
-      gb = s2[1];
-    } else {
-      const double *const xs[1] = {V.sy[cur]};
-      const double sc[1] = {invW};
-      tile_spmv<double, 1, true>(KT.ptr, KT.idx, KT.val, xs, sc, r0, r1, sm, s1);
-      gb = s1[0];
-    }
-    if ((int)threadIdx.x < r1 - r0) {
-      const int j = r0 + threadIdx.x;
-      if (!check || need_g)
-        V.g[j] = g;
-      else
-        g = V.g[j];
-      const double c = V.c[j], l = V.l[j], u = V.u[j], d2 = V.D2[j];
-      dual_piece(c, g, l, u, d2, x[j], acc);
-      if (check) {
-        V.gbar[j] = gb;
-        dual_piece(c, gb, l, u, d2, invW * sx[j], acc + 4);
-      }
-    }
+  for (int a = 0; a < NV_R1; ++a) ep.acc[a] = 0.0;
+  if (ep.kind == 0) {
+    const double *const xs[1] = {V.y[cur]};
+    const double sc[1] = {1.0};
+    spmv_tiles<double, 1, false>(KT, KT.val, xs, sc, sm, ep);
+  } else if (ep.kind == 1) {
+    const double *const xs[2] = {V.y[cur], V.sy[cur]};
+    const double sc[2] = {1.0, ep.invW};
+    spmv_tiles<double, 2, true>(KT, KT.val, xs, sc, sm, ep);
+  } else {
+    const double *const xs[1] = {V.sy[cur]};
+    const double sc[1] = {ep.invW};
+    spmv_tiles<double, 1, true>(KT, KT.val, xs, sc, sm, ep);
   }
-  block_sum<NV_R1>(acc, sm.red);
+  block_sum<NV_R1>(ep.acc, sm.red);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int a = 0; a < NV_R1; ++a) V.partR1[(size_t)blockIdx.x * NV_R1 + a] = acc[a];
+    for (int a = 0; a < NV_R1; ++a) V.partR1[(size_t)blockIdx.x * NV_R1 + a] = ep.acc[a];
   }
 }
 
@@ -900,49 +743,65 @@ __device__ void check_decide(DevState *st, TraceRec *trace, const double *p, con
   }
 }
 
+// Epilogue of the primal-side check pass.  check = 0: start point (sums =
+// {Kx}, stored as Kx); check = 1: sums = {K xbar}.
+struct CheckDualEpi {
+  const double *__restrict__ q, *__restrict__ d1, *__restrict__ y, *__restrict__ sy;
+  double *__restrict__ kx, *__restrict__ kxbar;
+  double invW;
+  int check, n_eq;
+  double acc[NV_R2];
+  double pq, pd1, py, psy, pkx;
+  __device__ __forceinline__ void prefetch(int i) {
+    pq = q[i];
+    pd1 = d1[i];
+    py = y[i];
+    psy = check ? sy[i] : 0.0;
+    pkx = check ? kx[i] : 0.0;
+  }
+  __device__ __forceinline__ void finish(int i, const double (&s)[1]) {
+    const bool ineq = i >= n_eq;
+    double kxi = pkx;
+    if (!check) {
+      kxi = s[0];
+      kx[i] = kxi;
+    }
+    primal_piece(pq, kxi, ineq, pd1, py, acc);
+    if (check) {
+      kxbar[i] = s[0];
+      primal_piece(pq, s[0], ineq, pd1, invW * psy, acc + 3);
+    }
+  }
+};
+
 __global__ void __launch_bounds__(NT) k_check_dual(Csr K, Vecs V, DevState *__restrict__ st) {
   __shared__ TileSmem<1> sm;
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur;
   const bool check = mode == MODE_CHECK;
-  const double invW = check ? 1.0 / st->W : 0.0;
-  const double *__restrict__ y = V.y[cur];
-  const double *__restrict__ sy = V.sy[cur];
-  double acc[NV_R2];
+  CheckDualEpi ep;
+  ep.q = V.q;
+  ep.d1 = V.D1;
+  ep.y = V.y[cur];
+  ep.sy = V.sy[cur];
+  ep.kx = V.Kx[cur];
+  ep.kxbar = V.Kxbar;
+  ep.invW = check ? 1.0 / st->W : 0.0;
+  ep.check = check ? 1 : 0;
+  ep.n_eq = V.n_eq;
 #pragma unroll
-  for (int a = 0; a < NV_R2; ++a) acc[a] = 0.0;
-  for (int t = blockIdx.x; t < K.ntiles; t += gridDim.x) {
-    const int r0 = K.tmeta[t].x, r1 = K.tmeta[t + 1].x;
-    double s1[1];
-    if (!check) {
-      const double *const xs[1] = {V.x[cur]};
-      const double sc[1] = {1.0};
-      tile_spmv<double, 1, false>(K.ptr, K.idx, K.val, xs, sc, r0, r1, sm, s1);
-    } else {
-      const double *const xs[1] = {V.sx[cur]};
-      const double sc[1] = {invW};
-      tile_spmv<double, 1, true>(K.ptr, K.idx, K.val, xs, sc, r0, r1, sm, s1);
-    }
-    if ((int)threadIdx.x < r1 - r0) {
-      const int i = r0 + threadIdx.x;
-      const bool ineq = i >= V.n_eq;
-      const double q = V.q[i], d1 = V.D1[i];
-      double kx;
-      if (!check) {
-        kx = s1[0];
-        V.Kx[cur][i] = kx;
-      } else {
-        kx = V.Kx[cur][i];
-      }
-      primal_piece(q, kx, ineq, d1, y[i], acc);
-      if (check) {
-        V.Kxbar[i] = s1[0];
-        primal_piece(q, s1[0], ineq, d1, invW * sy[i], acc + 3);
-      }
-    }
+  for (int a = 0; a < NV_R2; ++a) ep.acc[a] = 0.0;
+  if (!check) {
+    const double *const xs[1] = {V.x[cur]};
+    const double sc[1] = {1.0};
+    spmv_tiles<double, 1, false>(K, K.val, xs, sc, sm, ep);
+  } else {
+    const double *const xs[1] = {V.sx[cur]};
+    const double sc[1] = {ep.invW};
+    spmv_tiles<double, 1, true>(K, K.val, xs, sc, sm, ep);
   }
   double tot[NV_R2];
-  if (!grid_finish<NV_R2>(acc, V.partR2, &st->cnt[CNT_R2], sm.red, &sm.flag, tot)) return;
+  if (!grid_finish<NV_R2>(ep.acc, V.partR2, &st->cnt[CNT_R2], sm.red, &sm.flag, tot)) return;
   double p[NV_R1];
   sum_partials<NV_R1>(V.partR1, V.gridR1, sm.red, p);
   if (threadIdx.x == 0) check_decide(st, V.trace, p, tot);
@@ -1050,8 +909,8 @@ const char *kernel_class_name(int kc) {
 int occupancy_grid(int kc, int num_sms) {
   int nb = 1;
   switch (kc) {
-    case KC_PRIMAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_primal, NT, sizeof(PipeSmem)); break;
-    case KC_DUAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dual, NT, sizeof(PipeSmem)); break;
+    case KC_PRIMAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_primal, NT, 0); break;
+    case KC_DUAL: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dual, NT, 0); break;
     case KC_R1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_primal, NT, 0); break;
     case KC_R2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_dual, NT, 0); break;
     case KC_R3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_restart, NT, 0); break;
@@ -1061,18 +920,13 @@ int occupancy_grid(int kc, int num_sms) {
   return nb * num_sms;
 }
 
-cudaError_t kernels_init() {
-  cudaError_t e = cudaFuncSetAttribute(k_primal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_dual, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PipeSmem));
-  return e;
-}
+cudaError_t kernels_init() { return cudaSuccess; }
 cudaError_t launch_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
-  k_primal<<<grid, NT, sizeof(PipeSmem), s>>>(KT, V, st);
+  k_primal<<<grid, NT, 0, s>>>(KT, V, st);
   return cudaGetLastError();
 }
 cudaError_t launch_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
-  k_dual<<<grid, NT, sizeof(PipeSmem), s>>>(K, V, st);
+  k_dual<<<grid, NT, 0, s>>>(K, V, st);
   return cudaGetLastError();
 }
 cudaError_t launch_check_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
