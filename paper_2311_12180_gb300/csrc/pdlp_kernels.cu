@@ -393,7 +393,8 @@ struct PrimalEpi {
   }
 };
 
-__global__ void __launch_bounds__(NT) k_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
+// 64 registers: four CTAs (32 warps) per SM for gathers in flight
+__global__ void __launch_bounds__(NT, 4) k_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
   __shared__ TileSmem<1> sm;
   if (st->status != ST_RUNNING || st->check_pending) return;
   const int cur = st->cur, nxt = cur ^ 1, need_g = st->need_g, f32 = st->use_f32;
@@ -486,7 +487,7 @@ __device__ void step_test(DevState *st, double dx2, double dy2, double cross) {
   }
 }
 
-__global__ void __launch_bounds__(NT) k_dual(Csr K, Vecs V, DevState *__restrict__ st) {
+__global__ void __launch_bounds__(NT, 4) k_dual(Csr K, Vecs V, DevState *__restrict__ st) {
   __shared__ TileSmem<1> sm;
   if (st->status != ST_RUNNING || st->check_pending) return;
   const int cur = st->cur, nxt = cur ^ 1, f32 = st->use_f32;
