@@ -146,17 +146,18 @@ def make_workload(name: str, seed: int = 0):
     return lp, desc
 
 
-def algorithmic_bytes(lp, kernel: str) -> float:
+def algorithmic_bytes(lp, kernel: str, value_bytes: int = 8) -> float:
     """HBM bytes one launch must move at minimum (int32 indices, FP64 values):
     k_primal: K' (row_ptr, col_idx, val) + gather of y (m) + read x, c, l, u,
               sx + write g, x', sx' (8 n-vectors);
     k_dual:   K + gather of x' (n) + read y, q, Kx, sy + write y', Kx', sy'
               (7 m-vectors)."""
     m, n, nnz = lp.m, lp.n, lp.nnz
+    per_nz = 4.0 + value_bytes
     if kernel == "k_primal":
-        return 4.0 * (n + 1) + 12.0 * nnz + 8.0 * m + 8 * 8.0 * n
+        return 4.0 * (n + 1) + per_nz * nnz + 8.0 * m + 8 * 8.0 * n
     if kernel == "k_dual":
-        return 4.0 * (m + 1) + 12.0 * nnz + 8.0 * n + 7 * 8.0 * m
+        return 4.0 * (m + 1) + per_nz * nnz + 8.0 * n + 7 * 8.0 * m
     if kernel == "k_primal_reuse_g":
         return 9 * 8.0 * n
     raise KeyError(kernel)
@@ -228,7 +229,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "tiny"])
     ap.add_argument("--ttt", action="store_true", help="also time full solves to 1e-4 and 1e-8 KKT")
+    ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per --ttt solve (s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--value-bits", type=int, default=64, choices=[64, 32],
+                    help="32: step kernels read an FP32 copy of K (FP64 gathers, accumulation, iterates)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -256,7 +260,7 @@ def main():
 
     lp, desc = make_workload(args.workload)
     stream = torch.cuda.Stream()
-    solver = P.Solver(lp, stream=stream.cuda_stream)
+    solver = P.Solver(lp, stream=stream.cuda_stream, value_bits=args.value_bits)
     period = P.pdlp_default_params().check_period
 
     # ---- warm-up (cold start, then W periods) ----
@@ -292,7 +296,6 @@ def main():
     ms_max = float(ms_t.item())
     total_iters = float(it_t.item())
     value = total_iters / (ms_max / 1000.0)
-    info = solver.info()
 
     # ---- per-kernel event timing (same workload, direct launches) ----
     times = solver.time_kernels(max(2, min(args.steps, 8)))
@@ -300,11 +303,13 @@ def main():
     cands = {k: v for k, v in times.items() if k in ("k_primal", "k_dual") and v[1] > 0}
     dom = max(cands, key=lambda k: cands[k][0])
     dom_ms = cands[dom][0] / cands[dom][1]
-    dom_bytes = algorithmic_bytes(lp, dom)
+    vb = 8 if args.value_bits == 64 else 4
+    dom_bytes = algorithmic_bytes(lp, dom, vb)
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
     sha = kernel_source_sha()
     tr = NCU_TRAFFIC.get((dom, sha))
     solver.finish()
+    info = solver.info()
 
     # ---- end to end through the C ABI with host buffers ----
     e2e_iters = int(max(1, round(iters / max(world, 1))))
@@ -321,12 +326,16 @@ def main():
     ttt = None
     if args.ttt:
         ttt = {}
-        with P.Solver(lp, time_limit_s=600.0) as s3:
+        with P.Solver(lp, time_limit_s=args.ttt_limit, value_bits=args.value_bits) as s3:
             for tol in (1e-4, 1e-8):
                 t = time.perf_counter()
-                _, _, stt, itt = s3.solve(tol=tol, max_iter=10**9)
+                _ = s3.solve(tol=tol, max_iter=10**9)
+                stt, itt = _[2], _[3]
+                x_t, y_t = _[0], _[1]
                 ttt["%g" % tol] = {"seconds": time.perf_counter() - t, "status": P.STATUS_NAMES.get(stt, stt),
-                                   "iters": itt, "setup_excluded": True}
+                                   "iters": itt, "setup_excluded": True,
+                                   "obj_rel_err_vs_planted": abs(float(np.dot(lp.c, x_t)) - lp.obj_star)
+                                   / abs(lp.obj_star), "restarts": s3.info()["restarts"]}
 
     if rank != 0:
         if pg is not None:
@@ -348,14 +357,14 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if args.value_bits == 64 else "f64 (K values stored f32)",
         "data": "synthetic",
-        "config": {"workload": desc, "step": "one check period: %d accepted PDHG iterations + restart/termination "
+        "config": {"workload": desc, "value_bits": args.value_bits, "step": "one check period: %d accepted PDHG iterations + restart/termination "
                    "check" % period, "l2": "inputs larger than L2 (K + K' = %.0f MB)" % (24 * lp.nnz / 1e6),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "iters_timed": int(total_iters),
         "attempts_per_iter": info["attempts"] / max(info["iters"], 1),
-        "effective_hbm_gbs": (algorithmic_bytes(lp, "k_primal") + algorithmic_bytes(lp, "k_dual")) * value / 1e9,
+        "effective_hbm_gbs": (algorithmic_bytes(lp, "k_primal", vb) + algorithmic_bytes(lp, "k_dual", vb)) * value / 1e9,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": tr,
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,

@@ -178,18 +178,32 @@ __device__ __forceinline__ void load_chunk(const double *p, double (&v)[EPT]) {
     v[2 * k + 1] = a.y;
   }
 }
+// float -> double from the IEEE bits with integer operations (exact for
+// every normal float: the exponent is re-biased by 1023 - 127 = 896 and the
+// 23-bit mantissa moved to the top of the 52-bit one), keeping the widening
+// off GB300's narrow FP64 pipe; zero, subnormals, inf and NaN take the
+// hardware conversion.
+__device__ __forceinline__ double f2d(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int ex = (b >> 23) & 0xffu;
+  if (ex == 0u || ex == 0xffu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
+                               ((unsigned long long)(ex + 896u) << 52) |
+                               ((unsigned long long)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
 __device__ __forceinline__ void load_chunk(const float *p, double (&v)[EPT]) {
 #pragma unroll
   for (int k = 0; k < EPT / 4; ++k) {
     const float4 a = __ldcs(reinterpret_cast<const float4 *>(p) + k);
-    v[4 * k] = a.x;
-    v[4 * k + 1] = a.y;
-    v[4 * k + 2] = a.z;
-    v[4 * k + 3] = a.w;
+    v[4 * k] = f2d(a.x);
+    v[4 * k + 1] = f2d(a.y);
+    v[4 * k + 2] = f2d(a.z);
+    v[4 * k + 3] = f2d(a.w);
   }
 }
 __device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
-__device__ __forceinline__ double ld_val(const float *p) { return (double)__ldcs(p); }
+__device__ __forceinline__ double ld_val(const float *p) { return f2d(__ldcs(p)); }
 
 // One tile of y = A x for NV (1 or 2) gathered vectors, followed by the
 // epilogue ep.finish(row, sums) for row r0 + threadIdx.x.  With SCALED,

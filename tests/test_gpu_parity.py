@@ -239,3 +239,39 @@ def test_full_size_iterates_match_oracle():
     np.testing.assert_allclose(x, r.x, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.x).max()))
     np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))
     assert len(tr) == len(r.trace)
+
+
+# ---------------------------------------------------------------- FP32-values mode
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fp32_values_solution_parity(seed):
+    """K values stored FP32 for the step kernels (gathers, accumulation and
+    iterates FP64); termination is evaluated with the FP64 K, so the returned
+    point must pass the oracle's FP64 Sec. 4.1 test at the requested tol."""
+    lp = lpgen.tiny_lp(seed)
+    r8 = _oracle(lp, tol=1e-8)
+    with _solver(lp, value_bits=32) as s:
+        x6, y6, st6, it6 = s.solve(tol=1e-6)
+        x8, y8, st8, it8 = s.solve(tol=1e-8)
+        info = s.info()
+    assert st6 == st8 == P.OPTIMAL
+    assert oracle.passes(lp, x6, y6, 1e-6) and oracle.passes(lp, x8, y8, 1e-8)
+    _assert_feasible_signs(lp, x8, y8)
+    assert abs(float(lp.c @ x8) - r8.pobj) <= 1e-6 * abs(r8.pobj)
+    assert abs(float(lp.c @ x6) - lp.obj_star) <= 2e-6 * (1 + abs(lp.obj_star))
+    assert info["f64_switch_iter"] == -1 or 0 < info["f64_switch_iter"] <= it8
+
+
+def test_fp32_values_first_steps_track_fp64():
+    """Before any restart decision can differ, the FP32-valued steps follow
+    the FP64 trajectory to within the FP32 rounding of the matrix (2^-24
+    relative per value)."""
+    lp = lpgen.large_lp(4, m=20000, n=40000, nnz=400000)
+    with _solver(lp) as a, _solver(lp, value_bits=32) as b:
+        xa, ya, _, _ = a.solve(tol=1e-14, max_iter=10)
+        xb, yb, _, _ = b.solve(tol=1e-14, max_iter=10)
+    sx = max(1.0, np.abs(xa).max())
+    sy = max(1.0, np.abs(ya).max())
+    assert np.abs(xa - xb).max() <= 1e-5 * sx and np.abs(ya - yb).max() <= 1e-5 * sy
+    assert np.abs(xa - xb).max() > 0  # the FP32 copy is really in use
