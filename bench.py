@@ -221,13 +221,70 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world):
+    """Batched mode: many uneven planted LPs (m ~ logU[50,4000], n ~ logU[2m/3,
+    2.5m], density ~ U[0.5%,5%], N(0,1) values, half equality rows, 0<=x<=10)
+    solved to tol in one persistent launch; compared with the single-instance
+    GPU solver run one LP after another on a sample of the same LPs."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import lpgen
+    from paper_2311_12180_gb300 import _build
+    from paper_2311_12180_gb300 import pdlp as P
+
+    _build.build()
+    tol = args.batch_tol
+    t = time.perf_counter()
+    lps = lpgen.batch_lps(args.batch_count, seed=0)
+    gen_s = time.perf_counter() - t
+    t = time.perf_counter()
+    b = P.BatchSolver(lps)
+    create_s = time.perf_counter() - t
+    b.solve(tol=tol, max_iter=2)  # graph capture outside the timed solve
+    t = time.perf_counter()
+    xs, ys, st, it = b.solve(tol=tol, max_iter=args.batch_max_iter)
+    solve_s = time.perf_counter() - t
+    stats = b.stats()
+    b.close()
+    ok = int(np.sum(st == P.OPTIMAL))
+    rng = np.random.default_rng(1)
+    sample = sorted(rng.choice(len(lps), size=min(args.batch_sample, len(lps)), replace=False).tolist())
+    seq_s, seq_it = 0.0, 0
+    for i in sample:
+        with P.Solver(lps[i]) as s1:
+            t = time.perf_counter()
+            _, _, s1st, s1it = s1.solve(tol=tol, max_iter=args.batch_max_iter)
+            seq_s += time.perf_counter() - t
+            seq_it += s1it
+    seq_est = seq_s * len(lps) / len(sample)
+    line = {"metric": "batch time-to-%g KKT (s)" % tol, "value": solve_s, "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "%d planted LPs, m~logU[50,4000], n~logU[2m/3,2.5m], density~U[0.5%%,5%%], "
+                                   "N(0,1), half equality rows, 0<=x<=10; sum nnz %d" % (len(lps), stats["sum_nnz"])},
+            "optimal": ok, "count": len(lps), "iters_total": int(np.sum(it)), "iters_max": int(np.max(it)),
+            "agg_iters_per_s": float(np.sum(it)) / solve_s, "create_s": create_s, "generate_s": gen_s,
+            "autotune_entries_per_lane": stats["entries_per_lane"], "grid": stats["grid"],
+            "slowest": [{"index": int(i), "m": lps[i].m, "n": lps[i].n, "nnz": lps[i].nnz, "iters": int(it[i]),
+                         "status": int(st[i])} for i in np.argsort(-it)[:3]],
+            "sequential_single_instance": {"sample": len(sample), "seconds_sample": seq_s,
+                                           "estimated_seconds_all": seq_est, "iters_sample": seq_it},
+            "speedup_vs_sequential": seq_est / solve_s}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "tiny"])
+    ap.add_argument("--workload", default="large", choices=["large", "tiny", "batch"])
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-tol", type=float, default=1e-6)
+    ap.add_argument("--batch-max-iter", type=int, default=1_000_000)
+    ap.add_argument("--batch-sample", type=int, default=32)
     ap.add_argument("--ttt", action="store_true", help="also time full solves to 1e-4 and 1e-8 KKT")
     ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per --ttt solve (s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -239,6 +296,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batch":
+        run_batch(args, rank, world)
         return
 
     import numpy as np

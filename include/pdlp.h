@@ -188,6 +188,58 @@ void pdlp_destroy(pdlp_solver *s);
 /* Message for the last error on the calling thread ("" if none). */
 const char *pdlp_last_error(void);
 
+/* ---- batched solves ---------------------------------------------------------
+ * Many independent LPs solved together in one persistent launch: one CTA
+ * runs the whole restarted PDHG of one LP (Algorithms 1-2, Sec. 3.4 restarts,
+ * Sec. 4.1 termination, Sec. 2.2 scaling) with its own step size, primal
+ * weight, restart and termination state, taking LPs from a device queue in
+ * decreasing order of size.  Intended for many small and medium LPs (each
+ * solve is confined to one SM). */
+
+/* One LP of a batch, as in pdlp_create (HOST arrays). */
+typedef struct {
+  int32_t m, n, n_eq, pad_;
+  const double *c;
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const double *val;
+  const double *q, *l, *u;
+} pdlp_lp;
+
+typedef struct pdlp_batch pdlp_batch; /* opaque */
+
+typedef struct {
+  int32_t count;           /* LPs in the batch */
+  int32_t grid;            /* persistent CTAs launched */
+  int64_t sum_m, sum_n, sum_nnz;
+  double setup_ms;         /* create: validation, transposes, copies, batched scaling */
+  double tune_ms;          /* create: schedule autotuning */
+  double solve_ms;         /* last pdlp_batch_solve call, wall time */
+  double entries_per_lane; /* autotuned SpMV schedule: lanes per row = smallest power of two g <= 32
+                              with (mean row length) / g <= entries_per_lane */
+  size_t device_bytes;
+} pdlp_batch_stats;
+
+/* Validates every LP (same rules as pdlp_create; errors name the LP), copies
+ * the batch to the GPU, builds each K', scales every LP on the device and
+ * autotunes the SpMV schedule by timing short solves of the whole batch with
+ * a few candidate schedules.  params: NULL = defaults; value_bits must be 64.
+ * stream: cudaStream_t as void* (NULL = own stream). */
+int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const pdlp_params *params,
+                      void *stream);
+
+/* Solves every LP of the batch to tol / max_iter (as pdlp_solve_warm).
+ * x0 / y0: packed HOST warm starts (LP i's block follows LP i-1's; lengths
+ * sum of n / sum of m) or NULL for cold starts.  Outputs are packed the same
+ * way: x_out (sum of n), y_out (sum of m), status and iters (count each);
+ * any output pointer may be NULL.  Blocks until done. */
+int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double tol, int64_t max_iter,
+                     double *x_out, double *y_out, int32_t *status, int64_t *iters);
+int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *stats);
+/* Lanes per row chosen for each LP's K and K' (count entries each; NULL ok). */
+int pdlp_batch_lanes(const pdlp_batch *b, int32_t *lanes_K, int32_t *lanes_KT);
+void pdlp_batch_destroy(pdlp_batch *b);
+
 /* Allocation-free Ruiz + Pock-Chambolle scaling of a matrix the caller keeps
  * in DEVICE memory.  This entry point has no counterpart in the paper; it is
  * the same scaling pdlp_create applies (same kernels, same order of

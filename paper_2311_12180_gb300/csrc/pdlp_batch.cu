@@ -1,0 +1,972 @@
+// Batched restarted PDHG: many independent LPs of uneven size in one
+// persistent launch (cuPDLP.jl paper, Algorithms 1 and 2, eq. (kkt),
+// Sec. 3.4, Sec. 4.1, Sec. 2.2 preconditioning).
+//
+// One CTA of NTB threads solves one instance from start to finish: every
+// half-step is a CTA-wide pass over the instance's K' or K separated by
+// __syncthreads, so no grid-wide synchronisation or inter-CTA wait exists.
+// CTAs take instances from a device queue in decreasing order of nonzeros
+// (longest first keeps the tail short).  Each instance carries its own step
+// size, primal weight, restart and termination state in registers (identical
+// in every thread: all of them read the same block-reduced sums).  Its SpMVs
+// map G lanes to a row (G a power of two <= 32, chosen per instance from its
+// mean row length by the autotuned rule in pdlp_batch_create), with a fixed
+// lane order and fixed shuffle trees, so a solve is deterministic.
+//
+// Arithmetic matches the single-instance kernels in pdlp_kernels.cu (same
+// formulas and readings of the paper); only the summation order differs.
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "pdlp.h"
+#include "pdlp_internal.cuh"
+
+namespace pdlp {
+namespace batch {
+
+constexpr int NTB = 512;
+constexpr int NWB = NTB / 32;
+
+// per-instance vector blocks
+enum { VM_Q = 0, VM_D1, VM_Y0, VM_Y1, VM_SY0, VM_SY1, VM_KX0, VM_KX1, VM_KXB, VM_YL, VM_YOUT, VM_Q0, VM_COUNT };
+enum { VN_C = 0, VN_L, VN_U, VN_D2, VN_L0, VN_U0, VN_X0, VN_X1, VN_SX0, VN_SX1, VN_G, VN_GB, VN_XL, VN_XOUT, VN_C0,
+       VN_COUNT };
+
+struct Inst {
+  int m, n, n_eq, gk, gt;  // gk / gt: lanes per row for K / K'
+  int pad;
+  long long kp, ke, tp, te;  // offsets of K row_ptr / nonzeros, K' row_ptr / nonzeros
+  long long om, on;          // offsets of the m- and n-vector blocks
+  long long xo, yo;          // offsets in the packed outputs (sum of n / sum of m)
+  double eta0, omega0, qn, cn;
+};
+
+struct Params {
+  double tol, theta, eps_zero, beta_suff, beta_nec, beta_art;
+  long long max_iter;
+  int P, warm;
+};
+
+struct Arrays {
+  const int *kptr, *kidx, *tptr, *tidx;
+  double *kval, *tval;
+  double *vm, *vn;
+  const double *x0, *y0;  // packed warm start (or null)
+  double *xout, *yout;
+  int *status;
+  long long *iters;
+};
+
+// ---------------------------------------------------------------- CTA helpers
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double wmax(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// CTA-wide sums of NV values, result in every thread (fixed order).
+template <int NV>
+__device__ __forceinline__ void allsum(double (&v)[NV], double *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = wsum(v[a]);
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) red[a * NWB + wid] = v[a];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      const double s = wsum(lane < NWB ? red[a * NWB + lane] : 0.0);
+      if (lane == 0) red[16 * NWB + a] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < NV; ++a) v[a] = red[16 * NWB + a];
+  __syncthreads();
+}
+
+__device__ __forceinline__ double allmax(double v, double *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = wmax(v);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const double s = wmax(lane < NWB ? red[lane] : 0.0);
+    if (lane == 0) red[16 * NWB] = s;
+  }
+  __syncthreads();
+  v = red[16 * NWB];
+  __syncthreads();
+  return v;
+}
+
+// Rows of a CSR block with G lanes per row: for each row, f(row, sums) runs
+// in the group's first lane.  Every lane of a warp takes part in each round,
+// so the shuffles are always full-warp.
+template <int NV, bool SCALED, class F>
+__device__ __forceinline__ void rows_spmv(const int *__restrict__ ptr, const int *__restrict__ idx,
+                                          const double *__restrict__ val, int rows, int G,
+                                          const double *const (&xs)[NV], const double (&sc)[NV], F &f) {
+  const int gid = threadIdx.x / G, li = threadIdx.x % G, ngroups = NTB / G;
+  for (int base = 0; base < rows; base += ngroups) {
+    const int r = base + gid;
+    double s[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s[a] = 0.0;
+    if (r < rows) {
+      for (int e = ptr[r] + li; e < ptr[r + 1]; e += G) {
+        const double v = val[e];
+        const int c = idx[e];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) s[a] = fma(v, SCALED ? sc[a] * xs[a][c] : xs[a][c], s[a]);
+      }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o, G);
+    }
+    if (r < rows && li == 0) f(r, s);
+  }
+}
+
+__device__ __forceinline__ double proj_lambda(double d, double l, double u) {
+  const bool lf = isfinite(l), uf = isfinite(u);
+  if (lf && uf) return d;
+  if (lf) return d > 0.0 ? d : 0.0;
+  if (uf) return d < 0.0 ? d : 0.0;
+  return 0.0;
+}
+
+__device__ __forceinline__ double kkt_omega(double rp2, double rd2, double pobj, double dobj, double w) {
+  const double gap = dobj - pobj;
+  return sqrt(w * w * rp2 + rd2 / (w * w) + gap * gap);
+}
+
+__device__ __forceinline__ bool sec41_pass(double pobj, double dobj, double rp, double rd, double tol, double qn,
+                                           double cn) {
+  return fabs(dobj - pobj) <= tol * (1.0 + fabs(dobj) + fabs(pobj)) && rp <= tol * (1.0 + qn) &&
+         rd <= tol * (1.0 + cn);
+}
+
+// ---------------------------------------------------------------- batched scaling (Sec. 2.2)
+
+__global__ void __launch_bounds__(NTB) k_batch_scale(Arrays A, Inst *inst, int count, int ruiz_iters,
+                                                     double pc_alpha, double eps_zero) {
+  __shared__ double red[17 * NWB + 16];
+  const int id = blockIdx.x;
+  if (id >= count) return;
+  Inst I = inst[id];
+  const int *kp = A.kptr + I.kp, *ki = A.kidx + I.ke, *tp = A.tptr + I.tp, *ti = A.tidx + I.te;
+  double *kv = A.kval + I.ke, *tv = A.tval + I.te;
+  double *vm = A.vm + I.om, *vn = A.vn + I.on;
+  const int m = I.m, n = I.n;
+  double *D1 = vm + (long long)VM_D1 * m, *D2 = vn + (long long)VN_D2 * n;
+  double *r = vm + (long long)VM_KXB * m, *s = vn + (long long)VN_GB * n;  // per-pass factors (scratch)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < m; i += NTB) D1[i] = 1.0;
+  for (int j = threadIdx.x; j < n; j += NTB) D2[j] = 1.0;
+  const int passes = ruiz_iters + (pc_alpha >= 0.0 ? 1 : 0);
+  for (int it = 0; it < passes; ++it) {
+    const bool ruiz = it < ruiz_iters;
+    for (int i = wid; i < m; i += NWB) {
+      double acc = 0.0;
+      for (int e = kp[i] + lane; e < kp[i + 1]; e += 32) {
+        const double a = fabs(kv[e]);
+        acc = ruiz ? fmax(acc, a) : acc + (pc_alpha == 1.0 ? a : pow(a, 2.0 - pc_alpha));
+      }
+      acc = ruiz ? wmax(acc) : wsum(acc);
+      if (lane == 0) r[i] = acc > 0.0 ? sqrt(acc) : 1.0;
+    }
+    for (int j = wid; j < n; j += NWB) {
+      double acc = 0.0;
+      for (int e = tp[j] + lane; e < tp[j + 1]; e += 32) {
+        const double a = fabs(tv[e]);
+        acc = ruiz ? fmax(acc, a) : acc + (pc_alpha == 1.0 ? a : pow(a, pc_alpha));
+      }
+      acc = ruiz ? wmax(acc) : wsum(acc);
+      if (lane == 0) s[j] = acc > 0.0 ? sqrt(acc) : 1.0;
+    }
+    __syncthreads();
+    for (int i = wid; i < m; i += NWB)
+      for (int e = kp[i] + lane; e < kp[i + 1]; e += 32) kv[e] = kv[e] / r[i] / s[ki[e]];
+    for (int j = wid; j < n; j += NWB)
+      for (int e = tp[j] + lane; e < tp[j + 1]; e += 32) tv[e] = tv[e] / r[ti[e]] / s[j];
+    for (int i = threadIdx.x; i < m; i += NTB) D1[i] = D1[i] / r[i];
+    for (int j = threadIdx.x; j < n; j += NTB) D2[j] = D2[j] / s[j];
+    __syncthreads();
+  }
+  // scaled vectors, norms, initial step size and primal weight
+  double cc[1] = {0.0}, qq[1] = {0.0}, kmax = 0.0;
+  for (int j = threadIdx.x; j < n; j += NTB) {
+    const double c = D2[j] * vn[(long long)VN_C0 * n + j];
+    vn[(long long)VN_C * n + j] = c;
+    vn[(long long)VN_L * n + j] = vn[(long long)VN_L0 * n + j] / D2[j];
+    vn[(long long)VN_U * n + j] = vn[(long long)VN_U0 * n + j] / D2[j];
+    cc[0] = fma(c, c, cc[0]);
+  }
+  for (int i = threadIdx.x; i < m; i += NTB) {
+    const double q = D1[i] * vm[(long long)VM_Q0 * m + i];
+    vm[(long long)VM_Q * m + i] = q;
+    qq[0] = fma(q, q, qq[0]);
+  }
+  for (long long e = kp[0] + threadIdx.x; e < kp[m]; e += NTB) kmax = fmax(kmax, fabs(kv[e]));
+  allsum<1>(cc, red);
+  allsum<1>(qq, red);
+  kmax = allmax(kmax, red);
+  if (threadIdx.x == 0) {
+    const double cn = sqrt(cc[0]), qn = sqrt(qq[0]);
+    inst[id].eta0 = kmax > 0.0 ? 1.0 / kmax : 1.0;
+    inst[id].omega0 = (cn > eps_zero && qn > eps_zero) ? cn / qn : 1.0;
+  }
+}
+
+// ---------------------------------------------------------------- one instance, one CTA
+
+struct PrimalRow {
+  const double *c, *l, *u, *x, *sx;
+  double *g, *xn, *sxn;
+  double tau, eta, dx2;
+  bool store_g;
+  __device__ __forceinline__ void operator()(int j, const double (&s)[1]) { apply(j, s[0]); }
+  __device__ __forceinline__ void apply(int j, double gj) {
+    if (store_g) g[j] = gj;
+    double v = fma(-tau, c[j] - gj, x[j]);
+    const double lj = l[j], uj = u[j];
+    if (v < lj) v = lj;
+    if (v > uj) v = uj;
+    xn[j] = v;
+    sxn[j] = fma(eta, v, sx[j]);
+    const double d = v - x[j];
+    dx2 = fma(d, d, dx2);
+  }
+};
+
+struct DualRow {
+  const double *q, *y, *kx, *sy;
+  double *yn, *kxn, *syn;
+  double sigma, eta, dy2, cross;
+  int n_eq;
+  __device__ __forceinline__ void operator()(int i, const double (&s)[1]) {
+    const double kn = s[0], kxi = kx[i], yi = y[i];
+    double v = fma(sigma, q[i] - fma(2.0, kn, -kxi), yi);
+    if (i >= n_eq && v < 0.0) v = 0.0;
+    yn[i] = v;
+    kxn[i] = kn;
+    syn[i] = fma(eta, v, sy[i]);
+    const double d = v - yi;
+    dy2 = fma(d, d, dy2);
+    cross = fma(d, kn - kxi, cross);
+  }
+};
+
+// Dual-side KKT pieces for the current (and, with avg, the average) point.
+struct CheckT {
+  const double *c, *l, *u, *d2, *x, *sx;
+  double *g, *gbar;
+  double invW;
+  int kind;  // 0: start point {g}; 1: {g, gbar}; 2: {gbar}, g current
+  double acc[8];
+  __device__ __forceinline__ void piece(double cj, double gj, double lj, double uj, double dj, double xj, double *a) {
+    const double d = cj - gj;
+    const double lam = proj_lambda(d, lj, uj);
+    const double r = d - lam;
+    a[0] = fma(r, r, a[0]);
+    const double ro = r / dj;
+    a[1] = fma(ro, ro, a[1]);
+    a[2] = fma(cj, xj, a[2]);
+    if (lam > 0.0) a[3] = fma(lj, lam, a[3]);
+    if (lam < 0.0) a[3] = a[3] - uj * (-lam);
+  }
+  template <int NV>
+  __device__ __forceinline__ void operator()(int j, const double (&s)[NV]) {
+    double gj = g[j], gb = 0.0;
+    if (kind == 0) {
+      gj = s[0];
+      g[j] = gj;
+    } else if (kind == 1) {
+      gj = s[0];
+      gb = s[NV - 1];
+      g[j] = gj;
+    } else {
+      gb = s[0];
+    }
+    piece(c[j], gj, l[j], u[j], d2[j], x[j], acc);
+    if (kind) {
+      gbar[j] = gb;
+      piece(c[j], gb, l[j], u[j], d2[j], invW * sx[j], acc + 4);
+    }
+  }
+};
+
+struct CheckK {
+  const double *q, *d1, *y, *sy;
+  double *kx, *kxbar;
+  double invW;
+  int check, n_eq;
+  double acc[6];
+  __device__ __forceinline__ void piece(double qi, double kxi, bool ineq, double di, double yi, double *a) {
+    double r = qi - kxi;
+    if (ineq && r < 0.0) r = 0.0;
+    a[0] = fma(r, r, a[0]);
+    const double ro = r / di;
+    a[1] = fma(ro, ro, a[1]);
+    a[2] = fma(qi, yi, a[2]);
+  }
+  __device__ __forceinline__ void operator()(int i, const double (&s)[1]) {
+    const bool ineq = i >= n_eq;
+    double kxi = check ? kx[i] : s[0];
+    if (!check) kx[i] = kxi;
+    piece(q[i], kxi, ineq, d1[i], y[i], acc);
+    if (check) {
+      kxbar[i] = s[0];
+      piece(q[i], s[0], ineq, d1[i], invW * sy[i], acc + 3);
+    }
+  }
+};
+
+__device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, int id, double *red) {
+  const int m = I.m, n = I.n, tid = threadIdx.x;
+  const int *kp = A.kptr + I.kp, *ki = A.kidx + I.ke, *tp = A.tptr + I.tp, *ti = A.tidx + I.te;
+  const double *kv = A.kval + I.ke, *tv = A.tval + I.te;
+  double *vm = A.vm + I.om, *vn = A.vn + I.on;
+  auto VM = [&](int k) { return vm + (long long)k * m; };
+  auto VN = [&](int k) { return vn + (long long)k * n; };
+  double *x[2] = {VN(VN_X0), VN(VN_X1)}, *sx[2] = {VN(VN_SX0), VN(VN_SX1)};
+  double *y[2] = {VM(VM_Y0), VM(VM_Y1)}, *sy[2] = {VM(VM_SY0), VM(VM_SY1)}, *kx[2] = {VM(VM_KX0), VM(VM_KX1)};
+  double *g = VN(VN_G), *gbar = VN(VN_GB), *xl = VN(VN_XL), *yl = VM(VM_YL), *kxb = VM(VM_KXB);
+  const double *c = VN(VN_C), *l = VN(VN_L), *u = VN(VN_U), *D2 = VN(VN_D2), *q = VM(VM_Q), *D1 = VM(VM_D1);
+  // ---- start point (Sec. 4.1 "Initialization", or the warm start) ----
+  for (int j = tid; j < n; j += NTB) {
+    const double v = (p.warm && A.x0) ? A.x0[I.xo + j] / D2[j] : 0.0;
+    x[0][j] = v;
+    xl[j] = v;
+    sx[0][j] = 0.0;
+  }
+  for (int i = tid; i < m; i += NTB) {
+    const double v = (p.warm && A.y0) ? A.y0[I.yo + i] / D1[i] : 0.0;
+    y[0][i] = v;
+    yl[i] = v;
+    sy[0][i] = 0.0;
+  }
+  __syncthreads();
+  double eta = I.eta0, omega = I.omega0, W = 0.0, kkt_start, kkt_prev;
+  long long k = 0, t = 0;
+  int cur = 0, need_g = 0, status = ST_RUNNING, which = 0;
+  // KKT(z^{0,0}) with omega^0
+  {
+    CheckT ct{c, l, u, D2, x[0], sx[0], g, gbar, 0.0, 0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    const double *const xs[1] = {y[0]};
+    const double sc[1] = {1.0};
+    rows_spmv<1, false>(tp, ti, tv, n, I.gt, xs, sc, ct);
+    CheckK ck{q, D1, y[0], sy[0], kx[0], kxb, 0.0, 0, I.n_eq, {0, 0, 0, 0, 0, 0}};
+    const double *const xs2[1] = {x[0]};
+    rows_spmv<1, false>(kp, ki, kv, m, I.gk, xs2, sc, ck);
+    double s[5] = {ct.acc[0], ct.acc[2], ct.acc[3], ck.acc[0], ck.acc[2]};
+    allsum<5>(s, red);
+    kkt_start = kkt_omega(s[3], s[0], s[1], s[4] + s[2], omega);
+    kkt_prev = kkt_start;
+  }
+  while (status == ST_RUNNING) {
+    const int nxt = cur ^ 1;
+    // ---- Algorithm 2 trial: primal half-step ----
+    PrimalRow pr{c, l, u, x[cur], sx[cur], g, x[nxt], sx[nxt], eta / omega, eta, 0.0, need_g != 0};
+    if (need_g) {
+      const double *const xs[1] = {y[cur]};
+      const double sc[1] = {1.0};
+      rows_spmv<1, false>(tp, ti, tv, n, I.gt, xs, sc, pr);
+    } else {
+      for (int j = tid; j < n; j += NTB) pr.apply(j, g[j]);
+    }
+    __syncthreads();
+    // ---- dual half-step ----
+    DualRow dr{q, y[cur], kx[cur], sy[cur], y[nxt], kx[nxt], sy[nxt], eta * omega, eta, 0.0, 0.0, I.n_eq};
+    {
+      const double *const xs[1] = {x[nxt]};
+      const double sc[1] = {1.0};
+      rows_spmv<1, false>(kp, ki, kv, m, I.gk, xs, sc, dr);
+    }
+    double s3[3] = {pr.dx2, dr.dy2, dr.cross};
+    allsum<3>(s3, red);
+    // ---- step-size test (eq. step-size with |interaction|; exponent base k + 2) ----
+    const double ia = fabs(s3[2]);
+    const double eta_bar = ia > 0.0 ? (omega * s3[0] + s3[1] / omega) / (2.0 * ia) : CUDART_INF;
+    const double kk = (double)(k + 2);
+    const double e1 = (1.0 - pow(kk, -0.3)) * eta_bar, e2 = (1.0 + pow(kk, -0.6)) * eta;
+    const double eta_next = e1 < e2 ? e1 : e2;
+    if (!isfinite(s3[0]) || !isfinite(s3[1]) || !isfinite(s3[2]) || isnan(eta_bar) || !(eta_next > 0.0)) {
+      status = ST_NUMERICAL;
+      break;
+    }
+    const double eta_used = eta;
+    eta = eta_next;
+    if (!(eta_used <= eta_bar)) {
+      need_g = 0;
+      continue;
+    }
+    cur = nxt;
+    ++k;
+    ++t;
+    W += eta_used;
+    need_g = 1;
+    if (k % p.P != 0 && k < p.max_iter) continue;
+    // ---- restart / termination check (Sec. 3.4 / Sec. 4.1) ----
+    const double invW = 1.0 / W;
+    CheckT ct{c, l, u, D2, x[cur], sx[cur], g, gbar, invW, 1, {0, 0, 0, 0, 0, 0, 0, 0}};
+    {
+      const double *const xs[2] = {y[cur], sy[cur]};
+      const double sc[2] = {1.0, invW};
+      rows_spmv<2, true>(tp, ti, tv, n, I.gt, xs, sc, ct);
+    }
+    CheckK ck{q, D1, y[cur], sy[cur], kx[cur], kxb, invW, 1, I.n_eq, {0, 0, 0, 0, 0, 0}};
+    {
+      const double *const xs[1] = {sx[cur]};
+      const double sc[1] = {invW};
+      rows_spmv<1, true>(kp, ki, kv, m, I.gk, xs, sc, ck);
+    }
+    need_g = 0;
+    double s[14];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) s[a] = ct.acc[a];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) s[8 + a] = ck.acc[a];
+    allsum<14>(s, red);
+    const double pc = s[2], dc = s[10] + s[3], rpc = sqrt(s[9]), rdc = sqrt(s[1]);
+    const double pa = s[6], da = s[13] + s[7], rpa = sqrt(s[12]), rda = sqrt(s[5]);
+    if (sec41_pass(pc, dc, rpc, rdc, p.tol, I.qn, I.cn)) {
+      status = ST_OPTIMAL;
+      which = 0;
+      break;
+    }
+    if (sec41_pass(pa, da, rpa, rda, p.tol, I.qn, I.cn)) {
+      status = ST_OPTIMAL;
+      which = 1;
+      break;
+    }
+    if (k >= p.max_iter) {
+      status = ST_ITER_LIMIT;
+      which = 0;
+      break;
+    }
+    const double kc = kkt_omega(s[8], s[0], pc, dc, omega);
+    const double ka = kkt_omega(s[11], s[4], pa, da, omega);
+    const bool cand_avg = !(kc < ka);
+    const double kcand = cand_avg ? ka : kc;
+    const bool restart = kcand <= p.beta_suff * kkt_start || (kcand <= p.beta_nec * kkt_start && kcand > kkt_prev) ||
+                         (double)t >= p.beta_art * (double)k;
+    if (!restart) {
+      kkt_prev = kcand;
+      continue;
+    }
+    double dd[2] = {0.0, 0.0};
+    for (int j = tid; j < n; j += NTB) {
+      double xn = x[cur][j];
+      if (cand_avg) {
+        xn = invW * sx[cur][j];
+        x[cur][j] = xn;
+        g[j] = gbar[j];
+      }
+      const double d = xn - xl[j];
+      dd[0] = fma(d, d, dd[0]);
+      xl[j] = xn;
+      sx[cur][j] = 0.0;
+    }
+    for (int i = tid; i < m; i += NTB) {
+      double yn = y[cur][i];
+      if (cand_avg) {
+        yn = invW * sy[cur][i];
+        y[cur][i] = yn;
+        kx[cur][i] = kxb[i];
+      }
+      const double d = yn - yl[i];
+      dd[1] = fma(d, d, dd[1]);
+      yl[i] = yn;
+      sy[cur][i] = 0.0;
+    }
+    allsum<2>(dd, red);
+    const double dx = sqrt(dd[0]), dy = sqrt(dd[1]);
+    if (dx > p.eps_zero && dy > p.eps_zero) omega = exp(p.theta * log(dy / dx) + (1.0 - p.theta) * log(omega));
+    W = 0.0;
+    t = 0;
+    kkt_start = cand_avg ? kkt_omega(s[11], s[4], pa, da, omega) : kkt_omega(s[8], s[0], pc, dc, omega);
+    kkt_prev = kkt_start;
+  }
+  // ---- output in the original space ----
+  __syncthreads();
+  const double invW = which ? 1.0 / W : 0.0;
+  for (int j = tid; j < n; j += NTB) {
+    const double xs = which ? invW * sx[cur][j] : x[cur][j];
+    double v = D2[j] * xs;
+    const double l0 = vn[(long long)VN_L0 * n + j], u0 = vn[(long long)VN_U0 * n + j];
+    if (v < l0) v = l0;
+    if (v > u0) v = u0;
+    A.xout[I.xo + j] = v;
+  }
+  for (int i = tid; i < m; i += NTB) {
+    const double ys = which ? invW * sy[cur][i] : y[cur][i];
+    A.yout[I.yo + i] = D1[i] * ys;
+  }
+  if (tid == 0) {
+    A.status[id] = status;
+    A.iters[id] = k;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(NTB) k_batch_solve(Arrays A, const Inst *__restrict__ inst,
+                                                     const int *__restrict__ order, int count, int *queue,
+                                                     Params p) {
+  __shared__ double red[17 * NWB + 16];
+  __shared__ int s_id;
+  for (;;) {
+    if (threadIdx.x == 0) s_id = atomicAdd(queue, 1);
+    __syncthreads();
+    const int q = s_id;
+    __syncthreads();
+    if (q >= count) return;
+    const int id = order[q];
+    const Inst I = inst[id];
+    solve_instance(A, I, p, id, red);
+  }
+}
+
+}  // namespace batch
+}  // namespace pdlp
+
+// ================================================================ host side
+
+using namespace pdlp;
+using namespace pdlp::batch;
+
+struct pdlp_batch {
+  int device = 0, count = 0, num_sms = 0, grid = 0;
+  pdlp_params prm{};
+  cudaStream_t stream = nullptr, cap = nullptr;
+  bool own_stream = false;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  Arrays A{};
+  Inst *d_inst = nullptr;
+  int *d_order = nullptr, *d_queue = nullptr;
+  double *d_x0 = nullptr, *d_y0 = nullptr;
+  std::vector<Inst> h_inst;
+  long long sum_m = 0, sum_n = 0, sum_nnz = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  Params gp{};  // parameters baked into the graph
+  const double *g_x0 = nullptr, *g_y0 = nullptr;
+  double solve_ms = 0.0, setup_ms = 0.0, tune_ms = 0.0;
+  double lanes_target = 4.0;
+};
+
+namespace {
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int lanes_for(double mean_len, double target) {
+  int g = 1;
+  while (g < 32 && mean_len / g > target) g <<= 1;
+  return g;
+}
+
+void free_batch(pdlp_batch *b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->arena) cudaFree(b->arena);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+#define BCK(call)                                                                                              \
+  do {                                                                                                         \
+    cudaError_t e_ = (call);                                                                                   \
+    if (e_ != cudaSuccess) return set_error(PDLP_ERR_CUDA, (std::string(#call) + ": " + cudaGetErrorString(e_)).c_str()); \
+  } while (0)
+
+int launch_solve(pdlp_batch *b, const Arrays &A, const Params &p, cudaStream_t s) {
+  BCK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), s));
+  k_batch_solve<<<b->grid, NTB, 0, s>>>(A, b->d_inst, b->d_order, b->count, b->d_queue, p);
+  BCK(cudaGetLastError());
+  return PDLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const pdlp_params *params,
+                      void *stream) {
+  if (!out || count < 1 || !lps) return set_error(PDLP_ERR_INVALID, "pdlp_batch_create: need out, count >= 1, lps");
+  pdlp_params prm;
+  if (params)
+    prm = *params;
+  else
+    pdlp_default_params(&prm);
+  if (prm.check_period < 1 || prm.ruiz_iters < 0 || !(prm.pc_alpha <= 2.0) || prm.value_bits != 64)
+    return set_error(PDLP_ERR_INVALID, "pdlp_batch_create: invalid parameters (batched solves use value_bits 64)");
+  const double t0 = now_ms();
+  pdlp_batch *b = new pdlp_batch();
+  b->count = count;
+  b->prm = prm;
+  b->h_inst.resize(count);
+  // ---- validate and lay out ----
+  long long KP = 0, KE = 0, TP = 0, TE = 0, OM = 0, ON = 0, XO = 0, YO = 0;
+  for (int i = 0; i < count; ++i) {
+    const pdlp_lp &L = lps[i];
+    if (L.m < 0 || L.n < 1 || L.n_eq < 0 || L.n_eq > L.m || !L.c || !L.row_ptr || !L.l || !L.u ||
+        (L.m > 0 && !L.q) || L.row_ptr[0] != 0) {
+      delete b;
+      return set_error(PDLP_ERR_INVALID, ("pdlp_batch_create: bad dimensions or null array in LP " + std::to_string(i)).c_str());
+    }
+    for (int r = 0; r < L.m; ++r)
+      if (L.row_ptr[r + 1] < L.row_ptr[r]) {
+        delete b;
+        return set_error(PDLP_ERR_INVALID, ("pdlp_batch_create: row_ptr not non-decreasing in LP " + std::to_string(i)).c_str());
+      }
+    const long long nnz = L.row_ptr[L.m];
+    for (long long e = 0; e < nnz; ++e)
+      if (L.col_idx[e] < 0 || L.col_idx[e] >= L.n || !std::isfinite(L.val[e])) {
+        delete b;
+        return set_error(PDLP_ERR_INVALID, ("pdlp_batch_create: bad column index or value in LP " + std::to_string(i)).c_str());
+      }
+    for (int j = 0; j < L.n; ++j)
+      if (!std::isfinite(L.c[j]) || std::isnan(L.l[j]) || std::isnan(L.u[j]) || L.l[j] > L.u[j] || L.l[j] == INFINITY ||
+          L.u[j] == -INFINITY) {
+        delete b;
+        return set_error(PDLP_ERR_INVALID, ("pdlp_batch_create: bad c or bounds in LP " + std::to_string(i)).c_str());
+      }
+    for (int r = 0; r < L.m; ++r)
+      if (!std::isfinite(L.q[r])) {
+        delete b;
+        return set_error(PDLP_ERR_INVALID, ("pdlp_batch_create: non-finite q in LP " + std::to_string(i)).c_str());
+      }
+    Inst &I = b->h_inst[i];
+    std::memset(&I, 0, sizeof(I));
+    I.m = L.m;
+    I.n = L.n;
+    I.n_eq = L.n_eq;
+    I.kp = KP;
+    I.ke = KE;
+    I.tp = TP;
+    I.te = TE;
+    I.om = OM;
+    I.on = ON;
+    I.xo = XO;
+    I.yo = YO;
+    KP += L.m + 1;
+    TP += L.n + 1;
+    KE += nnz;
+    TE += nnz;
+    OM += (long long)VM_COUNT * L.m;
+    ON += (long long)VN_COUNT * L.n;
+    XO += L.n;
+    YO += L.m;
+    double qn = 0.0, cn = 0.0;
+    for (int r = 0; r < L.m; ++r) qn += L.q[r] * L.q[r];
+    for (int j = 0; j < L.n; ++j) cn += L.c[j] * L.c[j];
+    I.qn = std::sqrt(qn);
+    I.cn = std::sqrt(cn);
+  }
+  b->sum_m = YO;
+  b->sum_n = XO;
+  b->sum_nnz = KE;
+  // ---- host staging: K, K' (stable counting sort), vectors ----
+  std::vector<int> kptr(KP), kidx(KE), tptr(TP), tidx(TE);
+  std::vector<double> kval(KE), tval(TE), vm(OM > 0 ? OM : 1, 0.0), vn(ON, 0.0);
+  for (int i = 0; i < count; ++i) {
+    const pdlp_lp &L = lps[i];
+    const Inst &I = b->h_inst[i];
+    const long long nnz = L.row_ptr[L.m];
+    std::memcpy(&kptr[I.kp], L.row_ptr, sizeof(int) * (L.m + 1));
+    if (nnz) {
+      std::memcpy(&kidx[I.ke], L.col_idx, sizeof(int) * nnz);
+      std::memcpy(&kval[I.ke], L.val, sizeof(double) * nnz);
+    }
+    int *tp = &tptr[I.tp];
+    std::fill(tp, tp + L.n + 1, 0);
+    for (long long e = 0; e < nnz; ++e) tp[L.col_idx[e] + 1]++;
+    for (int j = 0; j < L.n; ++j) tp[j + 1] += tp[j];
+    std::vector<int> fill(tp, tp + L.n);
+    for (int r = 0; r < L.m; ++r)
+      for (int e = L.row_ptr[r]; e < L.row_ptr[r + 1]; ++e) {
+        const int pos = fill[L.col_idx[e]]++;
+        tidx[I.te + pos] = r;
+        tval[I.te + pos] = L.val[e];
+      }
+    for (int r = 0; r < L.m; ++r) vm[I.om + (long long)VM_Q0 * L.m + r] = L.q[r];
+    for (int j = 0; j < L.n; ++j) {
+      vn[I.on + (long long)VN_C0 * L.n + j] = L.c[j];
+      vn[I.on + (long long)VN_L0 * L.n + j] = L.l[j];
+      vn[I.on + (long long)VN_U0 * L.n + j] = L.u[j];
+    }
+  }
+  // ---- device ----
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
+  if (e == cudaSuccess) {
+    if (stream) {
+      b->stream = (cudaStream_t)stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+      b->own_stream = true;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  int per_sm = 1;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve, NTB, 0);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  b->grid = std::max(1, std::min(count, per_sm * b->num_sms));
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  size_t off = 0;
+  const size_t o_kptr = off; off += al(4 * KP);
+  const size_t o_kidx = off; off += al(4 * KE + 16);
+  const size_t o_kval = off; off += al(8 * KE + 16);
+  const size_t o_tptr = off; off += al(4 * TP);
+  const size_t o_tidx = off; off += al(4 * TE + 16);
+  const size_t o_tval = off; off += al(8 * TE + 16);
+  const size_t o_vm = off; off += al(8 * std::max<long long>(OM, 1));
+  const size_t o_vn = off; off += al(8 * ON);
+  const size_t o_xo = off; off += al(8 * XO);
+  const size_t o_yo = off; off += al(8 * std::max<long long>(YO, 1));
+  const size_t o_x0 = off; off += al(8 * XO);
+  const size_t o_y0 = off; off += al(8 * std::max<long long>(YO, 1));
+  const size_t o_st = off; off += al(4 * count);
+  const size_t o_it = off; off += al(8 * count);
+  const size_t o_in = off; off += al(sizeof(Inst) * count);
+  const size_t o_or = off; off += al(4 * count);
+  const size_t o_q = off; off += al(4);
+  b->arena_bytes = off;
+  e = cudaMalloc((void **)&b->arena, b->arena_bytes);
+  if (e != cudaSuccess) {
+    free_batch(b);
+    return set_error(e == cudaErrorMemoryAllocation ? PDLP_ERR_OOM : PDLP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  char *Ar = b->arena;
+  b->A.kptr = (int *)(Ar + o_kptr);
+  b->A.kidx = (int *)(Ar + o_kidx);
+  b->A.kval = (double *)(Ar + o_kval);
+  b->A.tptr = (int *)(Ar + o_tptr);
+  b->A.tidx = (int *)(Ar + o_tidx);
+  b->A.tval = (double *)(Ar + o_tval);
+  b->A.vm = (double *)(Ar + o_vm);
+  b->A.vn = (double *)(Ar + o_vn);
+  b->A.xout = (double *)(Ar + o_xo);
+  b->A.yout = (double *)(Ar + o_yo);
+  b->d_x0 = (double *)(Ar + o_x0);
+  b->d_y0 = (double *)(Ar + o_y0);
+  b->A.status = (int *)(Ar + o_st);
+  b->A.iters = (long long *)(Ar + o_it);
+  b->d_inst = (Inst *)(Ar + o_in);
+  b->d_order = (int *)(Ar + o_or);
+  b->d_queue = (int *)(Ar + o_q);
+  // longest instances first
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    const long long na = lps[a].row_ptr[lps[a].m], nc = lps[c].row_ptr[lps[c].m];
+    return na + lps[a].m + lps[a].n > nc + lps[c].m + lps[c].n;
+  });
+  cudaStream_t st = b->stream;
+#define BCKS(call)                                                                             \
+  do {                                                                                         \
+    cudaError_t e2_ = (call);                                                                  \
+    if (e2_ != cudaSuccess) {                                                                  \
+      std::string msg_ = std::string(#call) + ": " + cudaGetErrorString(e2_);                   \
+      free_batch(b);                                                                           \
+      return set_error(PDLP_ERR_CUDA, msg_.c_str());                                           \
+    }                                                                                          \
+  } while (0)
+  BCKS(cudaMemsetAsync(b->arena, 0, b->arena_bytes, st));
+  BCKS(cudaMemcpyAsync((void *)b->A.kptr, kptr.data(), 4 * KP, cudaMemcpyHostToDevice, st));
+  if (KE) {
+    BCKS(cudaMemcpyAsync((void *)b->A.kidx, kidx.data(), 4 * KE, cudaMemcpyHostToDevice, st));
+    BCKS(cudaMemcpyAsync(b->A.kval, kval.data(), 8 * KE, cudaMemcpyHostToDevice, st));
+    BCKS(cudaMemcpyAsync((void *)b->A.tidx, tidx.data(), 4 * TE, cudaMemcpyHostToDevice, st));
+    BCKS(cudaMemcpyAsync(b->A.tval, tval.data(), 8 * TE, cudaMemcpyHostToDevice, st));
+  }
+  BCKS(cudaMemcpyAsync((void *)b->A.tptr, tptr.data(), 4 * TP, cudaMemcpyHostToDevice, st));
+  if (OM) BCKS(cudaMemcpyAsync(b->A.vm, vm.data(), 8 * OM, cudaMemcpyHostToDevice, st));
+  BCKS(cudaMemcpyAsync(b->A.vn, vn.data(), 8 * ON, cudaMemcpyHostToDevice, st));
+  BCKS(cudaMemcpyAsync(b->d_order, order.data(), 4 * count, cudaMemcpyHostToDevice, st));
+  BCKS(cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, st));
+  k_batch_scale<<<count, NTB, 0, st>>>(b->A, b->d_inst, count, prm.ruiz_iters, prm.pc_alpha, prm.eps_zero);
+  BCKS(cudaGetLastError());
+  BCKS(cudaMemcpyAsync(b->h_inst.data(), b->d_inst, sizeof(Inst) * count, cudaMemcpyDeviceToHost, st));
+  BCKS(cudaStreamSynchronize(st));
+  b->setup_ms = now_ms() - t0;
+  // ---- schedule: lanes per row from the mean row length; the entries-per-lane
+  // target is autotuned by timing short solves of the whole batch ----
+  auto set_lanes = [&](double target) -> int {
+    for (int i = 0; i < count; ++i) {
+      Inst &I = b->h_inst[i];
+      const double nnz = (double)lps[i].row_ptr[lps[i].m];
+      I.gk = lanes_for(I.m ? nnz / I.m : 0.0, target);
+      I.gt = lanes_for(nnz / I.n, target);
+    }
+    cudaError_t e3 = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, st);
+    return e3 == cudaSuccess ? PDLP_OK : set_error(PDLP_ERR_CUDA, cudaGetErrorString(e3));
+  };
+  const double t1 = now_ms();
+  const double cands[4] = {2.0, 4.0, 8.0, 16.0};
+  double best = INFINITY, best_t = 4.0;
+  Params tp{};
+  tp.tol = 0.0;
+  tp.theta = prm.theta;
+  tp.eps_zero = prm.eps_zero;
+  tp.beta_suff = prm.beta_suff;
+  tp.beta_nec = prm.beta_nec;
+  tp.beta_art = prm.beta_art;
+  tp.max_iter = 2 * prm.check_period;
+  tp.P = prm.check_period;
+  tp.warm = 0;
+  cudaEvent_t ea, eb;
+  BCKS(cudaEventCreate(&ea));
+  BCKS(cudaEventCreate(&eb));
+  for (double c : cands) {
+    int rc = set_lanes(c);
+    if (rc) {
+      free_batch(b);
+      return rc;
+    }
+    BCKS(cudaEventRecord(ea, st));
+    rc = launch_solve(b, b->A, tp, st);
+    if (rc) {
+      free_batch(b);
+      return rc;
+    }
+    BCKS(cudaEventRecord(eb, st));
+    BCKS(cudaEventSynchronize(eb));
+    float ms = 0.f;
+    BCKS(cudaEventElapsedTime(&ms, ea, eb));
+    if (ms < best) {
+      best = ms;
+      best_t = c;
+    }
+  }
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+  int rc = set_lanes(best_t);
+  if (rc) {
+    free_batch(b);
+    return rc;
+  }
+  BCKS(cudaStreamSynchronize(st));
+  b->lanes_target = best_t;
+  b->tune_ms = now_ms() - t1;
+#undef BCKS
+  *out = b;
+  return PDLP_OK;
+}
+
+int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double tol, int64_t max_iter, double *x_out,
+                     double *y_out, int32_t *status, int64_t *iters) {
+  if (!b) return set_error(PDLP_ERR_INVALID, "pdlp_batch_solve: batch is NULL");
+  if (!(tol >= 0.0) || max_iter < 1) return set_error(PDLP_ERR_INVALID, "pdlp_batch_solve: need tol >= 0, max_iter >= 1");
+  BCK(cudaSetDevice(b->device));
+  const double t0 = now_ms();
+  cudaStream_t st = b->stream;
+  Params p{};
+  p.tol = tol;
+  p.theta = b->prm.theta;
+  p.eps_zero = b->prm.eps_zero;
+  p.beta_suff = b->prm.beta_suff;
+  p.beta_nec = b->prm.beta_nec;
+  p.beta_art = b->prm.beta_art;
+  p.max_iter = max_iter;
+  p.P = b->prm.check_period;
+  p.warm = (x0 || y0) ? 1 : 0;
+  Arrays A = b->A;
+  A.x0 = x0 ? b->d_x0 : nullptr;
+  A.y0 = y0 ? b->d_y0 : nullptr;
+  if (x0) BCK(cudaMemcpyAsync(b->d_x0, x0, 8 * b->sum_n, cudaMemcpyHostToDevice, st));
+  if (y0 && b->sum_m) BCK(cudaMemcpyAsync(b->d_y0, y0, 8 * b->sum_m, cudaMemcpyHostToDevice, st));
+  // one CUDA graph per (parameters, warm start) combination, rebuilt when they change
+  const bool same = b->gexec && std::memcmp(&b->gp, &p, sizeof(Params)) == 0 && b->g_x0 == A.x0 && b->g_y0 == A.y0;
+  if (!same) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    BCK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch_solve(b, A, p, b->cap);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e2 != cudaSuccess) return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e2));
+    b->graph = g;
+    BCK(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+    b->gp = p;
+    b->g_x0 = A.x0;
+    b->g_y0 = A.y0;
+  }
+  BCK(cudaGraphLaunch(b->gexec, st));
+  if (x_out) BCK(cudaMemcpyAsync(x_out, b->A.xout, 8 * b->sum_n, cudaMemcpyDeviceToHost, st));
+  if (y_out && b->sum_m) BCK(cudaMemcpyAsync(y_out, b->A.yout, 8 * b->sum_m, cudaMemcpyDeviceToHost, st));
+  if (status) BCK(cudaMemcpyAsync(status, b->A.status, 4 * (size_t)b->count, cudaMemcpyDeviceToHost, st));
+  if (iters) BCK(cudaMemcpyAsync(iters, b->A.iters, 8 * (size_t)b->count, cudaMemcpyDeviceToHost, st));
+  BCK(cudaStreamSynchronize(st));
+  b->solve_ms = now_ms() - t0;
+  return PDLP_OK;
+}
+
+int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *s) {
+  if (!b || !s) return set_error(PDLP_ERR_INVALID, "pdlp_batch_info: null argument");
+  std::memset(s, 0, sizeof(*s));
+  s->count = b->count;
+  s->grid = b->grid;
+  s->sum_m = b->sum_m;
+  s->sum_n = b->sum_n;
+  s->sum_nnz = b->sum_nnz;
+  s->setup_ms = b->setup_ms;
+  s->tune_ms = b->tune_ms;
+  s->solve_ms = b->solve_ms;
+  s->entries_per_lane = b->lanes_target;
+  s->device_bytes = b->arena_bytes;
+  return PDLP_OK;
+}
+
+int pdlp_batch_lanes(const pdlp_batch *b, int32_t *lanes_K, int32_t *lanes_KT) {
+  if (!b) return set_error(PDLP_ERR_INVALID, "pdlp_batch_lanes: batch is NULL");
+  for (int i = 0; i < b->count; ++i) {
+    if (lanes_K) lanes_K[i] = b->h_inst[i].gk;
+    if (lanes_KT) lanes_KT[i] = b->h_inst[i].gt;
+  }
+  return PDLP_OK;
+}
+
+void pdlp_batch_destroy(pdlp_batch *b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+}
+
+}  // extern "C"

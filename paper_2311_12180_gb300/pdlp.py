@@ -87,7 +87,39 @@ EXPORTS = (
     "pdlp_run_periods", "pdlp_poll", "pdlp_finish", "pdlp_time_kernels", "pdlp_kernel_count",
     "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
     "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error", "pdlp_scale_device_noalloc",
+    "pdlp_batch_create", "pdlp_batch_solve", "pdlp_batch_info", "pdlp_batch_lanes", "pdlp_batch_destroy",
 )
+
+
+class pdlp_lp(C.Structure):
+    _fields_ = [
+        ("m", C.c_int32),
+        ("n", C.c_int32),
+        ("n_eq", C.c_int32),
+        ("pad_", C.c_int32),
+        ("c", C.c_void_p),
+        ("row_ptr", C.c_void_p),
+        ("col_idx", C.c_void_p),
+        ("val", C.c_void_p),
+        ("q", C.c_void_p),
+        ("l", C.c_void_p),
+        ("u", C.c_void_p),
+    ]
+
+
+class pdlp_batch_stats(C.Structure):
+    _fields_ = [
+        ("count", C.c_int32),
+        ("grid", C.c_int32),
+        ("sum_m", C.c_int64),
+        ("sum_n", C.c_int64),
+        ("sum_nnz", C.c_int64),
+        ("setup_ms", C.c_double),
+        ("tune_ms", C.c_double),
+        ("solve_ms", C.c_double),
+        ("entries_per_lane", C.c_double),
+        ("device_bytes", C.c_size_t),
+    ]
 
 _lib = None
 
@@ -148,6 +180,16 @@ def lib():
     L.pdlp_last_error.restype = C.c_char_p
     L.pdlp_scale_device_noalloc.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, i32, d, vp, vp, vp]
     L.pdlp_scale_device_noalloc.restype = C.c_int
+    L.pdlp_batch_create.argtypes = [P(vp), i32, P(pdlp_lp), P(pdlp_params), vp]
+    L.pdlp_batch_create.restype = C.c_int
+    L.pdlp_batch_solve.argtypes = [vp, vp, vp, d, i64, vp, vp, vp, vp]
+    L.pdlp_batch_solve.restype = C.c_int
+    L.pdlp_batch_info.argtypes = [vp, P(pdlp_batch_stats)]
+    L.pdlp_batch_info.restype = C.c_int
+    L.pdlp_batch_lanes.argtypes = [vp, vp, vp]
+    L.pdlp_batch_lanes.restype = C.c_int
+    L.pdlp_batch_destroy.argtypes = [vp]
+    L.pdlp_batch_destroy.restype = None
     _lib = L
     return L
 
@@ -322,3 +364,77 @@ class Solver:
 
     def device_bytes(self) -> int:
         return int(lib().pdlp_device_bytes(self.h))
+
+
+class BatchSolver:
+    """Many LPs solved together in one persistent launch (pdlp_batch_*).
+    `lps` is a sequence of objects with the fields of lpgen.LP."""
+
+    def __init__(self, lps, params: pdlp_params | None = None, stream: int | None = None, **kw):
+        if kw:
+            params = params or pdlp_default_params()
+            for k, v in kw.items():
+                setattr(params, k, v)
+        self._keep = []
+        arr = (pdlp_lp * len(lps))()
+        self.ms, self.ns = [], []
+        for i, lp in enumerate(lps):
+            c, q, l, u = _f64(lp.c), _f64(lp.q), _f64(lp.l), _f64(lp.u)
+            rp, ci, v = _i32(lp.row_ptr), _i32(lp.col_idx), _f64(lp.val)
+            q = q if q.size else np.zeros(1)
+            ci = ci if ci.size else np.zeros(1, np.int32)
+            v = v if v.size else np.zeros(1)
+            self._keep += [c, q, l, u, rp, ci, v]
+            arr[i] = pdlp_lp(int(lp.m), int(lp.n), int(lp.n_eq), 0, _ptr(c), _ptr(rp), _ptr(ci), _ptr(v), _ptr(q),
+                             _ptr(l), _ptr(u))
+            self.ms.append(int(lp.m))
+            self.ns.append(int(lp.n))
+        self.count = len(lps)
+        self.xo = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+        self.yo = np.concatenate([[0], np.cumsum(self.ms)]).astype(np.int64)
+        self.h = C.c_void_p()
+        _check(lib().pdlp_batch_create(C.byref(self.h), self.count, arr, C.byref(params) if params else None,
+                                       C.c_void_p(stream) if stream else None))
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pdlp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def solve(self, tol=1e-6, max_iter=1_000_000, x0=None, y0=None):
+        """Returns (list of x, list of y, status array, iters array)."""
+        X = np.empty(int(self.xo[-1]))
+        Y = np.empty(max(int(self.yo[-1]), 1))
+        st = np.empty(self.count, dtype=np.int32)
+        it = np.empty(self.count, dtype=np.int64)
+        x0p = None if x0 is None else _f64(np.concatenate(x0) if isinstance(x0, (list, tuple)) else x0)
+        y0p = None if y0 is None else _f64(np.concatenate(y0) if isinstance(y0, (list, tuple)) else y0)
+        _check(lib().pdlp_batch_solve(self.h, _ptr(x0p), _ptr(y0p), tol, int(max_iter), _ptr(X), _ptr(Y), _ptr(st),
+                                      _ptr(it)))
+        xs = [X[self.xo[i]:self.xo[i + 1]] for i in range(self.count)]
+        ys = [Y[self.yo[i]:self.yo[i + 1]] for i in range(self.count)]
+        return xs, ys, st, it
+
+    def stats(self) -> dict:
+        s = pdlp_batch_stats()
+        _check(lib().pdlp_batch_info(self.h, C.byref(s)))
+        return {f: getattr(s, f) for f, _ in pdlp_batch_stats._fields_}
+
+    def lanes(self):
+        a = np.zeros(self.count, dtype=np.int32)
+        b = np.zeros(self.count, dtype=np.int32)
+        _check(lib().pdlp_batch_lanes(self.h, _ptr(a), _ptr(b)))
+        return a, b

@@ -108,3 +108,13 @@ def test_null_handles_are_safe(L):
     assert L.pdlp_get_stream(None) is None
     assert L.pdlp_run_periods(None, 1) == P.ERR_INVALID
     assert L.pdlp_begin(None, None, None, 1e-4, 10) == P.ERR_INVALID
+
+
+def test_batch_rejects_bad_lp_on_host(L):
+    good = lpgen.tiny_lp(0)
+    bad = lpgen.tiny_lp(1)
+    bad.col_idx = bad.col_idx.copy()
+    bad.col_idx[7] = bad.n + 3
+    with pytest.raises(P.PdlpError) as e:
+        P.BatchSolver([good, bad])
+    assert e.value.code == P.ERR_INVALID and "LP 1" in str(e.value)
