@@ -345,3 +345,80 @@ def batch_lps(count: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,
         out.append(plant(sub, m, n, n_eq, row_ptr, cols, val, np.zeros(n), np.full(n, 10.0),
                          meta=dict(kind="batch", seed=seed, index=i, density=d)))
     return out
+
+
+# ----------------------------------------------------------------------------
+# parametric transportation family
+# ----------------------------------------------------------------------------
+
+
+@dataclass
+class TransportFamily:
+    """min sum c_ij x_ij  s.t.  sum_i x_ij = d_j (sinks, equality rows first),
+    -sum_j x_ij >= -s_i (sources), x >= 0, with x_ij at column i * sinks + j.
+    Costs, supplies and demands are affine in a latent theta ~ N(0, I_dim)
+    through fixed seeded matrices, plus N(0, noise) noise; supplies and
+    demands are clipped at `floor` (keeps every instance feasible) and the
+    supplies rescaled so that sum s = slack * sum d."""
+
+    sources: int
+    sinks: int
+    dim: int
+    c0: np.ndarray
+    Cc: np.ndarray
+    s0: np.ndarray
+    Cs: np.ndarray
+    d0: np.ndarray
+    Cd: np.ndarray
+    noise: float
+    floor: float
+    slack: float
+    row_ptr: np.ndarray
+    col_idx: np.ndarray
+    val: np.ndarray
+
+    @property
+    def n(self):
+        return self.sources * self.sinks
+
+    @property
+    def m(self):
+        return self.sources + self.sinks
+
+
+def transport_family(seed: int = 0, sources: int = 200, sinks: int = 300, dim: int = 16, noise: float = 0.1,
+                     floor: float = 0.05, slack: float = 1.05) -> TransportFamily:
+    rng = np.random.default_rng([0x7A45, seed])
+    n = sources * sinks
+    # costs: a base geometry (sources and sinks on the unit square) plus latent directions
+    ps, pk = rng.random((sources, 2)), rng.random((sinks, 2))
+    c0 = np.sqrt(((ps[:, None, :] - pk[None, :, :]) ** 2).sum(-1)).ravel() * 10.0 + 1.0
+    Cc = rng.standard_normal((n, dim)) * 0.5
+    s0 = rng.uniform(1.0, 3.0, sources)
+    Cs = rng.standard_normal((sources, dim)) * 0.3
+    d0 = rng.uniform(1.0, 2.0, sinks)
+    Cd = rng.standard_normal((sinks, dim)) * 0.2
+    # K: sink rows (+1) first, then source rows (-1)
+    rows_sink = [np.arange(sources) * sinks + j for j in range(sinks)]
+    rows_src = [np.arange(sinks) + i * sinks for i in range(sources)]
+    cols = np.concatenate(rows_sink + rows_src)
+    val = np.concatenate([np.ones(n), -np.ones(n)])
+    row_ptr = np.concatenate([[0], np.cumsum([sources] * sinks + [sinks] * sources)])
+    return TransportFamily(sources, sinks, dim, c0, Cc, s0, Cs, d0, Cd, noise, floor, slack,
+                           row_ptr.astype(np.int32), cols.astype(np.int32), val)
+
+
+def transport_thetas(count: int, seed: int, dim: int = 16) -> np.ndarray:
+    return np.random.default_rng([0x7E7A, seed]).standard_normal((count, dim))
+
+
+def transport_lp(fam: TransportFamily, theta: np.ndarray, noise_seed: int) -> LP:
+    """The family member at latent `theta` (noise drawn from `noise_seed`)."""
+    rng = np.random.default_rng([0x7A46, noise_seed])
+    c = fam.c0 + fam.Cc @ theta + rng.normal(0.0, fam.noise, fam.n)
+    s = np.maximum(fam.s0 + fam.Cs @ theta + rng.normal(0.0, fam.noise, fam.sources), fam.floor)
+    d = np.maximum(fam.d0 + fam.Cd @ theta + rng.normal(0.0, fam.noise, fam.sinks), fam.floor)
+    s = s * (fam.slack * d.sum() / s.sum())
+    q = np.concatenate([d, -s])
+    return LP(m=fam.m, n=fam.n, n_eq=fam.sinks, c=c, row_ptr=fam.row_ptr, col_idx=fam.col_idx, val=fam.val, q=q,
+              l=np.zeros(fam.n), u=np.full(fam.n, np.inf), meta=dict(kind="transport", noise_seed=noise_seed))
