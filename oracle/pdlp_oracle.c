@@ -438,7 +438,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
               double *y_out, orc_info *info, orc_check *trace, int32_t trace_cap) {
   if (!lp || !p || !x_out || !y_out || !info) return ORC_ERR_INVALID;
   if (validate(lp) != ORC_OK) return ORC_ERR_INVALID;
-  if (p->check_period < 1 || p->max_iter < 0 || !(p->tol >= 0.0)) return ORC_ERR_INVALID;
+  if (p->check_period < 1 || p->max_iter < 1 || !(p->tol >= 0.0)) return ORC_ERR_INVALID;
   const int32_t m = lp->m, n = lp->n, n_eq = lp->n_eq;
   const int32_t *rp = lp->row_ptr, *ci = lp->col_idx;
   const int64_t nnz = m > 0 ? rp[m] : 0;

@@ -344,3 +344,9 @@ def test_first_solve_step_is_eq_pdhg(golden):
     y1[lp.n_eq:] = np.maximum(y1[lp.n_eq:], 0)
     np.testing.assert_allclose(r.x, x1, rtol=1e-14, atol=1e-15)
     np.testing.assert_allclose(r.y, y1, rtol=1e-14, atol=1e-15)
+
+
+def test_iteration_limit_below_one_is_rejected():
+    # the iteration limit counts accepted steps and must allow at least one
+    with pytest.raises(ValueError):
+        oracle.solve(lpgen.tiny_lp(0), tol=1e-6, max_iter=0)
