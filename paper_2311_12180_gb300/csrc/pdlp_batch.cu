@@ -692,36 +692,6 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   b->sum_m = YO;
   b->sum_n = XO;
   b->sum_nnz = KE;
-  // ---- host staging: K, K' (stable counting sort), vectors ----
-  std::vector<int> kptr(KP), kidx(KE), tptr(TP), tidx(TE);
-  std::vector<double> kval(KE), tval(TE), vm(OM > 0 ? OM : 1, 0.0), vn(ON, 0.0);
-  for (int i = 0; i < count; ++i) {
-    const pdlp_lp &L = lps[i];
-    const Inst &I = b->h_inst[i];
-    const long long nnz = L.row_ptr[L.m];
-    std::memcpy(&kptr[I.kp], L.row_ptr, sizeof(int) * (L.m + 1));
-    if (nnz) {
-      std::memcpy(&kidx[I.ke], L.col_idx, sizeof(int) * nnz);
-      std::memcpy(&kval[I.ke], L.val, sizeof(double) * nnz);
-    }
-    int *tp = &tptr[I.tp];
-    std::fill(tp, tp + L.n + 1, 0);
-    for (long long e = 0; e < nnz; ++e) tp[L.col_idx[e] + 1]++;
-    for (int j = 0; j < L.n; ++j) tp[j + 1] += tp[j];
-    std::vector<int> fill(tp, tp + L.n);
-    for (int r = 0; r < L.m; ++r)
-      for (int e = L.row_ptr[r]; e < L.row_ptr[r + 1]; ++e) {
-        const int pos = fill[L.col_idx[e]]++;
-        tidx[I.te + pos] = r;
-        tval[I.te + pos] = L.val[e];
-      }
-    for (int r = 0; r < L.m; ++r) vm[I.om + (long long)VM_Q0 * L.m + r] = L.q[r];
-    for (int j = 0; j < L.n; ++j) {
-      vn[I.on + (long long)VN_C0 * L.n + j] = L.c[j];
-      vn[I.on + (long long)VN_L0 * L.n + j] = L.l[j];
-      vn[I.on + (long long)VN_U0 * L.n + j] = L.u[j];
-    }
-  }
   // ---- device ----
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, b->device);
@@ -802,16 +772,46 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
     }                                                                                          \
   } while (0)
   BCKS(cudaMemsetAsync(b->arena, 0, b->arena_bytes, st));
-  BCKS(cudaMemcpyAsync((void *)b->A.kptr, kptr.data(), 4 * KP, cudaMemcpyHostToDevice, st));
-  if (KE) {
-    BCKS(cudaMemcpyAsync((void *)b->A.kidx, kidx.data(), 4 * KE, cudaMemcpyHostToDevice, st));
-    BCKS(cudaMemcpyAsync(b->A.kval, kval.data(), 8 * KE, cudaMemcpyHostToDevice, st));
-    BCKS(cudaMemcpyAsync((void *)b->A.tidx, tidx.data(), 4 * TE, cudaMemcpyHostToDevice, st));
-    BCKS(cudaMemcpyAsync(b->A.tval, tval.data(), 8 * TE, cudaMemcpyHostToDevice, st));
+  // per LP: K straight from the caller's arrays, K' by a stable counting sort
+  // into one reused host buffer, and the input vectors into their blocks
+  {
+    long long max_n = 1, max_nnz = 1;
+    for (int i = 0; i < count; ++i) {
+      max_n = std::max<long long>(max_n, lps[i].n);
+      max_nnz = std::max<long long>(max_nnz, lps[i].row_ptr[lps[i].m]);
+    }
+    std::vector<int> tp((size_t)max_n + 1), ti((size_t)max_nnz), fill((size_t)max_n);
+    std::vector<double> tv((size_t)max_nnz);
+    for (int i = 0; i < count; ++i) {
+      const pdlp_lp &L = lps[i];
+      const Inst &I = b->h_inst[i];
+      const long long nnz = L.row_ptr[L.m];
+      std::fill(tp.begin(), tp.begin() + L.n + 1, 0);
+      for (long long e = 0; e < nnz; ++e) tp[L.col_idx[e] + 1]++;
+      for (int j = 0; j < L.n; ++j) tp[j + 1] += tp[j];
+      std::copy(tp.begin(), tp.begin() + L.n, fill.begin());
+      for (int r = 0; r < L.m; ++r)
+        for (int e = L.row_ptr[r]; e < L.row_ptr[r + 1]; ++e) {
+          const int pos = fill[L.col_idx[e]]++;
+          ti[pos] = r;
+          tv[pos] = L.val[e];
+        }
+      // pageable sources: each copy has read its source when the call returns
+      BCKS(cudaMemcpyAsync((void *)(b->A.kptr + I.kp), L.row_ptr, 4 * (size_t)(L.m + 1), cudaMemcpyHostToDevice, st));
+      BCKS(cudaMemcpyAsync((void *)(b->A.tptr + I.tp), tp.data(), 4 * (size_t)(L.n + 1), cudaMemcpyHostToDevice, st));
+      if (nnz) {
+        BCKS(cudaMemcpyAsync((void *)(b->A.kidx + I.ke), L.col_idx, 4 * (size_t)nnz, cudaMemcpyHostToDevice, st));
+        BCKS(cudaMemcpyAsync(b->A.kval + I.ke, L.val, 8 * (size_t)nnz, cudaMemcpyHostToDevice, st));
+        BCKS(cudaMemcpyAsync((void *)(b->A.tidx + I.te), ti.data(), 4 * (size_t)nnz, cudaMemcpyHostToDevice, st));
+        BCKS(cudaMemcpyAsync(b->A.tval + I.te, tv.data(), 8 * (size_t)nnz, cudaMemcpyHostToDevice, st));
+      }
+      if (L.m) BCKS(cudaMemcpyAsync(b->A.vm + I.om + (long long)VM_Q0 * L.m, L.q, 8 * (size_t)L.m, cudaMemcpyHostToDevice, st));
+      BCKS(cudaMemcpyAsync(b->A.vn + I.on + (long long)VN_C0 * L.n, L.c, 8 * (size_t)L.n, cudaMemcpyHostToDevice, st));
+      BCKS(cudaMemcpyAsync(b->A.vn + I.on + (long long)VN_L0 * L.n, L.l, 8 * (size_t)L.n, cudaMemcpyHostToDevice, st));
+      BCKS(cudaMemcpyAsync(b->A.vn + I.on + (long long)VN_U0 * L.n, L.u, 8 * (size_t)L.n, cudaMemcpyHostToDevice, st));
+      BCKS(cudaStreamSynchronize(st));  // tp / ti / tv are reused by the next LP
+    }
   }
-  BCKS(cudaMemcpyAsync((void *)b->A.tptr, tptr.data(), 4 * TP, cudaMemcpyHostToDevice, st));
-  if (OM) BCKS(cudaMemcpyAsync(b->A.vm, vm.data(), 8 * OM, cudaMemcpyHostToDevice, st));
-  BCKS(cudaMemcpyAsync(b->A.vn, vn.data(), 8 * ON, cudaMemcpyHostToDevice, st));
   BCKS(cudaMemcpyAsync(b->d_order, order.data(), 4 * count, cudaMemcpyHostToDevice, st));
   BCKS(cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, st));
   k_batch_scale<<<count, NTB, 0, st>>>(b->A, b->d_inst, count, prm.ruiz_iters, prm.pc_alpha, prm.eps_zero);
