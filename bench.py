@@ -274,17 +274,116 @@ def run_batch(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_warmstart(args, rank, world):
+    """Learned warm start on the parametric transportation family: sources x
+    sinks flows, costs / supplies / demands affine in a 16-dim latent theta
+    plus N(0, noise) noise.  Training targets are the batched solver's own
+    solutions; the BF16 MLP theta -> (x, y) is trained by the library's
+    kernels; the held-out thetas are then solved to tol from the cold start,
+    from the MLP's prediction (with cold fallback), and from two naive starts
+    (mean training solution; solution of the nearest training theta)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import lpgen
+    from paper_2311_12180_gb300 import _build
+    from paper_2311_12180_gb300 import warmstart as W
+
+    _build.build()
+    tol = args.ws_tol
+    fam = lpgen.transport_family(0, sources=args.ws_sources, sinks=args.ws_sinks, dim=16, noise=args.ws_noise,
+                                 cost_scale=args.ws_cost_scale)
+    n, m = fam.n, fam.m
+    th_tr = lpgen.transport_thetas(args.ws_train, 1)
+    th_te = lpgen.transport_thetas(args.ws_test, 2)
+
+    def mk_tr(i):
+        return lpgen.transport_lp(fam, th_tr[i], i)
+
+    def mk_te(i):
+        return lpgen.transport_lp(fam, th_te[i], 10_000_000 + i)
+
+    T = np.empty((args.ws_train, n + m), np.float32)
+
+    def keep(i, x, y):
+        T[i, :n] = x
+        T[i, n:] = y
+
+    t = time.perf_counter()
+    st, it, data_solve_s, _ = W.solve_many(mk_tr, args.ws_train, args.ws_data_tol, on_solution=keep)
+    data_s = time.perf_counter() - t
+    steps = args.ws_steps
+    sched = ((int(steps * 0.6), 1e-3), (int(steps * 0.3), 3e-4), (steps - int(steps * 0.6) - int(steps * 0.3), 1e-4))
+    t = time.perf_counter()
+    net, losses = W.train(th_tr, T, hidden=256, schedule=sched, batch=256, seed=0)
+    train_s = time.perf_counter() - t
+    flops_step = 6.0 * 256 * (16 * 256 + 256 * 256 + 256 * (n + m))
+    t = time.perf_counter()
+    Yp = net.predict(th_te).astype(np.float64)
+    predict_s = time.perf_counter() - t
+    net.close()
+
+    Tc = np.empty((args.ws_test, n + m))
+
+    def keep_c(i, x, y):
+        Tc[i, :n] = x
+        Tc[i, n:] = y
+
+    arms = {}
+    st_c, it_c, cold_s, _ = W.solve_many(mk_te, args.ws_test, tol, on_solution=keep_c)
+    arms["cold"] = {"solve_s": cold_s, "optimal": int(np.sum(st_c == 0)), "iters_median": float(np.median(it_c)),
+                    "iters_mean": float(np.mean(it_c))}
+    mx, my = W.mean_start(T, n)
+    near = W.nearest_index(th_tr, th_te)
+    starts = {"mlp": lambda i: (Yp[i, :n], Yp[i, n:]), "mean": lambda i: (mx, my),
+              "nearest": lambda i: (T[near[i], :n], T[near[i], n:])}
+    preds = {"mlp": Yp, "mean": np.tile(np.concatenate([mx, my]), (args.ws_test, 1)), "nearest": T[near]}
+    for name, fn in starts.items():
+        r = W.solve_with_fallback(mk_te, args.ws_test, tol, fn)
+        P_ = preds[name]
+        ex = np.linalg.norm(P_[:, :n] - Tc[:, :n], axis=1) / np.maximum(np.linalg.norm(Tc[:, :n], axis=1), 1e-30)
+        ey = np.linalg.norm(P_[:, n:] - Tc[:, n:], axis=1) / np.maximum(np.linalg.norm(Tc[:, n:], axis=1), 1e-30)
+        arms[name] = {"solve_s": r["solve_s"], "optimal": int(np.sum(r["status"] == 0)), "fallbacks": r["fallbacks"],
+                      "iters_median": float(np.median(r["iters"])), "iters_mean": float(np.mean(r["iters"])),
+                      "iters_ratio_vs_cold_median": float(np.median(r["iters"] / np.maximum(it_c, 1))),
+                      "rel_err_x_median": float(np.median(ex)), "rel_err_y_median": float(np.median(ey))}
+    warm_total = arms["mlp"]["solve_s"] + predict_s
+    line = {"metric": "warm-start time-to-%g KKT (s)" % tol, "value": warm_total, "unit": "s", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f64 solve, bf16 MLP (f32 accumulate)", "data": "synthetic",
+            "config": {"workload": "transportation family %dx%d (n=%d, m=%d), theta~N(0,I16), noise %g, cost directions "
+                                   "x%g; %d training solutions (tol %g), %d held-out"
+                                   % (fam.sources, fam.sinks, n, m, args.ws_noise, args.ws_cost_scale, args.ws_train,
+                                      args.ws_data_tol, args.ws_test),
+                       "mlp": "16-256-256-%d, batch 256, Adam %d steps (lr 1e-3 / 3e-4 / 1e-4)" % (n + m, steps)},
+            "cold_s": cold_s, "speedup_vs_cold": cold_s / warm_total, "predict_s": predict_s,
+            "data_generation_s": data_s, "data_solve_s": data_solve_s, "data_optimal": int(np.sum(st == 0)),
+            "data_iters_median": float(np.median(it)), "train_s": train_s,
+            "train_tflops": flops_step * steps / train_s / 1e12,
+            "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean()), "arms": arms}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "tiny", "batch"])
+    ap.add_argument("--workload", default="large", choices=["large", "tiny", "batch", "warmstart"])
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-tol", type=float, default=1e-6)
     ap.add_argument("--batch-max-iter", type=int, default=1_000_000)
     ap.add_argument("--batch-sample", type=int, default=32)
+    ap.add_argument("--ws-sources", type=int, default=200)
+    ap.add_argument("--ws-sinks", type=int, default=300)
+    ap.add_argument("--ws-noise", type=float, default=0.1)
+    ap.add_argument("--ws-cost-scale", type=float, default=1.0, help="0: costs fixed, only supplies/demands move")
+    ap.add_argument("--ws-train", type=int, default=20000)
+    ap.add_argument("--ws-test", type=int, default=1000)
+    ap.add_argument("--ws-steps", type=int, default=4000)
+    ap.add_argument("--ws-tol", type=float, default=1e-6)
+    ap.add_argument("--ws-data-tol", type=float, default=1e-4)
     ap.add_argument("--ttt", action="store_true", help="also time full solves to 1e-4 and 1e-8 KKT")
     ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per --ttt solve (s)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -299,6 +398,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, rank, world)
+        return
+    if args.workload == "warmstart":
+        run_warmstart(args, rank, world)
         return
 
     import numpy as np

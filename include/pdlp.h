@@ -240,6 +240,48 @@ int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *stats);
 int pdlp_batch_lanes(const pdlp_batch *b, int32_t *lanes_K, int32_t *lanes_KT);
 void pdlp_batch_destroy(pdlp_batch *b);
 
+/* ---- learned warm start: BF16 MLP -----------------------------------------
+ * in -> hidden -> ReLU -> hidden -> ReLU -> out, mapping the parameters of a
+ * parametric LP family to a start point (x, y) for pdlp_solve_warm /
+ * pdlp_batch_solve.  Not in the paper.  Weights and activations enter the
+ * GEMMs as BF16 with FP32 accumulation on the tensor cores; the output layer,
+ * loss, gradients and Adam state (FP32 master weights) stay FP32.  The loss
+ * is the mean squared error on targets standardised per output with the
+ * mean / standard deviation of the data set given to pdlp_mlp_set_data;
+ * pdlp_mlp_predict returns values in target units.  All arrays below are
+ * HOST arrays, row-major. */
+typedef struct pdlp_mlp pdlp_mlp; /* opaque */
+
+/* max_batch (1..65535) bounds the mini-batch of train / gradients and the
+ * chunk of predict; each weight matrix must stay below 2^31 entries, else
+ * PDLP_ERR_INVALID.  Parameters start at zero: set them with
+ * pdlp_mlp_set_params. */
+int pdlp_mlp_create(pdlp_mlp **out, int32_t in_dim, int32_t hidden, int32_t out_dim, int32_t max_batch,
+                    void *stream);
+/* Number of FP32 parameters: layout W1 (in x hidden), b1 (hidden),
+ * W2 (hidden x hidden), b2, W3 (hidden x out), b3 (out); W row-major [in][out]. */
+int64_t pdlp_mlp_param_count(const pdlp_mlp *net);
+/* Sets / reads the FP32 master weights (setting also resets Adam's moments). */
+int pdlp_mlp_set_params(pdlp_mlp *net, const float *params);
+int pdlp_mlp_get_params(const pdlp_mlp *net, float *params);
+/* Copies the training set (X: samples x in, T: samples x out) to the GPU and
+ * computes the per-output standardisation there. */
+int pdlp_mlp_set_data(pdlp_mlp *net, int32_t samples, const float *X, const float *T);
+/* `steps` Adam steps; step s uses rows idx[s * batch .. s * batch + batch)
+ * of the data set (the caller draws them).  losses: per-step mean squared
+ * error before the update (NULL ok). */
+int pdlp_mlp_train(pdlp_mlp *net, int32_t steps, int32_t batch, const int32_t *idx, float lr, float beta1,
+                   float beta2, float eps, float *losses);
+/* Y (count x out) for inputs X (count x in), in target units. */
+int pdlp_mlp_predict(pdlp_mlp *net, int32_t count, const float *X, float *Y);
+/* One forward / backward pass on data-set rows idx[0 .. batch) without an
+ * update: the loss and the gradient of every parameter (param_count floats,
+ * layout as for set_params).  For checking the backward pass. */
+int pdlp_mlp_gradients(pdlp_mlp *net, int32_t batch, const int32_t *idx, float *loss, float *grads);
+/* Per-output standardisation in use (out floats each; NULL ok). */
+int pdlp_mlp_stats(const pdlp_mlp *net, float *mean, float *std_dev);
+void pdlp_mlp_destroy(pdlp_mlp *net);
+
 /* Allocation-free Ruiz + Pock-Chambolle scaling of a matrix the caller keeps
  * in DEVICE memory.  This entry point has no counterpart in the paper; it is
  * the same scaling pdlp_create applies (same kernels, same order of

@@ -387,13 +387,15 @@ class TransportFamily:
 
 
 def transport_family(seed: int = 0, sources: int = 200, sinks: int = 300, dim: int = 16, noise: float = 0.1,
-                     floor: float = 0.05, slack: float = 1.05) -> TransportFamily:
+                     floor: float = 0.05, slack: float = 1.05, cost_scale: float = 1.0) -> TransportFamily:
+    """cost_scale multiplies the latent cost directions (0: fixed costs, only
+    supplies and demands move with theta)."""
     rng = np.random.default_rng([0x7A45, seed])
     n = sources * sinks
     # costs: a base geometry (sources and sinks on the unit square) plus latent directions
     ps, pk = rng.random((sources, 2)), rng.random((sinks, 2))
     c0 = np.sqrt(((ps[:, None, :] - pk[None, :, :]) ** 2).sum(-1)).ravel() * 10.0 + 1.0
-    Cc = rng.standard_normal((n, dim)) * 0.5
+    Cc = rng.standard_normal((n, dim)) * 0.5 * cost_scale
     s0 = rng.uniform(1.0, 3.0, sources)
     Cs = rng.standard_normal((sources, dim)) * 0.3
     d0 = rng.uniform(1.0, 2.0, sinks)

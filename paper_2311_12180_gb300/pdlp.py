@@ -88,6 +88,8 @@ EXPORTS = (
     "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
     "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error", "pdlp_scale_device_noalloc",
     "pdlp_batch_create", "pdlp_batch_solve", "pdlp_batch_info", "pdlp_batch_lanes", "pdlp_batch_destroy",
+    "pdlp_mlp_create", "pdlp_mlp_param_count", "pdlp_mlp_set_params", "pdlp_mlp_get_params", "pdlp_mlp_set_data",
+    "pdlp_mlp_train", "pdlp_mlp_predict", "pdlp_mlp_gradients", "pdlp_mlp_stats", "pdlp_mlp_destroy",
 )
 
 
@@ -190,6 +192,26 @@ def lib():
     L.pdlp_batch_lanes.restype = C.c_int
     L.pdlp_batch_destroy.argtypes = [vp]
     L.pdlp_batch_destroy.restype = None
+    L.pdlp_mlp_create.argtypes = [P(vp), i32, i32, i32, i32, vp]
+    L.pdlp_mlp_create.restype = C.c_int
+    L.pdlp_mlp_param_count.argtypes = [vp]
+    L.pdlp_mlp_param_count.restype = i64
+    L.pdlp_mlp_set_params.argtypes = [vp, vp]
+    L.pdlp_mlp_set_params.restype = C.c_int
+    L.pdlp_mlp_get_params.argtypes = [vp, vp]
+    L.pdlp_mlp_get_params.restype = C.c_int
+    L.pdlp_mlp_set_data.argtypes = [vp, i32, vp, vp]
+    L.pdlp_mlp_set_data.restype = C.c_int
+    L.pdlp_mlp_train.argtypes = [vp, i32, i32, vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]
+    L.pdlp_mlp_train.restype = C.c_int
+    L.pdlp_mlp_predict.argtypes = [vp, i32, vp, vp]
+    L.pdlp_mlp_predict.restype = C.c_int
+    L.pdlp_mlp_gradients.argtypes = [vp, i32, vp, vp, vp]
+    L.pdlp_mlp_gradients.restype = C.c_int
+    L.pdlp_mlp_stats.argtypes = [vp, vp, vp]
+    L.pdlp_mlp_stats.restype = C.c_int
+    L.pdlp_mlp_destroy.argtypes = [vp]
+    L.pdlp_mlp_destroy.restype = None
     _lib = L
     return L
 
@@ -438,3 +460,80 @@ class BatchSolver:
         b = np.zeros(self.count, dtype=np.int32)
         _check(lib().pdlp_batch_lanes(self.h, _ptr(a), _ptr(b)))
         return a, b
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Mlp:
+    """The warm-start MLP (pdlp_mlp_*): in -> hidden -> hidden -> out."""
+
+    def __init__(self, in_dim, hidden, out_dim, max_batch=256, stream=None):
+        self.in_dim, self.hidden, self.out_dim, self.max_batch = int(in_dim), int(hidden), int(out_dim), int(max_batch)
+        self.h = C.c_void_p()
+        _check(lib().pdlp_mlp_create(C.byref(self.h), self.in_dim, self.hidden, self.out_dim, self.max_batch,
+                                     C.c_void_p(stream) if stream else None))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().pdlp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def param_count(self) -> int:
+        return int(lib().pdlp_mlp_param_count(self.h))
+
+    def set_params(self, p):
+        p = _f32(p)
+        assert p.size == self.param_count
+        _check(lib().pdlp_mlp_set_params(self.h, _ptr(p)))
+
+    def get_params(self):
+        p = np.empty(self.param_count, dtype=np.float32)
+        _check(lib().pdlp_mlp_get_params(self.h, _ptr(p)))
+        return p
+
+    def set_data(self, X, T):
+        X, T = _f32(X), _f32(T)
+        assert X.shape[1] == self.in_dim and T.shape[1] == self.out_dim and X.shape[0] == T.shape[0]
+        _check(lib().pdlp_mlp_set_data(self.h, X.shape[0], _ptr(X), _ptr(T)))
+
+    def train(self, idx, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        """idx: (steps, batch) int array of data-set rows; returns per-step losses."""
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        steps, batch = idx.shape
+        losses = np.empty(steps, dtype=np.float32)
+        _check(lib().pdlp_mlp_train(self.h, steps, batch, _ptr(idx), lr, beta1, beta2, eps, _ptr(losses)))
+        return losses
+
+    def predict(self, X):
+        X = _f32(X)
+        Y = np.empty((X.shape[0], self.out_dim), dtype=np.float32)
+        _check(lib().pdlp_mlp_predict(self.h, X.shape[0], _ptr(X), _ptr(Y)))
+        return Y
+
+    def gradients(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        loss = np.zeros(1, dtype=np.float32)
+        g = np.empty(self.param_count, dtype=np.float32)
+        _check(lib().pdlp_mlp_gradients(self.h, idx.size, _ptr(idx), _ptr(loss), _ptr(g)))
+        return float(loss[0]), g
+
+    def stats(self):
+        mu = np.empty(self.out_dim, dtype=np.float32)
+        sd = np.empty(self.out_dim, dtype=np.float32)
+        _check(lib().pdlp_mlp_stats(self.h, _ptr(mu), _ptr(sd)))
+        return mu, sd

@@ -118,3 +118,11 @@ def test_batch_rejects_bad_lp_on_host(L):
     with pytest.raises(P.PdlpError) as e:
         P.BatchSolver([good, bad])
     assert e.value.code == P.ERR_INVALID and "LP 1" in str(e.value)
+
+
+@pytest.mark.parametrize("dims", [(0, 8, 8, 8), (4, 0, 8, 8), (4, 8, 0, 8), (4, 8, 8, 0), (4, 8, 8, 70000),
+                                  (4, 65536, 65536, 8)])
+def test_mlp_create_rejects_bad_dims_on_host(L, dims):
+    h = C.c_void_p()
+    assert L.pdlp_mlp_create(C.byref(h), *dims, None) == P.ERR_INVALID
+    assert not h.value
