@@ -44,10 +44,14 @@ if ROOT not in sys.path:
 METRIC = "PDHG iters/s"
 UNIT = "iters/s"
 
-# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# dominant kernel from one ncu capture, keyed by the sha256 of the kernel
-# source it was taken on; reported as null once the source has changed.
-NCU_TRAFFIC = {}
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes)
+# of the step kernels from one ncu --set full capture of the 1e6 x 2e6 LP
+# (FP64 values), keyed by (kernel, sha256 prefix of the kernel source it was
+# taken on, value bits); reported as null once the source has changed.
+NCU_TRAFFIC = {
+    ("k_primal", "8a6336855fe4b3a7", 64): 337.193472e6 + 23.641344e6,
+    ("k_dual", "8a6336855fe4b3a7", 64): 292.569600e6 + 7.142400e6,
+}
 
 
 def kernel_source_sha() -> str:
@@ -386,6 +390,7 @@ def main():
     ap.add_argument("--ws-data-tol", type=float, default=1e-4)
     ap.add_argument("--ttt", action="store_true", help="also time full solves to 1e-4 and 1e-8 KKT")
     ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per --ttt solve (s)")
+    ap.add_argument("--ttt-tols", default="1e-4,1e-8", help="comma-separated tolerances for --ttt")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--value-bits", type=int, default=64, choices=[64, 32],
                     help="32: step kernels read an FP32 copy of K (FP64 gathers, accumulation, iterates)")
@@ -469,7 +474,7 @@ def main():
     dom_bytes = algorithmic_bytes(lp, dom, vb)
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
     sha = kernel_source_sha()
-    tr = NCU_TRAFFIC.get((dom, sha))
+    tr = NCU_TRAFFIC.get((dom, sha, args.value_bits)) if args.workload == "large" else None
     solver.finish()
     info = solver.info()
 
@@ -489,7 +494,7 @@ def main():
     if args.ttt:
         ttt = {}
         with P.Solver(lp, time_limit_s=args.ttt_limit, value_bits=args.value_bits) as s3:
-            for tol in (1e-4, 1e-8):
+            for tol in [float(v) for v in args.ttt_tols.split(",")]:
                 t = time.perf_counter()
                 _ = s3.solve(tol=tol, max_iter=10**9)
                 stt, itt = _[2], _[3]
@@ -497,7 +502,13 @@ def main():
                 ttt["%g" % tol] = {"seconds": time.perf_counter() - t, "status": P.STATUS_NAMES.get(stt, stt),
                                    "iters": itt, "setup_excluded": True,
                                    "obj_rel_err_vs_planted": abs(float(np.dot(lp.c, x_t)) - lp.obj_star)
-                                   / abs(lp.obj_star), "restarts": s3.info()["restarts"]}
+                                   / abs(lp.obj_star)}
+                inf = s3.info()
+                ttt["%g" % tol].update({
+                    "restarts": inf["restarts"], "f64_switch_iter": inf["f64_switch_iter"],
+                    "rel_gap": abs(inf["pobj"] - inf["dobj"]) / (1 + abs(inf["pobj"]) + abs(inf["dobj"])),
+                    "rel_primal_res": inf["rp_norm"] / (1 + inf["q_norm"]),
+                    "rel_dual_res": inf["rd_norm"] / (1 + inf["c_norm"])})
 
     if rank != 0:
         if pg is not None:
@@ -528,7 +539,7 @@ def main():
         "attempts_per_iter": info["attempts"] / max(info["iters"], 1),
         "effective_hbm_gbs": (algorithmic_bytes(lp, "k_primal", vb) + algorithmic_bytes(lp, "k_dual", vb)) * value / 1e9,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": tr,
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": tr, "traffic_unit": "bytes per launch (ncu)",
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
                      "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in times.items()}},
         "cpu_baseline": cpu,
