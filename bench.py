@@ -193,34 +193,49 @@ def cpu_baseline(lp, budget_s: float = 20.0):
 
 
 def run_reference(args, rank, world):
-    """Reference arm: the FP64 CPU oracle on the host cores, same metric."""
+    """Reference arm: the FP64 CPU oracle on the host cores, same metric.
+    Each step is one oracle solve of 1 + I iterations; the set-up of a solve
+    (Sec. 2.2 scaling, the median of three 1-iteration solves) is subtracted,
+    and I is sized so that the iterations take about 1.5 s per step."""
     if rank != 0:
         return
     import oracle
 
     oracle.build()
     lp, desc = make_workload(args.workload)
-    # each step: a bounded sample of the same workload (a few oracle iterations)
-    t = time.perf_counter()
-    oracle.solve(lp, tol=1e-14, max_iter=1, trace_cap=1)
-    t1 = time.perf_counter() - t
-    iters_per_step = 2 if args.workload == "large" else 64
-    for _ in range(args.warmup):
-        pass
-    t = time.perf_counter()
-    total_iters = 0
+
+    def timed(k):
+        t = time.perf_counter()
+        r = oracle.solve(lp, tol=0.0, max_iter=k, trace_cap=1)
+        return time.perf_counter() - t, r.iters
+
+    t_setup = statistics.median(timed(1)[0] for _ in range(3))
+    c = 2
+    while True:  # calibrate the per-iteration cost on a sample well above the timer noise
+        dt, k = timed(1 + c)
+        per_it = (dt - t_setup) / max(k - 1, 1)
+        if per_it * c > 0.05 or c >= 1 << 20:
+            break
+        c *= 8
+    per_it = max(per_it, 1e-9)
+    iters_per_step = int(max(2, min(1 << 22, 1.5 / per_it)))
+    for _ in range(min(args.warmup, 1)):
+        timed(1 + iters_per_step)
+    el, total_iters = 0.0, 0
     for _ in range(args.steps):
-        oracle.solve(lp, tol=1e-14, max_iter=1 + iters_per_step, trace_cap=1)
-        total_iters += iters_per_step
-    el = time.perf_counter() - t - args.steps * t1
-    val = total_iters / max(el, 1e-9)
+        dt, k = timed(1 + iters_per_step)
+        el += dt - t_setup
+        total_iters += k - 1
+    if el <= 0:
+        el = per_it * total_iters
+    val = total_iters / el
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d oracle iterations per step (set-up time of a 1-iteration solve "
-                                       "subtracted per step)" % iters_per_step},
+                             "sample": "%d oracle iterations per step, one thread (the %.2f s set-up of a solve "
+                                       "subtracted per step)" % (iters_per_step, t_setup)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
