@@ -2,22 +2,35 @@
 // theta (in) -> hidden -> ReLU -> hidden -> ReLU -> out, trained with MSE on
 // per-output standardised targets by Adam with FP32 master weights.
 //
-// Mixed precision: weights and activations feed the GEMMs in BF16, products
-// accumulate in FP32 on the tensor cores (wmma m16n16k16 BF16 -> FP32), the
+// Every GEMM runs on the 5th-generation tensor cores: C = A Bt', A (M x K)
+// and Bt (N x K) BF16 in global memory with K contiguous, staged into shared
+// memory by TMA (128-byte swizzle, a 3-stage mbarrier ring), multiplied by
+// tcgen05.mma (kind::f16, M = N = 128 per CTA, K = 16 per instruction)
+// issued by one thread, accumulated in FP32 in tensor memory and read back
+// with tcgen05.ld by the CTA's four warps (one TMEM lane quarter each) for a
+// fused epilogue.  Because both operands must have K contiguous, every
+// tensor that enters a GEMM once as "rows x K" and once as "K x rows" is kept
+// in both layouts: the epilogues and elementwise kernels that produce an
+// activation or gradient write its transpose too (coalesced across the warp,
+// whose lanes hold consecutive rows), and the BF16 weight copies are rebuilt
+// in both layouts from the FP32 masters after each Adam step.
+//
+// Mixed precision: weights and activations enter the GEMMs as BF16, the
 // output layer, the loss, all gradients and the Adam state stay FP32, and the
-// output gradient is rounded to BF16 only as a GEMM operand.  Every step
-// (gather of a mini-batch, forward, loss, backward, Adam) is a kernel here;
-// the host only passes the mini-batch indices (random numbers drawn by the
-// caller) and launches.  Split-K partial sums and column sums are reduced in
-// a fixed order, so training is deterministic.
+// output gradient is rounded to BF16 only as a GEMM operand.  The loss is
+// fused into the output-layer GEMM's epilogue.  Split-K partial sums, column
+// sums and the loss are reduced in a fixed order, so training is
+// deterministic.  Every wait on an mbarrier is bounded (2 s); a GEMM that
+// times out records an error that the host call returns.
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
-#include <mma.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -28,184 +41,298 @@ namespace pdlp {
 namespace mlp {
 
 using bf16 = __nv_bfloat16;
-namespace wm = nvcuda::wmma;
 
-constexpr int BM = 64, BN = 64, BK = 32, GT = 128;  // GEMM tile, 4 warps of 32 x 32
-constexpr int LDA_S = BK + 8, LDB_S = BN + 8, LDC_S = BN + 4;
+// ---------------------------------------------------------------- tcgen05 GEMM
 
-// C(m, n) = sum_k A(m, k) B(k, n) over k in [k0, k1), A / B in BF16, FP32
-// accumulation; A(m, k) at A[m * lda + k] (row) or A[k * lda + m] (A_COL);
-// B(k, n) at B[k * ldb + n] (row) or B[n * ldb + k] (B_COL).  The K range of
-// split s = blockIdx.z is [s * kchunk, min(K, (s + 1) * kchunk)).  The
-// finished tile goes through epi(m, n, value, split).
-template <bool A_COL, bool B_COL, class Epi>
-__global__ void __launch_bounds__(GT) k_gemm(int M, int N, int K, int kchunk, const bf16 *__restrict__ A, int lda,
-                                             const bf16 *__restrict__ B, int ldb, Epi epi) {
-  __shared__ __align__(32) bf16 As[BM][LDA_S];
-  __shared__ __align__(32) bf16 Bs[BK][LDB_S];
-  __shared__ __align__(32) float Cs[BM][LDC_S];
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  const int warp = threadIdx.x >> 5, wm_ = warp >> 1, wn_ = warp & 1;
-  wm::fragment<wm::accumulator, 16, 16, 16, float> acc[2][2];
+constexpr int TBM = 128, TBN = 128, TBK = 64, STAGES = 3;
+constexpr int A_BYTES = TBM * TBK * 2, B_BYTES = TBN * TBK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 1024 + 128;  // + alignment slack + barriers
+constexpr uint32_t TMEM_COLS = TBN;                           // FP32 accumulator: 128 lanes x 128 columns
+// instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
+// both K-major (bits 15, 16 = 0), N / 8 at bits 17-22, M / 16 at bits 24-28
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TBN >> 3) << 17) |
+                           ((uint32_t)(TBM >> 4) << 24);
+constexpr unsigned long long WAIT_LIMIT_NS = 2000000000ull;
+
+enum { GEMM_ERR_FULL = 1, GEMM_ERR_EMPTY = 2, GEMM_ERR_DONE = 3 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Waits for phase `parity` of the mbarrier; false after WAIT_LIMIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(a, parity))
+    if (gtimer() - t0 > WAIT_LIMIT_NS) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((unsigned long long)map), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// start address / 16 (bits 0-13), leading offset 16 B (unused by this
+// layout), stride between 8-row groups 1024 B (bits 32-45), descriptor
+// version 1 (bits 46-47), layout SWIZZLE_128B = 2 (bits 61-63).
+__device__ __forceinline__ unsigned long long sw128_desc(uint32_t addr) {
+  unsigned long long d = (unsigned long long)((addr & 0x3FFFF) >> 4);
+  d |= (unsigned long long)(16 >> 4) << 16;
+  d |= (unsigned long long)(1024 >> 4) << 32;
+  d |= 1ull << 46;
+  d |= 2ull << 61;
+  return d;
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, unsigned long long a, unsigned long long b,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(a), "l"(b), "r"(IDESC), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) wm::fill_fragment(acc[i][j], 0.0f);
-  const bf16 zero = __float2bfloat16(0.0f);
-  for (int k0 = kb; k0 < ke; k0 += BK) {
-    // A tile: BM x BK
-    for (int t = threadIdx.x; t < BM * BK; t += GT) {
-      int r, c;
-      if (A_COL) {
-        r = t % BM;
-        c = t / BM;
-      } else {
-        r = t / BK;
-        c = t % BK;
-      }
-      const int m = m0 + r, k = k0 + c;
-      bf16 v = zero;
-      if (m < M && k < ke) v = A_COL ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
-      As[r][c] = v;
-    }
-    // B tile: BK x BN
-    for (int t = threadIdx.x; t < BK * BN; t += GT) {
-      int r, c;
-      if (B_COL) {
-        r = t % BK;
-        c = t / BK;
-      } else {
-        r = t / BN;
-        c = t % BN;
-      }
-      const int k = k0 + r, n = n0 + c;
-      bf16 v = zero;
-      if (k < ke && n < N) v = B_COL ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
-      Bs[r][c] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; kk += 16) {
-      wm::fragment<wm::matrix_a, 16, 16, 16, bf16, wm::row_major> fa[2];
-      wm::fragment<wm::matrix_b, 16, 16, 16, bf16, wm::row_major> fb[2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) wm::load_matrix_sync(fa[i], &As[wm_ * 32 + i * 16][kk], LDA_S);
-#pragma unroll
-      for (int j = 0; j < 2; ++j) wm::load_matrix_sync(fb[j], &Bs[kk][wn_ * 32 + j * 16], LDB_S);
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) wm::mma_sync(acc[i][j], fa[i], fb[j], acc[i][j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-      wm::store_matrix_sync(&Cs[wm_ * 32 + i * 16][wn_ * 32 + j * 16], acc[i][j], LDC_S, wm::mem_row_major);
-  __syncthreads();
-  for (int t = threadIdx.x; t < BM * BN; t += GT) {
-    const int r = t / BN, c = t % BN;
-    const int m = m0 + r, n = n0 + c;
-    if (m < M && n < N) epi(m, n, Cs[r][c], blockIdx.z);
-  }
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// ---- epilogues ----
-struct EpiBiasReluBF16 {  // hidden layer: H = bf16(relu(z + b))
+// C(m, n) = sum_k A(m, k) Bt(n, k) over split z = blockIdx.z's K range
+// [z kchunk, min(K, (z + 1) kchunk)) (kchunk a multiple of TBK), A and Bt
+// described by the tensor maps (box TBK x 128, 128-byte swizzle).  Thread 0
+// issues the TMA loads and the MMAs; the finished tile passes through
+// epi(m, n, value, split) for m < M, n < N, then epi.finish() runs in every
+// thread.  A wait that exceeds its limit sets *err and skips the epilogue.
+template <class Epi>
+__global__ void __launch_bounds__(128) k_tc_gemm(const __grid_constant__ CUtensorMap ma,
+                                                 const __grid_constant__ CUtensorMap mb, int M, int N, int K,
+                                                 int kchunk, Epi epi, int *err) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                          ~static_cast<uintptr_t>(1023));
+  unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem + STAGES * STAGE_BYTES);
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * STAGES + 1);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done = smem_u32(bars + 2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TBM, n0 = blockIdx.x * TBN;
+  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
+  const int nk = ke > kb ? (ke - kb + TBK - 1) / TBK : 0;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    for (int s = 0; s < STAGES && s < nk; ++s) {
+      const uint32_t a = smem_u32(smem + s * STAGE_BYTES);
+      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      tma_load_2d(a, &ma, kb + s * TBK, m0, full0 + 8 * s);
+      tma_load_2d(a + A_BYTES, &mb, kb + s * TBK, n0, full0 + 8 * s);
+    }
+    for (int k = 0; k < nk && ok; ++k) {
+      const int s = k % STAGES;
+      const uint32_t ph = (uint32_t)(k / STAGES) & 1u;
+      if (!mbar_wait(full0 + 8 * s, ph)) {
+        atomicExch(err, GEMM_ERR_FULL);
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+#pragma unroll
+      for (int kk = 0; kk < TBK / 16; ++kk)
+        umma_bf16(tmem, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), (k | kk) != 0 ? 1u : 0u);
+      umma_commit(empty0 + 8 * s);
+      if (k + STAGES < nk) {
+        // the stage is refilled once the MMAs just issued have read it
+        if (!mbar_wait(empty0 + 8 * s, ph)) {
+          atomicExch(err, GEMM_ERR_EMPTY);
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        tma_load_2d(a, &ma, kb + (k + STAGES) * TBK, m0, full0 + 8 * s);
+        tma_load_2d(b, &mb, kb + (k + STAGES) * TBK, n0, full0 + 8 * s);
+      }
+    }
+    umma_commit(done);  // arrives when every MMA issued above has completed
+  }
+  __syncthreads();
+  const bool ok = mbar_wait(done, 0);
+  if (!ok) atomicExch(err, GEMM_ERR_DONE);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  // a split with an empty K range never wrote its accumulator: its tile is zero
+  const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < TBN && ok; c0 += 16) {
+    float v[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (row < M) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j)
+        if (n0 + c0 + j < N) epi(row, n0 + c0 + j, nk ? v[j] : 0.0f, (int)blockIdx.z);
+    }
+  }
+  epi.finish();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+}
+
+// ---------------------------------------------------------------- epilogues
+
+struct EpiBase {
+  __device__ __forceinline__ void finish() {}
+};
+// hidden layer: H = bf16(relu(z + b)), stored as H (rows x hidden) and H'
+struct EpiHidden : EpiBase {
   const float *bias;
-  bf16 *out;
-  int ld;
-  __device__ void operator()(int m, int n, float v, int) const {
+  bf16 *out, *outT;
+  int ld, ldT;
+  __device__ __forceinline__ void operator()(int m, int n, float v, int) const {
     const float z = v + bias[n];
-    out[(size_t)m * ld + n] = __float2bfloat16(z > 0.0f ? z : 0.0f);
+    const bf16 h = __float2bfloat16(z > 0.0f ? z : 0.0f);
+    out[(size_t)m * ld + n] = h;
+    outT[(size_t)n * ldT + m] = h;
   }
 };
-struct EpiBiasF32 {  // output layer: Y = z + b
+// output layer for prediction: Y = z + b (standardised units)
+struct EpiOut : EpiBase {
   const float *bias;
+  float *y;
+  int ld;
+  __device__ __forceinline__ void operator()(int m, int n, float v, int) const { y[(size_t)m * ld + n] = v + bias[n]; }
+};
+// output layer for training, with the loss fused: d = z + b - (t - mu) / sigma,
+// dY = 2 d / (B N) in FP32 (for the bias gradient) and as BF16 GEMM operand
+// in both layouts; each CTA writes its partial sum of d^2 (fixed order).
+struct EpiLoss {
+  const float *bias, *t, *mu, *sigma;
+  float *dy;
+  bf16 *dyh, *dyhT;
+  double *part;
+  float scale;
+  int ldt, ldh, ldT;
+  double acc;
+  __device__ __forceinline__ void operator()(int m, int n, float v, int) {
+    const float d = v + bias[n] - (t[(size_t)m * ldt + n] - mu[n]) / sigma[n];
+    acc += (double)d * d;
+    const float g = scale * d;
+    dy[(size_t)m * ldt + n] = g;
+    const bf16 gh = __float2bfloat16(g);
+    dyh[(size_t)m * ldh + n] = gh;
+    dyhT[(size_t)n * ldT + m] = gh;
+  }
+  __device__ __forceinline__ void finish() {
+    __shared__ double red[4];
+    double s = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
+  }
+};
+// plain FP32 store (weight gradients, dH1)
+struct EpiStore : EpiBase {
   float *out;
   int ld;
-  __device__ void operator()(int m, int n, float v, int) const { out[(size_t)m * ld + n] = v + bias[n]; }
+  __device__ __forceinline__ void operator()(int m, int n, float v, int) const { out[(size_t)m * ld + n] = v; }
 };
-struct EpiStoreF32 {  // weight gradient
-  float *out;
-  int ld;
-  __device__ void operator()(int m, int n, float v, int) const { out[(size_t)m * ld + n] = v; }
-};
-struct EpiPartial {  // split-K partial sums, summed later in split order
+// split-K partial sums, summed later in split order
+struct EpiPartial : EpiBase {
   float *part;
   int ld;
   size_t stride;
-  __device__ void operator()(int m, int n, float v, int s) const { part[s * stride + (size_t)m * ld + n] = v; }
+  __device__ __forceinline__ void operator()(int m, int n, float v, int s) const {
+    part[s * stride + (size_t)m * ld + n] = v;
+  }
 };
 
-// dH (sum of split partials, in split order), masked by the ReLU of the
-// layer's output H: dZ = dH where H > 0.  Writes FP32 and BF16 copies.
-__global__ void k_splitk_relu_grad(const float *__restrict__ part, int splits, size_t count,
-                                   const bf16 *__restrict__ H, float *__restrict__ dz, bf16 *__restrict__ dzh) {
+// ---------------------------------------------------------------- elementwise kernels
+
+// dZ2 = (sum of split partials, in split order) masked by H2 > 0: FP32 rows
+// (bias gradient) and BF16 in both layouts (GEMM operands).
+__global__ void k_splitk_relu_grad(const float *__restrict__ part, int splits, int B, int H,
+                                   const bf16 *__restrict__ h, int ldh, float *__restrict__ dz,
+                                   bf16 *__restrict__ dzh, bf16 *__restrict__ dzhT, int ldT) {
+  const size_t count = (size_t)B * H;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / H), j = (int)(i % H);
     float s = 0.0f;
     for (int k = 0; k < splits; ++k) s += part[k * count + i];
-    const float g = __bfloat162float(H[i]) > 0.0f ? s : 0.0f;
+    const float g = __bfloat162float(h[(size_t)b * ldh + j]) > 0.0f ? s : 0.0f;
     dz[i] = g;
-    dzh[i] = __float2bfloat16(g);
+    const bf16 gh = __float2bfloat16(g);
+    dzh[(size_t)b * ldh + j] = gh;
+    dzhT[(size_t)j * ldT + b] = gh;
   }
 }
 
-// dH with the mask of H, from a single FP32 product (no split).
-__global__ void k_relu_grad(const float *__restrict__ dh, size_t count, const bf16 *__restrict__ H,
-                            float *__restrict__ dz, bf16 *__restrict__ dzh) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const float g = __bfloat162float(H[i]) > 0.0f ? dh[i] : 0.0f;
-    dz[i] = g;
-    dzh[i] = __float2bfloat16(g);
-  }
-}
-
-// Mini-batch gather: inputs to BF16, targets (FP32) of the sampled rows.
+// Mini-batch gather: inputs to BF16 in both layouts, targets (FP32) of the
+// sampled rows.
 __global__ void k_gather(const float *__restrict__ X, const float *__restrict__ T, const int *__restrict__ idx,
-                         int batch, int in_dim, int out_dim, bf16 *__restrict__ xb, float *__restrict__ tb) {
+                         int batch, int in_dim, int out_dim, bf16 *__restrict__ xb, int ldx, bf16 *__restrict__ xbT,
+                         int ldT, float *__restrict__ tb) {
   const int b = blockIdx.y;
   if (b >= batch) return;
   const size_t row = (size_t)idx[b];
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < out_dim; i += gridDim.x * blockDim.x)
     tb[(size_t)b * out_dim + i] = T[row * out_dim + i];
   if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < in_dim; i += blockDim.x) xb[(size_t)b * in_dim + i] = __float2bfloat16(X[row * in_dim + i]);
+    for (int i = threadIdx.x; i < in_dim; i += blockDim.x) {
+      const bf16 v = __float2bfloat16(X[row * in_dim + i]);
+      xb[(size_t)b * ldx + i] = v;
+      xbT[(size_t)i * ldT + b] = v;
+    }
 }
 
-__global__ void k_to_bf16(const float *__restrict__ x, size_t count, bf16 *__restrict__ y) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-    y[i] = __float2bfloat16(x[i]);
-}
-
-// MSE on standardised targets: d = y - (t - mu) / sigma; dY = 2 d / (B N).
-// Per-block partial sums of d^2 (summed in block order by k_loss_finish).
-__global__ void k_loss(const float *__restrict__ y, const float *__restrict__ t, const float *__restrict__ mu,
-                       const float *__restrict__ sigma, int batch, int out_dim, float *__restrict__ dy,
-                       bf16 *__restrict__ dyh, double *__restrict__ part) {
-  __shared__ double red[32];
-  const size_t count = (size_t)batch * out_dim;
-  const float scale = 2.0f / (float)count;
-  double acc = 0.0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
-    const int o = (int)(i % out_dim);
-    const float d = y[i] - (t[i] - mu[o]) / sigma[o];
-    acc += (double)d * d;
-    const float g = scale * d;
-    dy[i] = g;
-    dyh[i] = __float2bfloat16(g);
-  }
-  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (threadIdx.x == 0) part[blockIdx.x] = v;
-  }
+// prediction input: X (count x in, FP32) -> BF16 rows
+__global__ void k_input_bf16(const float *__restrict__ x, int count, int in_dim, bf16 *__restrict__ xb, int ldx) {
+  const size_t total = (size_t)count * in_dim;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    xb[(i / in_dim) * ldx + i % in_dim] = __float2bfloat16(x[i]);
 }
 
 __global__ void k_loss_finish(const double *__restrict__ part, int nparts, size_t count, float *__restrict__ out) {
@@ -216,12 +343,25 @@ __global__ void k_loss_finish(const double *__restrict__ part, int nparts, size_
   }
 }
 
-// out[n] = sum over rows of X[rows x cols] (fixed row order): bias gradients.
+// out[c] = sum over rows of X[rows x cols] (fixed row order): bias gradients.
 __global__ void k_colsum(const float *__restrict__ X, int rows, int cols, float *__restrict__ out) {
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
     float s = 0.0f;
     for (int r = 0; r < rows; ++r) s += X[(size_t)r * cols + c];
     out[c] = s;
+  }
+}
+
+// dZ1 = dH1 masked by H1 > 0: FP32 rows (bias gradient) and BF16 transposed
+// (operand of the first layer's weight gradient).
+__global__ void k_relu_grad(const float *__restrict__ dh, int B, int H, const bf16 *__restrict__ h, int ldh,
+                            float *__restrict__ dz, bf16 *__restrict__ dzhT, int ldT) {
+  const size_t count = (size_t)B * H;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / H), j = (int)(i % H);
+    const float g = __bfloat162float(h[(size_t)b * ldh + j]) > 0.0f ? dh[i] : 0.0f;
+    dz[i] = g;
+    dzhT[(size_t)j * ldT + b] = __float2bfloat16(g);
   }
 }
 
@@ -251,10 +391,10 @@ __global__ void k_unstandardize(const float *__restrict__ y, size_t count, int o
   }
 }
 
-// Adam on the FP32 master copy; refreshes the BF16 copy the GEMMs read.
+// Adam on the FP32 master copy.
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m1,
-                       float *__restrict__ m2, bf16 *__restrict__ ph, size_t count, float lr, float b1, float b2,
-                       float eps, float c1, float c2) {
+                       float *__restrict__ m2, size_t count, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
     const float gi = g[i];
     const float a = b1 * m1[i] + (1.0f - b1) * gi;
@@ -262,9 +402,30 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
     m1[i] = a;
     m2[i] = b;
     const float mh = a / c1, vh = b / c2;
-    const float v = p[i] - lr * mh / (sqrtf(vh) + eps);
-    p[i] = v;
-    ph[i] = __float2bfloat16(v);
+    p[i] = p[i] - lr * mh / (sqrtf(vh) + eps);
+  }
+}
+
+// BF16 copies of a weight matrix W (rows x cols, FP32, row-major) as W
+// (ld ldw; skipped when wb is null) and W' (cols x rows, ld ldt), through
+// 32 x 32 shared tiles so that the reads and both writes are coalesced.
+__global__ void k_weight_bf16(const float *__restrict__ w, int rows, int cols, bf16 *__restrict__ wb, int ldw,
+                              bf16 *__restrict__ wt, int ldt) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    if (r < rows && c < cols) {
+      const float v = w[(size_t)r * cols + c];
+      tile[k][tx] = v;
+      if (wb) wb[(size_t)r * ldw + c] = __float2bfloat16(v);
+    }
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;
+    if (r < rows && c < cols) wt[(size_t)c * ldt + r] = __float2bfloat16(tile[tx][k]);
   }
 }
 
@@ -272,15 +433,6 @@ int grid1(size_t n, int bs = 256) {
   size_t g = (n + bs - 1) / bs;
   if (g > 65535 * 4) g = 65535 * 4;
   return (int)(g < 1 ? 1 : g);
-}
-
-template <bool AC, bool BC, class Epi>
-cudaError_t gemm(int M, int N, int K, int splits, const bf16 *A, int lda, const bf16 *B, int ldb, Epi epi,
-                 cudaStream_t s) {
-  const int kchunk = ((K + splits - 1) / splits + BK - 1) / BK * BK;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, splits);
-  k_gemm<AC, BC, Epi><<<grid, GT, 0, s>>>(M, N, K, kchunk, A, lda, B, ldb, epi);
-  return cudaGetLastError();
 }
 
 }  // namespace mlp
@@ -291,19 +443,64 @@ cudaError_t gemm(int M, int N, int K, int splits, const bf16 *A, int lda, const 
 using namespace pdlp;
 using namespace pdlp::mlp;
 
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a BF16 matrix (rows x cols, row stride ld elements, ld a
+// multiple of 8) read in TBK x 128 boxes with the 128-byte swizzle; rows and
+// columns past the extents read as zero.
+bool make_map(CUtensorMap *m, const bf16 *base, int rows, int cols, int ld) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {TBK, 128};
+  cuuint32_t es[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int pad8(int x) { return (x + 7) / 8 * 8; }
+
+}  // namespace
+
 struct pdlp_mlp {
   int device = 0;
   int in = 0, hid = 0, out = 0, maxb = 0, splits = 1;
+  int ldi = 0, ldh = 0, ldo = 0, ldb = 0;  // padded leading dimensions (multiples of 8)
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   size_t nparam = 0, oW1 = 0, ob1 = 0, oW2 = 0, ob2 = 0, oW3 = 0, ob3 = 0;
   float *p = nullptr, *g = nullptr, *m1 = nullptr, *m2 = nullptr;
-  bf16 *ph = nullptr;
-  // activations / gradients for one mini-batch
-  bf16 *xb = nullptr, *h1 = nullptr, *h2 = nullptr, *dyh = nullptr, *dz2h = nullptr, *dz1h = nullptr;
-  float *xin = nullptr, *tb = nullptr, *y = nullptr, *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr, *dh1 = nullptr, *part = nullptr;
+  // BF16 weights: W1' (hid x in), W2 (hid x hid) and W2', W3 (hid x out) and W3' (out x hid)
+  bf16 *w1t = nullptr, *w2 = nullptr, *w2t = nullptr, *w3 = nullptr, *w3t = nullptr;
+  // one mini-batch: BF16 GEMM operands in both layouts, FP32 loss path
+  bf16 *xb = nullptr, *xbT = nullptr, *h1 = nullptr, *h1T = nullptr, *h2 = nullptr, *h2T = nullptr;
+  bf16 *dyh = nullptr, *dyhT = nullptr, *dz2h = nullptr, *dz2hT = nullptr, *dz1hT = nullptr;
+  float *xin = nullptr, *tb = nullptr, *y = nullptr, *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr, *dh1 = nullptr,
+        *part = nullptr;
   double *lpart = nullptr;
+  int lparts = 0;
   float *loss_dev = nullptr, *mu = nullptr, *sigma = nullptr;
+  int *err = nullptr;
   // data set
   float *X = nullptr, *T = nullptr;
   int samples = 0;
@@ -314,8 +511,6 @@ struct pdlp_mlp {
 };
 
 namespace {
-
-constexpr int LOSS_BLOCKS = 512;
 
 #define MCK(...)                                                                                             \
   do {                                                                                                       \
@@ -341,38 +536,77 @@ void free_mlp(pdlp_mlp *M) {
   delete M;
 }
 
-// forward of rows [0, B) of xb (BF16 inputs) -> y (FP32, standardised units)
-int forward(pdlp_mlp *M, int B) {
-  cudaStream_t s = M->stream;
-  MCK(gemm<false, false>(B, M->hid, M->in, 1, M->xb, M->in, M->ph + M->oW1, M->hid,
-                         EpiBiasReluBF16{M->p + M->ob1, M->h1, M->hid}, s));
-  MCK(gemm<false, false>(B, M->hid, M->hid, 1, M->h1, M->hid, M->ph + M->oW2, M->hid,
-                         EpiBiasReluBF16{M->p + M->ob2, M->h2, M->hid}, s));
-  MCK(gemm<false, false>(B, M->out, M->hid, 1, M->h2, M->hid, M->ph + M->oW3, M->out,
-                         EpiBiasF32{M->p + M->ob3, M->y, M->out}, s));
+// C (M x N) = A (M x K, ld lda) Bt' (Bt: N x K, ld ldb) through epi.
+template <class Epi>
+int gemm(pdlp_mlp *Mn, int M, int N, int K, int splits, const bf16 *A, int lda, const bf16 *Bt, int ldb,
+         const Epi &epi) {
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, Bt, N, K, ldb))
+    return set_error(PDLP_ERR_CUDA, "MLP GEMM: cuTensorMapEncodeTiled unavailable or rejected the operand");
+  const int kchunk = ((K + splits - 1) / splits + TBK - 1) / TBK * TBK;
+  dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, splits);
+  k_tc_gemm<Epi><<<grid, 128, GEMM_SMEM, Mn->stream>>>(ma, mb, M, N, K, kchunk, epi, Mn->err);
+  MCK(cudaGetLastError());
   return PDLP_OK;
 }
 
-// loss + gradients of every parameter into M->g for the batch in xb / tb
-int backward(pdlp_mlp *M, int B) {
+template <class Epi>
+cudaError_t allow_smem() {
+  return cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, GEMM_SMEM);
+}
+
+// BF16 copies of the weights from the FP32 masters.
+int refresh_weights(pdlp_mlp *M) {
   cudaStream_t s = M->stream;
-  const size_t BO = (size_t)B * M->out, BH = (size_t)B * M->hid;
-  k_loss<<<LOSS_BLOCKS, 256, 0, s>>>(M->y, M->tb, M->mu, M->sigma, B, M->out, M->dy, M->dyh, M->lpart);
+  auto grid2 = [](int rows, int cols) { return dim3((cols + 31) / 32, (rows + 31) / 32); };
+  k_weight_bf16<<<grid2(M->in, M->hid), 256, 0, s>>>(M->p + M->oW1, M->in, M->hid, nullptr, 0, M->w1t, M->ldi);
+  k_weight_bf16<<<grid2(M->hid, M->hid), 256, 0, s>>>(M->p + M->oW2, M->hid, M->hid, M->w2, M->ldh, M->w2t, M->ldh);
+  k_weight_bf16<<<grid2(M->hid, M->out), 256, 0, s>>>(M->p + M->oW3, M->hid, M->out, M->w3, M->ldo, M->w3t, M->ldh);
   MCK(cudaGetLastError());
-  k_loss_finish<<<1, 32, 0, s>>>(M->lpart, LOSS_BLOCKS, BO, M->loss_dev);
-  // output layer
-  MCK(gemm<true, false>(M->hid, M->out, B, 1, M->h2, M->hid, M->dyh, M->out, EpiStoreF32{M->g + M->oW3, M->out}, s));
+  return PDLP_OK;
+}
+
+// hidden layers for rows [0, B) of xb
+int forward_hidden(pdlp_mlp *M, int B) {
+  int rc = gemm(M, B, M->hid, M->in, 1, M->xb, M->ldi, M->w1t, M->ldi,
+                EpiHidden{{}, M->p + M->ob1, M->h1, M->h1T, M->ldh, M->ldb});
+  if (!rc)
+    rc = gemm(M, B, M->hid, M->hid, 1, M->h1, M->ldh, M->w2t, M->ldh,
+              EpiHidden{{}, M->p + M->ob2, M->h2, M->h2T, M->ldh, M->ldb});
+  return rc;
+}
+
+// loss (fused into the output layer) and every gradient into M->g for the
+// batch in xb / tb
+int forward_backward(pdlp_mlp *M, int B) {
+  cudaStream_t s = M->stream;
+  int rc = forward_hidden(M, B);
+  if (rc) return rc;
+  const size_t BO = (size_t)B * M->out, BH = (size_t)B * M->hid;
+  const int tiles = ((M->out + TBN - 1) / TBN) * ((B + TBM - 1) / TBM);
+  EpiLoss el{M->p + M->ob3, M->tb, M->mu, M->sigma, M->dy, M->dyh, M->dyhT, M->lpart, 2.0f / (float)BO,
+             M->out, M->ldo, M->ldb, 0.0};
+  rc = gemm(M, B, M->out, M->hid, 1, M->h2, M->ldh, M->w3t, M->ldh, el);
+  if (rc) return rc;
+  k_loss_finish<<<1, 32, 0, s>>>(M->lpart, tiles, BO, M->loss_dev);
+  // output layer: gW3 = H2' dY, gb3 = column sums of dY, dH2 = dY W3'
+  rc = gemm(M, M->hid, M->out, B, 1, M->h2T, M->ldb, M->dyhT, M->ldb, EpiStore{{}, M->g + M->oW3, M->out});
+  if (rc) return rc;
   k_colsum<<<grid1(M->out), 256, 0, s>>>(M->dy, B, M->out, M->g + M->ob3);
-  MCK(gemm<false, true>(B, M->hid, M->out, M->splits, M->dyh, M->out, M->ph + M->oW3, M->out,
-                        EpiPartial{M->part, M->hid, BH}, s));
-  k_splitk_relu_grad<<<grid1(BH), 256, 0, s>>>(M->part, M->splits, BH, M->h2, M->dz2, M->dz2h);
+  rc = gemm(M, B, M->hid, M->out, M->splits, M->dyh, M->ldo, M->w3, M->ldo, EpiPartial{{}, M->part, M->hid, BH});
+  if (rc) return rc;
+  k_splitk_relu_grad<<<grid1(BH), 256, 0, s>>>(M->part, M->splits, B, M->hid, M->h2, M->ldh, M->dz2, M->dz2h,
+                                               M->dz2hT, M->ldb);
   // second layer
-  MCK(gemm<true, false>(M->hid, M->hid, B, 1, M->h1, M->hid, M->dz2h, M->hid, EpiStoreF32{M->g + M->oW2, M->hid}, s));
+  rc = gemm(M, M->hid, M->hid, B, 1, M->h1T, M->ldb, M->dz2hT, M->ldb, EpiStore{{}, M->g + M->oW2, M->hid});
+  if (rc) return rc;
   k_colsum<<<grid1(M->hid), 256, 0, s>>>(M->dz2, B, M->hid, M->g + M->ob2);
-  MCK(gemm<false, true>(B, M->hid, M->hid, 1, M->dz2h, M->hid, M->ph + M->oW2, M->hid, EpiStoreF32{M->dh1, M->hid}, s));
-  k_relu_grad<<<grid1(BH), 256, 0, s>>>(M->dh1, BH, M->h1, M->dz1, M->dz1h);
+  rc = gemm(M, B, M->hid, M->hid, 1, M->dz2h, M->ldh, M->w2, M->ldh, EpiStore{{}, M->dh1, M->hid});
+  if (rc) return rc;
+  k_relu_grad<<<grid1(BH), 256, 0, s>>>(M->dh1, B, M->hid, M->h1, M->ldh, M->dz1, M->dz1hT, M->ldb);
   // first layer
-  MCK(gemm<true, false>(M->in, M->hid, B, 1, M->xb, M->in, M->dz1h, M->hid, EpiStoreF32{M->g + M->oW1, M->hid}, s));
+  rc = gemm(M, M->in, M->hid, B, 1, M->xbT, M->ldb, M->dz1hT, M->ldb, EpiStore{{}, M->g + M->oW1, M->hid});
+  if (rc) return rc;
   k_colsum<<<grid1(M->hid), 256, 0, s>>>(M->dz1, B, M->hid, M->g + M->ob1);
   MCK(cudaGetLastError());
   return PDLP_OK;
@@ -388,6 +622,18 @@ int ensure_idx(pdlp_mlp *M, size_t count) {
   return PDLP_OK;
 }
 
+// after a synchronisation: a GEMM whose wait timed out fails the call
+int check_err(pdlp_mlp *M) {
+  int e = 0;
+  MCK(cudaMemcpy(&e, M->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    cudaMemset(M->err, 0, sizeof(int));
+    return set_error(PDLP_ERR_CUDA,
+                     ("MLP GEMM: a tensor-core pipeline wait timed out (stage " + std::to_string(e) + ")").c_str());
+  }
+  return PDLP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -397,14 +643,16 @@ int pdlp_mlp_create(pdlp_mlp **out, int32_t in_dim, int32_t hidden, int32_t out_
     return set_error(PDLP_ERR_INVALID, "pdlp_mlp_create: dimensions and max_batch must be >= 1");
   if (max_batch > 65535 || (int64_t)in_dim * hidden > INT32_MAX || (int64_t)hidden * out_dim > INT32_MAX)
     return set_error(PDLP_ERR_INVALID, "pdlp_mlp_create: max_batch above 65535 or a weight matrix above 2^31 entries");
+  *out = nullptr;
   pdlp_mlp *M = new pdlp_mlp();
   M->in = in_dim;
   M->hid = hidden;
   M->out = out_dim;
   M->maxb = max_batch;
-  // split the long reduction (over the outputs) of dH2 = dY W3' so the GEMM
-  // has enough CTAs: about 4 splits per 2048 outputs, at most 64
-  M->splits = std::max(1, std::min(64, out_dim / 512));
+  M->ldi = pad8(in_dim);
+  M->ldh = pad8(hidden);
+  M->ldo = pad8(out_dim);
+  M->ldb = pad8(max_batch);
   size_t o = 0;
   M->oW1 = o; o += (size_t)in_dim * hidden;
   M->ob1 = o; o += hidden;
@@ -414,6 +662,8 @@ int pdlp_mlp_create(pdlp_mlp **out, int32_t in_dim, int32_t hidden, int32_t out_
   M->ob3 = o; o += out_dim;
   M->nparam = o;
   cudaError_t e = cudaGetDevice(&M->device);
+  int sms = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, M->device);
   if (e == cudaSuccess) {
     if (stream) {
       M->stream = (cudaStream_t)stream;
@@ -422,23 +672,52 @@ int pdlp_mlp_create(pdlp_mlp **out, int32_t in_dim, int32_t hidden, int32_t out_
       M->own_stream = true;
     }
   }
+  if (e == cudaSuccess) e = allow_smem<EpiHidden>();
+  if (e == cudaSuccess) e = allow_smem<EpiOut>();
+  if (e == cudaSuccess) e = allow_smem<EpiLoss>();
+  if (e == cudaSuccess) e = allow_smem<EpiStore>();
+  if (e == cudaSuccess) e = allow_smem<EpiPartial>();
   if (e != cudaSuccess) {
     free_mlp(M);
     return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
   }
+  if (!encode_fn()) {
+    free_mlp(M);
+    return set_error(PDLP_ERR_CUDA, "pdlp_mlp_create: the driver offers no cuTensorMapEncodeTiled");
+  }
+  // split the long reduction of dH2 = dY W3' over the outputs so that the
+  // batch x hidden output tiles fill the SMs: about one CTA per SM, at least
+  // four 64-wide K blocks per split
+  {
+    const int tiles = ((hidden + TBN - 1) / TBN) * ((max_batch + TBM - 1) / TBM);
+    const int by_sm = std::max(1, sms / std::max(1, tiles));
+    const int by_k = std::max(1, out_dim / (4 * TBK));
+    M->splits = std::max(1, std::min(std::min(by_sm, by_k), 64));
+  }
   const size_t B = max_batch, BH = B * hidden, BO = B * out_dim;
+  const size_t LB = M->ldb;
+  M->lparts = ((out_dim + TBN - 1) / TBN) * ((max_batch + TBM - 1) / TBM);
   int rc = 0;
   rc = rc ? rc : dalloc(M, &M->p, M->nparam);
   rc = rc ? rc : dalloc(M, &M->g, M->nparam);
   rc = rc ? rc : dalloc(M, &M->m1, M->nparam);
   rc = rc ? rc : dalloc(M, &M->m2, M->nparam);
-  rc = rc ? rc : dalloc(M, &M->ph, M->nparam);
-  rc = rc ? rc : dalloc(M, &M->xb, B * in_dim);
-  rc = rc ? rc : dalloc(M, &M->h1, BH);
-  rc = rc ? rc : dalloc(M, &M->h2, BH);
-  rc = rc ? rc : dalloc(M, &M->dyh, BO);
-  rc = rc ? rc : dalloc(M, &M->dz2h, BH);
-  rc = rc ? rc : dalloc(M, &M->dz1h, BH);
+  rc = rc ? rc : dalloc(M, &M->w1t, (size_t)hidden * M->ldi);
+  rc = rc ? rc : dalloc(M, &M->w2, (size_t)hidden * M->ldh);
+  rc = rc ? rc : dalloc(M, &M->w2t, (size_t)hidden * M->ldh);
+  rc = rc ? rc : dalloc(M, &M->w3, (size_t)hidden * M->ldo);
+  rc = rc ? rc : dalloc(M, &M->w3t, (size_t)out_dim * M->ldh);
+  rc = rc ? rc : dalloc(M, &M->xb, B * M->ldi);
+  rc = rc ? rc : dalloc(M, &M->xbT, (size_t)in_dim * LB);
+  rc = rc ? rc : dalloc(M, &M->h1, B * M->ldh);
+  rc = rc ? rc : dalloc(M, &M->h1T, (size_t)hidden * LB);
+  rc = rc ? rc : dalloc(M, &M->h2, B * M->ldh);
+  rc = rc ? rc : dalloc(M, &M->h2T, (size_t)hidden * LB);
+  rc = rc ? rc : dalloc(M, &M->dyh, B * M->ldo);
+  rc = rc ? rc : dalloc(M, &M->dyhT, (size_t)out_dim * LB);
+  rc = rc ? rc : dalloc(M, &M->dz2h, B * M->ldh);
+  rc = rc ? rc : dalloc(M, &M->dz2hT, (size_t)hidden * LB);
+  rc = rc ? rc : dalloc(M, &M->dz1hT, (size_t)hidden * LB);
   rc = rc ? rc : dalloc(M, &M->xin, B * in_dim);
   rc = rc ? rc : dalloc(M, &M->tb, BO);
   rc = rc ? rc : dalloc(M, &M->y, BO);
@@ -447,10 +726,11 @@ int pdlp_mlp_create(pdlp_mlp **out, int32_t in_dim, int32_t hidden, int32_t out_
   rc = rc ? rc : dalloc(M, &M->dz1, BH);
   rc = rc ? rc : dalloc(M, &M->dh1, BH);
   rc = rc ? rc : dalloc(M, &M->part, BH * M->splits);
-  rc = rc ? rc : dalloc(M, &M->lpart, LOSS_BLOCKS);
+  rc = rc ? rc : dalloc(M, &M->lpart, (size_t)M->lparts);
   rc = rc ? rc : dalloc(M, &M->loss_dev, 1);
   rc = rc ? rc : dalloc(M, &M->mu, out_dim);
   rc = rc ? rc : dalloc(M, &M->sigma, out_dim);
+  rc = rc ? rc : dalloc(M, &M->err, 1);
   if (rc) {
     free_mlp(M);
     return rc;
@@ -458,15 +738,16 @@ int pdlp_mlp_create(pdlp_mlp **out, int32_t in_dim, int32_t hidden, int32_t out_
   cudaMemsetAsync(M->m1, 0, sizeof(float) * M->nparam, M->stream);
   cudaMemsetAsync(M->m2, 0, sizeof(float) * M->nparam, M->stream);
   cudaMemsetAsync(M->p, 0, sizeof(float) * M->nparam, M->stream);
-  cudaMemsetAsync(M->ph, 0, sizeof(bf16) * M->nparam, M->stream);
+  cudaMemsetAsync(M->err, 0, sizeof(int), M->stream);
   // identity standardisation until data is set
   std::vector<float> zeros(out_dim, 0.0f), ones(out_dim, 1.0f);
   cudaMemcpyAsync(M->mu, zeros.data(), sizeof(float) * out_dim, cudaMemcpyHostToDevice, M->stream);
   cudaMemcpyAsync(M->sigma, ones.data(), sizeof(float) * out_dim, cudaMemcpyHostToDevice, M->stream);
+  rc = refresh_weights(M);
   e = cudaStreamSynchronize(M->stream);
-  if (e != cudaSuccess) {
+  if (rc || e != cudaSuccess) {
     free_mlp(M);
-    return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
+    return rc ? rc : set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
   }
   *out = M;
   return PDLP_OK;
@@ -478,10 +759,11 @@ int pdlp_mlp_set_params(pdlp_mlp *M, const float *params) {
   if (!M || !params) return set_error(PDLP_ERR_INVALID, "pdlp_mlp_set_params: null argument");
   MCK(cudaSetDevice(M->device));
   MCK(cudaMemcpyAsync(M->p, params, sizeof(float) * M->nparam, cudaMemcpyHostToDevice, M->stream));
-  k_to_bf16<<<grid1(M->nparam), 256, 0, M->stream>>>(M->p, M->nparam, M->ph);
   MCK(cudaMemsetAsync(M->m1, 0, sizeof(float) * M->nparam, M->stream));
   MCK(cudaMemsetAsync(M->m2, 0, sizeof(float) * M->nparam, M->stream));
   M->adam_t = 0;
+  int rc = refresh_weights(M);
+  if (rc) return rc;
   MCK(cudaStreamSynchronize(M->stream));
   return PDLP_OK;
 }
@@ -527,23 +809,25 @@ int pdlp_mlp_train(pdlp_mlp *M, int32_t steps, int32_t batch, const int32_t *idx
   MCK(cudaMemcpyAsync(M->idx, idx, sizeof(int) * (size_t)steps * batch, cudaMemcpyHostToDevice, s));
   for (int st = 0; st < steps; ++st) {
     dim3 gg((M->out + 255) / 256 < 64 ? (M->out + 255) / 256 : 64, batch);
-    k_gather<<<gg, 256, 0, s>>>(M->X, M->T, M->idx + (size_t)st * batch, batch, M->in, M->out, M->xb, M->tb);
+    k_gather<<<gg, 256, 0, s>>>(M->X, M->T, M->idx + (size_t)st * batch, batch, M->in, M->out, M->xb, M->ldi, M->xbT,
+                                M->ldb, M->tb);
     MCK(cudaGetLastError());
-    rc = forward(M, batch);
-    if (!rc) rc = backward(M, batch);
+    rc = forward_backward(M, batch);
     if (rc) return rc;
     MCK(cudaMemcpyAsync(dloss + st, M->loss_dev, sizeof(float), cudaMemcpyDeviceToDevice, s));
     ++M->adam_t;
     const float c1 = 1.0f - powf(beta1, (float)M->adam_t), c2 = 1.0f - powf(beta2, (float)M->adam_t);
-    k_adam<<<grid1(M->nparam), 256, 0, s>>>(M->p, M->g, M->m1, M->m2, M->ph, M->nparam, lr, beta1, beta2, eps, c1, c2);
+    k_adam<<<grid1(M->nparam), 256, 0, s>>>(M->p, M->g, M->m1, M->m2, M->nparam, lr, beta1, beta2, eps, c1, c2);
     MCK(cudaGetLastError());
+    rc = refresh_weights(M);
+    if (rc) return rc;
   }
   if (losses) MCK(cudaMemcpyAsync(losses, dloss, sizeof(float) * steps, cudaMemcpyDeviceToHost, s));
   MCK(cudaStreamSynchronize(s));
   // free the per-call loss buffer
   cudaFree(dloss);
   M->allocs.pop_back();
-  return PDLP_OK;
+  return check_err(M);
 }
 
 int pdlp_mlp_predict(pdlp_mlp *M, int32_t count, const float *X, float *Y) {
@@ -553,15 +837,19 @@ int pdlp_mlp_predict(pdlp_mlp *M, int32_t count, const float *X, float *Y) {
   for (int b0 = 0; b0 < count; b0 += M->maxb) {
     const int B = std::min(M->maxb, count - b0);
     MCK(cudaMemcpyAsync(M->xin, X + (size_t)b0 * M->in, sizeof(float) * (size_t)B * M->in, cudaMemcpyHostToDevice, s));
-    k_to_bf16<<<grid1((size_t)B * M->in), 256, 0, s>>>(M->xin, (size_t)B * M->in, M->xb);
-    int rc = forward(M, B);
+    k_input_bf16<<<grid1((size_t)B * M->in), 256, 0, s>>>(M->xin, B, M->in, M->xb, M->ldi);
+    int rc = forward_hidden(M, B);
+    if (!rc)
+      rc = gemm(M, B, M->out, M->hid, 1, M->h2, M->ldh, M->w3t, M->ldh, EpiOut{{}, M->p + M->ob3, M->y, M->out});
     if (rc) return rc;
-    k_unstandardize<<<grid1((size_t)B * M->out), 256, 0, s>>>(M->y, (size_t)B * M->out, M->out, M->mu, M->sigma, M->dy);
+    k_unstandardize<<<grid1((size_t)B * M->out), 256, 0, s>>>(M->y, (size_t)B * M->out, M->out, M->mu, M->sigma,
+                                                               M->dy);
     MCK(cudaGetLastError());
-    MCK(cudaMemcpyAsync(Y + (size_t)b0 * M->out, M->dy, sizeof(float) * (size_t)B * M->out, cudaMemcpyDeviceToHost, s));
+    MCK(cudaMemcpyAsync(Y + (size_t)b0 * M->out, M->dy, sizeof(float) * (size_t)B * M->out, cudaMemcpyDeviceToHost,
+                        s));
   }
   MCK(cudaStreamSynchronize(s));
-  return PDLP_OK;
+  return check_err(M);
 }
 
 int pdlp_mlp_gradients(pdlp_mlp *M, int32_t batch, const int32_t *idx, float *loss, float *grads) {
@@ -575,14 +863,13 @@ int pdlp_mlp_gradients(pdlp_mlp *M, int32_t batch, const int32_t *idx, float *lo
   cudaStream_t s = M->stream;
   MCK(cudaMemcpyAsync(M->idx, idx, sizeof(int) * batch, cudaMemcpyHostToDevice, s));
   dim3 gg((M->out + 255) / 256 < 64 ? (M->out + 255) / 256 : 64, batch);
-  k_gather<<<gg, 256, 0, s>>>(M->X, M->T, M->idx, batch, M->in, M->out, M->xb, M->tb);
-  rc = forward(M, batch);
-  if (!rc) rc = backward(M, batch);
+  k_gather<<<gg, 256, 0, s>>>(M->X, M->T, M->idx, batch, M->in, M->out, M->xb, M->ldi, M->xbT, M->ldb, M->tb);
+  rc = forward_backward(M, batch);
   if (rc) return rc;
   if (loss) MCK(cudaMemcpyAsync(loss, M->loss_dev, sizeof(float), cudaMemcpyDeviceToHost, s));
   if (grads) MCK(cudaMemcpyAsync(grads, M->g, sizeof(float) * M->nparam, cudaMemcpyDeviceToHost, s));
   MCK(cudaStreamSynchronize(s));
-  return PDLP_OK;
+  return check_err(M);
 }
 
 int pdlp_mlp_stats(const pdlp_mlp *M, float *mu, float *sigma) {
