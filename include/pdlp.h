@@ -218,12 +218,16 @@ typedef struct {
   double entries_per_lane; /* autotuned SpMV schedule: lanes per row = smallest power of two g <= 32
                               with (mean row length) / g <= entries_per_lane */
   size_t device_bytes;
+  int32_t resident;        /* LPs small enough to be solved from the CTA's shared memory */
+  int32_t resident_max_bytes; /* shared-memory budget per CTA for such an LP */
 } pdlp_batch_stats;
 
 /* Validates every LP (same rules as pdlp_create; errors name the LP), copies
  * the batch to the GPU, builds each K', scales every LP on the device and
  * autotunes the SpMV schedule by timing short solves of the whole batch with
- * a few candidate schedules.  params: NULL = defaults; value_bits must be 64.
+ * a few candidate schedules.  Each LP is solved by one CTA; an LP whose K,
+ * K' and vectors fit in the CTA's shared-memory budget is copied there and
+ * solved from shared memory.  params: NULL = defaults; value_bits must be 64.
  * stream: cudaStream_t as void* (NULL = own stream). */
 int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const pdlp_params *params,
                       void *stream);

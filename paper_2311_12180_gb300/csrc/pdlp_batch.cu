@@ -34,7 +34,14 @@ namespace pdlp {
 namespace batch {
 
 constexpr int NTB = 512;
+// dynamic shared memory of k_batch_solve: an LP with resident_bytes() up to
+// this is solved from shared memory (one CTA per SM either way: the kernel
+// runs 512 threads at > 64 registers)
+constexpr int RESIDENT_MAX = 200 * 1024;
 constexpr int NWB = NTB / 32;
+// shared reduction buffer: NV partials per warp, NV results, 4 broadcast slots
+constexpr int RED_BCAST = 16 * NWB + 16;
+constexpr int RED_SIZE = RED_BCAST + 4;
 
 // per-instance vector blocks
 enum { VM_Q = 0, VM_D1, VM_Y0, VM_Y1, VM_SY0, VM_SY1, VM_KX0, VM_KX1, VM_KXB, VM_YL, VM_YOUT, VM_Q0, VM_COUNT };
@@ -170,7 +177,7 @@ __device__ __forceinline__ bool sec41_pass(double pobj, double dobj, double rp, 
 
 __global__ void __launch_bounds__(NTB) k_batch_scale(Arrays A, Inst *inst, int count, int ruiz_iters,
                                                      double pc_alpha, double eps_zero) {
-  __shared__ double red[17 * NWB + 16];
+  __shared__ double red[RED_SIZE];
   const int id = blockIdx.x;
   if (id >= count) return;
   Inst I = inst[id];
@@ -406,12 +413,25 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     double s3[3] = {pr.dx2, dr.dy2, dr.cross};
     allsum<3>(s3, red);
     // ---- step-size test (eq. step-size with |interaction|; exponent base k + 2) ----
-    const double ia = fabs(s3[2]);
-    const double eta_bar = ia > 0.0 ? (omega * s3[0] + s3[1] / omega) / (2.0 * ia) : CUDART_INF;
-    const double kk = (double)(k + 2);
-    const double e1 = (1.0 - pow(kk, -0.3)) * eta_bar, e2 = (1.0 + pow(kk, -0.6)) * eta;
-    const double eta_next = e1 < e2 ? e1 : e2;
-    if (!isfinite(s3[0]) || !isfinite(s3[1]) || !isfinite(s3[2]) || isnan(eta_bar) || !(eta_next > 0.0)) {
+    // one thread evaluates it and broadcasts: the two FP64 powers, run by
+    // every warp, would cost more than the whole iteration of a small LP on
+    // GB300's narrow FP64 pipe
+    if (tid == 0) {
+      const double ia = fabs(s3[2]);
+      const double eb = ia > 0.0 ? (omega * s3[0] + s3[1] / omega) / (2.0 * ia) : CUDART_INF;
+      const double kk = (double)(k + 2);
+      const double e1 = (1.0 - pow(kk, -0.3)) * eb, e2 = (1.0 + pow(kk, -0.6)) * eta;
+      const double en = e1 < e2 ? e1 : e2;
+      red[RED_BCAST] = eb;
+      red[RED_BCAST + 1] = en;
+      red[RED_BCAST + 2] =
+          (!isfinite(s3[0]) || !isfinite(s3[1]) || !isfinite(s3[2]) || isnan(eb) || !(en > 0.0)) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const double eta_bar = red[RED_BCAST], eta_next = red[RED_BCAST + 1];
+    const bool numerical = red[RED_BCAST + 2] != 0.0;
+    // (the slots are rewritten only after the next iteration's barriers)
+    if (numerical) {
       status = ST_NUMERICAL;
       break;
     }
@@ -530,11 +550,36 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
   __syncthreads();
 }
 
+// Shared-memory bytes an LP needs to run resident (K, K', and every m- and
+// n-vector block; each array 16-byte aligned).
+__host__ __device__ inline long long resident_bytes(int m, int n, long long nnz) {
+  auto a16 = [](long long b) { return (b + 15) & ~15LL; };
+  return a16(4LL * (m + 1)) + a16(4LL * (n + 1)) + 2 * a16(4 * nnz) + 2 * a16(8 * nnz) +
+         a16(8LL * VM_COUNT * m) + a16(8LL * VN_COUNT * n);
+}
+
+template <typename T>
+__device__ __forceinline__ T *carve(unsigned char *&p, long long count) {
+  T *r = reinterpret_cast<T *>(p);
+  p += (sizeof(T) * count + 15) & ~15LL;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ void copy_in(T *dst, const T *src, long long count) {
+  for (long long i = threadIdx.x; i < count; i += NTB) dst[i] = src[i];
+}
+
+// One CTA per LP, LPs taken from the queue.  An LP whose data fits in
+// `resident_max` bytes of the CTA's dynamic shared memory is copied there
+// (scaled K, K' and vectors; read-only data is never copied back, the outputs
+// go straight to global memory) and solved from shared memory: the small
+// LPs, which need the most iterations, then run at shared-memory latency.
 __global__ void __launch_bounds__(NTB) k_batch_solve(Arrays A, const Inst *__restrict__ inst,
                                                      const int *__restrict__ order, int count, int *queue,
-                                                     Params p) {
-  __shared__ double red[17 * NWB + 16];
+                                                     Params p, long long resident_max) {
+  __shared__ double red[RED_SIZE];
   __shared__ int s_id;
+  extern __shared__ __align__(16) unsigned char bsm[];
   for (;;) {
     if (threadIdx.x == 0) s_id = atomicAdd(queue, 1);
     __syncthreads();
@@ -543,7 +588,39 @@ __global__ void __launch_bounds__(NTB) k_batch_solve(Arrays A, const Inst *__res
     if (q >= count) return;
     const int id = order[q];
     const Inst I = inst[id];
-    solve_instance(A, I, p, id, red);
+    const long long nnz = A.kptr[I.kp + I.m] - A.kptr[I.kp];
+    if (resident_bytes(I.m, I.n, nnz) <= resident_max) {
+      unsigned char *cur = bsm;
+      Arrays R = A;
+      Inst J = I;
+      int *kptr = carve<int>(cur, I.m + 1), *tptr = carve<int>(cur, I.n + 1);
+      int *kidx = carve<int>(cur, nnz), *tidx = carve<int>(cur, nnz);
+      double *kval = carve<double>(cur, nnz), *tval = carve<double>(cur, nnz);
+      double *vm = carve<double>(cur, (long long)VM_COUNT * I.m), *vn = carve<double>(cur, (long long)VN_COUNT * I.n);
+      // row pointers relative to the LP's first nonzero
+      const int k0 = A.kptr[I.kp], t0 = A.tptr[I.tp];
+      for (int i = threadIdx.x; i <= I.m; i += NTB) kptr[i] = A.kptr[I.kp + i] - k0;
+      for (int j = threadIdx.x; j <= I.n; j += NTB) tptr[j] = A.tptr[I.tp + j] - t0;
+      copy_in(kidx, A.kidx + I.ke + k0, nnz);
+      copy_in(tidx, A.tidx + I.te + t0, nnz);
+      copy_in(kval, A.kval + I.ke + k0, nnz);
+      copy_in(tval, A.tval + I.te + t0, nnz);
+      copy_in(vm, A.vm + I.om, (long long)VM_COUNT * I.m);
+      copy_in(vn, A.vn + I.on, (long long)VN_COUNT * I.n);
+      __syncthreads();
+      R.kptr = kptr;
+      R.tptr = tptr;
+      R.kidx = kidx;
+      R.tidx = tidx;
+      R.kval = kval;
+      R.tval = tval;
+      R.vm = vm;
+      R.vn = vn;
+      J.kp = J.ke = J.tp = J.te = J.om = J.on = 0;
+      solve_instance(R, J, p, id, red);
+    } else {
+      solve_instance(A, I, p, id, red);
+    }
   }
 }
 
@@ -574,6 +651,7 @@ struct pdlp_batch {
   const double *g_x0 = nullptr, *g_y0 = nullptr;
   double solve_ms = 0.0, setup_ms = 0.0, tune_ms = 0.0;
   double lanes_target = 4.0;
+  int resident = 0;  // LPs that fit the shared-memory budget
 };
 
 namespace {
@@ -607,7 +685,8 @@ void free_batch(pdlp_batch *b) {
 
 int launch_solve(pdlp_batch *b, const Arrays &A, const Params &p, cudaStream_t s) {
   BCK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), s));
-  k_batch_solve<<<b->grid, NTB, 0, s>>>(A, b->d_inst, b->d_order, b->count, b->d_queue, p);
+  k_batch_solve<<<b->grid, NTB, RESIDENT_MAX, s>>>(A, b->d_inst, b->d_order, b->count, b->d_queue, p,
+                                                  (long long)RESIDENT_MAX);
   BCK(cudaGetLastError());
   return PDLP_OK;
 }
@@ -677,6 +756,7 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
     I.yo = YO;
     KP += L.m + 1;
     TP += L.n + 1;
+    if (resident_bytes(L.m, L.n, nnz) <= RESIDENT_MAX) ++b->resident;
     KE += nnz;
     TE += nnz;
     OM += (long long)VM_COUNT * L.m;
@@ -705,7 +785,8 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
   int per_sm = 1;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve, NTB, 0);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_batch_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, RESIDENT_MAX);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve, NTB, RESIDENT_MAX);
   if (e != cudaSuccess) {
     free_batch(b);
     return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
@@ -950,6 +1031,8 @@ int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *s) {
   s->solve_ms = b->solve_ms;
   s->entries_per_lane = b->lanes_target;
   s->device_bytes = b->arena_bytes;
+  s->resident = b->resident;
+  s->resident_max_bytes = RESIDENT_MAX;
   return PDLP_OK;
 }
 

@@ -121,6 +121,8 @@ class pdlp_batch_stats(C.Structure):
         ("solve_ms", C.c_double),
         ("entries_per_lane", C.c_double),
         ("device_bytes", C.c_size_t),
+        ("resident", C.c_int32),
+        ("resident_max_bytes", C.c_int32),
     ]
 
 _lib = None

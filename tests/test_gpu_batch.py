@@ -28,6 +28,8 @@ def batch():
 def test_batch_solutions_match_oracle(batch):
     with P.BatchSolver(batch) as b:
         xs, ys, st, it = b.solve(tol=1e-6)
+        # both schedules run: LPs solved from shared memory and from global memory
+        assert 0 < b.stats()["resident"] < len(batch)
         stats = b.stats()
         lk, lt = b.lanes()
     assert stats["count"] == len(batch) and stats["entries_per_lane"] in (2.0, 4.0, 8.0, 16.0)
