@@ -220,6 +220,8 @@ typedef struct {
   size_t device_bytes;
   int32_t resident;        /* LPs small enough to be solved from the CTA's shared memory */
   int32_t resident_max_bytes; /* shared-memory budget per CTA for such an LP */
+  int32_t team_lps;        /* LPs large enough to be solved by a team of CTAs */
+  int32_t team_size;       /* CTAs (SMs) per team */
 } pdlp_batch_stats;
 
 /* Validates every LP (same rules as pdlp_create; errors name the LP), copies
@@ -227,7 +229,10 @@ typedef struct {
  * autotunes the SpMV schedule by timing short solves of the whole batch with
  * a few candidate schedules.  Each LP is solved by one CTA; an LP whose K,
  * K' and vectors fit in the CTA's shared-memory budget is copied there and
- * solved from shared memory.  params: NULL = defaults; value_bits must be 64.
+ * solved from shared memory; an LP with at least 32768 nonzeros is solved by
+ * a team of CTAs on as many SMs, which meet at bounded global-memory
+ * barriers (the batch's CTAs must all be resident: a barrier that waits more
+ * than 2 s fails the solve with PDLP_ERR_CUDA).  params: NULL = defaults; value_bits must be 64.
  * stream: cudaStream_t as void* (NULL = own stream). */
 int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const pdlp_params *params,
                       void *stream);
@@ -240,6 +245,10 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
 int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double tol, int64_t max_iter,
                      double *x_out, double *y_out, int32_t *status, int64_t *iters);
 int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *stats);
+/* When each LP of the last pdlp_batch_solve started and finished (device
+ * global timer), in seconds after the earliest start (count entries each;
+ * NULL ok): the schedule behind the batch's makespan. */
+int pdlp_batch_times(const pdlp_batch *b, double *start_s, double *end_s);
 /* Lanes per row chosen for each LP's K and K' (count entries each; NULL ok). */
 int pdlp_batch_lanes(const pdlp_batch *b, int32_t *lanes_K, int32_t *lanes_KT);
 void pdlp_batch_destroy(pdlp_batch *b);

@@ -41,7 +41,8 @@ constexpr int RESIDENT_MAX = 200 * 1024;
 constexpr int NWB = NTB / 32;
 // shared reduction buffer: NV partials per warp, NV results, 4 broadcast slots
 constexpr int RED_BCAST = 16 * NWB + 16;
-constexpr int RED_SIZE = RED_BCAST + 4;
+constexpr int RED_TEAM = RED_BCAST + 8;  // 16 slots: team-reduction results
+constexpr int RED_SIZE = RED_TEAM + 16;
 
 // per-instance vector blocks
 enum { VM_Q = 0, VM_D1, VM_Y0, VM_Y1, VM_SY0, VM_SY1, VM_KX0, VM_KX1, VM_KXB, VM_YL, VM_YOUT, VM_Q0, VM_COUNT };
@@ -61,7 +62,22 @@ struct Params {
   double tol, theta, eps_zero, beta_suff, beta_nec, beta_art;
   long long max_iter;
   int P, warm;
+  // (k + 2)^-0.3 at pw[k] and (k + 2)^-0.6 at pw[npw + k] for k < npw
+  const double *pw;
+  long long npw;
 };
+
+// The Algorithm 2 exponent factors for every step index, computed once per
+// solve by the same pow() the step test would call: each LP then reads two
+// cached values per step instead of evaluating two FP64 powers, whose serial
+// latency on GB300's narrow FP64 pipe is a large part of a small LP's step.
+__global__ void k_pow_table(double *pw, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const double kk = (double)(i + 2);
+    pw[i] = pow(kk, -0.3);
+    pw[count + i] = pow(kk, -0.6);
+  }
+}
 
 struct Arrays {
   const int *kptr, *kidx, *tptr, *tidx;
@@ -71,6 +87,7 @@ struct Arrays {
   double *xout, *yout;
   int *status;
   long long *iters;
+  unsigned long long *t_start, *t_end;  // per-LP global-timer stamps (ns) of the last solve
 };
 
 // ---------------------------------------------------------------- CTA helpers
@@ -86,12 +103,20 @@ __device__ __forceinline__ double wmax(double v) {
   return v;
 }
 
-// CTA-wide sums of NV values, result in every thread (fixed order).
+// CTA-wide sums of NV values, result in every thread (fixed order).  A warp
+// whose values are all zero (no rows of a small LP) skips its FP64 shuffle
+// tree: GB300 issues FP64 at a small fraction of the FP32 rate, so the trees
+// of idle warps would dominate a small LP's iteration.
 template <int NV>
 __device__ __forceinline__ void allsum(double (&v)[NV], double *red) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  bool any = false;
 #pragma unroll
-  for (int a = 0; a < NV; ++a) v[a] = wsum(v[a]);
+  for (int a = 0; a < NV; ++a) any |= __double_as_longlong(v[a]) != 0;
+  if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = wsum(v[a]);
+  }
   if (lane == 0) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) red[a * NWB + wid] = v[a];
@@ -125,15 +150,130 @@ __device__ __forceinline__ double allmax(double v, double *red) {
   return v;
 }
 
+// Loads of vectors that the solve itself writes.  A team of CTAs (below)
+// reads entries that other SMs wrote inside this kernel, so those loads go
+// to the L2 (ld.cg), past the SM's non-coherent L1.
+template <bool CG>
+__device__ __forceinline__ double ldv(const double *p) {
+  if constexpr (CG)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// An LP solved by one CTA: every loop covers all rows, syncs are CTA barriers.
+struct Solo {
+  static constexpr bool kTeam = false;
+  __device__ __forceinline__ int rank() const { return 0; }
+  __device__ __forceinline__ int size() const { return 1; }
+  __device__ __forceinline__ bool sync() {
+    __syncthreads();
+    return true;
+  }
+  template <int NV>
+  __device__ __forceinline__ bool reduce(double (&v)[NV], double *red) {
+    allsum<NV>(v, red);
+    return true;
+  }
+};
+
+// Team-barrier and reduction state in global memory (one entry per team).
+struct TeamState {
+  unsigned *cnt, *gen;  // barrier arrival counter and generation
+  int *q;               // queue position broadcast by the team leader
+  double *slots;        // [team][2][TEAM][16] partial sums
+  int *abort;           // set when a barrier wait times out
+  int teams;
+};
+constexpr int TEAM = 8;                 // CTAs per team
+constexpr long long TEAM_MIN_NNZ = 32768;  // LPs at least this large are solved by a team
+constexpr unsigned long long TEAM_WAIT_NS = 2000000000ull;
+
+// An LP solved by TEAM CTAs (one per SM): rows and vector entries are dealt
+// round-robin in chunks, partial sums meet in global slots read in rank order
+// (every CTA obtains bitwise the same sums and therefore takes the same
+// decisions), and phases are separated by a sense-reversing barrier on a
+// global counter whose spin is bounded: a wait longer than TEAM_WAIT_NS sets
+// the abort flag, and every CTA of the batch then leaves its loops.
+struct Team {
+  static constexpr bool kTeam = true;
+  int r;
+  unsigned *cnt, *gen;
+  double *slots;
+  int *abort;
+  int buf;
+  __device__ __forceinline__ int rank() const { return r; }
+  __device__ __forceinline__ int size() const { return TEAM; }
+  __device__ bool sync() {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ok = 1;
+      __threadfence();  // this CTA's writes before its arrival
+      const unsigned g = *(volatile unsigned *)gen;
+      if (atomicAdd(cnt, 1u) == TEAM - 1) {
+        *(volatile unsigned *)cnt = 0u;
+        __threadfence();
+        atomicAdd(gen, 1u);
+      } else {
+        const unsigned long long t0 = gtimer_ns();
+        while (*(volatile unsigned *)gen == g) {
+          if (*(volatile int *)abort || gtimer_ns() - t0 > TEAM_WAIT_NS) {
+            atomicExch(abort, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+      s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+  }
+  template <int NV>
+  __device__ bool reduce(double (&v)[NV], double *red) {
+    static_assert(NV <= 16, "16 slots per rank");
+    allsum<NV>(v, red);
+    double *sl = slots + (size_t)buf * TEAM * 16;
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) sl[r * 16 + a] = v[a];
+    }
+    const bool ok = sync();
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        double t = 0.0;
+        for (int k = 0; k < TEAM; ++k) t += __ldcg(sl + k * 16 + a);
+        red[RED_TEAM + a] = t;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = red[RED_TEAM + a];
+    __syncthreads();
+    buf ^= 1;  // the other buffer: a rank rewrites this one only after the next barrier
+    return ok;
+  }
+};
+
 // Rows of a CSR block with G lanes per row: for each row, f(row, sums) runs
 // in the group's first lane.  Every lane of a warp takes part in each round,
 // so the shuffles are always full-warp.
-template <int NV, bool SCALED, class F>
+template <int NV, bool SCALED, bool CG = false, class F>
 __device__ __forceinline__ void rows_spmv(const int *__restrict__ ptr, const int *__restrict__ idx,
                                           const double *__restrict__ val, int rows, int G,
-                                          const double *const (&xs)[NV], const double (&sc)[NV], F &f) {
+                                          const double *const (&xs)[NV], const double (&sc)[NV], F &f,
+                                          int part = 0, int parts = 1) {
   const int gid = threadIdx.x / G, li = threadIdx.x % G, ngroups = NTB / G;
-  for (int base = 0; base < rows; base += ngroups) {
+  for (int base = part * ngroups; base < rows; base += parts * ngroups) {
     const int r = base + gid;
     double s[NV];
 #pragma unroll
@@ -143,7 +283,10 @@ __device__ __forceinline__ void rows_spmv(const int *__restrict__ ptr, const int
         const double v = val[e];
         const int c = idx[e];
 #pragma unroll
-        for (int a = 0; a < NV; ++a) s[a] = fma(v, SCALED ? sc[a] * xs[a][c] : xs[a][c], s[a]);
+        for (int a = 0; a < NV; ++a) {
+          const double xv = ldv<CG>(xs[a] + c);
+          s[a] = fma(v, SCALED ? sc[a] * xv : xv, s[a]);
+        }
       }
     }
     for (int o = G >> 1; o > 0; o >>= 1) {
@@ -247,6 +390,7 @@ __global__ void __launch_bounds__(NTB) k_batch_scale(Arrays A, Inst *inst, int c
 
 // ---------------------------------------------------------------- one instance, one CTA
 
+template <bool CG>
 struct PrimalRow {
   const double *c, *l, *u, *x, *sx;
   double *g, *xn, *sxn;
@@ -255,29 +399,28 @@ struct PrimalRow {
   __device__ __forceinline__ void operator()(int j, const double (&s)[1]) { apply(j, s[0]); }
   __device__ __forceinline__ void apply(int j, double gj) {
     if (store_g) g[j] = gj;
-    double v = fma(-tau, c[j] - gj, x[j]);
-    const double lj = l[j], uj = u[j];
-    if (v < lj) v = lj;
-    if (v > uj) v = uj;
+    const double xj = ldv<CG>(x + j);
+    const double v = clamp_bits(fma(-tau, c[j] - gj, xj), l[j], u[j]);  // integer compares, off the FP64 pipe
     xn[j] = v;
-    sxn[j] = fma(eta, v, sx[j]);
-    const double d = v - x[j];
+    sxn[j] = fma(eta, v, ldv<CG>(sx + j));
+    const double d = v - xj;
     dx2 = fma(d, d, dx2);
   }
 };
 
+template <bool CG>
 struct DualRow {
   const double *q, *y, *kx, *sy;
   double *yn, *kxn, *syn;
   double sigma, eta, dy2, cross;
   int n_eq;
   __device__ __forceinline__ void operator()(int i, const double (&s)[1]) {
-    const double kn = s[0], kxi = kx[i], yi = y[i];
+    const double kn = s[0], kxi = ldv<CG>(kx + i), yi = ldv<CG>(y + i);
     double v = fma(sigma, q[i] - fma(2.0, kn, -kxi), yi);
-    if (i >= n_eq && v < 0.0) v = 0.0;
+    if (i >= n_eq && __double_as_longlong(v) < 0) v = 0.0;  // proj_Y by the sign bit
     yn[i] = v;
     kxn[i] = kn;
-    syn[i] = fma(eta, v, sy[i]);
+    syn[i] = fma(eta, v, ldv<CG>(sy + i));
     const double d = v - yi;
     dy2 = fma(d, d, dy2);
     cross = fma(d, kn - kxi, cross);
@@ -285,6 +428,7 @@ struct DualRow {
 };
 
 // Dual-side KKT pieces for the current (and, with avg, the average) point.
+template <bool CG>
 struct CheckT {
   const double *c, *l, *u, *d2, *x, *sx;
   double *g, *gbar;
@@ -304,7 +448,7 @@ struct CheckT {
   }
   template <int NV>
   __device__ __forceinline__ void operator()(int j, const double (&s)[NV]) {
-    double gj = g[j], gb = 0.0;
+    double gj = kind == 2 ? ldv<CG>(g + j) : 0.0, gb = 0.0;
     if (kind == 0) {
       gj = s[0];
       g[j] = gj;
@@ -315,14 +459,15 @@ struct CheckT {
     } else {
       gb = s[0];
     }
-    piece(c[j], gj, l[j], u[j], d2[j], x[j], acc);
+    piece(c[j], gj, l[j], u[j], d2[j], ldv<CG>(x + j), acc);
     if (kind) {
       gbar[j] = gb;
-      piece(c[j], gb, l[j], u[j], d2[j], invW * sx[j], acc + 4);
+      piece(c[j], gb, l[j], u[j], d2[j], invW * ldv<CG>(sx + j), acc + 4);
     }
   }
 };
 
+template <bool CG>
 struct CheckK {
   const double *q, *d1, *y, *sy;
   double *kx, *kxbar;
@@ -339,18 +484,22 @@ struct CheckK {
   }
   __device__ __forceinline__ void operator()(int i, const double (&s)[1]) {
     const bool ineq = i >= n_eq;
-    double kxi = check ? kx[i] : s[0];
+    double kxi = check ? ldv<CG>(kx + i) : s[0];
     if (!check) kx[i] = kxi;
-    piece(q[i], kxi, ineq, d1[i], y[i], acc);
+    piece(q[i], kxi, ineq, d1[i], ldv<CG>(y + i), acc);
     if (check) {
       kxbar[i] = s[0];
-      piece(q[i], s[0], ineq, d1[i], invW * sy[i], acc + 3);
+      piece(q[i], s[0], ineq, d1[i], invW * ldv<CG>(sy + i), acc + 3);
     }
   }
 };
 
-__device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, int id, double *red) {
+template <class Grp>
+__device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, int id, double *red, Grp &grp) {
+  constexpr bool CG = Grp::kTeam;
   const int m = I.m, n = I.n, tid = threadIdx.x;
+  // this CTA's share of the element loops and of the row loops
+  const int part = grp.rank(), parts = grp.size(), e0 = part * NTB + tid, es = parts * NTB;
   const int *kp = A.kptr + I.kp, *ki = A.kidx + I.ke, *tp = A.tptr + I.tp, *ti = A.tidx + I.te;
   const double *kv = A.kval + I.ke, *tv = A.tval + I.te;
   double *vm = A.vm + I.om, *vn = A.vn + I.on;
@@ -361,57 +510,65 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
   double *g = VN(VN_G), *gbar = VN(VN_GB), *xl = VN(VN_XL), *yl = VM(VM_YL), *kxb = VM(VM_KXB);
   const double *c = VN(VN_C), *l = VN(VN_L), *u = VN(VN_U), *D2 = VN(VN_D2), *q = VM(VM_Q), *D1 = VM(VM_D1);
   // ---- start point (Sec. 4.1 "Initialization", or the warm start) ----
-  for (int j = tid; j < n; j += NTB) {
+  for (int j = e0; j < n; j += es) {
     const double v = (p.warm && A.x0) ? A.x0[I.xo + j] / D2[j] : 0.0;
     x[0][j] = v;
     xl[j] = v;
     sx[0][j] = 0.0;
   }
-  for (int i = tid; i < m; i += NTB) {
+  for (int i = e0; i < m; i += es) {
     const double v = (p.warm && A.y0) ? A.y0[I.yo + i] / D1[i] : 0.0;
     y[0][i] = v;
     yl[i] = v;
     sy[0][i] = 0.0;
   }
-  __syncthreads();
+  bool ok = grp.sync();
   double eta = I.eta0, omega = I.omega0, W = 0.0, kkt_start, kkt_prev;
+  double tau = eta / omega, sigma = eta * omega;  // primal / dual step sizes
   long long k = 0, t = 0;
   int cur = 0, need_g = 0, status = ST_RUNNING, which = 0;
   // KKT(z^{0,0}) with omega^0
   {
-    CheckT ct{c, l, u, D2, x[0], sx[0], g, gbar, 0.0, 0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    CheckT<CG> ct{c, l, u, D2, x[0], sx[0], g, gbar, 0.0, 0, {0, 0, 0, 0, 0, 0, 0, 0}};
     const double *const xs[1] = {y[0]};
     const double sc[1] = {1.0};
-    rows_spmv<1, false>(tp, ti, tv, n, I.gt, xs, sc, ct);
-    CheckK ck{q, D1, y[0], sy[0], kx[0], kxb, 0.0, 0, I.n_eq, {0, 0, 0, 0, 0, 0}};
+    rows_spmv<1, false, CG>(tp, ti, tv, n, I.gt, xs, sc, ct, part, parts);
+    CheckK<CG> ck{q, D1, y[0], sy[0], kx[0], kxb, 0.0, 0, I.n_eq, {0, 0, 0, 0, 0, 0}};
     const double *const xs2[1] = {x[0]};
-    rows_spmv<1, false>(kp, ki, kv, m, I.gk, xs2, sc, ck);
+    rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, xs2, sc, ck, part, parts);
     double s[5] = {ct.acc[0], ct.acc[2], ct.acc[3], ck.acc[0], ck.acc[2]};
-    allsum<5>(s, red);
+    ok = grp.template reduce<5>(s, red) && ok;
+    if (!ok) status = ST_NUMERICAL;
     kkt_start = kkt_omega(s[3], s[0], s[1], s[4] + s[2], omega);
     kkt_prev = kkt_start;
   }
   while (status == ST_RUNNING) {
     const int nxt = cur ^ 1;
     // ---- Algorithm 2 trial: primal half-step ----
-    PrimalRow pr{c, l, u, x[cur], sx[cur], g, x[nxt], sx[nxt], eta / omega, eta, 0.0, need_g != 0};
+    PrimalRow<CG> pr{c, l, u, x[cur], sx[cur], g, x[nxt], sx[nxt], tau, eta, 0.0, need_g != 0};
     if (need_g) {
       const double *const xs[1] = {y[cur]};
       const double sc[1] = {1.0};
-      rows_spmv<1, false>(tp, ti, tv, n, I.gt, xs, sc, pr);
+      rows_spmv<1, false, CG>(tp, ti, tv, n, I.gt, xs, sc, pr, part, parts);
     } else {
-      for (int j = tid; j < n; j += NTB) pr.apply(j, g[j]);
+      for (int j = e0; j < n; j += es) pr.apply(j, ldv<CG>(g + j));
     }
-    __syncthreads();
+    if (!grp.sync()) {
+      status = ST_NUMERICAL;
+      break;
+    }
     // ---- dual half-step ----
-    DualRow dr{q, y[cur], kx[cur], sy[cur], y[nxt], kx[nxt], sy[nxt], eta * omega, eta, 0.0, 0.0, I.n_eq};
+    DualRow<CG> dr{q, y[cur], kx[cur], sy[cur], y[nxt], kx[nxt], sy[nxt], sigma, eta, 0.0, 0.0, I.n_eq};
     {
       const double *const xs[1] = {x[nxt]};
       const double sc[1] = {1.0};
-      rows_spmv<1, false>(kp, ki, kv, m, I.gk, xs, sc, dr);
+      rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, xs, sc, dr, part, parts);
     }
     double s3[3] = {pr.dx2, dr.dy2, dr.cross};
-    allsum<3>(s3, red);
+    if (!grp.template reduce<3>(s3, red)) {
+      status = ST_NUMERICAL;
+      break;
+    }
     // ---- step-size test (eq. step-size with |interaction|; exponent base k + 2) ----
     // one thread evaluates it and broadcasts: the two FP64 powers, run by
     // every warp, would cost more than the whole iteration of a small LP on
@@ -420,46 +577,50 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
       const double ia = fabs(s3[2]);
       const double eb = ia > 0.0 ? (omega * s3[0] + s3[1] / omega) / (2.0 * ia) : CUDART_INF;
       const double kk = (double)(k + 2);
-      const double e1 = (1.0 - pow(kk, -0.3)) * eb, e2 = (1.0 + pow(kk, -0.6)) * eta;
+      const double p3 = k < p.npw ? p.pw[k] : pow(kk, -0.3), p6 = k < p.npw ? p.pw[p.npw + k] : pow(kk, -0.6);
+      const double e1 = (1.0 - p3) * eb, e2 = (1.0 + p6) * eta;
       const double en = e1 < e2 ? e1 : e2;
-      red[RED_BCAST] = eb;
-      red[RED_BCAST + 1] = en;
-      red[RED_BCAST + 2] =
+      const bool accept = eta <= eb;
+      red[RED_BCAST] = en;
+      red[RED_BCAST + 1] = en / omega;
+      red[RED_BCAST + 2] = en * omega;
+      red[RED_BCAST + 3] =
           (!isfinite(s3[0]) || !isfinite(s3[1]) || !isfinite(s3[2]) || isnan(eb) || !(en > 0.0)) ? 1.0 : 0.0;
+      red[RED_BCAST + 4] = accept ? 1.0 : 0.0;
+      red[RED_BCAST + 5] = accept ? W + eta : W;
     }
     __syncthreads();
-    const double eta_bar = red[RED_BCAST], eta_next = red[RED_BCAST + 1];
-    const bool numerical = red[RED_BCAST + 2] != 0.0;
     // (the slots are rewritten only after the next iteration's barriers)
-    if (numerical) {
+    if (red[RED_BCAST + 3] != 0.0) {
       status = ST_NUMERICAL;
       break;
     }
-    const double eta_used = eta;
-    eta = eta_next;
-    if (!(eta_used <= eta_bar)) {
+    eta = red[RED_BCAST];
+    tau = red[RED_BCAST + 1];
+    sigma = red[RED_BCAST + 2];
+    W = red[RED_BCAST + 5];
+    if (red[RED_BCAST + 4] == 0.0) {
       need_g = 0;
       continue;
     }
     cur = nxt;
     ++k;
     ++t;
-    W += eta_used;
     need_g = 1;
     if (k % p.P != 0 && k < p.max_iter) continue;
     // ---- restart / termination check (Sec. 3.4 / Sec. 4.1) ----
     const double invW = 1.0 / W;
-    CheckT ct{c, l, u, D2, x[cur], sx[cur], g, gbar, invW, 1, {0, 0, 0, 0, 0, 0, 0, 0}};
+    CheckT<CG> ct{c, l, u, D2, x[cur], sx[cur], g, gbar, invW, 1, {0, 0, 0, 0, 0, 0, 0, 0}};
     {
       const double *const xs[2] = {y[cur], sy[cur]};
       const double sc[2] = {1.0, invW};
-      rows_spmv<2, true>(tp, ti, tv, n, I.gt, xs, sc, ct);
+      rows_spmv<2, true, CG>(tp, ti, tv, n, I.gt, xs, sc, ct, part, parts);
     }
-    CheckK ck{q, D1, y[cur], sy[cur], kx[cur], kxb, invW, 1, I.n_eq, {0, 0, 0, 0, 0, 0}};
+    CheckK<CG> ck{q, D1, y[cur], sy[cur], kx[cur], kxb, invW, 1, I.n_eq, {0, 0, 0, 0, 0, 0}};
     {
       const double *const xs[1] = {sx[cur]};
       const double sc[1] = {invW};
-      rows_spmv<1, true>(kp, ki, kv, m, I.gk, xs, sc, ck);
+      rows_spmv<1, true, CG>(kp, ki, kv, m, I.gk, xs, sc, ck, part, parts);
     }
     need_g = 0;
     double s[14];
@@ -467,85 +628,121 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     for (int a = 0; a < 8; ++a) s[a] = ct.acc[a];
 #pragma unroll
     for (int a = 0; a < 6; ++a) s[8 + a] = ck.acc[a];
-    allsum<14>(s, red);
-    const double pc = s[2], dc = s[10] + s[3], rpc = sqrt(s[9]), rdc = sqrt(s[1]);
-    const double pa = s[6], da = s[13] + s[7], rpa = sqrt(s[12]), rda = sqrt(s[5]);
-    if (sec41_pass(pc, dc, rpc, rdc, p.tol, I.qn, I.cn)) {
-      status = ST_OPTIMAL;
-      which = 0;
+    if (!grp.template reduce<14>(s, red)) {
+      status = ST_NUMERICAL;
       break;
     }
-    if (sec41_pass(pa, da, rpa, rda, p.tol, I.qn, I.cn)) {
-      status = ST_OPTIMAL;
-      which = 1;
+    // Sec. 4.1 termination, GetRestartCandidate and the criteria of Sec. 3.4:
+    // scalar work, evaluated by one thread and broadcast (decision 0 / 1:
+    // optimal at the current / average point, 2: iteration limit, 3: go on,
+    // 4: restart)
+    if (tid == 0) {
+      const double pc = s[2], dc = s[10] + s[3], rpc = sqrt(s[9]), rdc = sqrt(s[1]);
+      const double pa = s[6], da = s[13] + s[7], rpa = sqrt(s[12]), rda = sqrt(s[5]);
+      double dec = 3.0, kcand = 0.0;
+      bool cand_avg = false;
+      if (sec41_pass(pc, dc, rpc, rdc, p.tol, I.qn, I.cn)) {
+        dec = 0.0;
+      } else if (sec41_pass(pa, da, rpa, rda, p.tol, I.qn, I.cn)) {
+        dec = 1.0;
+      } else if (k >= p.max_iter) {
+        dec = 2.0;
+      } else {
+        const double kc = kkt_omega(s[8], s[0], pc, dc, omega);
+        const double ka = kkt_omega(s[11], s[4], pa, da, omega);
+        cand_avg = !(kc < ka);
+        kcand = cand_avg ? ka : kc;
+        const bool restart = kcand <= p.beta_suff * kkt_start ||
+                             (kcand <= p.beta_nec * kkt_start && kcand > kkt_prev) ||
+                             (double)t >= p.beta_art * (double)k;
+        dec = restart ? 4.0 : 3.0;
+      }
+      red[RED_BCAST] = dec;
+      red[RED_BCAST + 1] = cand_avg ? 1.0 : 0.0;
+      red[RED_BCAST + 2] = kcand;
+    }
+    __syncthreads();
+    const int dec = (int)red[RED_BCAST];
+    if (dec <= 2) {
+      status = dec == 2 ? ST_ITER_LIMIT : ST_OPTIMAL;
+      which = dec == 1 ? 1 : 0;
       break;
     }
-    if (k >= p.max_iter) {
-      status = ST_ITER_LIMIT;
-      which = 0;
-      break;
-    }
-    const double kc = kkt_omega(s[8], s[0], pc, dc, omega);
-    const double ka = kkt_omega(s[11], s[4], pa, da, omega);
-    const bool cand_avg = !(kc < ka);
-    const double kcand = cand_avg ? ka : kc;
-    const bool restart = kcand <= p.beta_suff * kkt_start || (kcand <= p.beta_nec * kkt_start && kcand > kkt_prev) ||
-                         (double)t >= p.beta_art * (double)k;
-    if (!restart) {
-      kkt_prev = kcand;
+    if (dec == 3) {
+      kkt_prev = red[RED_BCAST + 2];
       continue;
     }
+    const bool cand_avg = red[RED_BCAST + 1] != 0.0;
     double dd[2] = {0.0, 0.0};
-    for (int j = tid; j < n; j += NTB) {
-      double xn = x[cur][j];
+    for (int j = e0; j < n; j += es) {
+      double xn = ldv<CG>(x[cur] + j);
       if (cand_avg) {
-        xn = invW * sx[cur][j];
+        xn = invW * ldv<CG>(sx[cur] + j);
         x[cur][j] = xn;
-        g[j] = gbar[j];
+        g[j] = ldv<CG>(gbar + j);
       }
-      const double d = xn - xl[j];
+      const double d = xn - ldv<CG>(xl + j);
       dd[0] = fma(d, d, dd[0]);
       xl[j] = xn;
       sx[cur][j] = 0.0;
     }
-    for (int i = tid; i < m; i += NTB) {
-      double yn = y[cur][i];
+    for (int i = e0; i < m; i += es) {
+      double yn = ldv<CG>(y[cur] + i);
       if (cand_avg) {
-        yn = invW * sy[cur][i];
+        yn = invW * ldv<CG>(sy[cur] + i);
         y[cur][i] = yn;
-        kx[cur][i] = kxb[i];
+        kx[cur][i] = ldv<CG>(kxb + i);
       }
-      const double d = yn - yl[i];
+      const double d = yn - ldv<CG>(yl + i);
       dd[1] = fma(d, d, dd[1]);
       yl[i] = yn;
       sy[cur][i] = 0.0;
     }
-    allsum<2>(dd, red);
-    const double dx = sqrt(dd[0]), dy = sqrt(dd[1]);
-    if (dx > p.eps_zero && dy > p.eps_zero) omega = exp(p.theta * log(dy / dx) + (1.0 - p.theta) * log(omega));
+    if (!grp.template reduce<2>(dd, red)) {
+      status = ST_NUMERICAL;
+      break;
+    }
+    // PrimalWeightUpdate and KKT of the new start point with the new omega
+    if (tid == 0) {
+      const double dx = sqrt(dd[0]), dy = sqrt(dd[1]);
+      double om = omega;
+      if (dx > p.eps_zero && dy > p.eps_zero) om = exp(p.theta * log(dy / dx) + (1.0 - p.theta) * log(om));
+      const double pc = s[2], dc = s[10] + s[3], pa = s[6], da = s[13] + s[7];
+      red[RED_BCAST + 3] = om;
+      red[RED_BCAST + 4] = cand_avg ? kkt_omega(s[11], s[4], pa, da, om) : kkt_omega(s[8], s[0], pc, dc, om);
+      red[RED_BCAST + 5] = eta / om;
+      red[RED_BCAST + 6] = eta * om;
+    }
+    __syncthreads();
+    omega = red[RED_BCAST + 3];
+    kkt_start = red[RED_BCAST + 4];
+    kkt_prev = kkt_start;
+    tau = red[RED_BCAST + 5];
+    sigma = red[RED_BCAST + 6];
     W = 0.0;
     t = 0;
-    kkt_start = cand_avg ? kkt_omega(s[11], s[4], pa, da, omega) : kkt_omega(s[8], s[0], pc, dc, omega);
-    kkt_prev = kkt_start;
   }
   // ---- output in the original space ----
   __syncthreads();
   const double invW = which ? 1.0 / W : 0.0;
-  for (int j = tid; j < n; j += NTB) {
-    const double xs = which ? invW * sx[cur][j] : x[cur][j];
+  for (int j = e0; j < n; j += es) {
+    const double xs = which ? invW * ldv<CG>(sx[cur] + j) : ldv<CG>(x[cur] + j);
     double v = D2[j] * xs;
     const double l0 = vn[(long long)VN_L0 * n + j], u0 = vn[(long long)VN_U0 * n + j];
     if (v < l0) v = l0;
     if (v > u0) v = u0;
     A.xout[I.xo + j] = v;
   }
-  for (int i = tid; i < m; i += NTB) {
-    const double ys = which ? invW * sy[cur][i] : y[cur][i];
+  for (int i = e0; i < m; i += es) {
+    const double ys = which ? invW * ldv<CG>(sy[cur] + i) : ldv<CG>(y[cur] + i);
     A.yout[I.yo + i] = D1[i] * ys;
   }
-  if (tid == 0) {
+  if (tid == 0 && part == 0) {
     A.status[id] = status;
     A.iters[id] = k;
+    unsigned long long tn;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tn));
+    A.t_end[id] = tn;
   }
   __syncthreads();
 }
@@ -569,58 +766,132 @@ __device__ __forceinline__ void copy_in(T *dst, const T *src, long long count) {
   for (long long i = threadIdx.x; i < count; i += NTB) dst[i] = src[i];
 }
 
-// One CTA per LP, LPs taken from the queue.  An LP whose data fits in
-// `resident_max` bytes of the CTA's dynamic shared memory is copied there
-// (scaled K, K' and vectors; read-only data is never copied back, the outputs
-// go straight to global memory) and solved from shared memory: the small
-// LPs, which need the most iterations, then run at shared-memory latency.
+// Solves the LP at queue position q with this CTA alone: from shared memory
+// when its data fits in `resident_max` bytes of the CTA's dynamic shared
+// memory (scaled K, K' and vectors copied in; read-only data is never copied
+// back, the outputs go straight to global memory), else from global memory.
+// The small LPs, which need the most iterations, thus run at shared-memory
+// latency.
+__device__ void solve_alone(const Arrays &A, const Inst *__restrict__ inst, int id, const Params &p,
+                            long long resident_max, double *red, unsigned char *bsm) {
+  const Inst I = inst[id];
+  if (threadIdx.x == 0) A.t_start[id] = gtimer_ns();
+  Solo solo;
+  const long long nnz = A.kptr[I.kp + I.m] - A.kptr[I.kp];
+  if (resident_bytes(I.m, I.n, nnz) <= resident_max) {
+    unsigned char *cur = bsm;
+    Arrays R = A;
+    Inst J = I;
+    int *kptr = carve<int>(cur, I.m + 1), *tptr = carve<int>(cur, I.n + 1);
+    int *kidx = carve<int>(cur, nnz), *tidx = carve<int>(cur, nnz);
+    double *kval = carve<double>(cur, nnz), *tval = carve<double>(cur, nnz);
+    double *vm = carve<double>(cur, (long long)VM_COUNT * I.m), *vn = carve<double>(cur, (long long)VN_COUNT * I.n);
+    // row pointers relative to the LP's first nonzero
+    const int k0 = A.kptr[I.kp], t0 = A.tptr[I.tp];
+    for (int i = threadIdx.x; i <= I.m; i += NTB) kptr[i] = A.kptr[I.kp + i] - k0;
+    for (int j = threadIdx.x; j <= I.n; j += NTB) tptr[j] = A.tptr[I.tp + j] - t0;
+    copy_in(kidx, A.kidx + I.ke + k0, nnz);
+    copy_in(tidx, A.tidx + I.te + t0, nnz);
+    copy_in(kval, A.kval + I.ke + k0, nnz);
+    copy_in(tval, A.tval + I.te + t0, nnz);
+    copy_in(vm, A.vm + I.om, (long long)VM_COUNT * I.m);
+    copy_in(vn, A.vn + I.on, (long long)VN_COUNT * I.n);
+    __syncthreads();
+    R.kptr = kptr;
+    R.tptr = tptr;
+    R.kidx = kidx;
+    R.tidx = tidx;
+    R.kval = kval;
+    R.tval = tval;
+    R.vm = vm;
+    R.vn = vn;
+    J.kp = J.ke = J.tp = J.te = J.om = J.on = 0;
+    solve_instance(R, J, p, id, red, solo);
+  } else {
+    solve_instance(A, I, p, id, red, solo);
+  }
+}
+
+// Claims of queue positions from either end.  queue[0] counts claims from
+// the front (largest LPs), queue[1] from the back (smallest); claimed[q] makes
+// each position go to exactly one CTA where the two ends meet.  Returns -1
+// when that end is exhausted.  A back claim stops, without claiming, at the
+// first LP that a team must take.
+__device__ __forceinline__ int claim_front(int *queue, int *claimed, int count) {
+  const int q = atomicAdd(queue, 1);
+  if (q >= count || atomicExch(claimed + q, 1) != 0) return -1;
+  return q;
+}
+__device__ __forceinline__ int claim_back(const Arrays &A, const Inst *__restrict__ inst, const int *__restrict__ order,
+                                          int *queue, int *claimed, int count, bool teams) {
+  const int q = count - 1 - atomicAdd(queue + 1, 1);
+  if (q < 0) return -1;
+  if (teams) {
+    const Inst &I = inst[order[q]];
+    if (A.kptr[I.kp + I.m] - A.kptr[I.kp] >= TEAM_MIN_NNZ) return -1;
+  }
+  if (atomicExch(claimed + q, 1) != 0) return -1;
+  return q;
+}
+
+// Persistent solver over the queue `order` (largest LPs first).  The first
+// ts.teams * TEAM CTAs work in teams of TEAM (CTA b in team b / TEAM) from
+// the front: the team leader claims the next LP and, while it has at least
+// TEAM_MIN_NNZ nonzeros, all TEAM CTAs solve it together, so one large LP
+// that needs many iterations no longer holds a single SM for the whole
+// batch; from the first smaller LP on, the team disbands and each of its
+// CTAs claims LPs alone.  The remaining CTAs start alone from the back, on
+// the smallest LPs: those need the most iterations, and starting them first
+// keeps them off the end of the schedule.  Large LPs are always solved by a
+// team and small ones always by one CTA, so results do not depend on timing.
 __global__ void __launch_bounds__(NTB) k_batch_solve(Arrays A, const Inst *__restrict__ inst,
                                                      const int *__restrict__ order, int count, int *queue,
-                                                     Params p, long long resident_max) {
+                                                     int *claimed, Params p, long long resident_max, TeamState ts) {
   __shared__ double red[RED_SIZE];
   __shared__ int s_id;
   extern __shared__ __align__(16) unsigned char bsm[];
+  const int team = blockIdx.x / TEAM;
+  if (team < ts.teams) {
+    Team grp{(int)(blockIdx.x % TEAM), ts.cnt + team, ts.gen + team, ts.slots + (size_t)team * 2 * TEAM * 16,
+             ts.abort, 0};
+    for (;;) {
+      if (grp.rank() == 0 && threadIdx.x == 0) ts.q[team] = claim_front(queue, claimed, count);
+      if (!grp.sync()) return;
+      if (threadIdx.x == 0) s_id = __ldcg(ts.q + team);
+      __syncthreads();
+      const int q = s_id;
+      // every rank has read the position before the leader may overwrite it
+      if (!grp.sync()) return;
+      if (q < 0) return;
+      const int id = order[q];
+      const Inst I = inst[id];
+      const long long nnz = A.kptr[I.kp + I.m] - A.kptr[I.kp];
+      if (nnz >= TEAM_MIN_NNZ) {
+        if (grp.rank() == 0 && threadIdx.x == 0) A.t_start[id] = gtimer_ns();
+        solve_instance(A, I, p, id, red, grp);
+        if (*(volatile int *)ts.abort) return;
+        continue;
+      }
+      // the first smaller LP: the leader solves it, and the team disbands
+      if (grp.rank() == 0) solve_alone(A, inst, id, p, resident_max, red, bsm);
+      break;
+    }
+    for (;;) {
+      if (threadIdx.x == 0) s_id = claim_front(queue, claimed, count);
+      __syncthreads();
+      const int q = s_id;
+      __syncthreads();
+      if (q < 0) return;
+      solve_alone(A, inst, order[q], p, resident_max, red, bsm);
+    }
+  }
   for (;;) {
-    if (threadIdx.x == 0) s_id = atomicAdd(queue, 1);
+    if (threadIdx.x == 0) s_id = claim_back(A, inst, order, queue, claimed, count, ts.teams > 0);
     __syncthreads();
     const int q = s_id;
     __syncthreads();
-    if (q >= count) return;
-    const int id = order[q];
-    const Inst I = inst[id];
-    const long long nnz = A.kptr[I.kp + I.m] - A.kptr[I.kp];
-    if (resident_bytes(I.m, I.n, nnz) <= resident_max) {
-      unsigned char *cur = bsm;
-      Arrays R = A;
-      Inst J = I;
-      int *kptr = carve<int>(cur, I.m + 1), *tptr = carve<int>(cur, I.n + 1);
-      int *kidx = carve<int>(cur, nnz), *tidx = carve<int>(cur, nnz);
-      double *kval = carve<double>(cur, nnz), *tval = carve<double>(cur, nnz);
-      double *vm = carve<double>(cur, (long long)VM_COUNT * I.m), *vn = carve<double>(cur, (long long)VN_COUNT * I.n);
-      // row pointers relative to the LP's first nonzero
-      const int k0 = A.kptr[I.kp], t0 = A.tptr[I.tp];
-      for (int i = threadIdx.x; i <= I.m; i += NTB) kptr[i] = A.kptr[I.kp + i] - k0;
-      for (int j = threadIdx.x; j <= I.n; j += NTB) tptr[j] = A.tptr[I.tp + j] - t0;
-      copy_in(kidx, A.kidx + I.ke + k0, nnz);
-      copy_in(tidx, A.tidx + I.te + t0, nnz);
-      copy_in(kval, A.kval + I.ke + k0, nnz);
-      copy_in(tval, A.tval + I.te + t0, nnz);
-      copy_in(vm, A.vm + I.om, (long long)VM_COUNT * I.m);
-      copy_in(vn, A.vn + I.on, (long long)VN_COUNT * I.n);
-      __syncthreads();
-      R.kptr = kptr;
-      R.tptr = tptr;
-      R.kidx = kidx;
-      R.tidx = tidx;
-      R.kval = kval;
-      R.tval = tval;
-      R.vm = vm;
-      R.vn = vn;
-      J.kp = J.ke = J.tp = J.te = J.om = J.on = 0;
-      solve_instance(R, J, p, id, red);
-    } else {
-      solve_instance(A, I, p, id, red);
-    }
+    if (q < 0) return;
+    solve_alone(A, inst, order[q], p, resident_max, red, bsm);
   }
 }
 
@@ -652,6 +923,12 @@ struct pdlp_batch {
   double solve_ms = 0.0, setup_ms = 0.0, tune_ms = 0.0;
   double lanes_target = 4.0;
   int resident = 0;  // LPs that fit the shared-memory budget
+  int team_lps = 0;  // LPs solved by a team
+  double *pw = nullptr;  // exponent-factor table (k_pow_table)
+  long long npw = 0;
+  TeamState ts{};               // team barriers / reductions (in the arena)
+  void *team_words = nullptr;   // counters, generations, positions, abort flag
+  size_t team_words_bytes = 0;
 };
 
 namespace {
@@ -672,6 +949,7 @@ void free_batch(pdlp_batch *b) {
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->arena) cudaFree(b->arena);
+  if (b->pw) cudaFree(b->pw);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
   delete b;
@@ -684,9 +962,11 @@ void free_batch(pdlp_batch *b) {
   } while (0)
 
 int launch_solve(pdlp_batch *b, const Arrays &A, const Params &p, cudaStream_t s) {
-  BCK(cudaMemsetAsync(b->d_queue, 0, sizeof(int), s));
-  k_batch_solve<<<b->grid, NTB, RESIDENT_MAX, s>>>(A, b->d_inst, b->d_order, b->count, b->d_queue, p,
-                                                  (long long)RESIDENT_MAX);
+  BCK(cudaMemsetAsync(b->d_queue, 0, 8 + 4 * (size_t)b->count, s));
+  // team barrier counters and the abort flag start at zero
+  BCK(cudaMemsetAsync(b->team_words, 0, b->team_words_bytes, s));
+  k_batch_solve<<<b->grid, NTB, RESIDENT_MAX, s>>>(A, b->d_inst, b->d_order, b->count, b->d_queue,
+                                                  b->d_queue + 2, p, (long long)RESIDENT_MAX, b->ts);
   BCK(cudaGetLastError());
   return PDLP_OK;
 }
@@ -757,6 +1037,7 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
     KP += L.m + 1;
     TP += L.n + 1;
     if (resident_bytes(L.m, L.n, nnz) <= RESIDENT_MAX) ++b->resident;
+    if (nnz >= TEAM_MIN_NNZ) ++b->team_lps;
     KE += nnz;
     TE += nnz;
     OM += (long long)VM_COUNT * L.m;
@@ -792,6 +1073,10 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
     return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
   }
   b->grid = std::max(1, std::min(count, per_sm * b->num_sms));
+  // with at least 3 TEAM CTAs: whole teams plus 2 TEAM CTAs that start from
+  // the small end of the queue
+  const int teams = b->grid >= 3 * TEAM ? (b->grid - 2 * TEAM) / TEAM : 0;
+  if (teams) b->grid = (teams + 2) * TEAM;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t off = 0;
   const size_t o_kptr = off; off += al(4 * KP);
@@ -808,9 +1093,12 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   const size_t o_y0 = off; off += al(8 * std::max<long long>(YO, 1));
   const size_t o_st = off; off += al(4 * count);
   const size_t o_it = off; off += al(8 * count);
+  const size_t o_ts = off; off += al(16 * (size_t)count);
   const size_t o_in = off; off += al(sizeof(Inst) * count);
   const size_t o_or = off; off += al(4 * count);
-  const size_t o_q = off; off += al(4);
+  const size_t o_q = off; off += al(8 + 4 * (size_t)count);  // front / back counters, claim flags
+  const size_t o_tw = off; off += al(4 * (3 * (size_t)teams + 1));
+  const size_t o_tsl = off; off += al(8 * (size_t)std::max(teams, 1) * 2 * TEAM * 16);
   b->arena_bytes = off;
   e = cudaMalloc((void **)&b->arena, b->arena_bytes);
   if (e != cudaSuccess) {
@@ -832,9 +1120,22 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   b->d_y0 = (double *)(Ar + o_y0);
   b->A.status = (int *)(Ar + o_st);
   b->A.iters = (long long *)(Ar + o_it);
+  b->A.t_start = (unsigned long long *)(Ar + o_ts);
+  b->A.t_end = b->A.t_start + count;
   b->d_inst = (Inst *)(Ar + o_in);
   b->d_order = (int *)(Ar + o_or);
   b->d_queue = (int *)(Ar + o_q);
+  {
+    unsigned *w = (unsigned *)(Ar + o_tw);
+    b->ts.cnt = w;
+    b->ts.gen = w + teams;
+    b->ts.q = (int *)(w + 2 * teams);
+    b->ts.abort = (int *)(w + 3 * teams);
+    b->ts.slots = (double *)(Ar + o_tsl);
+    b->ts.teams = teams;
+    b->team_words = w;
+    b->team_words_bytes = 4 * (3 * (size_t)teams + 1);
+  }
   // longest instances first
   std::vector<int> order(count);
   std::iota(order.begin(), order.end(), 0);
@@ -981,6 +1282,20 @@ int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double t
   p.max_iter = max_iter;
   p.P = b->prm.check_period;
   p.warm = (x0 || y0) ? 1 : 0;
+  {
+    const long long need = std::min<long long>(max_iter, 1LL << 22);
+    if (need > b->npw) {
+      if (b->pw) cudaFree(b->pw);
+      b->pw = nullptr;
+      b->npw = 0;
+      BCK(cudaMalloc(&b->pw, 2 * sizeof(double) * (size_t)need));
+      k_pow_table<<<256, 256, 0, st>>>(b->pw, need);
+      BCK(cudaGetLastError());
+      b->npw = need;
+    }
+    p.pw = b->pw;
+    p.npw = b->npw;
+  }
   Arrays A = b->A;
   A.x0 = x0 ? b->d_x0 : nullptr;
   A.y0 = y0 ? b->d_y0 : nullptr;
@@ -1013,7 +1328,12 @@ int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double t
   if (y_out && b->sum_m) BCK(cudaMemcpyAsync(y_out, b->A.yout, 8 * b->sum_m, cudaMemcpyDeviceToHost, st));
   if (status) BCK(cudaMemcpyAsync(status, b->A.status, 4 * (size_t)b->count, cudaMemcpyDeviceToHost, st));
   if (iters) BCK(cudaMemcpyAsync(iters, b->A.iters, 8 * (size_t)b->count, cudaMemcpyDeviceToHost, st));
+  int aborted = 0;
+  BCK(cudaMemcpyAsync(&aborted, b->ts.abort, sizeof(int), cudaMemcpyDeviceToHost, st));
   BCK(cudaStreamSynchronize(st));
+  if (aborted)
+    return set_error(PDLP_ERR_CUDA, "pdlp_batch_solve: a team of CTAs timed out at a barrier (another kernel holding "
+                                    "SMs?); the results are incomplete");
   b->solve_ms = now_ms() - t0;
   return PDLP_OK;
 }
@@ -1033,6 +1353,22 @@ int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *s) {
   s->device_bytes = b->arena_bytes;
   s->resident = b->resident;
   s->resident_max_bytes = RESIDENT_MAX;
+  s->team_lps = b->ts.teams > 0 ? b->team_lps : 0;
+  s->team_size = TEAM;
+  return PDLP_OK;
+}
+
+int pdlp_batch_times(const pdlp_batch *b, double *start_s, double *end_s) {
+  if (!b) return set_error(PDLP_ERR_INVALID, "pdlp_batch_times: batch is NULL");
+  BCK(cudaSetDevice(b->device));
+  std::vector<unsigned long long> h(2 * (size_t)b->count);
+  BCK(cudaMemcpy(h.data(), b->A.t_start, 16 * (size_t)b->count, cudaMemcpyDeviceToHost));
+  unsigned long long t0 = ~0ull;
+  for (int i = 0; i < b->count; ++i) t0 = std::min(t0, h[i]);
+  for (int i = 0; i < b->count; ++i) {
+    if (start_s) start_s[i] = 1e-9 * (double)(h[i] - t0);
+    if (end_s) end_s[i] = 1e-9 * (double)(h[b->count + i] - t0);
+  }
   return PDLP_OK;
 }
 

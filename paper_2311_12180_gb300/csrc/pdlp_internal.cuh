@@ -134,4 +134,23 @@ cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0,
 // Records `msg` as the calling thread's pdlp_last_error() and returns `code`.
 int set_error(int code, const char *msg);
 
+// Order-preserving integer key of an IEEE double (sign-magnitude -> two's
+// complement): a < b  <=>  key(a) < key(b) for non-NaN values (with -0 < +0).
+__device__ __forceinline__ long long dkey(double v) {
+  const long long b = __double_as_longlong(v);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+
+// proj onto [l, u] with integer compares, keeping the clamp off the FP64 pipe.
+// A NaN input maps to u (positive NaN) or l (negative NaN); with infinite
+// bounds it becomes +-inf and the step test flags it.
+__device__ __forceinline__ double clamp_bits(double v, double l, double u) {
+  const long long kv = dkey(v);
+  double r = v;
+  if (kv < dkey(l)) r = l;
+  if (kv > dkey(u)) r = u;
+  return r;
+}
+
+
 }  // namespace pdlp

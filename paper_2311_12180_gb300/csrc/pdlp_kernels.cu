@@ -132,24 +132,6 @@ __device__ __forceinline__ void sum_partials(const double *part, int count, doub
 
 // ---------------------------------------------------------------- IEEE-bit helpers
 
-// Order-preserving integer key of an IEEE double (sign-magnitude -> two's
-// complement): a < b  <=>  key(a) < key(b) for non-NaN values (with -0 < +0).
-__device__ __forceinline__ long long dkey(double v) {
-  const long long b = __double_as_longlong(v);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-
-// proj onto [l, u] with integer compares, keeping the clamp off the FP64 pipe.
-// A NaN input maps to u (positive NaN) or l (negative NaN); with infinite
-// bounds it becomes +-inf and the step test flags it.
-__device__ __forceinline__ double clamp_bits(double v, double l, double u) {
-  const long long kv = dkey(v);
-  double r = v;
-  if (kv < dkey(l)) r = l;
-  if (kv > dkey(u)) r = u;
-  return r;
-}
-
 // ---------------------------------------------------------------- tile SpMV
 
 constexpr int CHAIN_MAX = 8;

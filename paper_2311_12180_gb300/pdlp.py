@@ -87,7 +87,7 @@ EXPORTS = (
     "pdlp_run_periods", "pdlp_poll", "pdlp_finish", "pdlp_time_kernels", "pdlp_kernel_count",
     "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
     "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error", "pdlp_scale_device_noalloc",
-    "pdlp_batch_create", "pdlp_batch_solve", "pdlp_batch_info", "pdlp_batch_lanes", "pdlp_batch_destroy",
+    "pdlp_batch_create", "pdlp_batch_solve", "pdlp_batch_info", "pdlp_batch_lanes", "pdlp_batch_times", "pdlp_batch_destroy",
     "pdlp_mlp_create", "pdlp_mlp_param_count", "pdlp_mlp_set_params", "pdlp_mlp_get_params", "pdlp_mlp_set_data",
     "pdlp_mlp_train", "pdlp_mlp_predict", "pdlp_mlp_gradients", "pdlp_mlp_stats", "pdlp_mlp_destroy",
 )
@@ -123,6 +123,8 @@ class pdlp_batch_stats(C.Structure):
         ("device_bytes", C.c_size_t),
         ("resident", C.c_int32),
         ("resident_max_bytes", C.c_int32),
+        ("team_lps", C.c_int32),
+        ("team_size", C.c_int32),
     ]
 
 _lib = None
@@ -192,6 +194,8 @@ def lib():
     L.pdlp_batch_info.restype = C.c_int
     L.pdlp_batch_lanes.argtypes = [vp, vp, vp]
     L.pdlp_batch_lanes.restype = C.c_int
+    L.pdlp_batch_times.argtypes = [vp, vp, vp]
+    L.pdlp_batch_times.restype = C.c_int
     L.pdlp_batch_destroy.argtypes = [vp]
     L.pdlp_batch_destroy.restype = None
     L.pdlp_mlp_create.argtypes = [P(vp), i32, i32, i32, i32, vp]
@@ -456,6 +460,13 @@ class BatchSolver:
         s = pdlp_batch_stats()
         _check(lib().pdlp_batch_info(self.h, C.byref(s)))
         return {f: getattr(s, f) for f, _ in pdlp_batch_stats._fields_}
+
+    def times(self):
+        """(start, end) seconds of each LP in the last solve, after the earliest start."""
+        a = np.zeros(self.count)
+        b = np.zeros(self.count)
+        _check(lib().pdlp_batch_times(self.h, _ptr(a), _ptr(b)))
+        return a, b
 
     def lanes(self):
         a = np.zeros(self.count, dtype=np.int32)

@@ -126,3 +126,7 @@ def test_mlp_create_rejects_bad_dims_on_host(L, dims):
     h = C.c_void_p()
     assert L.pdlp_mlp_create(C.byref(h), *dims, None) == P.ERR_INVALID
     assert not h.value
+
+
+def test_batch_times_rejects_null(L):
+    assert L.pdlp_batch_times(None, None, None) == P.ERR_INVALID

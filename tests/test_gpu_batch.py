@@ -17,6 +17,8 @@ def batch():
     # edge cases: all equalities, all inequalities, no constraint rows
     lps.append(lpgen.tiny_lp(31, m_eq=60, m_ineq=0, n=150))
     lps.append(lpgen.tiny_lp(32, m_eq=0, m_ineq=60, n=150))
+    # large enough (72k nonzeros) to be solved by a team of CTAs (threshold 32768)
+    lps.append(lpgen.tiny_lp(41, m_eq=600, m_ineq=600, n=3000, density=0.02))
     rng = np.random.default_rng(9)
     n = 40
     lps.append(lpgen.LP(m=0, n=n, n_eq=0, c=rng.standard_normal(n), row_ptr=np.zeros(1, np.int32),
@@ -30,6 +32,7 @@ def test_batch_solutions_match_oracle(batch):
         xs, ys, st, it = b.solve(tol=1e-6)
         # both schedules run: LPs solved from shared memory and from global memory
         assert 0 < b.stats()["resident"] < len(batch)
+        assert b.stats()["team_lps"] == 1
         stats = b.stats()
         lk, lt = b.lanes()
     assert stats["count"] == len(batch) and stats["entries_per_lane"] in (2.0, 4.0, 8.0, 16.0)
@@ -82,3 +85,16 @@ def test_batch_matches_single_instance_solver(batch):
             x, y, s1, i1 = s.solve(tol=1e-8)
         assert st[i] == s1 == P.OPTIMAL
         assert float(lp.c @ xs[i]) == pytest.approx(float(lp.c @ x), rel=1e-6)
+
+
+def test_batch_times_describe_the_schedule(batch):
+    import time
+
+    with P.BatchSolver(batch) as b:
+        b.solve(tol=1e-6, max_iter=2)
+        t = time.perf_counter()
+        b.solve(tol=1e-6)
+        wall = time.perf_counter() - t
+        t0, t1 = b.times()
+    assert t0.min() == 0.0
+    assert np.all(t1 >= t0) and t1.max() <= wall
