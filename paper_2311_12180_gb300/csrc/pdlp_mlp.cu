@@ -7,8 +7,8 @@
 // memory by TMA (128-byte swizzle, a 3-stage mbarrier ring), multiplied by
 // tcgen05.mma (kind::f16, M = N = 128 per CTA, K = 16 per instruction)
 // issued by one thread, accumulated in FP32 in tensor memory and read back
-// with tcgen05.ld by the CTA's four warps (one TMEM lane quarter each) for a
-// fused epilogue.  Because both operands must have K contiguous, every
+// with tcgen05.ld by the CTA's eight warps (a TMEM lane quarter and half of
+// the columns each) for a fused epilogue.  Because both operands must have K contiguous, every
 // tensor that enters a GEMM once as "rows x K" and once as "K x rows" is kept
 // in both layouts: the epilogues and elementwise kernels that produce an
 // activation or gradient write its transpose too (coalesced across the warp,
@@ -45,6 +45,7 @@ using bf16 = __nv_bfloat16;
 // ---------------------------------------------------------------- tcgen05 GEMM
 
 constexpr int TBM = 128, TBN = 128, TBK = 64, STAGES = 3;
+constexpr int GEMM_THREADS = 256;  // 8 warps: warp w reads TMEM lanes 32 (w % 4).., columns 64 (w / 4)..
 constexpr int A_BYTES = TBM * TBK * 2, B_BYTES = TBN * TBK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int GEMM_SMEM = STAGES * STAGE_BYTES + 1024 + 128;  // + alignment slack + barriers
 constexpr uint32_t TMEM_COLS = TBN;                           // FP32 accumulator: 128 lanes x 128 columns
@@ -129,10 +130,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 // [z kchunk, min(K, (z + 1) kchunk)) (kchunk a multiple of TBK), A and Bt
 // described by the tensor maps (box TBK x 128, 128-byte swizzle).  Thread 0
 // issues the TMA loads and the MMAs; the finished tile passes through
-// epi(m, n, value, split) for m < M, n < N, then epi.finish() runs in every
-// thread.  A wait that exceeds its limit sets *err and skips the epilogue.
+// epi.chunk(m, n, values, count, split) -- 16 consecutive columns n.. of
+// row m, count of them inside the matrix -- for m < M, then epi.finish()
+// runs in every thread.  A wait that exceeds its limit sets *err and skips the epilogue.
 template <class Epi>
-__global__ void __launch_bounds__(128) k_tc_gemm(const __grid_constant__ CUtensorMap ma,
+__global__ void __launch_bounds__(GEMM_THREADS) k_tc_gemm(const __grid_constant__ CUtensorMap ma,
                                                  const __grid_constant__ CUtensorMap mb, int M, int N, int K,
                                                  int kchunk, Epi epi, int *err) {
   extern __shared__ unsigned char smem_raw[];
@@ -203,16 +205,17 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const __grid_constant__ CUtenso
   if (!ok) atomicExch(err, GEMM_ERR_DONE);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   // a split with an empty K range never wrote its accumulator: its tile is zero
-  const int row = m0 + warp * 32 + lane;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = m0 + quarter * 32 + lane;
 #pragma unroll 1
-  for (int c0 = 0; c0 < TBN && ok; c0 += 16) {
+  for (int c0 = half * (TBN / 2); c0 < (half + 1) * (TBN / 2) && ok; c0 += 16) {
     float v[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-    if (row < M) {
+    tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+    if (!nk) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j)
-        if (n0 + c0 + j < N) epi(row, n0 + c0 + j, nk ? v[j] : 0.0f, (int)blockIdx.z);
+      for (int j = 0; j < 16; ++j) v[j] = 0.0f;
     }
+    if (row < M && n0 + c0 < N) epi.chunk(row, n0 + c0, v, min(16, N - n0 - c0), (int)blockIdx.z);
   }
   epi.finish();
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -221,20 +224,57 @@ __global__ void __launch_bounds__(128) k_tc_gemm(const __grid_constant__ CUtenso
 }
 
 // ---------------------------------------------------------------- epilogues
+//
+// Each thread holds 16 consecutive columns of one row.  Row-major outputs are
+// written with 16-byte vector stores when the row stride and base allow it
+// (`vec`, decided on the host), transposed outputs element by element (the
+// 32 lanes of a warp hold 32 consecutive rows, so those stores coalesce).
+
+__device__ __forceinline__ void st16_f32(float *p, const float (&v)[16]) {
+  float4 *q = reinterpret_cast<float4 *>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) q[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+}
+__device__ __forceinline__ void ld16_f32(const float *p, float (&v)[16]) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 a = q[k];
+    v[4 * k] = a.x;
+    v[4 * k + 1] = a.y;
+    v[4 * k + 2] = a.z;
+    v[4 * k + 3] = a.w;
+  }
+}
+__device__ __forceinline__ void st16_bf16(bf16 *p, const bf16 (&h)[16]) {
+  uint4 *q = reinterpret_cast<uint4 *>(p);
+  const uint4 *src = reinterpret_cast<const uint4 *>(h);
+  q[0] = src[0];
+  q[1] = src[1];
+}
 
 struct EpiBase {
   __device__ __forceinline__ void finish() {}
 };
-// hidden layer: H = bf16(relu(z + b)), stored as H (rows x hidden) and H'
+// hidden layer: H = bf16(relu(z + b)), stored as H (rows x hidden, ld a
+// multiple of 8: vector stores) and H'
 struct EpiHidden : EpiBase {
   const float *bias;
   bf16 *out, *outT;
   int ld, ldT;
-  __device__ __forceinline__ void operator()(int m, int n, float v, int) const {
-    const float z = v + bias[n];
-    const bf16 h = __float2bfloat16(z > 0.0f ? z : 0.0f);
-    out[(size_t)m * ld + n] = h;
-    outT[(size_t)n * ldT + m] = h;
+  __device__ __forceinline__ void chunk(int m, int n, const float (&v)[16], int cnt, int) const {
+    __align__(16) bf16 h[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float z = j < cnt ? v[j] + bias[n + j] : 0.0f;
+      h[j] = __float2bfloat16(z > 0.0f ? z : 0.0f);
+    }
+    if (cnt == 16) {
+      st16_bf16(out + (size_t)m * ld + n, h);
+    } else {
+      for (int j = 0; j < cnt; ++j) out[(size_t)m * ld + n + j] = h[j];
+    }
+    for (int j = 0; j < cnt; ++j) outT[(size_t)(n + j) * ldT + m] = h[j];
   }
 };
 // output layer for prediction: Y = z + b (standardised units)
@@ -242,11 +282,22 @@ struct EpiOut : EpiBase {
   const float *bias;
   float *y;
   int ld;
-  __device__ __forceinline__ void operator()(int m, int n, float v, int) const { y[(size_t)m * ld + n] = v + bias[n]; }
+  bool vec;
+  __device__ __forceinline__ void chunk(int m, int n, const float (&v)[16], int cnt, int) const {
+    float o[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) o[j] = j < cnt ? v[j] + bias[n + j] : 0.0f;
+    if (vec && cnt == 16) {
+      st16_f32(y + (size_t)m * ld + n, o);
+    } else {
+      for (int j = 0; j < cnt; ++j) y[(size_t)m * ld + n + j] = o[j];
+    }
+  }
 };
 // output layer for training, with the loss fused: d = z + b - (t - mu) / sigma,
 // dY = 2 d / (B N) in FP32 (for the bias gradient) and as BF16 GEMM operand
-// in both layouts; each CTA writes its partial sum of d^2 (fixed order).
+// in both layouts; each CTA writes its partial sum of d^2 (fixed order:
+// FP32 over a thread's 16 columns, FP64 across chunks and threads).
 struct EpiLoss {
   const float *bias, *t, *mu, *sigma;
   float *dy;
@@ -254,39 +305,79 @@ struct EpiLoss {
   double *part;
   float scale;
   int ldt, ldh, ldT;
+  bool vec;  // t / dy rows allow 16-byte accesses
   double acc;
-  __device__ __forceinline__ void operator()(int m, int n, float v, int) {
-    const float d = v + bias[n] - (t[(size_t)m * ldt + n] - mu[n]) / sigma[n];
-    acc += (double)d * d;
-    const float g = scale * d;
-    dy[(size_t)m * ldt + n] = g;
-    const bf16 gh = __float2bfloat16(g);
-    dyh[(size_t)m * ldh + n] = gh;
-    dyhT[(size_t)n * ldT + m] = gh;
+  __device__ __forceinline__ void chunk(int m, int n, const float (&v)[16], int cnt, int) {
+    float tv[16];
+    if (vec && cnt == 16) {
+      ld16_f32(t + (size_t)m * ldt + n, tv);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) tv[j] = j < cnt ? t[(size_t)m * ldt + n + j] : 0.0f;
+    }
+    float g[16];
+    __align__(16) bf16 gh[16];
+    float sq = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      float d = 0.0f;
+      if (j < cnt) d = v[j] + bias[n + j] - (tv[j] - mu[n + j]) / sigma[n + j];
+      sq = fmaf(d, d, sq);
+      g[j] = scale * d;
+      gh[j] = __float2bfloat16(g[j]);
+    }
+    acc += (double)sq;
+    if (vec && cnt == 16) {
+      st16_f32(dy + (size_t)m * ldt + n, g);
+      st16_bf16(dyh + (size_t)m * ldh + n, gh);
+    } else {
+      for (int j = 0; j < cnt; ++j) {
+        dy[(size_t)m * ldt + n + j] = g[j];
+        dyh[(size_t)m * ldh + n + j] = gh[j];
+      }
+    }
+    for (int j = 0; j < cnt; ++j) dyhT[(size_t)(n + j) * ldT + m] = gh[j];
   }
   __device__ __forceinline__ void finish() {
-    __shared__ double red[4];
+    __shared__ double red[GEMM_THREADS / 32];
     double s = acc;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x == 0) part[blockIdx.y * gridDim.x + blockIdx.x] = ((red[0] + red[1]) + red[2]) + red[3];
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < GEMM_THREADS / 32; ++w) t += red[w];
+      part[blockIdx.y * gridDim.x + blockIdx.x] = t;
+    }
   }
 };
 // plain FP32 store (weight gradients, dH1)
 struct EpiStore : EpiBase {
   float *out;
   int ld;
-  __device__ __forceinline__ void operator()(int m, int n, float v, int) const { out[(size_t)m * ld + n] = v; }
+  bool vec;
+  __device__ __forceinline__ void chunk(int m, int n, const float (&v)[16], int cnt, int) const {
+    if (vec && cnt == 16) {
+      st16_f32(out + (size_t)m * ld + n, v);
+    } else {
+      for (int j = 0; j < cnt; ++j) out[(size_t)m * ld + n + j] = v[j];
+    }
+  }
 };
 // split-K partial sums, summed later in split order
 struct EpiPartial : EpiBase {
   float *part;
   int ld;
   size_t stride;
-  __device__ __forceinline__ void operator()(int m, int n, float v, int s) const {
-    part[s * stride + (size_t)m * ld + n] = v;
+  bool vec;
+  __device__ __forceinline__ void chunk(int m, int n, const float (&v)[16], int cnt, int s) const {
+    float *p = part + s * stride + (size_t)m * ld + n;
+    if (vec && cnt == 16) {
+      st16_f32(p, v);
+    } else {
+      for (int j = 0; j < cnt; ++j) p[j] = v[j];
+    }
   }
 };
 
@@ -335,11 +426,20 @@ __global__ void k_input_bf16(const float *__restrict__ x, int count, int in_dim,
     xb[(i / in_dim) * ldx + i % in_dim] = __float2bfloat16(x[i]);
 }
 
+// mean of the per-CTA partial sums (one block of 256 threads: strided sums,
+// then a fixed tree)
 __global__ void k_loss_finish(const double *__restrict__ part, int nparts, size_t count, float *__restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nparts; ++i) s += part[i];
-    *out = (float)(s / (double)count);
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) s += part[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    *out = (float)(t / (double)count);
   }
 }
 
@@ -480,6 +580,9 @@ bool make_map(CUtensorMap *m, const bf16 *base, int rows, int cols, int ld) {
 
 int pad8(int x) { return (x + 7) / 8 * 8; }
 
+// rows of ld floats starting at p allow 16-byte accesses at 16-column offsets
+bool vec4(const float *p, int ld) { return reinterpret_cast<uintptr_t>(p) % 16 == 0 && ld % 4 == 0; }
+
 }  // namespace
 
 struct pdlp_mlp {
@@ -545,7 +648,7 @@ int gemm(pdlp_mlp *Mn, int M, int N, int K, int splits, const bf16 *A, int lda, 
     return set_error(PDLP_ERR_CUDA, "MLP GEMM: cuTensorMapEncodeTiled unavailable or rejected the operand");
   const int kchunk = ((K + splits - 1) / splits + TBK - 1) / TBK * TBK;
   dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, splits);
-  k_tc_gemm<Epi><<<grid, 128, GEMM_SMEM, Mn->stream>>>(ma, mb, M, N, K, kchunk, epi, Mn->err);
+  k_tc_gemm<Epi><<<grid, GEMM_THREADS, GEMM_SMEM, Mn->stream>>>(ma, mb, M, N, K, kchunk, epi, Mn->err);
   MCK(cudaGetLastError());
   return PDLP_OK;
 }
@@ -585,27 +688,27 @@ int forward_backward(pdlp_mlp *M, int B) {
   const size_t BO = (size_t)B * M->out, BH = (size_t)B * M->hid;
   const int tiles = ((M->out + TBN - 1) / TBN) * ((B + TBM - 1) / TBM);
   EpiLoss el{M->p + M->ob3, M->tb, M->mu, M->sigma, M->dy, M->dyh, M->dyhT, M->lpart, 2.0f / (float)BO,
-             M->out, M->ldo, M->ldb, 0.0};
+             M->out, M->ldo, M->ldb, vec4(M->tb, M->out) && vec4(M->dy, M->out), 0.0};
   rc = gemm(M, B, M->out, M->hid, 1, M->h2, M->ldh, M->w3t, M->ldh, el);
   if (rc) return rc;
-  k_loss_finish<<<1, 32, 0, s>>>(M->lpart, tiles, BO, M->loss_dev);
+  k_loss_finish<<<1, 256, 0, s>>>(M->lpart, tiles, BO, M->loss_dev);
   // output layer: gW3 = H2' dY, gb3 = column sums of dY, dH2 = dY W3'
-  rc = gemm(M, M->hid, M->out, B, 1, M->h2T, M->ldb, M->dyhT, M->ldb, EpiStore{{}, M->g + M->oW3, M->out});
+  rc = gemm(M, M->hid, M->out, B, 1, M->h2T, M->ldb, M->dyhT, M->ldb, EpiStore{{}, M->g + M->oW3, M->out, vec4(M->g + M->oW3, M->out)});
   if (rc) return rc;
   k_colsum<<<grid1(M->out), 256, 0, s>>>(M->dy, B, M->out, M->g + M->ob3);
-  rc = gemm(M, B, M->hid, M->out, M->splits, M->dyh, M->ldo, M->w3, M->ldo, EpiPartial{{}, M->part, M->hid, BH});
+  rc = gemm(M, B, M->hid, M->out, M->splits, M->dyh, M->ldo, M->w3, M->ldo, EpiPartial{{}, M->part, M->hid, BH, vec4(M->part, M->hid) && BH % 4 == 0});
   if (rc) return rc;
   k_splitk_relu_grad<<<grid1(BH), 256, 0, s>>>(M->part, M->splits, B, M->hid, M->h2, M->ldh, M->dz2, M->dz2h,
                                                M->dz2hT, M->ldb);
   // second layer
-  rc = gemm(M, M->hid, M->hid, B, 1, M->h1T, M->ldb, M->dz2hT, M->ldb, EpiStore{{}, M->g + M->oW2, M->hid});
+  rc = gemm(M, M->hid, M->hid, B, 1, M->h1T, M->ldb, M->dz2hT, M->ldb, EpiStore{{}, M->g + M->oW2, M->hid, vec4(M->g + M->oW2, M->hid)});
   if (rc) return rc;
   k_colsum<<<grid1(M->hid), 256, 0, s>>>(M->dz2, B, M->hid, M->g + M->ob2);
-  rc = gemm(M, B, M->hid, M->hid, 1, M->dz2h, M->ldh, M->w2, M->ldh, EpiStore{{}, M->dh1, M->hid});
+  rc = gemm(M, B, M->hid, M->hid, 1, M->dz2h, M->ldh, M->w2, M->ldh, EpiStore{{}, M->dh1, M->hid, vec4(M->dh1, M->hid)});
   if (rc) return rc;
   k_relu_grad<<<grid1(BH), 256, 0, s>>>(M->dh1, B, M->hid, M->h1, M->ldh, M->dz1, M->dz1hT, M->ldb);
   // first layer
-  rc = gemm(M, M->in, M->hid, B, 1, M->xbT, M->ldb, M->dz1hT, M->ldb, EpiStore{{}, M->g + M->oW1, M->hid});
+  rc = gemm(M, M->in, M->hid, B, 1, M->xbT, M->ldb, M->dz1hT, M->ldb, EpiStore{{}, M->g + M->oW1, M->hid, vec4(M->g + M->oW1, M->hid)});
   if (rc) return rc;
   k_colsum<<<grid1(M->hid), 256, 0, s>>>(M->dz1, B, M->hid, M->g + M->ob1);
   MCK(cudaGetLastError());
@@ -840,7 +943,7 @@ int pdlp_mlp_predict(pdlp_mlp *M, int32_t count, const float *X, float *Y) {
     k_input_bf16<<<grid1((size_t)B * M->in), 256, 0, s>>>(M->xin, B, M->in, M->xb, M->ldi);
     int rc = forward_hidden(M, B);
     if (!rc)
-      rc = gemm(M, B, M->out, M->hid, 1, M->h2, M->ldh, M->w3t, M->ldh, EpiOut{{}, M->p + M->ob3, M->y, M->out});
+      rc = gemm(M, B, M->out, M->hid, 1, M->h2, M->ldh, M->w3t, M->ldh, EpiOut{{}, M->p + M->ob3, M->y, M->out, vec4(M->y, M->out)});
     if (rc) return rc;
     k_unstandardize<<<grid1((size_t)B * M->out), 256, 0, s>>>(M->y, (size_t)B * M->out, M->out, M->mu, M->sigma,
                                                                M->dy);
