@@ -6,7 +6,7 @@ parametric case).  The MLP theta -> (x, y) is trained by the library's own
 kernels on 2000 solutions computed by the batched solver; 200 held-out
 instances are then solved to 1e-6 from the cold start, from the MLP's
 prediction and from the mean training solution.  Measured on a GB300 with
-this seed: median iterations 2112 cold, 1920 MLP (-10 %), 2112 mean start."""
+this seed: median iterations 2112 cold, 1856 MLP (-12 %), 2048 mean start."""
 
 import numpy as np
 import pytest
