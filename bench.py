@@ -128,6 +128,20 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def aggregate_replicas(ms: float, iters: float, pg=None, device: str = "cpu"):
+    """Whole-job numbers of independent replicas: the slowest rank's time
+    (max) and the iterations of all ranks (sum); pg is torch.distributed or
+    None for one process."""
+    import torch
+
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=device)
+    it_t = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    if pg is not None:
+        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
+        pg.all_reduce(it_t, op=pg.ReduceOp.SUM)
+    return float(ms_t.item()), float(it_t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -470,13 +484,7 @@ def main():
     iters = k1 - k0
     if st1 != -1:
         raise SystemExit("solve ended inside the timed region (status %d): timing invalid" % st1)
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    it_t = torch.tensor([float(iters)], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(ms_t, op=pg.ReduceOp.MAX)
-        pg.all_reduce(it_t, op=pg.ReduceOp.SUM)
-    ms_max = float(ms_t.item())
-    total_iters = float(it_t.item())
+    ms_max, total_iters = aggregate_replicas(ms, iters, pg, "cuda")
     value = total_iters / (ms_max / 1000.0)
 
     # ---- per-kernel event timing (same workload, direct launches) ----
