@@ -44,13 +44,14 @@ if ROOT not in sys.path:
 METRIC = "PDHG iters/s"
 UNIT = "iters/s"
 
-# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes)
-# of the step kernels from one ncu --set full capture of the 1e6 x 2e6 LP
-# (FP64 values), keyed by (kernel, sha256 prefix of the kernel source it was
-# taken on, value bits); reported as null once the source has changed.
+# Per-launch DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes,
+# mean of two launches) of the step kernels from one ncu capture of the
+# 1e6 x 2e6 LP (FP64 values), keyed by (kernel, sha256 prefix of the kernel
+# source it was taken on, value bits); reported as null once the source has
+# changed.
 NCU_TRAFFIC = {
-    ("k_primal", "8a6336855fe4b3a7", 64): 337.193472e6 + 23.641344e6,
-    ("k_dual", "8a6336855fe4b3a7", 64): 292.569600e6 + 7.142400e6,
+    ("k_primal", "a66a5c062080edf4", 64): (337248000 + 23312896 + 337206784 + 20641024) / 2,
+    ("k_dual", "a66a5c062080edf4", 64): (292520448 + 4651776 + 292531968 + 2754304) / 2,
 }
 
 
