@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "pdlp.h"
+#include "pdlp_host.h"
 #include "pdlp_internal.cuh"
 
 namespace pdlp {
@@ -1155,44 +1156,44 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   } while (0)
   BCKS(cudaMemsetAsync(b->arena, 0, b->arena_bytes, st));
   // per LP: K straight from the caller's arrays, K' by a stable counting sort
-  // into one reused host buffer, and the input vectors into their blocks
+  // into a host buffer of the worker thread that handles the LP, and the
+  // input vectors into their blocks.  The sources are pageable: each copy has
+  // read its source when the call returns, so a buffer is reused at once.
   {
-    long long max_n = 1, max_nnz = 1;
+    long long max_n = 1, max_nnz = 1, tot_nnz = 0;
     for (int i = 0; i < count; ++i) {
       max_n = std::max<long long>(max_n, lps[i].n);
       max_nnz = std::max<long long>(max_nnz, lps[i].row_ptr[lps[i].m]);
+      tot_nnz += lps[i].row_ptr[lps[i].m];
     }
-    std::vector<int> tp((size_t)max_n + 1), ti((size_t)max_nnz), fill((size_t)max_n);
-    std::vector<double> tv((size_t)max_nnz);
-    for (int i = 0; i < count; ++i) {
-      const pdlp_lp &L = lps[i];
-      const Inst &I = b->h_inst[i];
-      const long long nnz = L.row_ptr[L.m];
-      std::fill(tp.begin(), tp.begin() + L.n + 1, 0);
-      for (long long e = 0; e < nnz; ++e) tp[L.col_idx[e] + 1]++;
-      for (int j = 0; j < L.n; ++j) tp[j + 1] += tp[j];
-      std::copy(tp.begin(), tp.begin() + L.n, fill.begin());
-      for (int r = 0; r < L.m; ++r)
-        for (int e = L.row_ptr[r]; e < L.row_ptr[r + 1]; ++e) {
-          const int pos = fill[L.col_idx[e]]++;
-          ti[pos] = r;
-          tv[pos] = L.val[e];
-        }
-      // pageable sources: each copy has read its source when the call returns
-      BCKS(cudaMemcpyAsync((void *)(b->A.kptr + I.kp), L.row_ptr, 4 * (size_t)(L.m + 1), cudaMemcpyHostToDevice, st));
-      BCKS(cudaMemcpyAsync((void *)(b->A.tptr + I.tp), tp.data(), 4 * (size_t)(L.n + 1), cudaMemcpyHostToDevice, st));
-      if (nnz) {
-        BCKS(cudaMemcpyAsync((void *)(b->A.kidx + I.ke), L.col_idx, 4 * (size_t)nnz, cudaMemcpyHostToDevice, st));
-        BCKS(cudaMemcpyAsync(b->A.kval + I.ke, L.val, 8 * (size_t)nnz, cudaMemcpyHostToDevice, st));
-        BCKS(cudaMemcpyAsync((void *)(b->A.tidx + I.te), ti.data(), 4 * (size_t)nnz, cudaMemcpyHostToDevice, st));
-        BCKS(cudaMemcpyAsync(b->A.tval + I.te, tv.data(), 8 * (size_t)nnz, cudaMemcpyHostToDevice, st));
+    const int T = std::min(host_threads(tot_nnz), count);
+    std::vector<cudaError_t> errs(T, cudaSuccess);
+    parallel_for(T, [&](int w) {
+      std::vector<int> tp((size_t)max_n + 1), ti((size_t)max_nnz);
+      std::vector<double> tv((size_t)max_nnz);
+      cudaError_t e = cudaSetDevice(b->device);
+      for (int i = w; i < count && e == cudaSuccess; i += T) {
+        const pdlp_lp &L = lps[i];
+        const Inst &I = b->h_inst[i];
+        const long long nnz = L.row_ptr[L.m];
+        csr_transpose(L.m, L.n, L.row_ptr, L.col_idx, L.val, tp.data(), ti.data(), tv.data());
+        auto cp = [&](void *dst, const void *src, size_t bytes) {
+          if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+        };
+        cp((void *)(b->A.kptr + I.kp), L.row_ptr, 4 * (size_t)(L.m + 1));
+        cp((void *)(b->A.tptr + I.tp), tp.data(), 4 * (size_t)(L.n + 1));
+        cp((void *)(b->A.kidx + I.ke), L.col_idx, 4 * (size_t)nnz);
+        cp(b->A.kval + I.ke, L.val, 8 * (size_t)nnz);
+        cp((void *)(b->A.tidx + I.te), ti.data(), 4 * (size_t)nnz);
+        cp(b->A.tval + I.te, tv.data(), 8 * (size_t)nnz);
+        cp(b->A.vm + I.om + (long long)VM_Q0 * L.m, L.q, 8 * (size_t)L.m);
+        cp(b->A.vn + I.on + (long long)VN_C0 * L.n, L.c, 8 * (size_t)L.n);
+        cp(b->A.vn + I.on + (long long)VN_L0 * L.n, L.l, 8 * (size_t)L.n);
+        cp(b->A.vn + I.on + (long long)VN_U0 * L.n, L.u, 8 * (size_t)L.n);
       }
-      if (L.m) BCKS(cudaMemcpyAsync(b->A.vm + I.om + (long long)VM_Q0 * L.m, L.q, 8 * (size_t)L.m, cudaMemcpyHostToDevice, st));
-      BCKS(cudaMemcpyAsync(b->A.vn + I.on + (long long)VN_C0 * L.n, L.c, 8 * (size_t)L.n, cudaMemcpyHostToDevice, st));
-      BCKS(cudaMemcpyAsync(b->A.vn + I.on + (long long)VN_L0 * L.n, L.l, 8 * (size_t)L.n, cudaMemcpyHostToDevice, st));
-      BCKS(cudaMemcpyAsync(b->A.vn + I.on + (long long)VN_U0 * L.n, L.u, 8 * (size_t)L.n, cudaMemcpyHostToDevice, st));
-      BCKS(cudaStreamSynchronize(st));  // tp / ti / tv are reused by the next LP
-    }
+      errs[w] = e;
+    });
+    for (cudaError_t e : errs) BCKS(e);
   }
   BCKS(cudaMemcpyAsync(b->d_order, order.data(), 4 * count, cudaMemcpyHostToDevice, st));
   BCKS(cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, st));

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "pdlp.h"
+#include "pdlp_host.h"
 #include "pdlp_internal.cuh"
 
 using namespace pdlp;
@@ -122,9 +124,22 @@ int validate(int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t 
     if (rp[i + 1] < rp[i]) return fail(PDLP_ERR_INVALID, "row_ptr is not non-decreasing at row " + std::to_string(i));
   const int64_t nnz = rp[m];
   if (nnz > 0 && (!ci || !v)) return fail(PDLP_ERR_INVALID, "null col_idx / val");
-  for (int64_t e = 0; e < nnz; ++e) {
-    if (ci[e] < 0 || ci[e] >= n) return fail(PDLP_ERR_INVALID, "col_idx out of range at nonzero " + std::to_string(e));
-    if (!std::isfinite(v[e])) return fail(PDLP_ERR_INVALID, "non-finite matrix value at nonzero " + std::to_string(e));
+  {
+    // first bad nonzero, searched in parallel chunks (the report names the first one)
+    const int T = host_threads(nnz);
+    std::vector<int64_t> first(T, nnz);
+    parallel_for(T, [&](int t) {
+      for (int64_t e = nnz * t / T; e < nnz * (t + 1) / T; ++e)
+        if (ci[e] < 0 || ci[e] >= n || !std::isfinite(v[e])) {
+          first[t] = e;
+          break;
+        }
+    });
+    const int64_t e = *std::min_element(first.begin(), first.end());
+    if (e < nnz) {
+      if (ci[e] < 0 || ci[e] >= n) return fail(PDLP_ERR_INVALID, "col_idx out of range at nonzero " + std::to_string(e));
+      return fail(PDLP_ERR_INVALID, "non-finite matrix value at nonzero " + std::to_string(e));
+    }
   }
   for (int32_t j = 0; j < n; ++j) {
     if (!std::isfinite(c[j])) return fail(PDLP_ERR_INVALID, "non-finite c at " + std::to_string(j));
@@ -225,17 +240,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   // ---- host: K' by a stable counting sort, tile schedules ----
   std::vector<int32_t> tp((size_t)n + 1, 0), ti((size_t)nnz);
   std::vector<double> tv((size_t)nnz);
-  for (int64_t e = 0; e < nnz; ++e) tp[col_idx[e] + 1]++;
-  for (int32_t j = 0; j < n; ++j) tp[j + 1] += tp[j];
-  {
-    std::vector<int32_t> fill(tp.begin(), tp.end() - 1);
-    for (int32_t i = 0; i < m; ++i)
-      for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-        const int32_t pos = fill[col_idx[e]]++;
-        ti[pos] = i;
-        tv[pos] = val[e];
-      }
-  }
+  csr_transpose(m, n, row_ptr, col_idx, val, tp.data(), ti.data(), tv.data());
   std::vector<int2> tilesK = build_tiles(row_ptr, m);
   std::vector<int2> tilesT = build_tiles(tp.data(), n);
   double qn = 0.0, cn = 0.0;
