@@ -83,7 +83,11 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        import tempfile
+
+        # the raw samples; BENCH_CLOCKS_CSV keeps them at a chosen path
+        self.path = os.environ.get("BENCH_CLOCKS_CSV") or os.path.join(tempfile.gettempdir(),
+                                                                         "pdlp_bench_clocks_%d.csv" % os.getpid())
 
     def __enter__(self):
         try:
