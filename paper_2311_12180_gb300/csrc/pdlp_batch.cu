@@ -63,22 +63,13 @@ struct Params {
   double tol, theta, eps_zero, beta_suff, beta_nec, beta_art;
   long long max_iter;
   int P, warm;
-  // (k + 2)^-0.3 at pw[k] and (k + 2)^-0.6 at pw[npw + k] for k < npw
+  // Algorithm 2 exponent factors, built once per solve by setup_pow_table
+  // (the same pow() the step test would call): (k + 2)^-0.3 at pw[k] and
+  // (k + 2)^-0.6 at pw[npw + k] for k < npw.  Two FP64 powers per step are
+  // a large part of a small LP's step on GB300's narrow FP64 pipe.
   const double *pw;
   long long npw;
 };
-
-// The Algorithm 2 exponent factors for every step index, computed once per
-// solve by the same pow() the step test would call: each LP then reads two
-// cached values per step instead of evaluating two FP64 powers, whose serial
-// latency on GB300's narrow FP64 pipe is a large part of a small LP's step.
-__global__ void k_pow_table(double *pw, long long count) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
-    const double kk = (double)(i + 2);
-    pw[i] = pow(kk, -0.3);
-    pw[count + i] = pow(kk, -0.6);
-  }
-}
 
 struct Arrays {
   const int *kptr, *kidx, *tptr, *tidx;
@@ -1290,8 +1281,7 @@ int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double t
       b->pw = nullptr;
       b->npw = 0;
       BCK(cudaMalloc(&b->pw, 2 * sizeof(double) * (size_t)need));
-      k_pow_table<<<256, 256, 0, st>>>(b->pw, need);
-      BCK(cudaGetLastError());
+      BCK(setup_pow_table(b->pw, need, st));
       b->npw = need;
     }
     p.pw = b->pw;

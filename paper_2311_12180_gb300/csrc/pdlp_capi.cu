@@ -316,6 +316,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const size_t o_pR3 = L.take(8 * (size_t)s->gridR3 * NV_R3);
   const size_t o_st = L.take(sizeof(DevState)), o_tr = L.take(sizeof(TraceRec) * TRACE_CAP);
   const size_t o_sc = L.take(8 * 8);
+  const long long npw = 1LL << 20;  // exponent factors for the first 2^20 steps (16 MB)
+  const size_t o_pw = L.take(16 * (size_t)npw);
   s->arena_bytes = L.off;
   CKS(cudaMalloc((void **)&s->arena, s->arena_bytes));
   char *A = s->arena;
@@ -381,6 +383,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.partR2 = (double *)(A + o_pR2);
   V.partR3 = (double *)(A + o_pR3);
   V.trace = (TraceRec *)(A + o_tr);
+  V.pw = (const double *)(A + o_pw);
+  V.npw = npw;
 
   s->K = Csr{m, (int32_t)tilesK.size() - 1, s->K_ptr, s->K_idx, s->K_val, s->K_val32, Ktl};
   s->KT = Csr{n, (int32_t)tilesT.size() - 1, s->T_ptr, s->T_idx, s->T_val, s->T_val32, Ttl};
@@ -412,6 +416,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
     CKS(setup_f32(nnz, s->T_val, s->T_val32, st));
   }
   CKS(setup_scalars(m, n, nnz, s->c, s->q, s->K_val, s->d_scal, st));
+  CKS(setup_pow_table((double *)(A + o_pw), npw, st));
   CKS(cudaMemcpyAsync(s->h_scal, s->d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CKS(cudaStreamSynchronize(st));
   const double cc = std::sqrt(s->h_scal[0]), qq = std::sqrt(s->h_scal[1]), kmax = s->h_scal[2];

@@ -95,6 +95,9 @@ struct Vecs {
   double *Kxbar, *ylast, *yout;     // m
   double *partA, *partB, *partR1, *partR2, *partR3;
   TraceRec *trace;
+  // (k + 2)^-0.3 at pw[k] and (k + 2)^-0.6 at pw[npw + k] for k < npw
+  const double *pw;
+  long long npw;
 };
 
 // ---- kernel launchers (pdlp_kernels.cu) ----
@@ -115,7 +118,10 @@ cudaError_t launch_restart(const Vecs &V, DevState *st, int grid, cudaStream_t s
 cudaError_t launch_output(const Vecs &V, DevState *st, cudaStream_t s);
 cudaError_t launch_time_limit(DevState *st, cudaStream_t s);
 int occupancy_grid(int kc, int num_sms);
-cudaError_t kernels_init();  // one-time function attributes (dynamic shared memory)
+cudaError_t kernels_init();
+// Fills the Algorithm 2 exponent-factor table: pw[k] = (k + 2)^-0.3 and
+// pw[count + k] = (k + 2)^-0.6 for k < count (the same pow() the step test calls).
+cudaError_t setup_pow_table(double *pw, long long count, cudaStream_t s);  // one-time function attributes (dynamic shared memory)
 
 // ---- setup kernels (pdlp_setup.cu) ----
 cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32_t *K_idx, double *K_val,

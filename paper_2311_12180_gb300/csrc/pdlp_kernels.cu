@@ -456,14 +456,18 @@ struct DualEpi {
 // Algorithm 2 acceptance test (one thread).  eq. (step-size) with the
 // interaction taken in absolute value; the exponent base counts the step
 // being taken from 1 (k + 2 for k accepted steps so far).
-__device__ void step_test(DevState *st, double dx2, double dy2, double cross) {
+__device__ void step_test(DevState *st, const Vecs &V, double dx2, double dy2, double cross) {
   const double eta = st->eta, omega = st->omega;
   const long long k = st->k;
   const double ia = fabs(cross);
   const double eta_bar = ia > 0.0 ? (omega * dx2 + dy2 / omega) / (2.0 * ia) : CUDART_INF;
   const double kk = (double)(k + 2);
-  const double e1 = (1.0 - pow(kk, -0.3)) * eta_bar;
-  const double e2 = (1.0 + pow(kk, -0.6)) * eta;
+  // the exponent factors come from a table built at create by the same pow()
+  // (two FP64 powers are microseconds of serial latency on GB300's FP64 pipe,
+  // on the critical path of every step)
+  const double p3 = k < V.npw ? V.pw[k] : pow(kk, -0.3), p6 = k < V.npw ? V.pw[V.npw + k] : pow(kk, -0.6);
+  const double e1 = (1.0 - p3) * eta_bar;
+  const double e2 = (1.0 + p6) * eta;
   const double eta_next = e1 < e2 ? e1 : e2;
   st->attempts += 1;
   if (!isfinite(dx2) || !isfinite(dy2) || !isfinite(cross) || isnan(eta_bar) || !(eta_next > 0.0)) {
@@ -512,7 +516,7 @@ __global__ void __launch_bounds__(NT, 4) k_dual(Csr K, Vecs V, DevState *__restr
   if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], sm.red, &sm.flag, tot)) return;
   double dx[1];
   sum_partials<1>(V.partA, V.gridA, sm.red, dx);
-  if (threadIdx.x == 0) step_test(st, dx[0], tot[0], tot[1]);
+  if (threadIdx.x == 0) step_test(st, V, dx[0], tot[0], tot[1]);
 }
 
 // ---------------------------------------------------------------- restart / termination check

@@ -198,6 +198,20 @@ cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0,
   return cudaGetLastError();
 }
 
+__global__ void k_pow_table(double *pw, long long count) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const double kk = (double)(i + 2);
+    pw[i] = pow(kk, -0.3);
+    pw[count + i] = pow(kk, -0.6);
+  }
+}
+
+cudaError_t setup_pow_table(double *pw, long long count, cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  k_pow_table<<<256, 256, 0, s>>>(pw, count);
+  return cudaGetLastError();
+}
+
 }  // namespace pdlp
 
 // ---------------------------------------------------------------------------
