@@ -584,7 +584,10 @@ struct CheckPrimalEpi {
   }
 };
 
-__global__ void __launch_bounds__(NT) k_check_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
+// three CTAs per SM (80 registers): the two-vector tile SpMV then spills ~100
+// bytes, which costs less than running two CTAs per SM (498 vs 560 us on the
+// 1e6 x 2e6 LP)
+__global__ void __launch_bounds__(NT, 3) k_check_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
   __shared__ TileSmem<2> sm;
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur, need_g = st->need_g;
