@@ -54,6 +54,12 @@
  *     Pock-Chambolle alpha = 1: row factor sqrt(sum_j |K~_ij|^(2-alpha)),
  *     column factor sqrt(sum_i |K~_ij|^alpha).
  *
+ * Pins (tests/test_oracle_pins.py) tie every routine to hand-worked
+ * examples, closed forms, brute force or an independent solver, except the
+ * restart constants themselves (beta = 0.2 / 0.8 / 0.36, theta = 0.5, the
+ * check period): those are "parity unpinned" beyond implementing the printed
+ * rules.
+ *
  * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fused multiply-add, so
  * the results are the same on x86-64 and aarch64).
  */
