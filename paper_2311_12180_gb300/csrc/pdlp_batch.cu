@@ -207,15 +207,22 @@ struct Team {
     __syncthreads();
     if (threadIdx.x == 0) {
       int ok = 1;
-      __threadfence();  // this CTA's writes before its arrival
-      const unsigned g = *(volatile unsigned *)gen;
-      if (atomicAdd(cnt, 1u) == TEAM - 1) {
-        *(volatile unsigned *)cnt = 0u;
-        __threadfence();
-        atomicAdd(gen, 1u);
+      unsigned g, old;
+      asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(gen) : "memory");
+      // arrival (acquire-release): the CTA's writes, ordered before this
+      // thread by the barrier above, are released; the last arrival acquires
+      // everything the earlier arrivals released and passes it on through the
+      // generation, which the waiting CTAs acquire
+      asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(cnt) : "memory");
+      if (old == TEAM - 1) {
+        asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(cnt) : "memory");
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(gen) : "memory");
       } else {
         const unsigned long long t0 = gtimer_ns();
-        while (*(volatile unsigned *)gen == g) {
+        for (;;) {
+          unsigned cur;
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(gen) : "memory");
+          if (cur != g) break;
           if (*(volatile int *)abort || gtimer_ns() - t0 > TEAM_WAIT_NS) {
             atomicExch(abort, 1);
             ok = 0;
@@ -223,7 +230,6 @@ struct Team {
           }
         }
       }
-      __threadfence();
       s_ok = ok;
     }
     __syncthreads();
