@@ -285,7 +285,24 @@ def run_batch(args, rank, world):
     xs, ys, st, it = b.solve(tol=tol, max_iter=args.batch_max_iter)
     solve_s = time.perf_counter() - t
     stats = b.stats()
+    t0s, t1s = b.times()
     b.close()
+    nnzs = np.array([lp.nnz for lp in lps])
+    team = nnzs >= stats["team_min_nnz"] if stats["team_lps"] else np.zeros(len(lps), bool)
+    dur = t1s - t0s
+    schedule = {
+        "kernel_span_s": float(t1s.max()),
+        "team_lps": int(team.sum()), "team_size": stats["team_size"],
+        "team_phase_end_s": float(t1s[team].max()) if team.any() else None,
+        "team_seconds": float(dur[team].sum()),
+        "single_cta_seconds": float(dur[~team].sum()),
+        "resident_lps": stats["resident"],
+        "longest": [{"index": int(i), "m": lps[i].m, "n": lps[i].n, "nnz": lps[i].nnz, "iters": int(it[i]),
+                     "team": bool(team[i]), "start_s": float(t0s[i]), "seconds": float(dur[i])}
+                    for i in np.argsort(-dur)[:3]],
+        "last_to_finish": [{"index": int(i), "nnz": lps[i].nnz, "iters": int(it[i]), "team": bool(team[i]),
+                            "start_s": float(t0s[i]), "end_s": float(t1s[i])} for i in np.argsort(-t1s)[:3]],
+    }
     ok = int(np.sum(st == P.OPTIMAL))
     rng = np.random.default_rng(1)
     sample = sorted(rng.choice(len(lps), size=min(args.batch_sample, len(lps)), replace=False).tolist())
@@ -308,7 +325,7 @@ def run_batch(args, rank, world):
                          "status": int(st[i])} for i in np.argsort(-it)[:3]],
             "sequential_single_instance": {"sample": len(sample), "seconds_sample": seq_s,
                                            "estimated_seconds_all": seq_est, "iters_sample": seq_it},
-            "speedup_vs_sequential": seq_est / solve_s}
+            "speedup_vs_sequential": seq_est / solve_s, "schedule": schedule}
     print(json.dumps(line), flush=True)
 
 

@@ -222,6 +222,7 @@ typedef struct {
   int32_t resident_max_bytes; /* shared-memory budget per CTA for such an LP */
   int32_t team_lps;        /* LPs large enough to be solved by a team of CTAs */
   int32_t team_size;       /* CTAs (SMs) per team */
+  int32_t team_min_nnz;    /* nonzeros from which an LP goes to a team */
 } pdlp_batch_stats;
 
 /* Validates every LP (same rules as pdlp_create; errors name the LP), copies

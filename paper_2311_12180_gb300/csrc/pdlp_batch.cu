@@ -1352,6 +1352,7 @@ int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *s) {
   s->resident_max_bytes = RESIDENT_MAX;
   s->team_lps = b->ts.teams > 0 ? b->team_lps : 0;
   s->team_size = TEAM;
+  s->team_min_nnz = (int32_t)TEAM_MIN_NNZ;
   return PDLP_OK;
 }
 

@@ -125,6 +125,7 @@ class pdlp_batch_stats(C.Structure):
         ("resident_max_bytes", C.c_int32),
         ("team_lps", C.c_int32),
         ("team_size", C.c_int32),
+        ("team_min_nnz", C.c_int32),
     ]
 
 _lib = None
