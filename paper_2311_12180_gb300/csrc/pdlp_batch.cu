@@ -142,6 +142,26 @@ __device__ __forceinline__ double allmax(double v, double *red) {
   return v;
 }
 
+// Warp sums of NV values (warps whose values are all zero skip the FP64
+// shuffle tree, as in allsum), written per warp to red[a * NWB + warp];
+// ends with a CTA barrier.
+template <int NV>
+__device__ __forceinline__ void warp_partials(double (&v)[NV], double *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  bool any = false;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) any |= __double_as_longlong(v[a]) != 0;
+  if (__any_sync(0xffffffffu, any)) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = wsum(v[a]);
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) red[a * NWB + wid] = v[a];
+  }
+  __syncthreads();
+}
+
 // Loads of vectors that the solve itself writes.  A team of CTAs (below)
 // reads entries that other SMs wrote inside this kernel, so those loads go
 // to the L2 (ld.cg), past the SM's non-coherent L1.
@@ -171,6 +191,22 @@ struct Solo {
   template <int NV>
   __device__ __forceinline__ bool reduce(double (&v)[NV], double *red) {
     allsum<NV>(v, red);
+    return true;
+  }
+  // The sums (same order as allsum) go to f in thread 0 only; whatever f
+  // writes to red[RED_BCAST..] is visible to every thread on return.  Two
+  // barriers instead of allsum's three plus one for the broadcast.
+  template <int NV, class F>
+  __device__ __forceinline__ bool reduce_apply(double (&v)[NV], double *red, F &&f) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    warp_partials<NV>(v, red);
+    if (wid == 0) {
+      double t[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) t[a] = wsum(lane < NWB ? red[a * NWB + lane] : 0.0);
+      if (lane == 0) f(t);
+    }
+    __syncthreads();
     return true;
   }
 };
@@ -258,6 +294,35 @@ struct Team {
     for (int a = 0; a < NV; ++a) v[a] = red[RED_TEAM + a];
     __syncthreads();
     buf ^= 1;  // the other buffer: a rank rewrites this one only after the next barrier
+    return ok;
+  }
+  // As Solo::reduce_apply over the whole team: every CTA's thread 0 gets the
+  // same team sums (rank order) and runs f.
+  template <int NV, class F>
+  __device__ bool reduce_apply(double (&v)[NV], double *red, F &&f) {
+    static_assert(NV <= 16, "16 slots per rank");
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    warp_partials<NV>(v, red);
+    double *sl = slots + (size_t)buf * TEAM * 16;
+    if (wid == 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const double c = wsum(lane < NWB ? red[a * NWB + lane] : 0.0);
+        if (lane == 0) sl[r * 16 + a] = c;
+      }
+    }
+    const bool ok = sync();
+    if (threadIdx.x == 0) {
+      double t[NV];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        t[a] = 0.0;
+        for (int k = 0; k < TEAM; ++k) t[a] += __ldcg(sl + k * 16 + a);
+      }
+      f(t);
+    }
+    __syncthreads();
+    buf ^= 1;
     return ok;
   }
 };
@@ -563,17 +628,13 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
       rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, xs, sc, dr, part, parts);
     }
     double s3[3] = {pr.dx2, dr.dy2, dr.cross};
-    if (!grp.template reduce<3>(s3, red)) {
-      status = ST_NUMERICAL;
-      break;
-    }
     // ---- step-size test (eq. step-size with |interaction|; exponent base k + 2) ----
-    // one thread evaluates it and broadcasts: the two FP64 powers, run by
-    // every warp, would cost more than the whole iteration of a small LP on
-    // GB300's narrow FP64 pipe
-    if (tid == 0) {
-      const double ia = fabs(s3[2]);
-      const double eb = ia > 0.0 ? (omega * s3[0] + s3[1] / omega) / (2.0 * ia) : CUDART_INF;
+    // one thread evaluates it and broadcasts: the FP64 divisions and powers,
+    // run by every warp, would cost more than the whole iteration of a small
+    // LP on GB300's narrow FP64 pipe
+    auto step = [&](const double (&q3)[3]) {
+      const double ia = fabs(q3[2]);
+      const double eb = ia > 0.0 ? (omega * q3[0] + q3[1] / omega) / (2.0 * ia) : CUDART_INF;
       const double kk = (double)(k + 2);
       const double p3 = k < p.npw ? p.pw[k] : pow(kk, -0.3), p6 = k < p.npw ? p.pw[p.npw + k] : pow(kk, -0.6);
       const double e1 = (1.0 - p3) * eb, e2 = (1.0 + p6) * eta;
@@ -583,11 +644,14 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
       red[RED_BCAST + 1] = en / omega;
       red[RED_BCAST + 2] = en * omega;
       red[RED_BCAST + 3] =
-          (!isfinite(s3[0]) || !isfinite(s3[1]) || !isfinite(s3[2]) || isnan(eb) || !(en > 0.0)) ? 1.0 : 0.0;
+          (!isfinite(q3[0]) || !isfinite(q3[1]) || !isfinite(q3[2]) || isnan(eb) || !(en > 0.0)) ? 1.0 : 0.0;
       red[RED_BCAST + 4] = accept ? 1.0 : 0.0;
       red[RED_BCAST + 5] = accept ? W + eta : W;
+    };
+    if (!grp.template reduce_apply<3>(s3, red, step)) {
+      status = ST_NUMERICAL;
+      break;
     }
-    __syncthreads();
     // (the slots are rewritten only after the next iteration's barriers)
     if (red[RED_BCAST + 3] != 0.0) {
       status = ST_NUMERICAL;
