@@ -231,7 +231,7 @@ typedef struct {
  * a few candidate schedules.  Each LP is solved by one CTA; an LP whose K,
  * K' and vectors fit in the CTA's shared-memory budget is copied there and
  * solved from shared memory; an LP with at least 32768 nonzeros is solved by
- * a team of CTAs on as many SMs, which meet at bounded global-memory
+ * a team of four CTAs on as many SMs, which meet at bounded global-memory
  * barriers (the batch's CTAs must all be resident: a barrier that waits more
  * than 2 s fails the solve with PDLP_ERR_CUDA).  params: NULL = defaults; value_bits must be 64.
  * stream: cudaStream_t as void* (NULL = own stream). */

@@ -219,7 +219,8 @@ struct TeamState {
   int *abort;           // set when a barrier wait times out
   int teams;
 };
-constexpr int TEAM = 8;                 // CTAs per team
+constexpr int TEAM = 4;                 // CTAs per team
+constexpr int BACK_CTAS = 16;           // CTAs that start from the small end of the queue
 constexpr long long TEAM_MIN_NNZ = 32768;  // LPs at least this large are solved by a team
 constexpr unsigned long long TEAM_WAIT_NS = 2000000000ull;
 
@@ -1135,10 +1136,10 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
     return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
   }
   b->grid = std::max(1, std::min(count, per_sm * b->num_sms));
-  // with at least 3 TEAM CTAs: whole teams plus 2 TEAM CTAs that start from
+  // with room for a team: whole teams plus BACK_CTAS CTAs that start from
   // the small end of the queue
-  const int teams = b->grid >= 3 * TEAM ? (b->grid - 2 * TEAM) / TEAM : 0;
-  if (teams) b->grid = (teams + 2) * TEAM;
+  const int teams = b->grid >= BACK_CTAS + TEAM ? (b->grid - BACK_CTAS) / TEAM : 0;
+  if (teams) b->grid = teams * TEAM + BACK_CTAS;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   size_t off = 0;
   const size_t o_kptr = off; off += al(4 * KP);
