@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -69,6 +70,9 @@ struct Params {
   // a large part of a small LP's step on GB300's narrow FP64 pipe.
   const double *pw;
   long long npw;
+  // test hook for the barrier timeout (environment PDLP_TEST_TEAM_STALL=1):
+  // rank 1 of team 0 leaves at once, so its team's first barrier runs out
+  int stall;
 };
 
 struct Arrays {
@@ -915,6 +919,7 @@ __global__ void __launch_bounds__(NTB) k_batch_solve(Arrays A, const Inst *__res
   extern __shared__ __align__(16) unsigned char bsm[];
   const int team = blockIdx.x / TEAM;
   if (team < ts.teams) {
+    if (p.stall && blockIdx.x == 1) return;
     Team grp{(int)(blockIdx.x % TEAM), ts.cnt + team, ts.gen + team, ts.slots + (size_t)team * 2 * TEAM * 16,
              ts.abort, 0};
     for (;;) {
@@ -1345,6 +1350,10 @@ int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double t
   p.max_iter = max_iter;
   p.P = b->prm.check_period;
   p.warm = (x0 || y0) ? 1 : 0;
+  {
+    const char *ev = std::getenv("PDLP_TEST_TEAM_STALL");
+    p.stall = (ev && ev[0] == '1' && b->ts.teams > 0) ? 1 : 0;
+  }
   {
     const long long need = std::min<long long>(max_iter, 1LL << 22);
     if (need > b->npw) {

@@ -98,3 +98,18 @@ def test_batch_times_describe_the_schedule(batch):
         t0, t1 = b.times()
     assert t0.min() == 0.0
     assert np.all(t1 >= t0) and t1.max() <= wall
+
+
+def test_team_barrier_timeout_is_reported_and_context_survives(batch, monkeypatch):
+    # a team member that never arrives: its teammates give up after 2 s, the
+    # call fails with an error, and the next solve on the same batch is normal
+    with P.BatchSolver(batch) as b:
+        ok = b.solve(tol=1e-6)
+        monkeypatch.setenv("PDLP_TEST_TEAM_STALL", "1")
+        with pytest.raises(P.PdlpError) as e:
+            b.solve(tol=1e-6)
+        assert "timed out" in str(e.value)
+        monkeypatch.delenv("PDLP_TEST_TEAM_STALL")
+        again = b.solve(tol=1e-6)
+    assert np.array_equal(ok[2], again[2]) and np.array_equal(ok[3], again[3])
+    assert all(np.array_equal(a, c) for a, c in zip(ok[0], again[0]))
