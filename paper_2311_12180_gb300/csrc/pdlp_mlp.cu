@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -136,7 +137,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 template <class Epi>
 __global__ void __launch_bounds__(GEMM_THREADS) k_tc_gemm(const __grid_constant__ CUtensorMap ma,
                                                  const __grid_constant__ CUtensorMap mb, int M, int N, int K,
-                                                 int kchunk, Epi epi, int *err) {
+                                                 int kchunk, Epi epi, int *err, int stall) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                           ~static_cast<uintptr_t>(1023));
@@ -167,6 +168,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) k_tc_gemm(const __grid_constant_
   if (threadIdx.x == 0) {
     bool ok = true;
     for (int s = 0; s < STAGES && s < nk; ++s) {
+      // test hook: CTA 0 never loads stage 0, so its first wait runs out
+      if (stall && s == 0 && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0) continue;
       const uint32_t a = smem_u32(smem + s * STAGE_BYTES);
       mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
       tma_load_2d(a, &ma, kb + s * TBK, m0, full0 + 8 * s);
@@ -610,6 +613,9 @@ struct pdlp_mlp {
   int *idx = nullptr;
   size_t idx_cap = 0;
   long long adam_t = 0;
+  // test hook for the bounded waits (environment PDLP_TEST_GEMM_STALL=1 at a
+  // call): the call's first GEMM starves one CTA of its first stage
+  int stall_next = 0;
   std::vector<void *> allocs;
 };
 
@@ -648,7 +654,9 @@ int gemm(pdlp_mlp *Mn, int M, int N, int K, int splits, const bf16 *A, int lda, 
     return set_error(PDLP_ERR_CUDA, "MLP GEMM: cuTensorMapEncodeTiled unavailable or rejected the operand");
   const int kchunk = ((K + splits - 1) / splits + TBK - 1) / TBK * TBK;
   dim3 grid((N + TBN - 1) / TBN, (M + TBM - 1) / TBM, splits);
-  k_tc_gemm<Epi><<<grid, GEMM_THREADS, GEMM_SMEM, Mn->stream>>>(ma, mb, M, N, K, kchunk, epi, Mn->err);
+  const int stall = Mn->stall_next;
+  Mn->stall_next = 0;
+  k_tc_gemm<Epi><<<grid, GEMM_THREADS, GEMM_SMEM, Mn->stream>>>(ma, mb, M, N, K, kchunk, epi, Mn->err, stall);
   MCK(cudaGetLastError());
   return PDLP_OK;
 }
@@ -956,6 +964,10 @@ int pdlp_mlp_predict(pdlp_mlp *M, int32_t count, const float *X, float *Y) {
 }
 
 int pdlp_mlp_gradients(pdlp_mlp *M, int32_t batch, const int32_t *idx, float *loss, float *grads) {
+  if (M) {
+    const char *ev = std::getenv("PDLP_TEST_GEMM_STALL");
+    M->stall_next = (ev && ev[0] == '1') ? 1 : 0;
+  }
   if (!M || batch < 1 || batch > M->maxb || !idx || M->samples < 1)
     return set_error(PDLP_ERR_INVALID, "pdlp_mlp_gradients: need data and 1 <= batch <= max_batch");
   for (int i = 0; i < batch; ++i)

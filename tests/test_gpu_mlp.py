@@ -139,3 +139,23 @@ def test_invalid_arguments_rejected():
             net.gradients(np.zeros(9, np.int32))
         with pytest.raises(P.PdlpError):  # index out of range
             net.train(np.full((2, 4), 10, np.int32))
+
+
+def test_gemm_wait_timeout_is_reported_and_context_survives(monkeypatch):
+    # one CTA of the first GEMM never receives its first operand stage: its
+    # bounded mbarrier wait runs out (2 s), the call reports the error, and
+    # the next call computes the same gradients as before
+    din, h, dout, batch = 16, 64, 300, 32
+    p, X, T = _problem(din, h, dout, 64, 8)
+    idx = np.arange(batch, dtype=np.int32)
+    with P.Mlp(din, h, dout, max_batch=batch) as net:
+        net.set_params(p)
+        net.set_data(X, T)
+        loss0, g0 = net.gradients(idx)
+        monkeypatch.setenv("PDLP_TEST_GEMM_STALL", "1")
+        with pytest.raises(P.PdlpError) as e:
+            net.gradients(idx)
+        assert "timed out" in str(e.value)
+        monkeypatch.delenv("PDLP_TEST_GEMM_STALL")
+        loss1, g1 = net.gradients(idx)
+    assert loss1 == loss0 and np.array_equal(g1, g0)
