@@ -237,10 +237,17 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const int64_t nnz = row_ptr[m];
   if (nnz >= ((int64_t)1 << 31)) return fail(PDLP_ERR_INVALID, "nnz must be < 2^31");
 
-  // ---- host: K' by a stable counting sort, tile schedules ----
-  std::vector<int32_t> tp((size_t)n + 1, 0), ti((size_t)nnz);
-  std::vector<double> tv((size_t)nnz);
-  csr_transpose(m, n, row_ptr, col_idx, val, tp.data(), ti.data(), tv.data());
+  // ---- host: K' row starts and tile schedules; K' itself on the device
+  // (setup_transpose) unless a column is too long for its per-column sort ----
+  std::vector<int32_t> tp((size_t)n + 1, 0), ti;
+  std::vector<double> tv;
+  const bool device_transpose =
+      csr_column_starts(m, n, row_ptr, col_idx, tp.data()) <= transpose_max_segment();
+  if (!device_transpose) {
+    ti.resize((size_t)nnz);
+    tv.resize((size_t)nnz);
+    csr_transpose(m, n, row_ptr, col_idx, val, tp.data(), ti.data(), tv.data());
+  }
   std::vector<int2> tilesK = build_tiles(row_ptr, m);
   std::vector<int2> tilesT = build_tiles(tp.data(), n);
   double qn = 0.0, cn = 0.0;
@@ -396,10 +403,21 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   if (nnz) {
     CKS(cudaMemcpyAsync(s->K_idx, col_idx, 4 * Z, cudaMemcpyHostToDevice, st));
     CKS(cudaMemcpyAsync(s->K_val, val, 8 * Z, cudaMemcpyHostToDevice, st));
-    CKS(cudaMemcpyAsync(s->T_idx, ti.data(), 4 * Z, cudaMemcpyHostToDevice, st));
-    CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
+    if (!device_transpose) {
+      CKS(cudaMemcpyAsync(s->T_idx, ti.data(), 4 * Z, cudaMemcpyHostToDevice, st));
+      CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
+    }
   }
   CKS(cudaMemcpyAsync(s->T_ptr, tp.data(), 4 * (N + 1), cudaMemcpyHostToDevice, st));
+  if (device_transpose && nnz) {
+    int32_t *work = nullptr;
+    CKS(cudaMallocAsync((void **)&work, sizeof(int32_t) * transpose_work_ints(n, nnz), st));
+    const cudaError_t et = setup_transpose(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val,
+                                           work, st);
+    const cudaError_t ef = cudaFreeAsync(work, st);
+    CKS(et);
+    CKS(ef);
+  }
   CKS(cudaMemcpyAsync(Ktl, tilesK.data(), sizeof(int2) * tilesK.size(), cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(Ttl, tilesT.data(), sizeof(int2) * tilesT.size(), cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(s->l0, l, 8 * N, cudaMemcpyHostToDevice, st));

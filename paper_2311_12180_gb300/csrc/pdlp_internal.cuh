@@ -121,7 +121,16 @@ int occupancy_grid(int kc, int num_sms);
 cudaError_t kernels_init();
 // Fills the Algorithm 2 exponent-factor table: pw[k] = (k + 2)^-0.3 and
 // pw[count + k] = (k + 2)^-0.6 for k < count (the same pow() the step test calls).
-cudaError_t setup_pow_table(double *pw, long long count, cudaStream_t s);  // one-time function attributes (dynamic shared memory)
+cudaError_t setup_pow_table(double *pw, long long count, cudaStream_t s);
+// K' on the device (pdlp_setup.cu), given its row starts T_ptr (already on
+// the device): the stable transpose, equal to the host counting sort, for
+// columns of at most transpose_max_segment() entries, with
+// transpose_work_ints(n, nnz) ints of scratch.
+cudaError_t setup_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
+                            const double *K_val, const int32_t *T_ptr, int32_t *T_idx, double *T_val, int32_t *work,
+                            cudaStream_t s);
+size_t transpose_work_ints(int32_t n, int64_t nnz);
+int transpose_max_segment();  // one-time function attributes (dynamic shared memory)
 
 // ---- setup kernels (pdlp_setup.cu) ----
 cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32_t *K_idx, double *K_val,

@@ -198,6 +198,121 @@ cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- K' on the device
+//
+// Stable transpose, given K' row starts (from the host's column counts): a
+// scatter of entry numbers into their columns (atomic cursors: arbitrary
+// order), a sort of each column's entry numbers (which restores the row
+// order, since K's entries are numbered row by row), and a gather of rows and
+// values.  The result equals the host counting sort.  Columns longer than
+// TRANSPOSE_MAX_SEG entries are left to the host sort.
+
+namespace {
+
+__global__ void k_scatter_entries(const int32_t *__restrict__ idx, int64_t nnz, const int32_t *__restrict__ tp,
+                                  int32_t *__restrict__ cursor, int32_t *__restrict__ perm) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = idx[e];
+    perm[tp[c] + atomicAdd(cursor + c, 1)] = (int32_t)e;
+  }
+}
+
+// One warp per column of at most 32 entries: bitonic sort of the entry
+// numbers across the lanes (padding INT_MAX).
+__global__ void k_sort_short(const int32_t *__restrict__ tp, int32_t n, int32_t *__restrict__ perm) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < n;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int32_t b = tp[w], len = tp[w + 1] - b;
+    if (len <= 1 || len > 32) continue;
+    int32_t v = lane < len ? perm[b + lane] : INT32_MAX;
+    for (int k = 2; k <= 32; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const int32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+        const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+        v = (lower == up) ? min(v, o) : max(v, o);
+      }
+    if (lane < len) perm[b + lane] = v;
+  }
+}
+
+// One CTA per column of 33..TRANSPOSE_MAX_SEG entries: bitonic sort in
+// shared memory.
+constexpr int TRANSPOSE_MAX_SEG = 4096;
+__global__ void k_sort_long(const int32_t *__restrict__ tp, int32_t n, int32_t *__restrict__ perm) {
+  __shared__ int32_t sh[TRANSPOSE_MAX_SEG];
+  for (int32_t c = blockIdx.x; c < n; c += gridDim.x) {
+    const int32_t b = tp[c], len = tp[c + 1] - b;
+    if (len <= 32) continue;  // uniform across the CTA
+    int P2 = 64;
+    while (P2 < len) P2 <<= 1;
+    for (int t = threadIdx.x; t < P2; t += blockDim.x) sh[t] = t < len ? perm[b + t] : INT32_MAX;
+    __syncthreads();
+    for (int k = 2; k <= P2; k <<= 1)
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < P2; t += blockDim.x) {
+          const int u = t ^ j;
+          if (u > t) {
+            const bool up = (t & k) == 0;
+            const int32_t a = sh[t], d = sh[u];
+            if ((a > d) == up) {
+              sh[t] = d;
+              sh[u] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    for (int t = threadIdx.x; t < len; t += blockDim.x) perm[b + t] = sh[t];
+    __syncthreads();
+  }
+}
+
+// row number of every entry of K (one warp per row)
+__global__ void k_entry_rows(const int32_t *__restrict__ ptr, int32_t rows, int32_t *__restrict__ rowid) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((int64_t)gridDim.x * blockDim.x) >> 5)
+    for (int32_t e = ptr[r] + lane; e < ptr[r + 1]; e += 32) rowid[e] = (int32_t)r;
+}
+
+__global__ void k_gather_entries(const int32_t *__restrict__ perm, int64_t nnz, const int32_t *__restrict__ rowid,
+                                 const double *__restrict__ val, int32_t *__restrict__ ti, double *__restrict__ tv) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = perm[p];
+    ti[p] = rowid[e];
+    tv[p] = val[e];
+  }
+}
+
+int tgrid(int64_t work, int per = 256) {
+  int64_t g = (work + per - 1) / per;
+  if (g > 152 * 64) g = 152 * 64;
+  return (int)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+cudaError_t setup_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
+                            const double *K_val, const int32_t *T_ptr, int32_t *T_idx, double *T_val, int32_t *work,
+                            cudaStream_t s) {
+  // work: cursor (n), perm (nnz), rowid (nnz)
+  int32_t *cursor = work, *perm = cursor + n, *rowid = perm + nnz;
+  cudaError_t e = cudaMemsetAsync(cursor, 0, sizeof(int32_t) * (size_t)n, s);
+  if (e != cudaSuccess) return e;
+  if (nnz) {
+    k_scatter_entries<<<tgrid(nnz), 256, 0, s>>>(K_idx, nnz, T_ptr, cursor, perm);
+    k_sort_short<<<tgrid((int64_t)n * 32), 256, 0, s>>>(T_ptr, n, perm);
+    k_sort_long<<<tgrid(n, 1), 1024, 0, s>>>(T_ptr, n, perm);
+    k_entry_rows<<<tgrid((int64_t)m * 32), 256, 0, s>>>(K_ptr, m, rowid);
+    k_gather_entries<<<tgrid(nnz), 256, 0, s>>>(perm, nnz, rowid, K_val, T_idx, T_val);
+  }
+  return cudaGetLastError();
+}
+
+size_t transpose_work_ints(int32_t n, int64_t nnz) { return (size_t)n + 2 * (size_t)nnz; }
+int transpose_max_segment() { return TRANSPOSE_MAX_SEG; }
+
 __global__ void k_pow_table(double *pw, long long count) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
     const double kk = (double)(i + 2);

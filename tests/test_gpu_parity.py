@@ -89,6 +89,47 @@ def test_iterates_match_oracle(case, P_, N):
     np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))
 
 
+def _long_column_lp(seed, longest):
+    """K whose columns run from 1 entry to `longest`: columns of at most 32
+    entries, of 33..4096 entries and (longest > 4096) longer ones, with K's
+    rows drawn per column, so that the stable transpose sorts every kind."""
+    rng = np.random.default_rng(seed)
+    m, n = longest + 300, 260
+    lens = np.concatenate([rng.integers(1, 33, 200), rng.integers(33, 600, 50), [1000, 2048, 3000, 4095, 4096],
+                           rng.integers(100, 300, 4), [longest]])
+    cp, rows = lpgen._sample_rows(rng, lens, m)  # K' pattern: row j holds column j's rows
+    cols = np.repeat(np.arange(n, dtype=np.int64), np.diff(cp))
+    order = np.lexsort((cols, rows))
+    rows, cols = rows[order], cols[order]
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=row_ptr[1:])
+    row_ptr, cols = lpgen._cover_columns(rng, row_ptr, cols, m, n)
+    assert np.all(np.diff(row_ptr) > 0), "every row needs an entry"
+    val = rng.standard_normal(cols.size)
+    return lpgen.plant(rng, m, n, m // 3, row_ptr, cols, val, np.zeros(n), np.full(n, 10.0))
+
+
+@pytest.mark.parametrize("longest", [4096, 5000])
+def test_long_columns_match_oracle(longest):
+    # 4096: K' built on the device (every column sorted there); 5000: one
+    # column too long for the per-column device sort, K' built on the host
+    lp = _long_column_lp(31, longest)
+    assert np.bincount(lp.col_idx, minlength=lp.n).max() == longest
+    with _solver(lp) as s:
+        D1, D2, v = s.scaling()
+    sv, oD1, oD2 = oracle.precondition(lp, ruiz_iters=10, pc_alpha=1.0)
+    np.testing.assert_allclose(D1, oD1, rtol=1e-13)
+    np.testing.assert_allclose(D2, oD2, rtol=1e-13)
+    np.testing.assert_allclose(v, sv, rtol=1e-13)
+    N = 40
+    with _solver(lp, check_period=8) as s:
+        x, y, st, it = s.solve(tol=1e-14, max_iter=N)
+    r = _oracle(lp, tol=1e-14, max_iter=N, check_period=8)
+    assert it == N == r.iters
+    np.testing.assert_allclose(x, r.x, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.x).max()))
+    np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))
+
+
 def test_deterministic():
     lp = lpgen.large_lp(6, m=20000, n=40000, nnz=400000)
     with _solver(lp) as s:
