@@ -349,6 +349,62 @@ def run_batch(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, rank, world):
+    """Size sweep: planted LPs of the large recipe (Zipf(1.5) row lengths,
+    lognormal(0,2) values, m = nnz/20, n = nnz/10) from 1e5 to 5e7 nonzeros;
+    per size the device-timed PDHG iteration rate (as the large workload:
+    warm-up periods, then timed check periods) and the FP64 oracle's rate on
+    a bounded sample, and their ratio (the paper reports the GPU's advantage
+    growing with the LP's size)."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+
+    import lpgen
+    from paper_2311_12180_gb300 import _build
+    from paper_2311_12180_gb300 import pdlp as P
+
+    _build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    rows = []
+    for nnz in [int(float(v)) for v in args.sweep_nnz.split(",")]:
+        lp = lpgen.large_lp(0, m=max(nnz // 20, 10), n=max(nnz // 10, 20), nnz=nnz)
+        with P.Solver(lp, stream=stream.cuda_stream) as s:
+            s.begin(tol=0.0, max_iter=10**12)
+            s.run_periods(args.warmup)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            periods, ms = args.steps, 0.0
+            while True:  # at least 0.2 s of timed work
+                torch.cuda.synchronize()
+                _, k0 = s.poll()
+                ev0.record(stream)
+                s.run_periods(periods)
+                ev1.record(stream)
+                ev1.synchronize()
+                st1, k1 = s.poll()
+                ms = ev0.elapsed_time(ev1)
+                if st1 != -1:
+                    raise SystemExit("sweep solve ended inside the timed region (status %d)" % st1)
+                if ms >= 200.0 or periods >= 100000:
+                    break
+                periods = int(periods * max(2.0, 250.0 / max(ms, 1e-3)))
+            gpu = (k1 - k0) / (ms / 1000.0)
+        cpu = None if args.no_cpu else cpu_baseline(lp, budget_s=args.sweep_cpu_s)
+        rows.append({"nnz": lp.nnz, "m": lp.m, "n": lp.n, "gpu_iters_per_s": gpu, "periods_timed": periods,
+                     "cpu_iters_per_s": cpu["value"] if cpu else None,
+                     "gpu_over_cpu": gpu / cpu["value"] if cpu else None,
+                     "cpu_sample": cpu["sample"] if cpu else None})
+        del lp
+    line = {"metric": "PDHG iters/s by LP size", "unit": UNIT, "n_gpus": 1, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "planted LPs, Zipf(1.5) row lengths, lognormal(0,2) values, m = nnz/20, "
+                                   "n = nnz/10, bounds 50% [0,inf) 30% [l,u] 20% free"},
+            "cpu": "FP64 oracle, one host core, bounded sample per size", "sizes": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args, rank, world):
     """Learned warm start on the parametric transportation family: sources x
     sinks flows, costs / supplies / demands affine in a 16-dim latent theta
@@ -445,7 +501,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "tiny", "batch", "warmstart"])
+    ap.add_argument("--workload", default="large", choices=["large", "tiny", "batch", "warmstart", "sweep"])
+    ap.add_argument("--sweep-nnz", default="1e5,1e6,1e7,5e7", help="comma-separated nonzero counts (sweep)")
+    ap.add_argument("--sweep-cpu-s", type=float, default=5.0, help="oracle sample budget per size (sweep)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-tol", type=float, default=1e-6)
     ap.add_argument("--batch-max-iter", type=int, default=1_000_000)
@@ -477,6 +535,9 @@ def main():
         return
     if args.workload == "warmstart":
         run_warmstart(args, rank, world)
+        return
+    if args.workload == "sweep":
+        run_sweep(args, rank, world)
         return
 
     import numpy as np
@@ -587,7 +648,7 @@ def main():
     if not args.no_cpu and world == 1:
         cpu = cpu_baseline(lp)
 
-    kernels_per_period = 2 * (period + max(4, period // 8)) + 3
+    kernels_per_period = 2 * (period + max(4, period // 8)) + 4  # + check_primal, infeas, check_dual, restart
     line = {
         "metric": METRIC,
         "value": value,

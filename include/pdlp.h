@@ -52,6 +52,16 @@ extern "C" {
 #define PDLP_ITER_LIMIT 1 /* max_iter accepted PDHG steps taken first */
 #define PDLP_TIME_LIMIT 2 /* params.time_limit_s wall-clock seconds elapsed first */
 #define PDLP_NUMERICAL 3  /* a NaN / Inf appeared in the step-size test */
+/* Infeasibility detection (Sec. 2.2, last bullet; params.eps_infeas > 0): at
+ * a check, the difference of the last two accepted iterates, or the current
+ * iterate minus the epoch's first, unscaled to the original LP, is an
+ * approximate certificate (pdlp_info.ray_obj > 0 and ray_res <= eps_infeas *
+ * ray_obj; definitions at pdlp_info).  The ray is returned in place of the
+ * iterate it concerns. */
+#define PDLP_PRIMAL_INFEASIBLE 4 /* y_out holds a dual ray yr: yr_i >= 0 on ">=" rows, lambda =
+                                    proj_Lambda(-K'yr), q'yr + l'lambda+ - u'lambda- > 0 */
+#define PDLP_DUAL_INFEASIBLE 5   /* x_out holds a primal ray xr: K_E xr = 0, K_G xr >= 0, xr in the
+                                    recession cone of the bounds, c'xr < 0 (unbounded if feasible) */
 
 typedef struct pdlp_solver pdlp_solver; /* opaque */
 
@@ -75,12 +85,17 @@ typedef struct {
                              and termination always use the FP64 K) */
   int32_t f32_polish;     /* with value_bits = 32: switch the steps to the FP64 K when the original-
                              space relative KKT error stalls over two restarts above tol (1 = on) */
+  double eps_infeas;      /* relative tolerance of the infeasibility certificates (default 1e-8);
+                             0 turns infeasibility detection off.  Single-LP solver only: the
+                             batched solver runs infeasible LPs to max_iter. */
 } pdlp_params;
 
 /* Summary of the last solve (pdlp_get_info). */
 typedef struct {
   int32_t status;   /* PDLP_* status of the last solve, -1 while running / never solved */
-  int32_t which;    /* 0: the returned point is the current iterate, 1: the epoch average */
+  int32_t which;    /* 0: the returned point is the current iterate, 1: the epoch average;
+                       infeasible: 2: the certificate is the difference of the last two accepted
+                       iterates, 3: the current iterate minus the epoch's first */
   int64_t iters;    /* accepted PDHG steps (k of Algorithm 1) */
   int64_t attempts; /* Algorithm 2 trials, accepted + rejected */
   int64_t restarts; /* restarts taken (n of Algorithm 1) */
@@ -93,6 +108,12 @@ typedef struct {
   double solve_ms;        /* wall time of the last solve call */
   int64_t graph_launches; /* CUDA-graph launches in the last solve */
   int64_t f64_switch_iter; /* value_bits = 32 only: k at which the steps moved to FP64 K, -1 never */
+  /* infeasible statuses only (else 0), on the original LP: PDLP_PRIMAL_INFEASIBLE: ray_obj =
+     q'yr + l'lambda+ - u'lambda-, ray_res = ||(-K'yr - lambda, min(yr_G, 0))||_2;
+     PDLP_DUAL_INFEASIBLE: ray_obj = -c'xr, ray_res = ||(K_E xr, min(K_G xr, 0), v)||_2 with v
+     the distance of xr to the bounds' recession cone (xr_j >= 0 where l_j is finite, <= 0 where
+     u_j is finite) */
+  double ray_obj, ray_res;
 } pdlp_info;
 
 /* One restart / termination check (pdlp_get_trace), values on the scaled LP. */

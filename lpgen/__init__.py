@@ -41,6 +41,7 @@ __all__ = [
     "large_lp",
     "random_boxed_lp",
     "batch_lps",
+    "infeasible_lp",
 ]
 
 
@@ -326,6 +327,82 @@ def random_boxed_lp(seed: int, m_eq: int, m_ineq: int, n: int, density: float = 
     return LP(m=m, n=n, n_eq=m_eq, c=c, row_ptr=row_ptr.astype(np.int32),
               col_idx=cols.astype(np.int32), val=val, q=q, l=l, u=u,
               meta=dict(kind="boxed-random", seed=seed))
+
+
+def _from_coo(m, rows, cols, vals):
+    """CSR (row_ptr, cols, vals) of COO entries, sorted by (row, column)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    order = np.lexsort((cols, rows))
+    row_ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=row_ptr[1:])
+    return row_ptr, cols[order], vals[order]
+
+
+def infeasible_lp(seed: int, kind: str, m_eq: int = 30, m_ineq: int = 30, n: int = 120,
+                  density: float = 0.05) -> LP:
+    """A small LP with a known infeasibility, built around a planted feasible
+    one (0 <= x <= 10, N(0,1) values); meta["ray"] holds an exact certificate.
+
+      "primal":        two ">=" rows a'x >= h1 and -a'x >= -h2 with h2 < h1
+                       (dual ray: 1 on both rows);
+      "primal_bounds": one ">=" row a'x >= h with h above the largest value
+                       of a'x over the box (dual ray: 1 on that row);
+      "dual":          two extra columns v and -v with bounds [0, inf) and
+                       costs -1 and 0.5, so x = t (e_n + e_{n+1}) is feasible
+                       for all t >= 0 and lowers c'x without bound (primal
+                       ray e_n + e_{n+1}).
+    """
+    rng = np.random.default_rng([0x1F3A, seed, ["primal", "primal_bounds", "dual"].index(kind)])
+    base = tiny_lp(1000 + seed, m_eq=m_eq, m_ineq=m_ineq, n=n, density=density)
+    rows = np.repeat(np.arange(base.m, dtype=np.int64), np.diff(base.row_ptr))
+    cols = base.col_idx.astype(np.int64)
+    vals = base.val.copy()
+    m, nn = base.m, base.n
+    q, c, l, u = base.q.copy(), base.c.copy(), base.l.copy(), base.u.copy()
+    if kind in ("primal", "primal_bounds"):
+        k = max(3, n // 10)
+        a_cols = np.sort(rng.choice(n, size=k, replace=False))
+        a_val = rng.standard_normal(k)
+        if kind == "primal":
+            h1 = float(a_val @ base.x_star[a_cols]) + rng.uniform(0.5, 1.0)
+            h2 = h1 - rng.uniform(0.5, 1.0)
+            new_rows = [(a_cols, a_val, h1), (a_cols, -a_val, -h2)]
+            ray_y = np.zeros(m + 2)
+            ray_y[m:] = 1.0
+        else:
+            top = float(np.sum(np.maximum(a_val * l[a_cols], a_val * u[a_cols])))
+            new_rows = [(a_cols, a_val, top + rng.uniform(0.5, 1.0))]
+            ray_y = np.zeros(m + 1)
+            ray_y[m] = 1.0
+        for cc_, vv_, hh_ in new_rows:
+            rows = np.concatenate([rows, np.full(cc_.size, m, dtype=np.int64)])
+            cols = np.concatenate([cols, cc_])
+            vals = np.concatenate([vals, vv_])
+            q = np.concatenate([q, [hh_]])
+            m += 1
+        row_ptr, cols, vals = _from_coo(m, rows, cols, vals)
+        return LP(m=m, n=nn, n_eq=base.n_eq, c=c, row_ptr=row_ptr.astype(np.int32),
+                  col_idx=cols.astype(np.int32), val=vals, q=q, l=l, u=u,
+                  meta=dict(kind="infeasible-" + kind, seed=seed, ray_y=ray_y, ray_x=None))
+    if kind != "dual":
+        raise ValueError("kind must be 'primal', 'primal_bounds' or 'dual'")
+    k = max(3, m // 10)
+    v_rows = np.sort(rng.choice(m, size=k, replace=False))
+    v_val = rng.standard_normal(k)
+    rows = np.concatenate([rows, v_rows, v_rows])
+    cols = np.concatenate([cols, np.full(k, nn, dtype=np.int64), np.full(k, nn + 1, dtype=np.int64)])
+    vals = np.concatenate([vals, v_val, -v_val])
+    row_ptr, cols, vals = _from_coo(m, rows, cols, vals)
+    c = np.concatenate([c, [-1.0, 0.5]])
+    l = np.concatenate([l, [0.0, 0.0]])
+    u = np.concatenate([u, [np.inf, np.inf]])
+    ray_x = np.zeros(nn + 2)
+    ray_x[nn:] = 1.0
+    return LP(m=m, n=nn + 2, n_eq=base.n_eq, c=c, row_ptr=row_ptr.astype(np.int32),
+              col_idx=cols.astype(np.int32), val=vals, q=q, l=l, u=u,
+              meta=dict(kind="infeasible-dual", seed=seed, ray_x=ray_x, ray_y=None))
 
 
 def batch_lps(count: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,

@@ -25,7 +25,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pdlp_oracle.c")
 _LIB = os.path.join(_HERE, "libpdlp_oracle.so")
 
-OPTIMAL, ITER_LIMIT, NUMERICAL = 0, 1, 3
+OPTIMAL, ITER_LIMIT, NUMERICAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE = 0, 1, 3, 4, 5
 
 
 def build(force: bool = False) -> str:
@@ -67,6 +67,7 @@ class _Params(C.Structure):
         ("beta_suff", C.c_double),
         ("beta_nec", C.c_double),
         ("beta_art", C.c_double),
+        ("eps_infeas", C.c_double),
     ]
 
 
@@ -86,6 +87,8 @@ class _Info(C.Structure):
         ("c_norm", C.c_double),
         ("omega", C.c_double),
         ("eta_hat", C.c_double),
+        ("ray_obj", C.c_double),
+        ("ray_res", C.c_double),
     ]
 
 
@@ -120,6 +123,10 @@ def lib():
         L.orc_kkt_omega.restype = d
         L.orc_terms_pass.argtypes = [vp, d]
         L.orc_terms_pass.restype = C.c_int
+        L.orc_infeas_terms.argtypes = [vp, vp, vp, vp]
+        L.orc_infeas_terms.restype = C.c_int
+        L.orc_infeas_status.argtypes = [vp, d]
+        L.orc_infeas_status.restype = C.c_int
         L.orc_primal_weight_init.argtypes = [d, d, d]
         L.orc_primal_weight_init.restype = d
         L.orc_primal_weight_update.argtypes = [d, d, d, d, d]
@@ -183,10 +190,12 @@ class Params:
     beta_suff: float = 0.2
     beta_nec: float = 0.8
     beta_art: float = 0.36
+    eps_infeas: float = 1e-8
 
     def struct(self):
         return _Params(self.tol, self.max_iter, self.check_period, self.ruiz_iters, self.pc_alpha,
-                       self.theta, self.eps_zero, self.beta_suff, self.beta_nec, self.beta_art)
+                       self.theta, self.eps_zero, self.beta_suff, self.beta_nec, self.beta_art,
+                       self.eps_infeas)
 
 
 @dataclass
@@ -208,6 +217,8 @@ class Result:
     omega: float
     eta_hat: float
     trace: np.ndarray
+    ray_obj: float = 0.0
+    ray_res: float = 0.0
 
 
 def solve(lp, params: Params | None = None, x0=None, y0=None, trace_cap: int = 4096, **kw) -> Result:
@@ -228,7 +239,8 @@ def solve(lp, params: Params | None = None, x0=None, y0=None, trace_cap: int = 4
     return Result(x=x[: lp.n], y=y[: lp.m], status=info.status, which=info.which, iters=info.iters,
                   attempts=info.attempts, restarts=info.restarts, checks=info.checks, pobj=info.pobj,
                   dobj=info.dobj, rp_norm=info.rp_norm, rd_norm=info.rd_norm, q_norm=info.q_norm,
-                  c_norm=info.c_norm, omega=info.omega, eta_hat=info.eta_hat, trace=trace[:nt].copy())
+                  c_norm=info.c_norm, omega=info.omega, eta_hat=info.eta_hat, trace=trace[:nt].copy(),
+                  ray_obj=info.ray_obj, ray_res=info.ray_res)
 
 
 def precondition(lp, ruiz_iters: int = 10, pc_alpha: float = 1.0):
@@ -269,6 +281,27 @@ def relative_kkt(lp, x, y):
 def passes(lp, x, y, tol: float) -> bool:
     t = kkt_terms(lp, x, y)
     return bool(lib().orc_terms_pass(_p(t["raw"]), tol))
+
+
+def infeas_terms(lp, xr, yr):
+    """Certificate measures of a primal ray xr and a dual ray yr on the LP as
+    given: {dual-ray objective, dual-ray residual, primal-ray objective
+    (-c'xr), primal-ray residual}."""
+    h = _holder(lp)
+    xa = np.ascontiguousarray(xr, dtype=np.float64)
+    ya = np.ascontiguousarray(yr, dtype=np.float64)
+    xa = xa if xa.size else np.zeros(1)
+    ya = ya if ya.size else np.zeros(1)
+    out = np.zeros(4)
+    lib().orc_infeas_terms(h.ref, _p(xa), _p(ya), _p(out))
+    return out
+
+
+def infeas_status(terms, eps: float) -> int:
+    """PRIMAL_INFEASIBLE / DUAL_INFEASIBLE certified by infeas_terms' output at
+    relative tolerance eps, else -1."""
+    t = np.ascontiguousarray(terms, dtype=np.float64)
+    return int(lib().orc_infeas_status(_p(t), eps))
 
 
 def kkt_omega(lp, x, y, omega: float) -> float:

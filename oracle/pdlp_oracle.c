@@ -53,6 +53,15 @@
  *   - Ruiz: 10 passes, row/col factor sqrt(max|K~|) (1 for an empty line);
  *     Pock-Chambolle alpha = 1: row factor sqrt(sum_j |K~_ij|^(2-alpha)),
  *     column factor sqrt(sum_i |K~_ij|^alpha).
+ *   - Infeasibility detection (Sec. 2.2, last bullet, which names the two
+ *     sequences but not the certificate tests): at every check, after the
+ *     Sec. 4.1 test fails, the ray z^{n,t} - z^{n,t-1} (difference of the
+ *     last two accepted iterates) and then z^{n,t} - z^{n,0} (the normalised
+ *     iterate times t; the tests are invariant to positive scaling) are
+ *     unscaled to the original LP and tested by orc_infeas_terms /
+ *     infeas_status, dual ray (primal infeasibility) before primal ray (dual
+ *     infeasibility); both tests use relative tolerance eps_infeas (0 turns
+ *     detection off).  Then the iteration limit, then the restart.
  *
  * Pins (tests/test_oracle_pins.py) tie every routine to hand-worked
  * examples, closed forms, brute force or an independent solver, except the
@@ -76,6 +85,8 @@
 #define ORC_OPTIMAL 0
 #define ORC_ITER_LIMIT 1
 #define ORC_NUMERICAL 3
+#define ORC_PRIMAL_INFEASIBLE 4
+#define ORC_DUAL_INFEASIBLE 5
 
 typedef struct {
   int32_t m, n, n_eq, pad_;
@@ -94,17 +105,20 @@ typedef struct {
   double theta;
   double eps_zero;
   double beta_suff, beta_nec, beta_art;
+  double eps_infeas; /* relative tolerance of the infeasibility certificates; 0 = off */
 } orc_params;
 
 typedef struct {
   int32_t status;
-  int32_t which; /* 0 = current iterate returned, 1 = average */
+  int32_t which; /* 0 = current iterate returned, 1 = average; infeasible:
+                    2 = difference ray, 3 = normalised-iterate ray */
   int64_t iters;
   int64_t attempts;
   int64_t restarts;
   int64_t checks;
   double pobj, dobj, rp_norm, rd_norm, q_norm, c_norm;
   double omega, eta_hat;
+  double ray_obj, ray_res; /* infeasible: the certificate's objective and residual norm */
 } orc_info;
 
 typedef struct {
@@ -294,6 +308,74 @@ double orc_kkt_omega(const orc_lp *lp, const double *x, const double *y, double 
   return kkt_omega_from(t[2] * t[2], t[3] * t[3], t[0], t[1], omega);
 }
 
+/* Infeasibility certificates of the LP as given, for a primal ray xr (n)
+ * and a dual ray yr (m), by LP duality:
+ *   dual ray (certifies primal infeasibility): lambda = proj_Lambda(-K'yr),
+ *     out[0] = q'yr + l'lambda+ - u'lambda-   (must be > 0),
+ *     out[1] = ||(-K'yr - lambda, min(yr_i, 0) on ">=" rows)||_2;
+ *   primal ray (certifies dual infeasibility):
+ *     out[2] = -c'xr                          (must be > 0),
+ *     out[3] = ||(K_E xr, min(K_G xr, 0), distance of xr to the recession
+ *              cone of X: xr_j >= 0 where l_j is finite, <= 0 where u_j is
+ *              finite)||_2.
+ * Lambda_j is the cone of the header's lambda reading, so lambda_j > 0 only
+ * where l_j is finite and lambda_j < 0 only where u_j is finite.  Exported
+ * for tests. */
+int orc_infeas_terms(const orc_lp *lp, const double *xr, const double *yr, double *out) {
+  int32_t m = lp->m, n = lp->n;
+  double *Kx = (double *)calloc((size_t)m + 1, sizeof(double));
+  double *KTy = (double *)calloc((size_t)n + 1, sizeof(double));
+  if (!Kx || !KTy) {
+    free(Kx);
+    free(KTy);
+    return ORC_ERR_NOMEM;
+  }
+  spmv(m, lp->row_ptr, lp->col_idx, lp->val, xr, Kx);
+  for (int32_t i = 0; i < m; ++i)
+    for (int32_t e = lp->row_ptr[i]; e < lp->row_ptr[i + 1]; ++e) KTy[lp->col_idx[e]] += lp->val[e] * yr[i];
+  double obj_d = 0.0, res_d = 0.0, obj_p = 0.0, res_p = 0.0;
+  for (int32_t i = 0; i < m; ++i) {
+    obj_d += lp->q[i] * yr[i];
+    if (i >= lp->n_eq) {
+      double v = yr[i] < 0.0 ? yr[i] : 0.0;
+      res_d += v * v;
+      double r = Kx[i] < 0.0 ? Kx[i] : 0.0;
+      res_p += r * r;
+    } else {
+      res_p += Kx[i] * Kx[i];
+    }
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    double a = -KTy[j];
+    double lam = proj_lambda(a, lp->l[j], lp->u[j]);
+    double r = a - lam;
+    res_d += r * r;
+    if (lam > 0.0) obj_d += lp->l[j] * lam;
+    if (lam < 0.0) obj_d -= lp->u[j] * (-lam);
+    obj_p -= lp->c[j] * xr[j];
+    double v = 0.0;
+    if (isfinite(lp->l[j]) && xr[j] < 0.0) v += xr[j] * xr[j];
+    if (isfinite(lp->u[j]) && xr[j] > 0.0) v += xr[j] * xr[j];
+    res_p += v;
+  }
+  out[0] = obj_d;
+  out[1] = sqrt(res_d);
+  out[2] = obj_p;
+  out[3] = sqrt(res_p);
+  free(Kx);
+  free(KTy);
+  return ORC_OK;
+}
+
+/* Status certified by orc_infeas_terms' output t at tolerance eps: primal
+ * infeasible (dual ray) first, then dual infeasible (primal ray), else -1. */
+static int infeas_status(const double *t, double eps) {
+  if (t[0] > 0.0 && t[1] <= eps * t[0]) return ORC_PRIMAL_INFEASIBLE;
+  if (t[2] > 0.0 && t[3] <= eps * t[2]) return ORC_DUAL_INFEASIBLE;
+  return -1;
+}
+int orc_infeas_status(const double *t, double eps) { return infeas_status(t, eps); }
+
 /* Sec. 4.1: all three relative inequalities hold with epsilon = tol. */
 static int terms_pass(const double *t, double tol) {
   double pobj = t[0], dobj = t[1];
@@ -397,13 +479,14 @@ typedef struct {
   double *x, *y, *Kx, *KTy, *xp, *yp, *v, *Kv, *dxv, *Kdx;
   double *sum_x, *sum_y, *xb, *yb, *Kxb, *KTyb, *x_last, *y_last;
   double *xo, *yo;
+  double *x_prev, *y_prev; /* the accepted iterate before the last one */
 } orc_work;
 
 static void free_work(orc_work *w) {
   double **d[] = {&w->sv, &w->D1, &w->D2, &w->sc, &w->sq, &w->sl, &w->su, &w->tv,
                   &w->x, &w->y, &w->Kx, &w->KTy, &w->xp, &w->yp, &w->v, &w->Kv,
                   &w->dxv, &w->Kdx, &w->sum_x, &w->sum_y, &w->xb, &w->yb, &w->Kxb,
-                  &w->KTyb, &w->x_last, &w->y_last, &w->xo, &w->yo};
+                  &w->KTyb, &w->x_last, &w->y_last, &w->xo, &w->yo, &w->x_prev, &w->y_prev};
   for (size_t i = 0; i < sizeof(d) / sizeof(d[0]); ++i) {
     free(*d[i]);
     *d[i] = NULL;
@@ -444,7 +527,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
               double *y_out, orc_info *info, orc_check *trace, int32_t trace_cap) {
   if (!lp || !p || !x_out || !y_out || !info) return ORC_ERR_INVALID;
   if (validate(lp) != ORC_OK) return ORC_ERR_INVALID;
-  if (p->check_period < 1 || p->max_iter < 1 || !(p->tol >= 0.0)) return ORC_ERR_INVALID;
+  if (p->check_period < 1 || p->max_iter < 1 || !(p->tol >= 0.0) || !(p->eps_infeas >= 0.0)) return ORC_ERR_INVALID;
   const int32_t m = lp->m, n = lp->n, n_eq = lp->n_eq;
   const int32_t *rp = lp->row_ptr, *ci = lp->col_idx;
   const int64_t nnz = m > 0 ? rp[m] : 0;
@@ -490,6 +573,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
   ALLOC(w.y_last, M, double);
   ALLOC(w.xo, N, double);
   ALLOC(w.yo, M, double);
+  ALLOC(w.x_prev, N, double);
+  ALLOC(w.y_prev, M, double);
 #undef ALLOC
 
   /* ---- Sec. 2.2 preconditioning ---- */
@@ -527,6 +612,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
   int64_t k = 0, t = 0, attempts = 0, restarts = 0, checks = 0;
   int status = -1, which = 0;
   double terms[6] = {0, 0, 0, 0, 0, 0};
+  double ray[2] = {0.0, 0.0};
   int32_t ntrace = 0;
 
   while (status < 0) {
@@ -563,6 +649,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     }
     if (status >= 0) break;
     /* accepted step: z <- (x', y') */
+    memcpy(w.x_prev, w.x, sizeof(double) * (size_t)n);
+    memcpy(w.y_prev, w.y, sizeof(double) * (size_t)m);
     memcpy(w.x, w.xp, sizeof(double) * (size_t)n);
     memcpy(w.y, w.yp, sizeof(double) * (size_t)m);
     spmv(m, rp, ci, w.sv, w.x, w.Kx);
@@ -593,6 +681,31 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
       status = ORC_OPTIMAL;
       which = 1;
       break;
+    }
+    /* Sec. 2.2 infeasibility detection: difference ray, then normalised-
+     * iterate ray, both unscaled to the original LP */
+    if (p->eps_infeas > 0.0) {
+      for (int seq = 0; seq < 2 && status < 0; ++seq) {
+        const double *xr0 = seq == 0 ? w.x_prev : w.x_last, *yr0 = seq == 0 ? w.y_prev : w.y_last;
+        for (int32_t j = 0; j < n; ++j) w.xo[j] = w.D2[j] * (w.x[j] - xr0[j]);
+        for (int32_t i = 0; i < m; ++i) w.yo[i] = w.D1[i] * (w.y[i] - yr0[i]);
+        double it[4];
+        if (orc_infeas_terms(lp, w.xo, w.yo, it) != ORC_OK) {
+          free_work(&w);
+          return ORC_ERR_NOMEM;
+        }
+        int st = infeas_status(it, p->eps_infeas);
+        if (st >= 0) {
+          status = st;
+          which = 2 + seq;
+          ray[0] = st == ORC_PRIMAL_INFEASIBLE ? it[0] : it[2];
+          ray[1] = st == ORC_PRIMAL_INFEASIBLE ? it[1] : it[3];
+        }
+      }
+      if (status >= 0) {
+        check_original(lp, &w, w.x, w.y, p->tol, terms);
+        break;
+      }
     }
     if (k >= p->max_iter) {
       check_original(lp, &w, w.x, w.y, p->tol, terms);
@@ -650,10 +763,20 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
 
   /* output in the original space; x = D2 x^ is projected onto X so that the
    * rounding of l / D2 * D2 cannot leave it an ulp outside its bounds */
-  const double *xs = which ? w.xb : w.x;
-  const double *ys = which ? w.yb : w.y;
+  const double *xs = which == 1 ? w.xb : w.x;
+  const double *ys = which == 1 ? w.yb : w.y;
   for (int32_t j = 0; j < n; ++j) x_out[j] = clamp(w.D2[j] * xs[j], lp->l[j], lp->u[j]);
   for (int32_t i = 0; i < m; ++i) y_out[i] = w.D1[i] * ys[i];
+  /* an infeasibility certificate is returned in place of the iterate it
+   * concerns: the dual ray in y (primal infeasible), the primal ray in x
+   * (dual infeasible), unprojected */
+  if (status == ORC_PRIMAL_INFEASIBLE || status == ORC_DUAL_INFEASIBLE) {
+    const double *xr0 = which == 2 ? w.x_prev : w.x_last, *yr0 = which == 2 ? w.y_prev : w.y_last;
+    if (status == ORC_PRIMAL_INFEASIBLE)
+      for (int32_t i = 0; i < m; ++i) y_out[i] = w.D1[i] * (w.y[i] - yr0[i]);
+    else
+      for (int32_t j = 0; j < n; ++j) x_out[j] = w.D2[j] * (w.x[j] - xr0[j]);
+  }
   if (status == ORC_NUMERICAL) orc_kkt_terms(lp, x_out, y_out, terms);
   info->status = status;
   info->which = which;
@@ -669,6 +792,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
   info->c_norm = terms[5];
   info->omega = omega;
   info->eta_hat = eta_hat;
+  info->ray_obj = ray[0];
+  info->ray_res = ray[1];
   free_work(&w);
   return ntrace;
 }

@@ -98,7 +98,7 @@ struct pdlp_solver {
   float *K_val32 = nullptr, *T_val32 = nullptr;
   double *D1 = nullptr, *D2 = nullptr, *work_m = nullptr, *work_n = nullptr;
   double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr, *l0 = nullptr, *u0 = nullptr;
-  int gridA = 1, gridB = 1, gridR1 = 1, gridR2 = 1, gridR3 = 1;
+  int gridA = 1, gridB = 1, gridR1 = 1, gridR2 = 1, gridR3 = 1, gridI = 1;
   int slots = 0;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -154,6 +154,7 @@ int validate(int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t 
 int check_params(const pdlp_params &p) {
   if (p.check_period < 1 || p.ruiz_iters < 0 || !(p.pc_alpha <= 2.0) || !(p.theta >= 0.0 && p.theta <= 1.0) ||
       !(p.eps_zero >= 0.0) || !(p.beta_suff > 0.0) || !(p.beta_nec > 0.0) || !(p.beta_art > 0.0) ||
+      !(p.eps_infeas >= 0.0) ||
       (p.value_bits != 64 && p.value_bits != 32))
     return fail(PDLP_ERR_INVALID, "invalid parameters");
   return PDLP_OK;
@@ -183,6 +184,7 @@ int build_graph(pdlp_solver *s) {
     if (e == cudaSuccess) e = launch_dual(s->K, s->V, s->st, s->gridB, s->cap_stream);
   }
   if (e == cudaSuccess) e = launch_check_primal(s->KT, s->V, s->st, s->gridR1, s->cap_stream);
+  if (e == cudaSuccess) e = launch_infeas(s->V, s->st, s->gridI, s->cap_stream);
   if (e == cudaSuccess) e = launch_check_dual(s->K, s->V, s->st, s->gridR2, s->cap_stream);
   if (e == cudaSuccess) e = launch_restart(s->V, s->st, s->gridR3, s->cap_stream);
   cudaGraph_t g = nullptr;
@@ -215,6 +217,7 @@ void pdlp_default_params(pdlp_params *p) {
   p->time_limit_s = 0.0;
   p->value_bits = 64;
   p->f32_polish = 1;
+  p->eps_infeas = 1e-8;
 }
 
 const char *pdlp_last_error(void) { return g_err.c_str(); }
@@ -303,6 +306,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
     int g = occupancy_grid(KC_R3, s->num_sms);
     const int64_t need = (mx + NT - 1) / NT;
     s->gridR3 = (int)(need < g ? (need > 0 ? need : 1) : g);
+    const int gi = occupancy_grid(KC_INFEAS, s->num_sms);
+    s->gridI = (int)(need < gi ? (need > 0 ? need : 1) : gi);
   }
   const bool f32 = prm.value_bits == 32;
 
@@ -316,11 +321,11 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + PADB), o_Tval = L.take(8 * Z + PADB);
   const size_t o_Kv32 = f32 ? L.take(4 * Z + PADB) : 0, o_Tv32 = f32 ? L.take(4 * Z + PADB) : 0;
   const size_t o_Ktl = L.take(sizeof(int2) * tilesK.size()), o_Ttl = L.take(sizeof(int2) * tilesT.size());
-  const size_t nvec_n = 17, nvec_m = 13;
+  const size_t nvec_n = 18, nvec_m = 14;
   const size_t o_vn = L.take(8 * N * nvec_n), o_vm = L.take(8 * (M + 1) * nvec_m);
   const size_t o_pA = L.take(8 * (size_t)s->gridA * NV_A), o_pB = L.take(8 * (size_t)s->gridB * NV_B);
   const size_t o_pR1 = L.take(8 * (size_t)s->gridR1 * NV_R1), o_pR2 = L.take(8 * (size_t)s->gridR2 * NV_R2);
-  const size_t o_pR3 = L.take(8 * (size_t)s->gridR3 * NV_R3);
+  const size_t o_pR3 = L.take(8 * (size_t)s->gridR3 * NV_R3), o_pI = L.take(8 * (size_t)s->gridI * NV_I);
   const size_t o_st = L.take(sizeof(DevState)), o_tr = L.take(sizeof(TraceRec) * TRACE_CAP);
   const size_t o_sc = L.take(8 * 8);
   const long long npw = 1LL << 20;  // exponent factors for the first 2^20 steps (16 MB)
@@ -367,6 +372,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.u0 = s->u0;
   V.q = s->q;
   V.D1 = s->D1;
+  V.rD2 = VN(17);
+  V.rD1 = VM(13);
   V.x[0] = VN(6);
   V.x[1] = VN(7);
   V.sx[0] = VN(8);
@@ -375,6 +382,10 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.gbar = VN(11);
   V.xlast = VN(12);
   V.xout = VN(13);
+  V.g0 = VN(14);
+  V.gprev = VN(15);
+  V.kx0 = VM(11);
+  V.gridI = s->gridI;
   V.y[0] = VM(2);
   V.y[1] = VM(3);
   V.sy[0] = VM(4);
@@ -389,6 +400,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.partR1 = (double *)(A + o_pR1);
   V.partR2 = (double *)(A + o_pR2);
   V.partR3 = (double *)(A + o_pR3);
+  V.partI = (double *)(A + o_pI);
   V.trace = (TraceRec *)(A + o_tr);
   V.pw = (const double *)(A + o_pw);
   V.npw = npw;
@@ -429,6 +441,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   CKS(setup_scale(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, s->D1, s->D2, s->work_m,
                   s->work_n, prm.ruiz_iters, prm.pc_alpha, st));
   CKS(setup_vectors(m, n, V.xout, V.yout, s->l0, s->u0, s->D1, s->D2, s->c, s->q, s->l, s->u, st));
+  CKS(setup_recip(n, s->D2, VN(17), st));
+  CKS(setup_recip(m, s->D1, VM(13), st));
   if (f32) {
     CKS(setup_f32(nnz, s->K_val, s->K_val32, st));
     CKS(setup_f32(nnz, s->T_val, s->T_val32, st));
@@ -506,6 +520,7 @@ int pdlp_begin(pdlp_solver *s, const double *x0, const double *y0, double tol, i
   h.trace_cap = TRACE_CAP;
   h.use_f32 = s->prm.value_bits == 32 ? 1 : 0;
   h.polish = s->prm.f32_polish ? 1 : 0;
+  h.eps_infeas = s->prm.eps_infeas;
   CK(cudaMemcpyAsync(s->st, s->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
   // KKT(z^{0,0}): K'y, Kx and the pieces of eq. (kkt) at the start point
   CK(launch_check_primal(s->KT, V, s->st, s->gridR1, st));
@@ -632,6 +647,8 @@ int pdlp_time_kernels(pdlp_solver *s, int32_t n_periods, double *ms, int64_t *la
       continue;
     }
     rc = timed(KC_R1, [](pdlp_solver *t, cudaStream_t q) { return launch_check_primal(t->KT, t->V, t->st, t->gridR1, q); });
+    if (!rc && h.mode == MODE_CHECK && h.eps_infeas > 0.0)
+      rc = timed(KC_INFEAS, [](pdlp_solver *t, cudaStream_t q) { return launch_infeas(t->V, t->st, t->gridI, q); });
     if (!rc) rc = timed(KC_R2, [](pdlp_solver *t, cudaStream_t q) { return launch_check_dual(t->K, t->V, t->st, t->gridR2, q); });
     if (!rc) rc = poll(h);
     if (!rc && h.status == ST_RUNNING && h.restart_to)
@@ -666,6 +683,10 @@ int pdlp_get_info(const pdlp_solver *s, pdlp_info *info) {
   info->solve_ms = s->solve_ms;
   info->graph_launches = s->launches;
   info->f64_switch_iter = h.f64_switch_k;
+  if (info->status == ST_PRIMAL_INFEASIBLE || info->status == ST_DUAL_INFEASIBLE) {
+    info->ray_obj = h.ray[0];
+    info->ray_res = h.ray[1];
+  }
   return PDLP_OK;
 }
 

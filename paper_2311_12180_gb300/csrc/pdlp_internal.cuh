@@ -21,6 +21,8 @@ constexpr int ST_OPTIMAL = 0;
 constexpr int ST_ITER_LIMIT = 1;
 constexpr int ST_TIME_LIMIT = 2;
 constexpr int ST_NUMERICAL = 3;
+constexpr int ST_PRIMAL_INFEASIBLE = 4;
+constexpr int ST_DUAL_INFEASIBLE = 5;
 
 constexpr int MODE_CHECK = 0;
 constexpr int MODE_INIT = 1;
@@ -34,6 +36,11 @@ constexpr int NV_B = 2;   // ||y'-y||^2, (y'-y)'(Kx'-Kx)
 constexpr int NV_R1 = 8;  // per point (cur, avg): rd2 scaled, rd2 original, c'x, l'lam+ - u'lam-
 constexpr int NV_R2 = 6;  // per point: rp2 scaled, rp2 original, q'y
 constexpr int NV_R3 = 2;  // ||x_new - x_last||^2, ||y_new - y_last||^2
+// Infeasibility pieces per ray (difference, normalised iterate), original LP:
+// ||-K'yr - lam||^2, l'lam+ - u'lam-, c'xr, ||bound-cone violation of xr||^2,
+// ||(K_E xr, min(K_G xr, 0))||^2, q'yr, ||min(yr_G, 0)||^2.
+constexpr int NV_I1 = 7;
+constexpr int NV_I = 2 * NV_I1;
 
 struct Csr {
   int32_t rows;
@@ -59,12 +66,15 @@ struct DevState {
   double cand[4];    // candidate pieces: rp2, rd2, pobj, dobj (scaled)
   double term[4];    // original-space pobj, dobj, ||rp||, ||rd|| at the last check
   double rel_kkt_best;     // FP32 polish: best original relative KKT seen at a restart
+  double eps_infeas;       // relative tolerance of the infeasibility certificates (0: off)
+  double ray[2];           // certificate found: its objective and residual norm
   long long k, t, attempts, restarts, checks, max_iter, f64_switch_k;
   int cur;           // which of the two buffers holds the accepted iterate
   int need_g;        // 1: g = K'y is stale (y changed since it was computed)
   int check_pending; // 1: a restart / termination check is due
   int status;        // ST_*
-  int which;         // 0: output the current iterate, 1: the average
+  int which;         // 0: output the current iterate, 1: the average; infeasible:
+                     // 2: difference ray, 3: normalised-iterate ray
   int restart_to;    // 0: none, 1: restart to current, 2: to average
   int mode;          // MODE_CHECK / MODE_INIT
   int P;
@@ -85,15 +95,19 @@ struct Vecs {
   int n, m, n_eq;
   int gridA, gridR1;
   // scaled problem data
-  const double *c, *l, *u, *D2;  // n
+  const double *c, *l, *u, *D2, *rD2;  // n (rD2 = 1 / D2)
   const double *l0, *u0;         // n, original bounds (output projection)
-  const double *q, *D1;          // m
+  const double *q, *D1, *rD1;    // m (rD1 = 1 / D1)
   // iterates (two buffers, DevState::cur selects the accepted one)
   double *x[2], *sx[2];          // n: iterate, epoch sum of eta * x
   double *y[2], *sy[2], *Kx[2];  // m
   double *g, *gbar, *xlast, *xout;  // n
   double *Kxbar, *ylast, *yout;     // m
-  double *partA, *partB, *partR1, *partR2, *partR3;
+  // infeasibility detection: K'y at the epoch start and at the previous
+  // accepted iterate (n), K x at the epoch start (m)
+  double *g0, *gprev, *kx0;
+  int gridI;
+  double *partA, *partB, *partR1, *partR2, *partR3, *partI;
   TraceRec *trace;
   // (k + 2)^-0.3 at pw[k] and (k + 2)^-0.6 at pw[npw + k] for k < npw
   const double *pw;
@@ -103,7 +117,7 @@ struct Vecs {
 // ---- kernel launchers (pdlp_kernels.cu) ----
 // KC_PRIMAL_REUSE: a k_primal launch that reuses the stored g = K'y (after a
 // rejected trial or a check) instead of recomputing it; timed separately.
-enum KernelClass { KC_PRIMAL = 0, KC_DUAL, KC_R1, KC_R2, KC_R3, KC_OUTPUT, KC_PRIMAL_REUSE, KC_NUM };
+enum KernelClass { KC_PRIMAL = 0, KC_DUAL, KC_R1, KC_R2, KC_R3, KC_OUTPUT, KC_PRIMAL_REUSE, KC_INFEAS, KC_NUM };
 const char *kernel_class_name(int kc);
 
 struct LaunchCfg {
@@ -115,6 +129,7 @@ cudaError_t launch_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cud
 cudaError_t launch_check_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s);
 cudaError_t launch_check_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cudaStream_t s);
 cudaError_t launch_restart(const Vecs &V, DevState *st, int grid, cudaStream_t s);
+cudaError_t launch_infeas(const Vecs &V, DevState *st, int grid, cudaStream_t s);
 cudaError_t launch_output(const Vecs &V, DevState *st, cudaStream_t s);
 cudaError_t launch_time_limit(DevState *st, cudaStream_t s);
 int occupancy_grid(int kc, int num_sms);
@@ -140,6 +155,8 @@ cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *
                           const double *u0, const double *D1, const double *D2, double *c, double *q, double *l,
                           double *u, cudaStream_t s);
 cudaError_t setup_f32(int64_t nnz, const double *val, float *val32, cudaStream_t s);
+// rD = 1 / D elementwise (the infeasibility pieces unscale with products)
+cudaError_t setup_recip(int32_t count, const double *D, double *rD, cudaStream_t s);
 // out[0] = sum (c~)^2, out[1] = sum (q~)^2, out[2] = max |K~|
 cudaError_t setup_scalars(int32_t m, int32_t n, int64_t nnz, const double *c, const double *q, const double *val,
                           double *out, cudaStream_t s);

@@ -18,6 +18,10 @@
 //   k_check_dual   (rows of K):   K xbar, primal residual pieces; its last CTA
 //             applies Sec. 4.1 termination, GetRestartCandidate and the three
 //             restart criteria of Sec. 3.4.
+//   k_infeas (elementwise, between the two):  pieces of the infeasibility
+//             certificates (Sec. 2.2, last bullet) for the difference of the
+//             last two accepted iterates and for the normalised iterate,
+//             from stored products (no SpMV).
 //   k_restart (elementwise):      moves the candidate into the iterate, resets
 //             the epoch average, and (last CTA) PrimalWeightUpdate.
 // Every kernel reads the device state at entry and returns at once when it
@@ -550,8 +554,9 @@ struct CheckPrimalEpi {
   const double *__restrict__ c, *__restrict__ l, *__restrict__ u, *__restrict__ d2, *__restrict__ x,
       *__restrict__ sx;
   double *__restrict__ g, *__restrict__ gbar;
+  double *__restrict__ g0, *__restrict__ gprev;  // kept for infeasibility detection when keep
   double invW;
-  int kind;
+  int kind, keep;
   double acc[NV_R1];
   double pc, pl, pu, pd2, px, psx, pg;
   __device__ __forceinline__ void prefetch(int j) {
@@ -561,7 +566,7 @@ struct CheckPrimalEpi {
     pd2 = d2[j];
     px = x[j];
     psx = kind ? sx[j] : 0.0;
-    pg = kind == 2 ? g[j] : 0.0;
+    pg = (kind == 2 || (kind == 1 && keep)) ? g[j] : 0.0;
   }
   template <int NV>
   __device__ __forceinline__ void finish(int j, const double (&s)[NV]) {
@@ -569,9 +574,11 @@ struct CheckPrimalEpi {
     if (kind == 0) {
       gj = s[0];
       g[j] = gj;
+      if (keep) g0[j] = gj;  // K'y at the epoch start
     } else if (kind == 1) {
       gj = s[0];
       gb = s[NV - 1];
+      if (keep) gprev[j] = pg;  // K'y of the previous accepted iterate
       g[j] = gj;
     } else {
       gb = s[0];
@@ -601,8 +608,11 @@ __global__ void __launch_bounds__(NT, 3) k_check_primal(Csr KT, Vecs V, DevState
   ep.sx = V.sx[cur];
   ep.g = V.g;
   ep.gbar = V.gbar;
+  ep.g0 = V.g0;
+  ep.gprev = V.gprev;
   ep.invW = check ? 1.0 / st->W : 0.0;
   ep.kind = !check ? 0 : (need_g ? 1 : 2);
+  ep.keep = st->eps_infeas > 0.0;
 #pragma unroll
   for (int a = 0; a < NV_R1; ++a) ep.acc[a] = 0.0;
   if (ep.kind == 0) {
@@ -656,7 +666,29 @@ __device__ __forceinline__ double sec41_rel(double pobj, double dobj, double rp,
 
 // p: the 8 dual-side sums (current 0..3, average 4..7); d: the 6 primal-side
 // sums (current 0..2, average 3..5).
-__device__ void check_decide(DevState *st, TraceRec *trace, const double *p, const double *d) {
+// Sec. 2.2 infeasibility detection on k_infeas' sums for one ray (original
+// LP): the dual ray certifies primal infeasibility when its objective
+// q'yr + l'lam+ - u'lam- is positive and ||(-K'yr - lam, min(yr_G, 0))||
+// is at most eps times it; the primal ray certifies dual infeasibility when
+// -c'xr is positive and ||(K_E xr, min(K_G xr, 0), cone violation)|| is at
+// most eps times it.  Returns the status, or ST_RUNNING.
+__device__ int infeas_status(const double *a, double eps, double *ray) {
+  const double obj_d = a[5] + a[1], res_d = sqrt(a[0] + a[6]);
+  if (obj_d > 0.0 && res_d <= eps * obj_d) {
+    ray[0] = obj_d;
+    ray[1] = res_d;
+    return ST_PRIMAL_INFEASIBLE;
+  }
+  const double obj_p = -a[2], res_p = sqrt(a[4] + a[3]);
+  if (obj_p > 0.0 && res_p <= eps * obj_p) {
+    ray[0] = obj_p;
+    ray[1] = res_p;
+    return ST_DUAL_INFEASIBLE;
+  }
+  return ST_RUNNING;
+}
+
+__device__ void check_decide(DevState *st, TraceRec *trace, const double *p, const double *d, const double *inf) {
   const double omega = st->omega;
   if (st->mode == MODE_INIT) {
     const double k0 = kkt_omega(d[0], p[0], p[2], d[2] + p[3], omega);
@@ -689,6 +721,16 @@ __device__ void check_decide(DevState *st, TraceRec *trace, const double *p, con
     st->status = ST_OPTIMAL;
     st->which = 1;
     return;
+  }
+  if (inf) {  // difference ray, then normalised-iterate ray
+    for (int r = 0; r < 2; ++r) {
+      const int stt = infeas_status(inf + r * NV_I1, st->eps_infeas, st->ray);
+      if (stt != ST_RUNNING) {
+        st->status = stt;
+        st->which = 2 + r;
+        return;
+      }
+    }
   }
   if (st->k >= st->max_iter) {
     st->status = ST_ITER_LIMIT;
@@ -751,9 +793,9 @@ __device__ void check_decide(DevState *st, TraceRec *trace, const double *p, con
 // {Kx}, stored as Kx); check = 1: sums = {K xbar}.
 struct CheckDualEpi {
   const double *__restrict__ q, *__restrict__ d1, *__restrict__ y, *__restrict__ sy;
-  double *__restrict__ kx, *__restrict__ kxbar;
+  double *__restrict__ kx, *__restrict__ kxbar, *__restrict__ kx0;
   double invW;
-  int check, n_eq;
+  int check, n_eq, keep;
   double acc[NV_R2];
   double pq, pd1, py, psy, pkx;
   __device__ __forceinline__ void prefetch(int i) {
@@ -769,6 +811,7 @@ struct CheckDualEpi {
     if (!check) {
       kxi = s[0];
       kx[i] = kxi;
+      if (keep) kx0[i] = kxi;  // K x at the epoch start
     }
     primal_piece(pq, kxi, ineq, pd1, py, acc);
     if (check) {
@@ -790,9 +833,11 @@ __global__ void __launch_bounds__(NT) k_check_dual(Csr K, Vecs V, DevState *__re
   ep.sy = V.sy[cur];
   ep.kx = V.Kx[cur];
   ep.kxbar = V.Kxbar;
+  ep.kx0 = V.kx0;
   ep.invW = check ? 1.0 / st->W : 0.0;
   ep.check = check ? 1 : 0;
   ep.n_eq = V.n_eq;
+  ep.keep = st->eps_infeas > 0.0;
 #pragma unroll
   for (int a = 0; a < NV_R2; ++a) ep.acc[a] = 0.0;
   if (!check) {
@@ -808,7 +853,89 @@ __global__ void __launch_bounds__(NT) k_check_dual(Csr K, Vecs V, DevState *__re
   if (!grid_finish<NV_R2>(ep.acc, V.partR2, &st->cnt[CNT_R2], sm.red, &sm.flag, tot)) return;
   double p[NV_R1];
   sum_partials<NV_R1>(V.partR1, V.gridR1, sm.red, p);
-  if (threadIdx.x == 0) check_decide(st, V.trace, p, tot);
+  double inf[NV_I];
+  const bool infeas = check && st->eps_infeas > 0.0;
+  if (infeas) sum_partials<NV_I>(V.partI, V.gridI, sm.red, inf);
+  if (threadIdx.x == 0) check_decide(st, V.trace, p, tot, infeas ? inf : nullptr);
+}
+
+// ---------------------------------------------------------------- infeasibility detection
+
+// Pieces of the two certificates (NV_I1 each, layout of NV_I1) for the rays
+// z - z_prev (difference of the last two accepted iterates; only when this
+// check's K'y pass stored K'y_prev) and z - z^{n,0} (the normalised iterate
+// times t: the tests are invariant to positive scaling), unscaled to the
+// original LP: xr = D2 dx^, yr = D1 dy^, K xr = (K~ dx^) / D1 and
+// K'yr = (K~' dy^) / D2 from the stored products, c'xr = c~'dx^ and
+// q'yr = q~'dy^.  Since D2 > 0, lambda = proj_Lambda(-K'yr) = p / D2 with
+// p = proj_Lambda(-K~' dy^), so l'lambda+ - u'lambda- = sum of l~ p (p > 0)
+// and u~ p (p < 0) in scaled terms.  Sign and finiteness tests read the IEEE
+// bits (integer pipe); GB300's FP64 pipe does only the arithmetic.  Runs
+// between k_check_primal (which refreshed g = K'y) and k_check_dual, whose
+// last CTA sums the block partials and decides.
+__device__ __forceinline__ bool neg_bits(double v) { return __double_as_longlong(v) < 0; }
+__device__ __forceinline__ bool pos_bits(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+__global__ void __launch_bounds__(NT) k_infeas(Vecs V, DevState *__restrict__ st) {
+  __shared__ double s_red[16 * NW];
+  if (st->status != ST_RUNNING || !st->check_pending || st->mode != MODE_CHECK || !(st->eps_infeas > 0.0)) return;
+  const int cur = st->cur, prv = cur ^ 1;
+  const int r0 = st->need_g ? 0 : 1;  // the difference ray needs this check's stored K'y_prev
+  double a[NV_I];
+#pragma unroll
+  for (int k = 0; k < NV_I; ++k) a[k] = 0.0;
+  const int stride = gridDim.x * NT;
+  for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += stride) {
+    const double d2 = V.D2[j], rd2 = V.rD2[j], lt = V.l[j], ut = V.u[j], cj = V.c[j], gj = V.g[j];
+    const double xj = V.x[cur][j];
+    const bool lf = finite_bits(lt), uf = finite_bits(ut);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (r < r0) continue;
+      double *b = a + r * NV_I1;
+      const double mg = (r == 0 ? V.gprev[j] : V.g0[j]) - gj;  // -(K~' dy^)_j
+      double p = mg;                                             // proj onto the cone of the bounds
+      if (!lf && !uf) p = 0.0;
+      else if (!uf && neg_bits(p)) p = 0.0;
+      else if (!lf && pos_bits(p)) p = 0.0;
+      const double res = (mg - p) * rd2;
+      b[0] = fma(res, res, b[0]);
+      if (pos_bits(p)) b[1] = fma(lt, p, b[1]);
+      else if (neg_bits(p)) b[1] = fma(ut, p, b[1]);
+      const double dx = xj - (r == 0 ? V.x[prv][j] : V.xlast[j]);
+      b[2] = fma(cj, dx, b[2]);
+      if ((lf && neg_bits(dx)) || (uf && pos_bits(dx))) {
+        const double xo = d2 * dx;
+        b[3] = fma(xo, xo, b[3]);
+      }
+    }
+  }
+  for (int i = blockIdx.x * NT + threadIdx.x; i < V.m; i += stride) {
+    const double d1 = V.D1[i], rd1 = V.rD1[i], qi = V.q[i], yi = V.y[cur][i], kxi = V.Kx[cur][i];
+    const bool ineq = i >= V.n_eq;
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (r < r0) continue;
+      double *b = a + r * NV_I1;
+      double kr = (kxi - (r == 0 ? V.Kx[prv][i] : V.kx0[i])) * rd1;
+      if (ineq && pos_bits(kr)) kr = 0.0;
+      b[4] = fma(kr, kr, b[4]);
+      const double dy = yi - (r == 0 ? V.y[prv][i] : V.ylast[i]);
+      b[5] = fma(qi, dy, b[5]);
+      if (ineq && neg_bits(dy)) {
+        const double yo = d1 * dy;
+        b[6] = fma(yo, yo, b[6]);
+      }
+    }
+  }
+  block_sum<NV_I>(a, s_red);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV_I; ++k) V.partI[(size_t)blockIdx.x * NV_I + k] = a[k];
+  }
 }
 
 // ---------------------------------------------------------------- restart
@@ -818,6 +945,7 @@ __global__ void __launch_bounds__(NT) k_restart(Vecs V, DevState *__restrict__ s
   __shared__ int s_flag;
   if (st->status != ST_RUNNING || !st->check_pending || st->restart_to == 0) return;
   const bool avg = st->restart_to == 2;
+  const bool keep = st->eps_infeas > 0.0;
   const int cur = st->cur;
   const double invW = 1.0 / st->W;
   double acc[2] = {0.0, 0.0};
@@ -833,6 +961,7 @@ __global__ void __launch_bounds__(NT) k_restart(Vecs V, DevState *__restrict__ s
     } else {
       xn = x[j];
     }
+    if (keep) V.g0[j] = V.g[j];  // K'y at the new epoch start
     const double d = xn - V.xlast[j];
     acc[0] = fma(d, d, acc[0]);
     V.xlast[j] = xn;
@@ -850,6 +979,7 @@ __global__ void __launch_bounds__(NT) k_restart(Vecs V, DevState *__restrict__ s
     } else {
       yn = y[i];
     }
+    if (keep) V.kx0[i] = kx[i];  // K x at the new epoch start
     const double d = yn - V.ylast[i];
     acc[1] = fma(d, d, acc[1]);
     V.ylast[i] = yn;
@@ -881,19 +1011,33 @@ __global__ void __launch_bounds__(NT) k_restart(Vecs V, DevState *__restrict__ s
 
 // ---------------------------------------------------------------- output
 
+// Original-space output: the current iterate or the average (projected onto
+// X), or, for an infeasibility status, the certificate ray in place of the
+// iterate it concerns (y for primal infeasibility, x for dual
+// infeasibility; unprojected).
 __global__ void __launch_bounds__(NT) k_output(Vecs V, DevState *__restrict__ st) {
-  const int which = st->which, cur = st->cur;
-  const double invW = which ? 1.0 / st->W : 0.0;
+  const int which = st->which, cur = st->cur, prv = cur ^ 1, status = st->status;
+  const bool avg = which == 1;
+  const bool xray = status == ST_DUAL_INFEASIBLE, yray = status == ST_PRIMAL_INFEASIBLE;
+  const double invW = avg ? 1.0 / st->W : 0.0;
   const int stride = gridDim.x * NT;
   for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += stride) {
-    const double xs = which ? invW * V.sx[cur][j] : V.x[cur][j];
+    if (xray) {
+      V.xout[j] = V.D2[j] * (V.x[cur][j] - (which == 2 ? V.x[prv][j] : V.xlast[j]));
+      continue;
+    }
+    const double xs = avg ? invW * V.sx[cur][j] : V.x[cur][j];
     double v = V.D2[j] * xs;
     if (v < V.l0[j]) v = V.l0[j];
     if (v > V.u0[j]) v = V.u0[j];
     V.xout[j] = v;
   }
   for (int i = blockIdx.x * NT + threadIdx.x; i < V.m; i += stride) {
-    const double ys = which ? invW * V.sy[cur][i] : V.y[cur][i];
+    if (yray) {
+      V.yout[i] = V.D1[i] * (V.y[cur][i] - (which == 2 ? V.y[prv][i] : V.ylast[i]));
+      continue;
+    }
+    const double ys = avg ? invW * V.sy[cur][i] : V.y[cur][i];
     V.yout[i] = V.D1[i] * ys;
   }
 }
@@ -906,7 +1050,7 @@ __global__ void k_time_limit(DevState *st) {
 
 const char *kernel_class_name(int kc) {
   static const char *names[KC_NUM] = {"k_primal", "k_dual", "k_check_primal", "k_check_dual", "k_restart",
-                                      "k_output", "k_primal_reuse_g"};
+                                      "k_output", "k_primal_reuse_g", "k_infeas"};
   return (kc >= 0 && kc < KC_NUM) ? names[kc] : "";
 }
 
@@ -918,6 +1062,7 @@ int occupancy_grid(int kc, int num_sms) {
     case KC_R1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_primal, NT, 0); break;
     case KC_R2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_check_dual, NT, 0); break;
     case KC_R3: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_restart, NT, 0); break;
+    case KC_INFEAS: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_infeas, NT, 0); break;
     default: nb = 4;
   }
   if (nb < 1) nb = 1;
@@ -943,6 +1088,10 @@ cudaError_t launch_check_dual(const Csr &K, const Vecs &V, DevState *st, int gri
 }
 cudaError_t launch_restart(const Vecs &V, DevState *st, int grid, cudaStream_t s) {
   k_restart<<<grid, NT, 0, s>>>(V, st);
+  return cudaGetLastError();
+}
+cudaError_t launch_infeas(const Vecs &V, DevState *st, int grid, cudaStream_t s) {
+  k_infeas<<<grid, NT, 0, s>>>(V, st);
   return cudaGetLastError();
 }
 cudaError_t launch_output(const Vecs &V, DevState *st, cudaStream_t s) {

@@ -181,6 +181,15 @@ cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *
   return cudaGetLastError();
 }
 
+__global__ void k_recip(int32_t count, const double *D, double *rD) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) rD[i] = 1.0 / D[i];
+}
+
+cudaError_t setup_recip(int32_t count, const double *D, double *rD, cudaStream_t s) {
+  if (count > 0) k_recip<<<grid_for(count), ST, 0, s>>>(count, D, rD);
+  return cudaGetLastError();
+}
+
 cudaError_t setup_f32(int64_t nnz, const double *val, float *val32, cudaStream_t s) {
   if (nnz > 0) k_f32<<<grid_for(nnz), ST, 0, s>>>(nnz, val, val32);
   return cudaGetLastError();

@@ -18,9 +18,10 @@ import numpy as np
 from . import _build
 
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM = 0, -1, -2, -3
-OPTIMAL, ITER_LIMIT, TIME_LIMIT, NUMERICAL = 0, 1, 2, 3
+OPTIMAL, ITER_LIMIT, TIME_LIMIT, NUMERICAL, PRIMAL_INFEASIBLE, DUAL_INFEASIBLE = 0, 1, 2, 3, 4, 5
 STATUS_NAMES = {OPTIMAL: "optimal", ITER_LIMIT: "iteration_limit", TIME_LIMIT: "time_limit",
-                NUMERICAL: "numerical_error", -1: "running"}
+                NUMERICAL: "numerical_error", PRIMAL_INFEASIBLE: "primal_infeasible",
+                DUAL_INFEASIBLE: "dual_infeasible", -1: "running"}
 
 
 class PdlpError(RuntimeError):
@@ -42,6 +43,7 @@ class pdlp_params(C.Structure):
         ("time_limit_s", C.c_double),
         ("value_bits", C.c_int32),
         ("f32_polish", C.c_int32),
+        ("eps_infeas", C.c_double),
     ]
 
 
@@ -65,6 +67,8 @@ class pdlp_info(C.Structure):
         ("solve_ms", C.c_double),
         ("graph_launches", C.c_int64),
         ("f64_switch_iter", C.c_int64),
+        ("ray_obj", C.c_double),
+        ("ray_res", C.c_double),
     ]
 
 

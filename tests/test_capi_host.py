@@ -41,11 +41,13 @@ def test_default_params(L):
     assert p.check_period == 64 and p.ruiz_iters == 10 and p.pc_alpha == 1.0
     assert (p.beta_suff, p.beta_nec, p.beta_art) == (0.2, 0.8, 0.36)
     assert p.theta == 0.5 and p.eps_zero == 1e-10 and p.value_bits == 64
+    assert p.eps_infeas == 1e-8
 
 
 def test_kernel_names(L):
     names = P.kernel_names()
     assert names[:2] == ["k_primal", "k_dual"]
+    assert "k_infeas" in names
 
 
 def _create(lp, **kw):
@@ -100,6 +102,12 @@ def test_invalid_params_rejected(L):
     p.value_bits = 16
     with pytest.raises(P.PdlpError):
         _create(lp, params=p)
+    for bad in (-1e-8, float("nan")):
+        p = P.pdlp_default_params()
+        p.eps_infeas = bad
+        with pytest.raises(P.PdlpError) as e:
+            _create(lp, params=p)
+        assert e.value.code == P.ERR_INVALID
 
 
 def test_null_handles_are_safe(L):
