@@ -86,8 +86,7 @@ typedef struct {
   int32_t f32_polish;     /* with value_bits = 32: switch the steps to the FP64 K when the original-
                              space relative KKT error stalls over two restarts above tol (1 = on) */
   double eps_infeas;      /* relative tolerance of the infeasibility certificates (default 1e-8);
-                             0 turns infeasibility detection off.  Single-LP solver only: the
-                             batched solver runs infeasible LPs to max_iter. */
+                             0 turns infeasibility detection off (single-LP and batched solvers) */
 } pdlp_params;
 
 /* Summary of the last solve (pdlp_get_info). */
@@ -263,7 +262,9 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
  * x0 / y0: packed HOST warm starts (LP i's block follows LP i-1's; lengths
  * sum of n / sum of m) or NULL for cold starts.  Outputs are packed the same
  * way: x_out (sum of n), y_out (sum of m), status and iters (count each);
- * any output pointer may be NULL.  Blocks until done. */
+ * any output pointer may be NULL.  An LP certified infeasible gets
+ * PDLP_PRIMAL_INFEASIBLE / PDLP_DUAL_INFEASIBLE with its ray in its y / x
+ * block, as in pdlp_solve.  Blocks until done. */
 int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double tol, int64_t max_iter,
                      double *x_out, double *y_out, int32_t *status, int64_t *iters);
 int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *stats);

@@ -47,21 +47,29 @@ constexpr int RED_TEAM = RED_BCAST + 8;  // 16 slots: team-reduction results
 constexpr int RED_SIZE = RED_TEAM + 16;
 
 // per-instance vector blocks
-enum { VM_Q = 0, VM_D1, VM_Y0, VM_Y1, VM_SY0, VM_SY1, VM_KX0, VM_KX1, VM_KXB, VM_YL, VM_YOUT, VM_Q0, VM_COUNT };
+// (VM_KXS / VN_GS: K x and K'y at the epoch start, VN_GP: K'y of the
+// previous accepted iterate, kept for infeasibility detection; touched only
+// at checks, they stay in global memory when the rest of an LP is resident
+// in shared memory: VM_RES / VN_RES blocks are copied in)
+enum { VM_Q = 0, VM_D1, VM_Y0, VM_Y1, VM_SY0, VM_SY1, VM_KX0, VM_KX1, VM_KXB, VM_YL, VM_YOUT, VM_Q0, VM_KXS,
+       VM_COUNT };
 enum { VN_C = 0, VN_L, VN_U, VN_D2, VN_L0, VN_U0, VN_X0, VN_X1, VN_SX0, VN_SX1, VN_G, VN_GB, VN_XL, VN_XOUT, VN_C0,
-       VN_COUNT };
+       VN_GS, VN_GP, VN_COUNT };
+constexpr int VM_RES = VM_KXS, VN_RES = VN_GS;
 
 struct Inst {
   int m, n, n_eq, gk, gt;  // gk / gt: lanes per row for K / K'
   int pad;
   long long kp, ke, tp, te;  // offsets of K row_ptr / nonzeros, K' row_ptr / nonzeros
   long long om, on;          // offsets of the m- and n-vector blocks
+  long long okm, okn;        // the same offsets, kept when om / on point into shared memory
   long long xo, yo;          // offsets in the packed outputs (sum of n / sum of m)
   double eta0, omega0, qn, cn;
 };
 
 struct Params {
   double tol, theta, eps_zero, beta_suff, beta_nec, beta_art;
+  double eps_infeas;  // relative tolerance of the infeasibility certificates (0: off)
   long long max_iter;
   int P, warm;
   // Algorithm 2 exponent factors, built once per solve by setup_pow_table
@@ -79,6 +87,7 @@ struct Arrays {
   const int *kptr, *kidx, *tptr, *tidx;
   double *kval, *tval;
   double *vm, *vn;
+  double *vmk, *vnk;      // global bases of the vector blocks (the kept vectors live there)
   const double *x0, *y0;  // packed warm start (or null)
   double *xout, *yout;
   int *status;
@@ -503,6 +512,10 @@ struct CheckT {
   double invW;
   int kind;  // 0: start point {g}; 1: {g, gbar}; 2: {gbar}, g current
   double acc[8];
+  // infeasibility detection (keep): K'y at the epoch start (kind 0) and of
+  // the previous accepted iterate (kind 1, the value this pass overwrites)
+  bool keep = false;
+  double *gs = nullptr, *gp = nullptr;
   __device__ __forceinline__ void piece(double cj, double gj, double lj, double uj, double dj, double xj, double *a) {
     const double d = cj - gj;
     const double lam = proj_lambda(d, lj, uj);
@@ -520,9 +533,11 @@ struct CheckT {
     if (kind == 0) {
       gj = s[0];
       g[j] = gj;
+      if (keep) gs[j] = gj;
     } else if (kind == 1) {
       gj = s[0];
       gb = s[NV - 1];
+      if (keep) gp[j] = ldv<CG>(g + j);
       g[j] = gj;
     } else {
       gb = s[0];
@@ -542,6 +557,9 @@ struct CheckK {
   double invW;
   int check, n_eq;
   double acc[6];
+  // infeasibility detection (keep): K x at the epoch start (start pass)
+  bool keep = false;
+  double *kxs = nullptr;
   __device__ __forceinline__ void piece(double qi, double kxi, bool ineq, double di, double yi, double *a) {
     double r = qi - kxi;
     if (ineq && r < 0.0) r = 0.0;
@@ -553,7 +571,10 @@ struct CheckK {
   __device__ __forceinline__ void operator()(int i, const double (&s)[1]) {
     const bool ineq = i >= n_eq;
     double kxi = check ? ldv<CG>(kx + i) : s[0];
-    if (!check) kx[i] = kxi;
+    if (!check) {
+      kx[i] = kxi;
+      if (keep) kxs[i] = kxi;
+    }
     piece(q[i], kxi, ineq, d1[i], ldv<CG>(y + i), acc);
     if (check) {
       kxbar[i] = s[0];
@@ -561,6 +582,65 @@ struct CheckK {
     }
   }
 };
+
+// This thread's share of the Sec. 2.2 infeasibility pieces for one ray,
+// z - z_prev (difference of the last two accepted iterates) or z - z^{n,0}
+// (the normalised iterate times t), unscaled to the original LP from the
+// stored products: xr = D2 dx^, yr = D1 dy^, K'yr = (K~' dy^) / D2,
+// K xr = (K~ dx^) / D1, c'xr = c~'dx^, q'yr = q~'dy^; with D2 > 0,
+// lambda = proj_Lambda(-K'yr) = pp / D2 for pp = proj_Lambda(-K~' dy^), so
+// l'lambda+ - u'lambda- = l~'pp+ - u~'pp- in scaled terms.  Layout:
+// {||-K'yr - lambda||^2, l'lambda+ - u'lambda-, c'xr, cone violation of xr
+// squared, ||(K_E xr, min(K_G xr, 0))||^2, q'yr, ||min(yr_G, 0)||^2}.
+template <bool CG>
+__device__ __forceinline__ void infeas_pieces(double (&f)[7], int n, int m, int n_eq, int e0, int es,
+                                              const double *g, const double *gref, const double *x,
+                                              const double *xref, const double *c, const double *l, const double *u,
+                                              const double *D2, const double *kx, const double *kxref,
+                                              const double *y, const double *yref, const double *q,
+                                              const double *D1) {
+#pragma unroll
+  for (int a = 0; a < 7; ++a) f[a] = 0.0;
+  for (int j = e0; j < n; j += es) {
+    const double lj = l[j], uj = u[j], dj = D2[j];
+    const bool lf = isfinite(lj), uf = isfinite(uj);
+    const double mg = ldv<CG>(gref + j) - ldv<CG>(g + j);  // -(K~' dy^)_j
+    const double pp = proj_lambda(mg, lj, uj);
+    const double res = (mg - pp) / dj;
+    f[0] = fma(res, res, f[0]);
+    if (pp > 0.0) f[1] = fma(lj, pp, f[1]);
+    if (pp < 0.0) f[1] = fma(uj, pp, f[1]);
+    const double dx = ldv<CG>(x + j) - ldv<CG>(xref + j);
+    f[2] = fma(c[j], dx, f[2]);
+    if ((lf && dx < 0.0) || (uf && dx > 0.0)) {
+      const double xo = dj * dx;
+      f[3] = fma(xo, xo, f[3]);
+    }
+  }
+  for (int i = e0; i < m; i += es) {
+    const bool ineq = i >= n_eq;
+    double kr = (ldv<CG>(kx + i) - ldv<CG>(kxref + i)) / D1[i];
+    if (ineq && kr > 0.0) kr = 0.0;
+    f[4] = fma(kr, kr, f[4]);
+    const double dy = ldv<CG>(y + i) - ldv<CG>(yref + i);
+    f[5] = fma(q[i], dy, f[5]);
+    if (ineq && dy < 0.0) {
+      const double yo = D1[i] * dy;
+      f[6] = fma(yo, yo, f[6]);
+    }
+  }
+}
+
+// Sec. 2.2 infeasibility tests on one ray's reduced pieces, the dual-ray
+// (primal infeasibility) test first; the same rule as the single-LP check.
+// Returns the status, ST_RUNNING if neither certificate holds.
+__device__ __forceinline__ int infeas_decide(const double (&a)[7], double eps) {
+  const double obj_d = a[5] + a[1], res_d = sqrt(a[0] + a[6]);
+  if (obj_d > 0.0 && res_d <= eps * obj_d) return ST_PRIMAL_INFEASIBLE;
+  const double obj_p = -a[2], res_p = sqrt(a[4] + a[3]);
+  if (obj_p > 0.0 && res_p <= eps * obj_p) return ST_DUAL_INFEASIBLE;
+  return ST_RUNNING;
+}
 
 template <class Grp>
 __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, int id, double *red, Grp &grp) {
@@ -577,6 +657,9 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
   double *y[2] = {VM(VM_Y0), VM(VM_Y1)}, *sy[2] = {VM(VM_SY0), VM(VM_SY1)}, *kx[2] = {VM(VM_KX0), VM(VM_KX1)};
   double *g = VN(VN_G), *gbar = VN(VN_GB), *xl = VN(VN_XL), *yl = VM(VM_YL), *kxb = VM(VM_KXB);
   const double *c = VN(VN_C), *l = VN(VN_L), *u = VN(VN_U), *D2 = VN(VN_D2), *q = VM(VM_Q), *D1 = VM(VM_D1);
+  const bool keep = p.eps_infeas > 0.0;  // infeasibility detection (vectors VN_GS, VN_GP, VM_KXS)
+  auto VMK = [&](int k) { return A.vmk + I.okm + (long long)k * m; };  // global memory always
+  auto VNK = [&](int k) { return A.vnk + I.okn + (long long)k * n; };
   // ---- start point (Sec. 4.1 "Initialization", or the warm start) ----
   for (int j = e0; j < n; j += es) {
     const double v = (p.warm && A.x0) ? A.x0[I.xo + j] / D2[j] : 0.0;
@@ -598,10 +681,14 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
   // KKT(z^{0,0}) with omega^0
   {
     CheckT<CG> ct{c, l, u, D2, x[0], sx[0], g, gbar, 0.0, 0, {0, 0, 0, 0, 0, 0, 0, 0}};
+    ct.keep = keep;
+    ct.gs = VNK(VN_GS);
     const double *const xs[1] = {y[0]};
     const double sc[1] = {1.0};
     rows_spmv<1, false, CG>(tp, ti, tv, n, I.gt, xs, sc, ct, part, parts);
     CheckK<CG> ck{q, D1, y[0], sy[0], kx[0], kxb, 0.0, 0, I.n_eq, {0, 0, 0, 0, 0, 0}};
+    ck.keep = keep;
+    ck.kxs = VMK(VM_KXS);
     const double *const xs2[1] = {x[0]};
     rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, xs2, sc, ck, part, parts);
     double s[5] = {ct.acc[0], ct.acc[2], ct.acc[3], ck.acc[0], ck.acc[2]};
@@ -678,12 +765,17 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     // ---- restart / termination check (Sec. 3.4 / Sec. 4.1) ----
     const double invW = 1.0 / W;
     CheckT<CG> ct{c, l, u, D2, x[cur], sx[cur], g, gbar, invW, 1, {0, 0, 0, 0, 0, 0, 0, 0}};
+    ct.keep = keep;
+    ct.gs = VNK(VN_GS);
+    ct.gp = VNK(VN_GP);
     {
       const double *const xs[2] = {y[cur], sy[cur]};
       const double sc[2] = {1.0, invW};
       rows_spmv<2, true, CG>(tp, ti, tv, n, I.gt, xs, sc, ct, part, parts);
     }
     CheckK<CG> ck{q, D1, y[cur], sy[cur], kx[cur], kxb, invW, 1, I.n_eq, {0, 0, 0, 0, 0, 0}};
+    ck.keep = keep;
+    ck.kxs = VMK(VM_KXS);
     {
       const double *const xs[1] = {sx[cur]};
       const double sc[1] = {invW};
@@ -699,10 +791,29 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
       status = ST_NUMERICAL;
       break;
     }
-    // Sec. 4.1 termination, GetRestartCandidate and the criteria of Sec. 3.4:
-    // scalar work, evaluated by one thread and broadcast (decision 0 / 1:
-    // optimal at the current / average point, 2: iteration limit, 3: go on,
-    // 4: restart)
+    // Sec. 2.2 infeasibility: the difference ray, then the normalised one
+    // (after the reduction's barriers: g, the kept K'y and Kx are written)
+    int istat = ST_RUNNING, iray = 0;
+    for (int r = 0; keep && r < 2 && istat == ST_RUNNING; ++r) {
+      double f[7];
+      infeas_pieces<CG>(f, n, m, I.n_eq, e0, es, g, VNK(r == 0 ? VN_GP : VN_GS), x[cur], r == 0 ? x[cur ^ 1] : xl,
+                        c, l, u, D2, kx[cur], r == 0 ? kx[cur ^ 1] : VMK(VM_KXS), y[cur], r == 0 ? y[cur ^ 1] : yl,
+                        q, D1);
+      if (!grp.template reduce<7>(f, red)) {
+        istat = ST_NUMERICAL;
+        break;
+      }
+      istat = infeas_decide(f, p.eps_infeas);
+      iray = 2 + r;
+    }
+    if (istat == ST_NUMERICAL) {
+      status = ST_NUMERICAL;
+      break;
+    }
+    // Sec. 4.1 termination, Sec. 2.2 infeasibility, GetRestartCandidate and
+    // the criteria of Sec. 3.4: scalar work, evaluated by one thread and
+    // broadcast (decision 0 / 1: optimal at the current / average point,
+    // 2: iteration limit, 3: go on, 4: restart, 5: infeasible)
     if (tid == 0) {
       const double pc = s[2], dc = s[10] + s[3], rpc = sqrt(s[9]), rdc = sqrt(s[1]);
       const double pa = s[6], da = s[13] + s[7], rpa = sqrt(s[12]), rda = sqrt(s[5]);
@@ -712,6 +823,10 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
         dec = 0.0;
       } else if (sec41_pass(pa, da, rpa, rda, p.tol, I.qn, I.cn)) {
         dec = 1.0;
+      } else if (istat != ST_RUNNING) {
+        dec = 5.0;
+        red[RED_BCAST + 3] = (double)istat;
+        red[RED_BCAST + 4] = (double)iray;
       } else if (k >= p.max_iter) {
         dec = 2.0;
       } else {
@@ -735,6 +850,11 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
       which = dec == 1 ? 1 : 0;
       break;
     }
+    if (dec == 5) {
+      status = (int)red[RED_BCAST + 3];
+      which = (int)red[RED_BCAST + 4];
+      break;
+    }
     if (dec == 3) {
       kkt_prev = red[RED_BCAST + 2];
       continue;
@@ -748,6 +868,7 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
         x[cur][j] = xn;
         g[j] = ldv<CG>(gbar + j);
       }
+      if (keep) VNK(VN_GS)[j] = cand_avg ? ldv<CG>(gbar + j) : ldv<CG>(g + j);  // K'y at the new epoch start
       const double d = xn - ldv<CG>(xl + j);
       dd[0] = fma(d, d, dd[0]);
       xl[j] = xn;
@@ -760,6 +881,7 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
         y[cur][i] = yn;
         kx[cur][i] = ldv<CG>(kxb + i);
       }
+      if (keep) VMK(VM_KXS)[i] = cand_avg ? ldv<CG>(kxb + i) : ldv<CG>(kx[cur] + i);  // K x at the new epoch start
       const double d = yn - ldv<CG>(yl + i);
       dd[1] = fma(d, d, dd[1]);
       yl[i] = yn;
@@ -789,11 +911,18 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     W = 0.0;
     t = 0;
   }
-  // ---- output in the original space ----
+  // ---- output in the original space (an infeasibility certificate in place
+  // of the iterate it concerns: y for primal, x for dual infeasibility) ----
   __syncthreads();
-  const double invW = which ? 1.0 / W : 0.0;
+  const bool avg = which == 1;
+  const bool xray = status == ST_DUAL_INFEASIBLE, yray = status == ST_PRIMAL_INFEASIBLE;
+  const double invW = avg ? 1.0 / W : 0.0;
   for (int j = e0; j < n; j += es) {
-    const double xs = which ? invW * ldv<CG>(sx[cur] + j) : ldv<CG>(x[cur] + j);
+    if (xray) {
+      A.xout[I.xo + j] = D2[j] * (ldv<CG>(x[cur] + j) - ldv<CG>((which == 2 ? x[cur ^ 1] : xl) + j));
+      continue;
+    }
+    const double xs = avg ? invW * ldv<CG>(sx[cur] + j) : ldv<CG>(x[cur] + j);
     double v = D2[j] * xs;
     const double l0 = vn[(long long)VN_L0 * n + j], u0 = vn[(long long)VN_U0 * n + j];
     if (v < l0) v = l0;
@@ -801,7 +930,11 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     A.xout[I.xo + j] = v;
   }
   for (int i = e0; i < m; i += es) {
-    const double ys = which ? invW * ldv<CG>(sy[cur] + i) : ldv<CG>(y[cur] + i);
+    if (yray) {
+      A.yout[I.yo + i] = D1[i] * (ldv<CG>(y[cur] + i) - ldv<CG>((which == 2 ? y[cur ^ 1] : yl) + i));
+      continue;
+    }
+    const double ys = avg ? invW * ldv<CG>(sy[cur] + i) : ldv<CG>(y[cur] + i);
     A.yout[I.yo + i] = D1[i] * ys;
   }
   if (tid == 0 && part == 0) {
@@ -819,7 +952,7 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
 __host__ __device__ inline long long resident_bytes(int m, int n, long long nnz) {
   auto a16 = [](long long b) { return (b + 15) & ~15LL; };
   return a16(4LL * (m + 1)) + a16(4LL * (n + 1)) + 2 * a16(4 * nnz) + 2 * a16(8 * nnz) +
-         a16(8LL * VM_COUNT * m) + a16(8LL * VN_COUNT * n);
+         a16(8LL * VM_RES * m) + a16(8LL * VN_RES * n);
 }
 
 template <typename T>
@@ -852,7 +985,7 @@ __device__ void solve_alone(const Arrays &A, const Inst *__restrict__ inst, int 
     int *kptr = carve<int>(cur, I.m + 1), *tptr = carve<int>(cur, I.n + 1);
     int *kidx = carve<int>(cur, nnz), *tidx = carve<int>(cur, nnz);
     double *kval = carve<double>(cur, nnz), *tval = carve<double>(cur, nnz);
-    double *vm = carve<double>(cur, (long long)VM_COUNT * I.m), *vn = carve<double>(cur, (long long)VN_COUNT * I.n);
+    double *vm = carve<double>(cur, (long long)VM_RES * I.m), *vn = carve<double>(cur, (long long)VN_RES * I.n);
     // row pointers relative to the LP's first nonzero
     const int k0 = A.kptr[I.kp], t0 = A.tptr[I.tp];
     for (int i = threadIdx.x; i <= I.m; i += NTB) kptr[i] = A.kptr[I.kp + i] - k0;
@@ -861,8 +994,8 @@ __device__ void solve_alone(const Arrays &A, const Inst *__restrict__ inst, int 
     copy_in(tidx, A.tidx + I.te + t0, nnz);
     copy_in(kval, A.kval + I.ke + k0, nnz);
     copy_in(tval, A.tval + I.te + t0, nnz);
-    copy_in(vm, A.vm + I.om, (long long)VM_COUNT * I.m);
-    copy_in(vn, A.vn + I.on, (long long)VN_COUNT * I.n);
+    copy_in(vm, A.vm + I.om, (long long)VM_RES * I.m);
+    copy_in(vn, A.vn + I.on, (long long)VN_RES * I.n);
     __syncthreads();
     R.kptr = kptr;
     R.tptr = tptr;
@@ -1098,8 +1231,8 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
     I.ke = KE;
     I.tp = TP;
     I.te = TE;
-    I.om = OM;
-    I.on = ON;
+    I.om = I.okm = OM;
+    I.on = I.okn = ON;
     I.xo = XO;
     I.yo = YO;
     KP += L.m + 1;
@@ -1180,8 +1313,8 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   b->A.tptr = (int *)(Ar + o_tptr);
   b->A.tidx = (int *)(Ar + o_tidx);
   b->A.tval = (double *)(Ar + o_tval);
-  b->A.vm = (double *)(Ar + o_vm);
-  b->A.vn = (double *)(Ar + o_vn);
+  b->A.vm = b->A.vmk = (double *)(Ar + o_vm);
+  b->A.vn = b->A.vnk = (double *)(Ar + o_vn);
   b->A.xout = (double *)(Ar + o_xo);
   b->A.yout = (double *)(Ar + o_yo);
   b->d_x0 = (double *)(Ar + o_x0);
@@ -1288,6 +1421,7 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   tp.tol = 0.0;
   tp.theta = prm.theta;
   tp.eps_zero = prm.eps_zero;
+  tp.eps_infeas = prm.eps_infeas;
   tp.beta_suff = prm.beta_suff;
   tp.beta_nec = prm.beta_nec;
   tp.beta_art = prm.beta_art;
@@ -1344,6 +1478,7 @@ int pdlp_batch_solve(pdlp_batch *b, const double *x0, const double *y0, double t
   p.tol = tol;
   p.theta = b->prm.theta;
   p.eps_zero = b->prm.eps_zero;
+  p.eps_infeas = b->prm.eps_infeas;
   p.beta_suff = b->prm.beta_suff;
   p.beta_nec = b->prm.beta_nec;
   p.beta_art = b->prm.beta_art;

@@ -70,3 +70,26 @@ def test_detection_leaves_feasible_solves_unchanged():
         assert st1 == st0 == P.OPTIMAL and it1 == it0
         assert np.array_equal(x1, x0) and np.array_equal(y1, y0)
 
+
+
+def test_batch_detects_like_the_oracle():
+    """The batched solver runs the same tests per LP; two of the infeasible
+    LPs are large enough for a team of CTAs (>= 32768 nonzeros)."""
+    big = dict(m_eq=600, m_ineq=600, n=3000, density=0.02)
+    lps = [lpgen.tiny_lp(50), lpgen.infeasible_lp(0, "primal"), lpgen.infeasible_lp(1, "primal_bounds"),
+           lpgen.infeasible_lp(2, "dual"), lpgen.tiny_lp(51), lpgen.infeasible_lp(5, "primal", **big),
+           lpgen.infeasible_lp(6, "dual", **big)]
+    assert lps[5].nnz >= 32768 and lps[6].nnz >= 32768
+    with P.BatchSolver(lps, eps_infeas=EPS) as b:
+        xs, ys, st, it = b.solve(tol=1e-8, max_iter=400000)
+    for i, lp in enumerate(lps):
+        r = oracle.solve(lp, tol=1e-8, max_iter=400000, eps_infeas=EPS)
+        assert st[i] == r.status, (i, st[i], r.status)
+        assert it[i] <= 2 * r.iters + 128 and r.iters <= 2 * it[i] + 128
+        if st[i] == P.OPTIMAL:
+            assert oracle.passes(lp, xs[i], ys[i], 1e-8)
+        else:
+            _check_ray(lp, st[i], xs[i], ys[i])
+    with P.BatchSolver(lps[1:4], eps_infeas=0.0) as b:
+        _, _, st0, it0 = b.solve(tol=1e-8, max_iter=4096)
+    assert list(st0) == [P.ITER_LIMIT] * 3 and list(it0) == [4096] * 3
