@@ -31,6 +31,7 @@
 #include "pdlp.h"
 #include "pdlp_host.h"
 #include "pdlp_internal.cuh"
+#include "pdlp_setup.cuh"
 
 namespace pdlp {
 namespace batch {

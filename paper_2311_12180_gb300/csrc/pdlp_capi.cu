@@ -18,6 +18,7 @@
 #include "pdlp.h"
 #include "pdlp_host.h"
 #include "pdlp_internal.cuh"
+#include "pdlp_setup.cuh"
 
 using namespace pdlp;
 
@@ -240,19 +241,9 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const int64_t nnz = row_ptr[m];
   if (nnz >= ((int64_t)1 << 31)) return fail(PDLP_ERR_INVALID, "nnz must be < 2^31");
 
-  // ---- host: K' row starts and tile schedules; K' itself on the device
-  // (setup_transpose) unless a column is too long for its per-column sort ----
-  std::vector<int32_t> tp((size_t)n + 1, 0), ti;
-  std::vector<double> tv;
-  const bool device_transpose =
-      csr_column_starts(m, n, row_ptr, col_idx, tp.data()) <= transpose_max_segment();
-  if (!device_transpose) {
-    ti.resize((size_t)nnz);
-    tv.resize((size_t)nnz);
-    csr_transpose(m, n, row_ptr, col_idx, val, tp.data(), ti.data(), tv.data());
-  }
+  // ---- host: K's tile schedule; K' (row starts, entries) is built on the
+  // device after the upload, and its tile schedule from the row starts ----
   std::vector<int2> tilesK = build_tiles(row_ptr, m);
-  std::vector<int2> tilesT = build_tiles(tp.data(), n);
   double qn = 0.0, cn = 0.0;
   for (int32_t i = 0; i < m; ++i) qn += q[i] * q[i];
   for (int32_t j = 0; j < n; ++j) cn += c[j] * c[j];
@@ -297,9 +288,12 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   s->h_st->status = ST_RUNNING;
 
   auto capped = [](int g, int ntiles) { return g < (ntiles > 0 ? ntiles : 1) ? g : (ntiles > 0 ? ntiles : 1); };
-  s->gridA = capped(occupancy_grid(KC_PRIMAL, s->num_sms), (int)tilesT.size() - 1);
+  // K' grids: the occupancy bound sizes the partial-sum arrays; capped by
+  // K''s tile count once it is known
+  const int gridA_max = occupancy_grid(KC_PRIMAL, s->num_sms), gridR1_max = occupancy_grid(KC_R1, s->num_sms);
+  s->gridA = gridA_max;
   s->gridB = capped(occupancy_grid(KC_DUAL, s->num_sms), (int)tilesK.size() - 1);
-  s->gridR1 = capped(occupancy_grid(KC_R1, s->num_sms), (int)tilesT.size() - 1);
+  s->gridR1 = gridR1_max;
   s->gridR2 = capped(occupancy_grid(KC_R2, s->num_sms), (int)tilesK.size() - 1);
   {
     const int64_t mx = n > m ? n : m;
@@ -320,7 +314,8 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z + PADB), o_Kval = L.take(8 * Z + PADB);
   const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + PADB), o_Tval = L.take(8 * Z + PADB);
   const size_t o_Kv32 = f32 ? L.take(4 * Z + PADB) : 0, o_Tv32 = f32 ? L.take(4 * Z + PADB) : 0;
-  const size_t o_Ktl = L.take(sizeof(int2) * tilesK.size()), o_Ttl = L.take(sizeof(int2) * tilesT.size());
+  // K''s tiles: at most one per row
+  const size_t o_Ktl = L.take(sizeof(int2) * tilesK.size()), o_Ttl = L.take(sizeof(int2) * (N + 1));
   const size_t nvec_n = 18, nvec_m = 14;
   const size_t o_vn = L.take(8 * N * nvec_n), o_vm = L.take(8 * (M + 1) * nvec_m);
   const size_t o_pA = L.take(8 * (size_t)s->gridA * NV_A), o_pB = L.take(8 * (size_t)s->gridB * NV_B);
@@ -362,8 +357,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.n = n;
   V.m = m;
   V.n_eq = n_eq;
-  V.gridA = s->gridA;
-  V.gridR1 = s->gridR1;
+
   V.c = s->c;
   V.l = s->l;
   V.u = s->u;
@@ -406,7 +400,6 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.npw = npw;
 
   s->K = Csr{m, (int32_t)tilesK.size() - 1, s->K_ptr, s->K_idx, s->K_val, s->K_val32, Ktl};
-  s->KT = Csr{n, (int32_t)tilesT.size() - 1, s->T_ptr, s->T_idx, s->T_val, s->T_val32, Ttl};
 
   // ---- transfers ----
   cudaStream_t st = s->stream;
@@ -415,23 +408,44 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   if (nnz) {
     CKS(cudaMemcpyAsync(s->K_idx, col_idx, 4 * Z, cudaMemcpyHostToDevice, st));
     CKS(cudaMemcpyAsync(s->K_val, val, 8 * Z, cudaMemcpyHostToDevice, st));
-    if (!device_transpose) {
-      CKS(cudaMemcpyAsync(s->T_idx, ti.data(), 4 * Z, cudaMemcpyHostToDevice, st));
-      CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
-    }
-  }
-  CKS(cudaMemcpyAsync(s->T_ptr, tp.data(), 4 * (N + 1), cudaMemcpyHostToDevice, st));
-  if (device_transpose && nnz) {
-    int32_t *work = nullptr;
-    CKS(cudaMallocAsync((void **)&work, sizeof(int32_t) * transpose_work_ints(n, nnz), st));
-    const cudaError_t et = setup_transpose(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val,
-                                           work, st);
-    const cudaError_t ef = cudaFreeAsync(work, st);
-    CKS(et);
-    CKS(ef);
   }
   CKS(cudaMemcpyAsync(Ktl, tilesK.data(), sizeof(int2) * tilesK.size(), cudaMemcpyHostToDevice, st));
+
+  // ---- K' on the device: row starts from K's column counts, then the
+  // stable transpose (the threaded host counting sort when a column is
+  // longer than the device's per-column sort takes); its tile schedule on
+  // the host from the row starts ----
+  std::vector<int32_t> tp((size_t)n + 1, 0);
+  int32_t longest = 0;
+  {
+    const size_t wcs = col_starts_work_ints(n);
+    int32_t *work = nullptr;
+    CKS(cudaMallocAsync((void **)&work, sizeof(int32_t) * (wcs + transpose_work_ints(n, nnz)), st));
+    cudaError_t e = setup_col_starts(n, nnz, s->K_idx, s->T_ptr, work, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tp.data(), s->T_ptr, 4 * (N + 1), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&longest, work, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && nnz && longest <= transpose_max_segment())
+      e = setup_transpose(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, work + wcs, st);
+    const cudaError_t ef = cudaFreeAsync(work, st);
+    CKS(e);
+    CKS(ef);
+  }
+  if (nnz && longest > transpose_max_segment()) {
+    std::vector<int32_t> tp_h((size_t)n + 1), ti((size_t)nnz);
+    std::vector<double> tv((size_t)nnz);
+    csr_transpose(m, n, row_ptr, col_idx, val, tp_h.data(), ti.data(), tv.data());
+    CKS(cudaMemcpyAsync(s->T_idx, ti.data(), 4 * Z, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
+    CKS(cudaStreamSynchronize(st));  // the host arrays go out of scope
+  }
+  std::vector<int2> tilesT = build_tiles(tp.data(), n);
   CKS(cudaMemcpyAsync(Ttl, tilesT.data(), sizeof(int2) * tilesT.size(), cudaMemcpyHostToDevice, st));
+  s->gridA = capped(gridA_max, (int)tilesT.size() - 1);
+  s->gridR1 = capped(gridR1_max, (int)tilesT.size() - 1);
+  V.gridA = s->gridA;
+  V.gridR1 = s->gridR1;
+  s->KT = Csr{n, (int32_t)tilesT.size() - 1, s->T_ptr, s->T_idx, s->T_val, s->T_val32, Ttl};
   CKS(cudaMemcpyAsync(s->l0, l, 8 * N, cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(s->u0, u, 8 * N, cudaMemcpyHostToDevice, st));
   CKS(cudaMemcpyAsync(V.xout, c, 8 * N, cudaMemcpyHostToDevice, st));  // original c, consumed below

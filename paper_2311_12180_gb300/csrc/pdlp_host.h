@@ -1,5 +1,7 @@
 // Host-side helpers of the create paths: a small thread pool loop and the
-// stable CSR transpose that builds K' from K.
+// stable CSR transpose that builds K' from K on the host (the batched
+// solver's LPs, and a single LP with a column longer than the device
+// transpose's per-column sort takes).
 #pragma once
 
 #include <stdint.h>
@@ -81,37 +83,6 @@ inline void csr_transpose(int32_t m, int32_t n, const int32_t *rp, const int32_t
         tv[pos] = v[e];
       }
   });
-}
-
-// Row starts tp (n + 1) of K' from K's column counts; returns the largest
-// column count.  Rows of K are split into T ranges, counted per thread and
-// summed per column.
-inline int32_t csr_column_starts(int32_t m, int32_t n, const int32_t *rp, const int32_t *ci, int32_t *tp) {
-  const int64_t nnz = rp[m];
-  const int T = std::max(1, std::min(host_threads(nnz), std::max(1, m)));
-  std::vector<int32_t> cnt((size_t)T * n, 0);
-  parallel_for(T, [&](int t) {
-    int32_t *c = cnt.data() + (size_t)t * n;
-    const int64_t e0 = nnz * t / T, e1 = nnz * (t + 1) / T;
-    for (int64_t e = e0; e < e1; ++e) ++c[ci[e]];
-  });
-  // per-column totals into tp[c + 1], column ranges in parallel
-  const int TC = host_threads(n);
-  parallel_for(TC, [&](int w) {
-    const int32_t c0 = (int32_t)((int64_t)n * w / TC), c1 = (int32_t)((int64_t)n * (w + 1) / TC);
-    for (int32_t c = c0; c < c1; ++c) tp[c + 1] = cnt[c];
-    for (int t = 1; t < T; ++t) {
-      const int32_t *row = cnt.data() + (size_t)t * n;
-      for (int32_t c = c0; c < c1; ++c) tp[c + 1] += row[c];
-    }
-  });
-  tp[0] = 0;
-  int32_t mx = 0;
-  for (int32_t c = 0; c < n; ++c) {
-    mx = std::max(mx, tp[c + 1]);
-    tp[c + 1] += tp[c];
-  }
-  return mx;
 }
 
 }  // namespace pdlp

@@ -133,35 +133,7 @@ cudaError_t launch_infeas(const Vecs &V, DevState *st, int grid, cudaStream_t s)
 cudaError_t launch_output(const Vecs &V, DevState *st, cudaStream_t s);
 cudaError_t launch_time_limit(DevState *st, cudaStream_t s);
 int occupancy_grid(int kc, int num_sms);
-cudaError_t kernels_init();
-// Fills the Algorithm 2 exponent-factor table: pw[k] = (k + 2)^-0.3 and
-// pw[count + k] = (k + 2)^-0.6 for k < count (the same pow() the step test calls).
-cudaError_t setup_pow_table(double *pw, long long count, cudaStream_t s);
-// K' on the device (pdlp_setup.cu), given its row starts T_ptr (already on
-// the device): the stable transpose, equal to the host counting sort, for
-// columns of at most transpose_max_segment() entries, with
-// transpose_work_ints(n, nnz) ints of scratch.
-cudaError_t setup_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
-                            const double *K_val, const int32_t *T_ptr, int32_t *T_idx, double *T_val, int32_t *work,
-                            cudaStream_t s);
-size_t transpose_work_ints(int32_t n, int64_t nnz);
-int transpose_max_segment();  // one-time function attributes (dynamic shared memory)
-
-// ---- setup kernels (pdlp_setup.cu) ----
-cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32_t *K_idx, double *K_val,
-                        int32_t *T_ptr, int32_t *T_idx, double *T_val, double *D1, double *D2, double *work_m,
-                        double *work_n, int ruiz_iters, double pc_alpha, cudaStream_t s);
-cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *q0, const double *l0,
-                          const double *u0, const double *D1, const double *D2, double *c, double *q, double *l,
-                          double *u, cudaStream_t s);
-cudaError_t setup_f32(int64_t nnz, const double *val, float *val32, cudaStream_t s);
-// rD = 1 / D elementwise (the infeasibility pieces unscale with products)
-cudaError_t setup_recip(int32_t count, const double *D, double *rD, cudaStream_t s);
-// out[0] = sum (c~)^2, out[1] = sum (q~)^2, out[2] = max |K~|
-cudaError_t setup_scalars(int32_t m, int32_t n, int64_t nnz, const double *c, const double *q, const double *val,
-                          double *out, cudaStream_t s);
-cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0, const double *D1,
-                       const double *D2, double *x, double *y, cudaStream_t s);
+cudaError_t kernels_init();  // one-time kernel attributes (none needed at present)
 
 // Records `msg` as the calling thread's pdlp_last_error() and returns `code`.
 int set_error(int code, const char *msg);

@@ -14,6 +14,7 @@
 
 #include "pdlp.h"
 #include "pdlp_internal.cuh"
+#include "pdlp_setup.cuh"
 
 namespace pdlp {
 
@@ -207,9 +208,112 @@ cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0,
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- K' row starts on the device
+//
+// Column counts of K (atomic increments into T_ptr[1 + column]), then an
+// inclusive scan of T_ptr[1..n] in place: T_ptr becomes K''s row starts.
+// The scan is per 1024-element block (warp shuffles, then the warp totals),
+// an exclusive scan of the block totals, and a final add; the largest column
+// count is kept for the choice between the device and the host transpose.
+
+namespace {
+
+constexpr int SCAN_B = 1024;
+
+__global__ void k_col_count(const int32_t *__restrict__ idx, int64_t nnz, int32_t *__restrict__ cnt1) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(cnt1 + idx[e], 1);
+}
+
+// Inclusive scan of x over the SCAN_B threads of the block (every thread
+// gets its prefix); sh holds 32 ints.
+__device__ __forceinline__ int32_t block_incl_scan(int32_t x, int32_t *sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sh[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = sh[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sh[lane] = w;
+  }
+  __syncthreads();
+  if (warp > 0) x += sh[warp - 1];
+  __syncthreads();  // sh is reused by the caller's next scan
+  return x;
+}
+
+__global__ void __launch_bounds__(SCAN_B) k_scan_local(int32_t *__restrict__ a, int32_t count,
+                                                       int32_t *__restrict__ bsum, int32_t *__restrict__ mx) {
+  __shared__ int32_t sh[32];
+  const int64_t i = (int64_t)blockIdx.x * SCAN_B + threadIdx.x;
+  const int32_t v = i < count ? a[i] : 0;
+  int32_t m = v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, m);
+  const int32_t x = block_incl_scan(v, sh);
+  if (i < count) a[i] = x;
+  if (threadIdx.x == SCAN_B - 1) bsum[blockIdx.x] = x;
+}
+
+// Exclusive scan of the nb block totals in place (one block, chunks of SCAN_B).
+__global__ void __launch_bounds__(SCAN_B) k_scan_blocks(int32_t *__restrict__ bsum, int32_t nb) {
+  __shared__ int32_t sh[32];
+  __shared__ int32_t total;
+  int32_t carry = 0;  // sum of the earlier chunks, the same in every thread
+  for (int32_t base = 0; base < nb; base += SCAN_B) {
+    const int32_t i = base + threadIdx.x;
+    const int32_t v = i < nb ? bsum[i] : 0;
+    const int32_t x = block_incl_scan(v, sh);
+    if (i < nb) bsum[i] = carry + x - v;
+    if (threadIdx.x == SCAN_B - 1) total = x;
+    __syncthreads();
+    carry += total;
+    __syncthreads();
+  }
+}
+
+__global__ void k_scan_add(int32_t *__restrict__ a, int32_t count, const int32_t *__restrict__ bsum) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] += bsum[i / SCAN_B];
+}
+
+}  // namespace
+
+size_t col_starts_work_ints(int32_t n) { return 4 + ((size_t)n + SCAN_B - 1) / SCAN_B; }
+
+cudaError_t setup_col_starts(int32_t n, int64_t nnz, const int32_t *K_idx, int32_t *T_ptr, int32_t *work,
+                             cudaStream_t s) {
+  // work: the largest column count (work[0]), block totals (work + 4)
+  const int32_t nb = (int32_t)(((int64_t)n + SCAN_B - 1) / SCAN_B);
+  cudaError_t e = cudaMemsetAsync(T_ptr, 0, sizeof(int32_t) * ((size_t)n + 1), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(work, 0, sizeof(int32_t) * 4, s);
+  if (e != cudaSuccess) return e;
+  if (nnz > 0) {
+    int64_t g = (nnz + 255) / 256;
+    if (g > 152 * 64) g = 152 * 64;
+    k_col_count<<<(int)g, 256, 0, s>>>(K_idx, nnz, T_ptr + 1);
+  }
+  k_scan_local<<<nb, SCAN_B, 0, s>>>(T_ptr + 1, n, work + 4, work);
+  k_scan_blocks<<<1, SCAN_B, 0, s>>>(work + 4, nb);
+  int64_t g = ((int64_t)n + 255) / 256;
+  if (g > 152 * 64) g = 152 * 64;
+  k_scan_add<<<(int)g, 256, 0, s>>>(T_ptr + 1, n, work + 4);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- K' on the device
 //
-// Stable transpose, given K' row starts (from the host's column counts): a
+// Stable transpose, given K' row starts (setup_col_starts): a
 // scatter of entry numbers into their columns (atomic cursors: arbitrary
 // order), a sort of each column's entry numbers (which restores the row
 // order, since K's entries are numbered row by row), and a gather of rows and
