@@ -289,7 +289,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
 
   auto capped = [](int g, int ntiles) { return g < (ntiles > 0 ? ntiles : 1) ? g : (ntiles > 0 ? ntiles : 1); };
   // K' grids: the occupancy bound sizes the partial-sum arrays; capped by
-  // K''s tile count once it is known
+  // the tile count of K' once it is known
   const int gridA_max = occupancy_grid(KC_PRIMAL, s->num_sms), gridR1_max = occupancy_grid(KC_R1, s->num_sms);
   s->gridA = gridA_max;
   s->gridB = capped(occupancy_grid(KC_DUAL, s->num_sms), (int)tilesK.size() - 1);
@@ -314,7 +314,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z + PADB), o_Kval = L.take(8 * Z + PADB);
   const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + PADB), o_Tval = L.take(8 * Z + PADB);
   const size_t o_Kv32 = f32 ? L.take(4 * Z + PADB) : 0, o_Tv32 = f32 ? L.take(4 * Z + PADB) : 0;
-  // K''s tiles: at most one per row
+  // tiles of K': at most one per row
   const size_t o_Ktl = L.take(sizeof(int2) * tilesK.size()), o_Ttl = L.take(sizeof(int2) * (N + 1));
   const size_t nvec_n = 18, nvec_m = 14;
   const size_t o_vn = L.take(8 * N * nvec_n), o_vm = L.take(8 * (M + 1) * nvec_m);

@@ -211,7 +211,7 @@ cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0,
 // ---------------------------------------------------------------- K' row starts on the device
 //
 // Column counts of K (atomic increments into T_ptr[1 + column]), then an
-// inclusive scan of T_ptr[1..n] in place: T_ptr becomes K''s row starts.
+// inclusive scan of T_ptr[1..n] in place: T_ptr becomes the row starts of K'.
 // The scan is per 1024-element block (warp shuffles, then the warp totals),
 // an exclusive scan of the block totals, and a final add; the largest column
 // count is kept for the choice between the device and the host transpose.

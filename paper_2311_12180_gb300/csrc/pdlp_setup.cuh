@@ -1,5 +1,5 @@
-// Create-time device work of the single-LP solver (pdlp_setup.cu): K''s row
-// starts and the stable transpose, Sec. 2.2 scaling, the scaled vectors and
+// Create-time device work of the single-LP solver (pdlp_setup.cu): the row
+// starts of K' and the stable transpose, Sec. 2.2 scaling, the scaled vectors and
 // scalars, and small tables.  Separate from pdlp_internal.cuh, which holds
 // what the step and check kernels share.
 #pragma once
@@ -13,7 +13,7 @@ namespace pdlp {
 // Fills the Algorithm 2 exponent-factor table: pw[k] = (k + 2)^-0.3 and
 // pw[count + k] = (k + 2)^-0.6 for k < count (the same pow() the step test calls).
 cudaError_t setup_pow_table(double *pw, long long count, cudaStream_t s);
-// K''s row starts on the device (pdlp_setup.cu): T_ptr (n + 1) = exclusive
+// Row starts of K' on the device: T_ptr (n + 1) = exclusive
 // scan of K's column counts; work[0] = the largest column count; work holds
 // col_starts_work_ints(n) ints.
 cudaError_t setup_col_starts(int32_t n, int64_t nnz, const int32_t *K_idx, int32_t *T_ptr, int32_t *work,
