@@ -322,7 +322,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   const size_t o_pR1 = L.take(8 * (size_t)s->gridR1 * NV_R1), o_pR2 = L.take(8 * (size_t)s->gridR2 * NV_R2);
   const size_t o_pR3 = L.take(8 * (size_t)s->gridR3 * NV_R3), o_pI = L.take(8 * (size_t)s->gridI * NV_I);
   const size_t o_st = L.take(sizeof(DevState)), o_tr = L.take(sizeof(TraceRec) * TRACE_CAP);
-  const size_t o_sc = L.take(8 * 8);
+  const size_t o_sc = L.take(8 * (8 + scalars_work_doubles()));
   const long long npw = 1LL << 20;  // exponent factors for the first 2^20 steps (16 MB)
   const size_t o_pw = L.take(16 * (size_t)npw);
   s->arena_bytes = L.off;
@@ -417,20 +417,25 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   // the host from the row starts ----
   std::vector<int32_t> tp((size_t)n + 1, 0);
   int32_t longest = 0;
-  {
-    const size_t wcs = col_starts_work_ints(n);
-    int32_t *work = nullptr;
-    CKS(cudaMallocAsync((void **)&work, sizeof(int32_t) * (wcs + transpose_work_ints(n, nnz)), st));
-    cudaError_t e = setup_col_starts(n, nnz, s->K_idx, s->T_ptr, work, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(tp.data(), s->T_ptr, 4 * (N + 1), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&longest, work, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e == cudaSuccess && nnz && longest <= transpose_max_segment())
-      e = setup_transpose(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, work + wcs, st);
-    const cudaError_t ef = cudaFreeAsync(work, st);
-    CKS(e);
-    CKS(ef);
-  }
+  // scratch of the row starts, then of the transpose; the transpose leaves
+  // in it the permutation and entry rows that the scaling reuses (freed
+  // after the scaling)
+  const size_t wcs = col_starts_work_ints(n);
+  struct ScratchBuffer {  // an error exit releases it (synchronously: the stream may be gone)
+    int32_t *p = nullptr;
+    ~ScratchBuffer() {
+      if (p) cudaFree(p);
+    }
+  } tw;
+  CKS(cudaMallocAsync((void **)&tw.p, sizeof(int32_t) * (wcs + transpose_work_ints(n, nnz)), st));
+  int32_t *const twork = tw.p;
+  CKS(setup_col_starts(n, nnz, s->K_idx, s->T_ptr, twork, st));
+  CKS(cudaMemcpyAsync(tp.data(), s->T_ptr, 4 * (N + 1), cudaMemcpyDeviceToHost, st));
+  CKS(cudaMemcpyAsync(&longest, twork, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CKS(cudaStreamSynchronize(st));
+  if (nnz && longest <= transpose_max_segment())
+    CKS(setup_transpose(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, twork + wcs, st));
+  const bool have_perm = nnz && longest <= transpose_max_segment();
   if (nnz && longest > transpose_max_segment()) {
     std::vector<int32_t> tp_h((size_t)n + 1), ti((size_t)nnz);
     std::vector<double> tv((size_t)nnz);
@@ -452,8 +457,21 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   if (m) CKS(cudaMemcpyAsync(V.yout, q, 8 * M, cudaMemcpyHostToDevice, st));
 
   // ---- Sec. 2.2 scaling on the device ----
-  CKS(setup_scale(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, s->D1, s->D2, s->work_m,
-                  s->work_n, prm.ruiz_iters, prm.pc_alpha, st));
+  {
+    cudaError_t e;
+    if (have_perm) {
+      const int32_t *perm = twork + wcs + n, *rowid = perm + nnz;
+      e = setup_scale_perm(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_val, rowid, perm, s->D1, s->D2,
+                           s->work_m, s->work_n, prm.ruiz_iters, prm.pc_alpha, st);
+    } else {
+      e = setup_scale(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, s->D1, s->D2,
+                      s->work_m, s->work_n, prm.ruiz_iters, prm.pc_alpha, st);
+    }
+    CKS(e);
+    const cudaError_t ef = cudaFreeAsync(tw.p, st);
+    tw.p = nullptr;
+    CKS(ef);
+  }
   CKS(setup_vectors(m, n, V.xout, V.yout, s->l0, s->u0, s->D1, s->D2, s->c, s->q, s->l, s->u, st));
   CKS(setup_recip(n, s->D2, VN(17), st));
   CKS(setup_recip(m, s->D1, VM(13), st));
@@ -461,7 +479,7 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
     CKS(setup_f32(nnz, s->K_val, s->K_val32, st));
     CKS(setup_f32(nnz, s->T_val, s->T_val32, st));
   }
-  CKS(setup_scalars(m, n, nnz, s->c, s->q, s->K_val, s->d_scal, st));
+  CKS(setup_scalars(m, n, nnz, s->c, s->q, s->K_val, s->d_scal, s->d_scal + 8, st));
   CKS(setup_pow_table((double *)(A + o_pw), npw, st));
   CKS(cudaMemcpyAsync(s->h_scal, s->d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CKS(cudaStreamSynchronize(st));

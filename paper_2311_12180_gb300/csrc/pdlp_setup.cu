@@ -84,6 +84,35 @@ __global__ void k_div(double *__restrict__ D, const double *__restrict__ f, int3
   for (int i = blockIdx.x * ST + threadIdx.x; i < n; i += gridDim.x * ST) D[i] = D[i] / f[i];
 }
 
+// Ruiz maxima in one pass over K's entries: the IEEE bits of |v| are
+// ordered like the values, so an integer atomicMax per entry on the row's
+// and the column's slot gives max |K~_ij| exactly (order-independent).
+__global__ void k_entry_max(const int32_t *__restrict__ idx, const int32_t *__restrict__ rowid,
+                            const double *__restrict__ val, int64_t nnz, unsigned long long *__restrict__ rmax,
+                            unsigned long long *__restrict__ cmax) {
+  for (int64_t e = (int64_t)blockIdx.x * ST + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * ST) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(val[e]) & 0x7fffffffffffffffull;
+    atomicMax(rmax + rowid[e], bits);
+    atomicMax(cmax + idx[e], bits);
+  }
+}
+
+// K's entries in storage order: val[e] = (val[e] / r[row]) / s[column], the
+// same two divisions in the same order as the row-wise k_scale.
+__global__ void k_scale_entries(const int32_t *__restrict__ idx, const int32_t *__restrict__ rowid,
+                                double *__restrict__ val, int64_t nnz, const double *__restrict__ r,
+                                const double *__restrict__ s) {
+  for (int64_t e = (int64_t)blockIdx.x * ST + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * ST)
+    val[e] = val[e] / r[rowid[e]] / s[idx[e]];
+}
+
+// K' values as a copy of K's through the transpose permutation.
+__global__ void k_copy_perm(const int32_t *__restrict__ perm, const double *__restrict__ kval, int64_t nnz,
+                            double *__restrict__ tval) {
+  for (int64_t p = (int64_t)blockIdx.x * ST + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * ST)
+    tval[p] = kval[perm[p]];
+}
+
 __global__ void k_fill(double *__restrict__ a, int32_t n, double v) {
   for (int i = blockIdx.x * ST + threadIdx.x; i < n; i += gridDim.x * ST) a[i] = v;
 }
@@ -105,34 +134,75 @@ __global__ void k_f32(long long nnz, const double *__restrict__ v, float *__rest
     f[e] = (float)v[e];
 }
 
-// Single CTA of 1024 threads: out = {sum c^2, sum q^2, max |val|}; fixed order.
-__global__ void k_scalars(int32_t m, int32_t n, long long nnz, const double *__restrict__ c,
-                          const double *__restrict__ q, const double *__restrict__ val, double *__restrict__ out) {
-  __shared__ double red[3][32];
-  double a = 0.0, b = 0.0, mx = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) a += c[j] * c[j];
-  for (int i = threadIdx.x; i < m; i += blockDim.x) b += q[i] * q[i];
-  for (long long e = threadIdx.x; e < nnz; e += blockDim.x) mx = fmax(mx, fabs(val[e]));
+// out = {sum c^2, sum q^2, max |val|} in two steps with a fixed order for a
+// fixed grid: SCAL_BLOCKS block partials (grid-strided shares, block tree),
+// then one block adds them in block order.  The maximum is taken on the
+// IEEE bits of |val| (integer compares, exact, off the FP64 pipe).
+constexpr int SCAL_BLOCKS = 256;
+
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+__global__ void __launch_bounds__(ST) k_scalars_part(int32_t m, int32_t n, long long nnz,
+                                                     const double *__restrict__ c, const double *__restrict__ q,
+                                                     const double *__restrict__ val, double *__restrict__ part) {
+  __shared__ double red[2][ST / 32];
+  __shared__ unsigned long long rmx[ST / 32];
+  double a = 0.0, b = 0.0;
+  unsigned long long mx = 0;
+  const long long t0 = (long long)blockIdx.x * ST + threadIdx.x, stride = (long long)gridDim.x * ST;
+  for (long long j = t0; j < n; j += stride) a = fma(c[j], c[j], a);
+  for (long long i = t0; i < m; i += stride) b = fma(q[i], q[i], b);
+  for (long long e = t0; e < nnz; e += stride) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(val[e]) & 0x7fffffffffffffffull;
+    mx = bits > mx ? bits : mx;
+  }
   a = warp_add(a);
   b = warp_add(b);
-  mx = warp_max(mx);
+  mx = warp_umax(mx);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = a;
     red[1][wid] = b;
-    red[2][wid] = mx;
+    rmx[wid] = mx;
   }
   __syncthreads();
   if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    a = warp_add(lane < nw ? red[0][lane] : 0.0);
-    b = warp_add(lane < nw ? red[1][lane] : 0.0);
-    mx = warp_max(lane < nw ? red[2][lane] : 0.0);
+    a = warp_add(lane < ST / 32 ? red[0][lane] : 0.0);
+    b = warp_add(lane < ST / 32 ? red[1][lane] : 0.0);
+    mx = warp_umax(lane < ST / 32 ? rmx[lane] : 0ull);
     if (lane == 0) {
-      out[0] = a;
-      out[1] = b;
-      out[2] = mx;
+      part[3 * blockIdx.x] = a;
+      part[3 * blockIdx.x + 1] = b;
+      part[3 * blockIdx.x + 2] = __longlong_as_double((long long)mx);
     }
+  }
+}
+
+__global__ void __launch_bounds__(32) k_scalars_final(const double *__restrict__ part, int blocks,
+                                                      double *__restrict__ out) {
+  const int lane = threadIdx.x;
+  double a = 0.0, b = 0.0;
+  unsigned long long mx = 0;
+  for (int k = lane; k < blocks; k += 32) {
+    a += part[3 * k];
+    b += part[3 * k + 1];
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(part[3 * k + 2]);
+    mx = bits > mx ? bits : mx;
+  }
+  a = warp_add(a);
+  b = warp_add(b);
+  mx = warp_umax(mx);
+  if (lane == 0) {
+    out[0] = a;
+    out[1] = b;
+    out[2] = __longlong_as_double((long long)mx);
   }
 }
 
@@ -175,6 +245,40 @@ cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32
   return cudaGetLastError();
 }
 
+cudaError_t setup_scale_perm(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
+                             double *K_val, const int32_t *T_ptr, double *T_val, const int32_t *rowid,
+                             const int32_t *perm, double *D1, double *D2, double *work_m, double *work_n,
+                             int ruiz_iters, double pc_alpha, cudaStream_t s) {
+  if (m > 0) k_fill<<<grid_for(m), ST, 0, s>>>(D1, m, 1.0);
+  k_fill<<<grid_for(n), ST, 0, s>>>(D2, n, 1.0);
+  const int eg = grid_for(nnz);
+  for (int it = 0; it < ruiz_iters; ++it) {
+    cudaError_t e = cudaMemsetAsync(work_m, 0, sizeof(double) * (size_t)m, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(work_n, 0, sizeof(double) * (size_t)n, s);
+    if (e != cudaSuccess) return e;
+    if (nnz > 0)
+      k_entry_max<<<eg, ST, 0, s>>>(K_idx, rowid, K_val, nnz, reinterpret_cast<unsigned long long *>(work_m),
+                                    reinterpret_cast<unsigned long long *>(work_n));
+    if (m > 0) k_factor<<<grid_for(m), ST, 0, s>>>(work_m, m);
+    k_factor<<<grid_for(n), ST, 0, s>>>(work_n, n);
+    if (nnz > 0) k_scale_entries<<<eg, ST, 0, s>>>(K_idx, rowid, K_val, nnz, work_m, work_n);
+    if (m > 0) k_div<<<grid_for(m), ST, 0, s>>>(D1, work_m, m);
+    k_div<<<grid_for(n), ST, 0, s>>>(D2, work_n, n);
+  }
+  if (nnz > 0) k_copy_perm<<<eg, ST, 0, s>>>(perm, K_val, nnz, T_val);
+  if (pc_alpha >= 0.0) {  // Pock-Chambolle: row sums over K, column sums over K' (fixed order)
+    if (m > 0) k_row_norm<<<grid_for((long long)m * 32), ST, 0, s>>>(K_ptr, K_val, m, work_m, 1, 2.0 - pc_alpha);
+    k_row_norm<<<grid_for((long long)n * 32), ST, 0, s>>>(T_ptr, T_val, n, work_n, 1, pc_alpha);
+    if (m > 0) k_factor<<<grid_for(m), ST, 0, s>>>(work_m, m);
+    k_factor<<<grid_for(n), ST, 0, s>>>(work_n, n);
+    if (nnz > 0) k_scale_entries<<<eg, ST, 0, s>>>(K_idx, rowid, K_val, nnz, work_m, work_n);
+    if (m > 0) k_div<<<grid_for(m), ST, 0, s>>>(D1, work_m, m);
+    k_div<<<grid_for(n), ST, 0, s>>>(D2, work_n, n);
+    if (nnz > 0) k_copy_perm<<<eg, ST, 0, s>>>(perm, K_val, nnz, T_val);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *q0, const double *l0,
                           const double *u0, const double *D1, const double *D2, double *c, double *q, double *l,
                           double *u, cudaStream_t s) {
@@ -196,9 +300,12 @@ cudaError_t setup_f32(int64_t nnz, const double *val, float *val32, cudaStream_t
   return cudaGetLastError();
 }
 
+size_t scalars_work_doubles() { return 3 * (size_t)SCAL_BLOCKS; }
+
 cudaError_t setup_scalars(int32_t m, int32_t n, int64_t nnz, const double *c, const double *q, const double *val,
-                          double *out, cudaStream_t s) {
-  k_scalars<<<1, 1024, 0, s>>>(m, n, nnz, c, q, val, out);
+                          double *out, double *work, cudaStream_t s) {
+  k_scalars_part<<<SCAL_BLOCKS, ST, 0, s>>>(m, n, nnz, c, q, val, work);
+  k_scalars_final<<<1, 32, 0, s>>>(work, SCAL_BLOCKS, out);
   return cudaGetLastError();
 }
 

@@ -22,25 +22,39 @@ size_t col_starts_work_ints(int32_t n);
 // K' on the device (pdlp_setup.cu), given its row starts T_ptr (already on
 // the device): the stable transpose, equal to the host counting sort, for
 // columns of at most transpose_max_segment() entries, with
-// transpose_work_ints(n, nnz) ints of scratch.
+// transpose_work_ints(n, nnz) ints of scratch, which it leaves holding the
+// transpose permutation at work + n and the row of every entry of K at
+// work + n + nnz.
 cudaError_t setup_transpose(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
                             const double *K_val, const int32_t *T_ptr, int32_t *T_idx, double *T_val, int32_t *work,
                             cudaStream_t s);
 size_t transpose_work_ints(int32_t n, int64_t nnz);
 int transpose_max_segment();
 
+// Sec. 2.2 scaling of K and K' in place (row-wise passes over both).
 cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32_t *K_idx, double *K_val,
                         int32_t *T_ptr, int32_t *T_idx, double *T_val, double *D1, double *D2, double *work_m,
                         double *work_n, int ruiz_iters, double pc_alpha, cudaStream_t s);
+// The same scaling, bitwise equal, given the row of every entry of K
+// (rowid) and the transpose permutation (perm: K' position -> K entry), as
+// setup_transpose leaves them in its scratch: the Ruiz maxima come from one
+// pass over K's entries (atomic maxima on the IEEE bits), only K's values
+// are divided, and K''s values are copied through perm.
+cudaError_t setup_scale_perm(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
+                             double *K_val, const int32_t *T_ptr, double *T_val, const int32_t *rowid,
+                             const int32_t *perm, double *D1, double *D2, double *work_m, double *work_n,
+                             int ruiz_iters, double pc_alpha, cudaStream_t s);
 cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *q0, const double *l0,
                           const double *u0, const double *D1, const double *D2, double *c, double *q, double *l,
                           double *u, cudaStream_t s);
 cudaError_t setup_f32(int64_t nnz, const double *val, float *val32, cudaStream_t s);
 // rD = 1 / D elementwise (the infeasibility pieces unscale with products)
 cudaError_t setup_recip(int32_t count, const double *D, double *rD, cudaStream_t s);
-// out[0] = sum (c~)^2, out[1] = sum (q~)^2, out[2] = max |K~|
+// out[0] = sum (c~)^2, out[1] = sum (q~)^2, out[2] = max |K~|, with
+// scalars_work_doubles() doubles of scratch
 cudaError_t setup_scalars(int32_t m, int32_t n, int64_t nnz, const double *c, const double *q, const double *val,
-                          double *out, cudaStream_t s);
+                          double *out, double *work, cudaStream_t s);
+size_t scalars_work_doubles();
 cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0, const double *D1,
                        const double *D2, double *x, double *y, cudaStream_t s);
 
