@@ -46,6 +46,9 @@
 // thread boundaries are completed from per-thread carries (serially for up to
 // CHAIN_MAX threads, else by a warp-strided sum).  The epilogue runs one row
 // per thread on operands prefetched into registers before the reduction.
+// As soon as a thread's own sums are done, it issues the loads of its chunk
+// of the CTA's next tile into the registers just freed, so that HBM latency
+// overlaps the carries, barriers and epilogue of the current tile.
 // Reductions are deterministic: fixed per-thread order, fixed shuffle trees,
 // fixed block order in the last CTA.  No atomics touch floating point.
 
@@ -191,13 +194,34 @@ __device__ __forceinline__ void load_chunk(const float *p, double (&v)[EPT]) {
 __device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
 __device__ __forceinline__ double ld_val(const float *p) { return f2d(__ldcs(p)); }
 
+// Loads a regular tile's column indices and values into this thread's
+// registers (a tile holding one row longer than a tile loads as it strides).
+template <typename VT>
+__device__ __forceinline__ void tile_load(const Csr &A, const VT *__restrict__ val, int2 m0, int2 m1,
+                                          int (&col)[EPT], double (&v)[EPT]) {
+  const int e0 = m0.y, e1 = m1.y;
+  if (e1 - e0 > TILE_NNZ) return;
+  const int base = e0 & ~(EPT - 1), c0 = EPT * threadIdx.x;
+  if (base + c0 < e1) {
+    load_chunk(A.idx + base + c0, col);
+    load_chunk(val + base + c0, v);
+  } else {
+#pragma unroll
+    for (int i = 0; i < EPT; ++i) {
+      col[i] = 0;
+      v[i] = 0.0;
+    }
+  }
+}
+
 // One tile of y = A x for NV (1 or 2) gathered vectors, followed by the
 // epilogue ep.finish(row, sums) for row r0 + threadIdx.x.  With SCALED,
 // vector a is multiplied by sc[a] entry by entry (the epoch average 1/W sum).
 template <typename VT, int NV, bool SCALED, int NVS, class Epi>
 __device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__ val,
                                             const double *const (&xs)[NV], const double (&sc)[NV], int2 m0, int2 m1,
-                                            TileSmem<NVS> &sm, Epi &ep) {
+                                            TileSmem<NVS> &sm, Epi &ep, int (&col)[EPT], double (&v)[EPT],
+                                            const int2 *next) {
   static_assert(NV == 1 || NV == 2, "one or two gathered vectors");
   static_assert(NV <= NVS, "tile shared memory holds fewer vectors");
   const int tid = threadIdx.x;
@@ -218,25 +242,14 @@ __device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__
       }
     }
     block_sum<NV>(acc, sm.red);
+    if (next) tile_load(A, val, next[0], next[1], col, v);
     if (tid == 0) ep.finish(r0, acc);
     return;
   }
   // ---- loads and gathers (registers) ----
   const int base = e0 & ~(EPT - 1);
-  const int c0 = EPT * tid;  // this thread's chunk, relative to base
-  int col[EPT];
-  double v[EPT];
+  const int c0 = EPT * tid;  // this thread's chunk, relative to base (col, v loaded by tile_load)
   double xv[NV][EPT];
-  if (base + c0 < e1) {
-    load_chunk(A.idx + base + c0, col);
-    load_chunk(val + base + c0, v);
-  } else {
-#pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      col[i] = 0;
-      v[i] = 0.0;
-    }
-  }
   const int lo = e0 - base, hi = e1 - base;  // tile entries, relative to base
 #pragma unroll
   for (int i = 0; i < EPT; ++i) {
@@ -304,6 +317,9 @@ __device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__
       for (int a = 0; a < NV; ++a) carry[a] = acc[a];
     }
   }
+  // the next tile's indices and values stream in while this one's carries,
+  // barriers and epilogue run
+  if (next) tile_load(A, val, next[0], next[1], col, v);
 #pragma unroll
   for (int a = 0; a < NV; ++a) sm.carry[a][tid] = carry[a];
   __syncthreads();
@@ -364,8 +380,14 @@ __device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__
 template <typename VT, int NV, bool SCALED, int NVS, class Epi>
 __device__ __forceinline__ void spmv_tiles(const Csr &A, const VT *__restrict__ val, const double *const (&xs)[NV],
                                            const double (&sc)[NV], TileSmem<NVS> &sm, Epi &ep) {
-  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x)
-    tile_direct<VT, NV, SCALED>(A, val, xs, sc, A.tmeta[t], A.tmeta[t + 1], sm, ep);
+  int col[EPT];
+  double v[EPT];
+  if (blockIdx.x < A.ntiles) tile_load(A, val, A.tmeta[blockIdx.x], A.tmeta[blockIdx.x + 1], col, v);
+  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
+    const int tn = t + gridDim.x;
+    tile_direct<VT, NV, SCALED>(A, val, xs, sc, A.tmeta[t], A.tmeta[t + 1], sm, ep, col, v,
+                                tn < A.ntiles ? A.tmeta + tn : nullptr);
+  }
 }
 
 // ---------------------------------------------------------------- primal step
