@@ -7,8 +7,9 @@
 // __syncthreads, so no grid-wide synchronisation or inter-CTA wait exists.
 // CTAs take instances from a device queue in decreasing order of nonzeros
 // (longest first keeps the tail short).  Each instance carries its own step
-// size, primal weight, restart and termination state in registers (identical
-// in every thread: all of them read the same block-reduced sums).  Its SpMVs
+// size, primal weight, restart, termination and infeasibility state in
+// registers (identical in every thread: all of them read the same
+// block-reduced sums).  Its SpMVs
 // map G lanes to a row (G a power of two <= 32, chosen per instance from its
 // mean row length by the autotuned rule in pdlp_batch_create), with a fixed
 // lane order and fixed shuffle trees, so a solve is deterministic.
