@@ -610,7 +610,7 @@ def main():
     lp_host, _pinned = pinned_lp(lp)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    s2 = P.Solver(lp_host)
+    s2 = P.Solver(lp_host, value_bits=args.value_bits)
     x, y, st, it2 = s2.solve(tol=1e-14, max_iter=e2e_iters)
     e2e_s = time.perf_counter() - t
     e2e_setup_ms = s2.info()["setup_ms"]
