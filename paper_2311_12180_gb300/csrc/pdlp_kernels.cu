@@ -181,6 +181,18 @@ __device__ __forceinline__ double f2d(float f) {
                                ((unsigned long long)(b & 0x7fffffu) << 29);
   return __longlong_as_double((long long)d);
 }
+__device__ __forceinline__ void load_chunk(const float *p, float (&v)[EPT]) {
+#pragma unroll
+  for (int k = 0; k < EPT / 4; ++k) {
+    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p) + k);
+    v[4 * k] = a.x;
+    v[4 * k + 1] = a.y;
+    v[4 * k + 2] = a.z;
+    v[4 * k + 3] = a.w;
+  }
+}
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return f2d(v); }
 __device__ __forceinline__ void load_chunk(const float *p, double (&v)[EPT]) {
 #pragma unroll
   for (int k = 0; k < EPT / 4; ++k) {
@@ -198,7 +210,7 @@ __device__ __forceinline__ double ld_val(const float *p) { return f2d(__ldcs(p))
 // registers (a tile holding one row longer than a tile loads as it strides).
 template <typename VT>
 __device__ __forceinline__ void tile_load(const Csr &A, const VT *__restrict__ val, int2 m0, int2 m1,
-                                          int (&col)[EPT], double (&v)[EPT]) {
+                                          int (&col)[EPT], VT (&v)[EPT]) {
   const int e0 = m0.y, e1 = m1.y;
   if (e1 - e0 > TILE_NNZ) return;
   const int base = e0 & ~(EPT - 1), c0 = EPT * threadIdx.x;
@@ -209,7 +221,7 @@ __device__ __forceinline__ void tile_load(const Csr &A, const VT *__restrict__ v
 #pragma unroll
     for (int i = 0; i < EPT; ++i) {
       col[i] = 0;
-      v[i] = 0.0;
+      v[i] = VT(0);
     }
   }
 }
@@ -220,7 +232,7 @@ __device__ __forceinline__ void tile_load(const Csr &A, const VT *__restrict__ v
 template <typename VT, int NV, bool SCALED, int NVS, class Epi>
 __device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__ val,
                                             const double *const (&xs)[NV], const double (&sc)[NV], int2 m0, int2 m1,
-                                            TileSmem<NVS> &sm, Epi &ep, int (&col)[EPT], double (&v)[EPT],
+                                            TileSmem<NVS> &sm, Epi &ep, int (&col)[EPT], VT (&v)[EPT],
                                             const int2 *next) {
   static_assert(NV == 1 || NV == 2, "one or two gathered vectors");
   static_assert(NV <= NVS, "tile shared memory holds fewer vectors");
@@ -289,7 +301,7 @@ __device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__
       const int e = c0 + i;
       if (e >= s0 && e < s1) {
 #pragma unroll
-        for (int a = 0; a < NV; ++a) acc[a] = fma(v[i], xv[a][i], acc[a]);
+        for (int a = 0; a < NV; ++a) acc[a] = fma(widen(v[i]), xv[a][i], acc[a]);
         if (e + 1 == rend) {
           if (rstart >= s0) {
 #pragma unroll
@@ -381,7 +393,7 @@ template <typename VT, int NV, bool SCALED, int NVS, class Epi>
 __device__ __forceinline__ void spmv_tiles(const Csr &A, const VT *__restrict__ val, const double *const (&xs)[NV],
                                            const double (&sc)[NV], TileSmem<NVS> &sm, Epi &ep) {
   int col[EPT];
-  double v[EPT];
+  VT v[EPT];  // values as stored (FP32 values widen at use)
   if (blockIdx.x < A.ntiles) tile_load(A, val, A.tmeta[blockIdx.x], A.tmeta[blockIdx.x + 1], col, v);
   for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
     const int tn = t + gridDim.x;
