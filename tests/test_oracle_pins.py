@@ -286,6 +286,19 @@ def test_alg3_restart_decay_and_bounded_length():
     assert oracle.kkt_standard(S.indptr, S.indices, S.data, b, c, xs, ys, m, n) < 1e-12
 
 
+def test_kkt_standard_hand(golden):
+    """Appendix A's KKT error at two non-optimal points worked by hand: every
+    term (primal residual, [-x]^+, [A'y - c]^+, [c'x - b'y]^+) is nonzero at
+    the first, and the gap is negative at the second (its positive part is 0)."""
+    g = golden["kkt_standard"]
+    S = sp.csr_matrix(np.array(g["A"]))
+    m, n = S.shape
+    b, c = np.array(g["b"]), np.array(g["c"])
+    for p in g["points"]:
+        k = oracle.kkt_standard(S.indptr, S.indices, S.data, b, c, np.array(p["x"]), np.array(p["y"]), m, n)
+        assert k * k == pytest.approx(p["kkt_sq"], rel=1e-14)
+
+
 # ---------------------------------------------------------------- driver behaviour
 
 
