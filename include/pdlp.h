@@ -320,8 +320,11 @@ void pdlp_mlp_destroy(pdlp_mlp *net);
 
 /* Allocation-free Ruiz + Pock-Chambolle scaling of a matrix the caller keeps
  * in DEVICE memory.  This entry point has no counterpart in the paper; it is
- * the same scaling pdlp_create applies (same kernels, same order of
- * operations, so the results equal pdlp_get_scaling's), offered for callers
+ * the same scaling pdlp_create applies, with the same divisions in the same
+ * order (row by row here, entry by entry in pdlp_create; l_inf maxima and the
+ * fixed-order Pock-Chambolle row sums do not depend on that), so D1, D2 and
+ * the scaled values are bitwise equal to pdlp_get_scaling's.  It is offered
+ * for callers
  * that cannot call cudaMalloc or cudaFree: code that must take every byte of
  * device memory from its own pool (a framework's caching allocator, a
  * service with a fixed memory budget) and code that must not stall the device,
@@ -337,8 +340,9 @@ void pdlp_mlp_destroy(pdlp_mlp *net);
  *   stream: a cudaStream_t as void* (NULL = the legacy default stream); the
  *   work is enqueued there and the call returns without waiting.
  * Limits and errors: 0 <= m <= 262144 and 1 <= n <= 262144, else
- * PDLP_ERR_INVALID with a message naming the limit; null pointers also give
- * PDLP_ERR_INVALID.  The first call on each device looks up the device
+ * PDLP_ERR_INVALID with a message naming the limit.  A null KT_ptr or D2, or
+ * (when m > 0) a null K_ptr, K_idx, K_val, KT_idx, KT_val or D1, gives
+ * PDLP_ERR_INVALID before any CUDA call.  The first call on each device looks up the device
  * address of the internal array (with that device current), so make that
  * first call before any stream capture begins.  All calls share the one
  * array: calls whose work overlaps on the GPU (different streams, or several

@@ -581,7 +581,9 @@ extern "C" int pdlp_scale_device_noalloc(int32_t m, int32_t n, const int32_t *K_
                          .c_str());
   if (ruiz_iters < 0 || !(pc_alpha <= 2.0))
     return set_error(PDLP_ERR_INVALID, "pdlp_scale_device_noalloc: need ruiz_iters >= 0 and pc_alpha <= 2");
-  if (!KT_ptr || !D2 || (m > 0 && (!K_ptr || !D1)))
+  // K' rows always exist (n >= 1); entries, and so K and the entry arrays of
+  // both matrices, exist only when m > 0
+  if (!KT_ptr || !D2 || (m > 0 && (!K_ptr || !K_idx || !K_val || !KT_idx || !KT_val || !D1)))
     return set_error(PDLP_ERR_INVALID, "pdlp_scale_device_noalloc: null pointer argument");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

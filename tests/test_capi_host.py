@@ -138,3 +138,15 @@ def test_mlp_create_rejects_bad_dims_on_host(L, dims):
 
 def test_batch_times_rejects_null(L):
     assert L.pdlp_batch_times(None, None, None) == P.ERR_INVALID
+
+
+@pytest.mark.parametrize("null", ["K_ptr", "K_idx", "K_val", "KT_ptr", "KT_idx", "KT_val", "D1", "D2"])
+def test_noalloc_scaling_rejects_null_pointers_on_host(L, null):
+    # non-null dummies that are never dereferenced: the checks run before any
+    # CUDA call, so a null argument must be rejected without touching the GPU
+    args = dict(K_ptr=8, K_idx=8, K_val=8, KT_ptr=8, KT_idx=8, KT_val=8, D1=8, D2=8)
+    args[null] = None
+    rc = L.pdlp_scale_device_noalloc(4, 6, args["K_ptr"], args["K_idx"], args["K_val"], args["KT_ptr"],
+                                     args["KT_idx"], args["KT_val"], 10, 1.0, args["D1"], args["D2"], None)
+    assert rc == P.ERR_INVALID
+    assert "null" in L.pdlp_last_error().decode()

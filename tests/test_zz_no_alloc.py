@@ -1,6 +1,6 @@
 """The allocation-free scaling entry point, called through the C ABI on
 device buffers, against the scaling pdlp_create computes with its own
-allocations (pdlp_get_scaling).
+allocations (pdlp_get_scaling, bitwise) and against the FP64 oracle.
 
 Kept in its own file, collected after every other test file, so that a run
 stopping at the first failure has already run the rest of the suite."""
@@ -10,6 +10,7 @@ import pytest
 import scipy.sparse as sp
 
 import lpgen
+import oracle
 from paper_2311_12180_gb300 import pdlp as P
 
 pytestmark = pytest.mark.gpu
@@ -51,10 +52,15 @@ def test_noalloc_scaling_matches_solver_scaling(case):
     for _ in range(2):  # two calls in a row, each on fresh unscaled copies
         d = _device_case(lp, torch)
         outs.append(_call(lp, d, torch))
+    sv, oD1, oD2 = oracle.precondition(lp, ruiz_iters=10, pc_alpha=1.0)
     for D1, D2, v, vt in outs:
-        np.testing.assert_allclose(D1, D1e, rtol=1e-13)
-        np.testing.assert_allclose(D2, D2e, rtol=1e-13)
-        np.testing.assert_allclose(v, ve, rtol=1e-13)
+        # the same divisions in the same order as pdlp_create's scaling: bitwise
+        assert np.array_equal(D1, D1e) and np.array_equal(D2, D2e) and np.array_equal(v, ve)
+        # and the FP64 oracle's Sec. 2.2 scaling up to the order of the
+        # Pock-Chambolle sums
+        np.testing.assert_allclose(D1, oD1, rtol=1e-13)
+        np.testing.assert_allclose(D2, oD2, rtol=1e-13)
+        np.testing.assert_allclose(v, sv, rtol=1e-13)
         # K' scaled with the same divisions stays the exact transpose of K
         Ks = sp.csr_matrix((v, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)).T.tocsr()
         Ks.sort_indices()
