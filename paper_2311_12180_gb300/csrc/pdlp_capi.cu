@@ -1,6 +1,7 @@
 // C ABI of the GB300 PDLP solver (declared in include/pdlp.h): input
-// validation, the transpose of K and the SpMV tile schedules (host, once per
-// LP), one device arena per solver, Sec. 2.2 scaling on the device, and the
+// validation, the sliced-ELL layout of K and K' (host, once per LP: the
+// internal row order and the work items), the transpose of K, Sec. 2.2
+// scaling and the sliced-ELL copies on the device, and the
 // solve driver that replays a captured CUDA graph of one check period and
 // polls a pinned copy of the device state one period behind, so the GPU never
 // waits for the host.
@@ -18,6 +19,7 @@
 #include "pdlp.h"
 #include "pdlp_host.h"
 #include "pdlp_internal.cuh"
+#include "pdlp_sell.h"
 #include "pdlp_setup.cuh"
 
 using namespace pdlp;
@@ -44,28 +46,6 @@ double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-// Tiles: runs of consecutive rows with at most TILE_NNZ nonzeros and
-// TILE_ROWS rows; a row longer than TILE_NNZ forms a tile of its own.  Each
-// entry is {first row, first nonzero}; a final entry {rows, nnz} closes the list.
-std::vector<int2> build_tiles(const int32_t *ptr, int32_t rows) {
-  std::vector<int2> t;
-  int32_t r = 0;
-  while (r < rows) {
-    const int32_t start = r;
-    t.push_back(make_int2(start, ptr[start]));
-    long long nz = 0;
-    while (r < rows && r - start < TILE_ROWS) {
-      const long long len = (long long)ptr[r + 1] - ptr[r];
-      if (r > start && nz + len > TILE_NNZ) break;
-      nz += len;
-      ++r;
-      if (nz > TILE_NNZ) break;
-    }
-  }
-  t.push_back(make_int2(rows, ptr[rows]));
-  return t;
-}
-
 struct Layout {
   size_t off = 0;
   size_t take(size_t bytes) {
@@ -90,14 +70,17 @@ struct pdlp_solver {
   int num_sms = 0;
   char *arena = nullptr;
   size_t arena_bytes = 0;
-  Csr K{}, KT{};
+  SellMat K{}, KT{};
+  char *sell_arena = nullptr;  // sliced-ELL copies of K and K', their work items
+  size_t sell_bytes = 0;
   Vecs V{};
   DevState *st = nullptr;
   double *d_scal = nullptr;
   int32_t *K_ptr = nullptr, *K_idx = nullptr, *T_ptr = nullptr, *T_idx = nullptr;
   double *K_val = nullptr, *T_val = nullptr;
-  float *K_val32 = nullptr, *T_val32 = nullptr;
-  double *D1 = nullptr, *D2 = nullptr, *work_m = nullptr, *work_n = nullptr;
+  double *D1 = nullptr, *D2 = nullptr, *work_m = nullptr, *work_n = nullptr;  // D1, D2: original order
+  int32_t *perm_r = nullptr, *perm_c = nullptr;  // internal -> original row / column
+  std::vector<int32_t> h_perm_r, h_perm_c;        // the same on the host (state export / import)
   double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr, *l0 = nullptr, *u0 = nullptr;
   int gridA = 1, gridB = 1, gridR1 = 1, gridR2 = 1, gridR3 = 1, gridI = 1;
   int slots = 0;
@@ -116,32 +99,14 @@ struct pdlp_solver {
 
 namespace {
 
-int validate(int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *rp, const int32_t *ci,
-             const double *v, const double *q, const double *l, const double *u) {
+// Dimensions, row starts and the vectors (host arrays).
+int validate_vectors(int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *rp, const double *q,
+                     const double *l, const double *u) {
   if (m < 0 || n < 1 || n_eq < 0 || n_eq > m) return fail(PDLP_ERR_INVALID, "dimensions: need m >= 0, n >= 1, 0 <= n_eq <= m");
   if (!c || !rp || !l || !u || (m > 0 && !q)) return fail(PDLP_ERR_INVALID, "null input array");
   if (rp[0] != 0) return fail(PDLP_ERR_INVALID, "row_ptr[0] must be 0");
   for (int32_t i = 0; i < m; ++i)
     if (rp[i + 1] < rp[i]) return fail(PDLP_ERR_INVALID, "row_ptr is not non-decreasing at row " + std::to_string(i));
-  const int64_t nnz = rp[m];
-  if (nnz > 0 && (!ci || !v)) return fail(PDLP_ERR_INVALID, "null col_idx / val");
-  {
-    // first bad nonzero, searched in parallel chunks (the report names the first one)
-    const int T = host_threads(nnz);
-    std::vector<int64_t> first(T, nnz);
-    parallel_for(T, [&](int t) {
-      for (int64_t e = nnz * t / T; e < nnz * (t + 1) / T; ++e)
-        if (ci[e] < 0 || ci[e] >= n || !std::isfinite(v[e])) {
-          first[t] = e;
-          break;
-        }
-    });
-    const int64_t e = *std::min_element(first.begin(), first.end());
-    if (e < nnz) {
-      if (ci[e] < 0 || ci[e] >= n) return fail(PDLP_ERR_INVALID, "col_idx out of range at nonzero " + std::to_string(e));
-      return fail(PDLP_ERR_INVALID, "non-finite matrix value at nonzero " + std::to_string(e));
-    }
-  }
   for (int32_t j = 0; j < n; ++j) {
     if (!std::isfinite(c[j])) return fail(PDLP_ERR_INVALID, "non-finite c at " + std::to_string(j));
     if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY)
@@ -149,6 +114,30 @@ int validate(int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t 
   }
   for (int32_t i = 0; i < m; ++i)
     if (!std::isfinite(q[i])) return fail(PDLP_ERR_INVALID, "non-finite q at row " + std::to_string(i));
+  return PDLP_OK;
+}
+
+int bad_entry(int64_t e, bool col_bad) {
+  if (col_bad) return fail(PDLP_ERR_INVALID, "col_idx out of range at nonzero " + std::to_string(e));
+  return fail(PDLP_ERR_INVALID, "non-finite matrix value at nonzero " + std::to_string(e));
+}
+
+// Column indices in [0, n) and finite values (host arrays); the report names
+// the first bad nonzero.
+int validate_entries(int64_t nnz, int32_t n, const int32_t *ci, const double *v) {
+  if (nnz > 0 && (!ci || !v)) return fail(PDLP_ERR_INVALID, "null col_idx / val");
+  // first bad nonzero, searched in parallel chunks
+  const int T = host_threads(nnz);
+  std::vector<int64_t> first(T, nnz);
+  parallel_for(T, [&](int t) {
+    for (int64_t e = nnz * t / T; e < nnz * (t + 1) / T; ++e)
+      if (ci[e] < 0 || ci[e] >= n || !std::isfinite(v[e])) {
+        first[t] = e;
+        break;
+      }
+  });
+  const int64_t e = *std::min_element(first.begin(), first.end());
+  if (e < nnz) return bad_entry(e, ci[e] < 0 || ci[e] >= n);
   return PDLP_OK;
 }
 
@@ -168,6 +157,7 @@ void free_solver(pdlp_solver *s) {
   for (auto &e : s->ev)
     if (e) cudaEventDestroy(e);
   if (s->arena) cudaFree(s->arena);
+  if (s->sell_arena) cudaFree(s->sell_arena);
   if (s->h_st) cudaFreeHost(s->h_st);
   if (s->h_poll) cudaFreeHost(s->h_poll);
   if (s->h_scal) cudaFreeHost(s->h_scal);
@@ -199,6 +189,10 @@ int build_graph(pdlp_solver *s) {
   CK(cudaGraphInstantiate(&s->gexec, s->graph, 0));
   return PDLP_OK;
 }
+
+int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *row_ptr,
+                  const int32_t *col_idx, const double *val, const double *q, const double *l, const double *u,
+                  const pdlp_params &prm, void *stream, bool dev_entries, double t_start);
 
 }  // namespace
 
@@ -235,15 +229,32 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
     pdlp_default_params(&prm);
   int rc = check_params(prm);
   if (rc) return rc;
-  rc = validate(m, n, n_eq, c, row_ptr, col_idx, val, q, l, u);
+  rc = validate_vectors(m, n, n_eq, c, row_ptr, q, l, u);
   if (rc) return rc;
   const double t_start = now_ms();
   const int64_t nnz = row_ptr[m];
   if (nnz >= ((int64_t)1 << 31)) return fail(PDLP_ERR_INVALID, "nnz must be < 2^31");
+  rc = validate_entries(nnz, n, col_idx, val);
+  if (rc) return rc;
+  return create_common(out, m, n, n_eq, c, row_ptr, col_idx, val, q, l, u, prm, stream, false, t_start);
+}
 
-  // ---- host: K's tile schedule; K' (row starts, entries) is built on the
-  // device after the upload, and its tile schedule from the row starts ----
-  std::vector<int2> tilesK = build_tiles(row_ptr, m);
+}  // extern "C"
+
+namespace {
+
+// The create path after validation.  c, row_ptr, q, l, u are host arrays;
+// col_idx and val are host arrays, or device arrays when dev_entries.
+int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *row_ptr,
+                  const int32_t *col_idx, const double *val, const double *q, const double *l, const double *u,
+                  const pdlp_params &prm, void *stream, bool dev_entries, double t_start) {
+  const int64_t nnz = row_ptr[m];
+  const cudaMemcpyKind entry_kind = dev_entries ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+
+  // ---- host: the sliced-ELL layout of K (row lengths are known here); K'
+  // (row starts, entries) is built on the device after the upload, and its
+  // layout from the row starts ----
+  SellLayout LK = sell_layout(row_ptr, m, n_eq);
   double qn = 0.0, cn = 0.0;
   for (int32_t i = 0; i < m; ++i) qn += q[i] * q[i];
   for (int32_t j = 0; j < n; ++j) cn += c[j] * c[j];
@@ -287,14 +298,18 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   std::memset(s->h_st, 0, sizeof(DevState));
   s->h_st->status = ST_RUNNING;
 
-  auto capped = [](int g, int ntiles) { return g < (ntiles > 0 ? ntiles : 1) ? g : (ntiles > 0 ? ntiles : 1); };
-  // K' grids: the occupancy bound sizes the partial-sum arrays; capped by
-  // the tile count of K' once it is known
+  // grids: the occupancy bound, at most one warp per work item (the K'
+  // grids are set once its layout is known; the occupancy bound sizes the
+  // partial-sum arrays)
+  auto capped = [](int g, int nitems) {
+    const int need = (nitems + NW - 1) / NW;
+    return std::max(1, std::min(g, need));
+  };
   const int gridA_max = occupancy_grid(KC_PRIMAL, s->num_sms), gridR1_max = occupancy_grid(KC_R1, s->num_sms);
   s->gridA = gridA_max;
-  s->gridB = capped(occupancy_grid(KC_DUAL, s->num_sms), (int)tilesK.size() - 1);
+  s->gridB = capped(occupancy_grid(KC_DUAL, s->num_sms), (int)LK.items.size());
   s->gridR1 = gridR1_max;
-  s->gridR2 = capped(occupancy_grid(KC_R2, s->num_sms), (int)tilesK.size() - 1);
+  s->gridR2 = capped(occupancy_grid(KC_R2, s->num_sms), (int)LK.items.size());
   {
     const int64_t mx = n > m ? n : m;
     int g = occupancy_grid(KC_R3, s->num_sms);
@@ -305,19 +320,16 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   }
   const bool f32 = prm.value_bits == 32;
 
-  // ---- one device arena ----
+  // ---- one device arena for K, K' (CSR, original order: transpose and
+  // scaling), the vectors and the state; a second one, once K''s layout is
+  // known, for the sliced-ELL copies ----
   Layout L;
   const size_t M = (size_t)m, N = (size_t)n, Z = (size_t)nnz;
-  // matrix arrays are padded: the SpMV's 8-entry vector loads may read up to
-  // EPT - 1 entries past the last nonzero (masked, never used)
-  const size_t PADB = 256;
-  const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z + PADB), o_Kval = L.take(8 * Z + PADB);
-  const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z + PADB), o_Tval = L.take(8 * Z + PADB);
-  const size_t o_Kv32 = f32 ? L.take(4 * Z + PADB) : 0, o_Tv32 = f32 ? L.take(4 * Z + PADB) : 0;
-  // tiles of K': at most one per row
-  const size_t o_Ktl = L.take(sizeof(int2) * tilesK.size()), o_Ttl = L.take(sizeof(int2) * (N + 1));
-  const size_t nvec_n = 18, nvec_m = 14;
+  const size_t o_Kptr = L.take(4 * (M + 1)), o_Kidx = L.take(4 * Z), o_Kval = L.take(8 * Z);
+  const size_t o_Tptr = L.take(4 * (N + 1)), o_Tidx = L.take(4 * Z), o_Tval = L.take(8 * Z);
+  const size_t nvec_n = 19, nvec_m = 15;
   const size_t o_vn = L.take(8 * N * nvec_n), o_vm = L.take(8 * (M + 1) * nvec_m);
+  const size_t o_pr = L.take(4 * (M + 1)), o_pc = L.take(4 * N);
   const size_t o_pA = L.take(8 * (size_t)s->gridA * NV_A), o_pB = L.take(8 * (size_t)s->gridB * NV_B);
   const size_t o_pR1 = L.take(8 * (size_t)s->gridR1 * NV_R1), o_pR2 = L.take(8 * (size_t)s->gridR2 * NV_R2);
   const size_t o_pR3 = L.take(8 * (size_t)s->gridR3 * NV_R3), o_pI = L.take(8 * (size_t)s->gridI * NV_I);
@@ -334,22 +346,23 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   s->T_ptr = (int32_t *)(A + o_Tptr);
   s->T_idx = (int32_t *)(A + o_Tidx);
   s->T_val = (double *)(A + o_Tval);
-  s->K_val32 = f32 ? (float *)(A + o_Kv32) : nullptr;
-  s->T_val32 = f32 ? (float *)(A + o_Tv32) : nullptr;
-  int2 *Ktl = (int2 *)(A + o_Ktl), *Ttl = (int2 *)(A + o_Ttl);
+  s->perm_r = (int32_t *)(A + o_pr);
+  s->perm_c = (int32_t *)(A + o_pc);
   double *vn = (double *)(A + o_vn), *vm = (double *)(A + o_vm);
   auto VN = [&](int i) { return vn + (size_t)i * N; };
   auto VM = [&](int i) { return vm + (size_t)i * (M + 1); };
+  // internal order: c~, l~, u~, D2, l, u (original bounds, for the output
+  // projection), q~, D1; original order: D2, D1 (the scaling's result)
   s->c = VN(0);
   s->l = VN(1);
   s->u = VN(2);
-  s->D2 = VN(3);
   s->l0 = VN(4);
   s->u0 = VN(5);
   s->work_n = VN(16);
+  s->D2 = VN(18);
   s->q = VM(0);
-  s->D1 = VM(1);
   s->work_m = VM(12);
+  s->D1 = VM(14);
   s->st = (DevState *)(A + o_st);
   s->d_scal = (double *)(A + o_sc);
 
@@ -361,11 +374,11 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.c = s->c;
   V.l = s->l;
   V.u = s->u;
-  V.D2 = s->D2;
+  V.D2 = VN(3);
   V.l0 = s->l0;
   V.u0 = s->u0;
   V.q = s->q;
-  V.D1 = s->D1;
+  V.D1 = VM(1);
   V.rD2 = VN(17);
   V.rD1 = VM(13);
   V.x[0] = VN(6);
@@ -398,23 +411,22 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   V.trace = (TraceRec *)(A + o_tr);
   V.pw = (const double *)(A + o_pw);
   V.npw = npw;
-
-  s->K = Csr{m, (int32_t)tilesK.size() - 1, s->K_ptr, s->K_idx, s->K_val, s->K_val32, Ktl};
+  V.perm_r = s->perm_r;
+  V.perm_c = s->perm_c;
 
   // ---- transfers ----
   cudaStream_t st = s->stream;
   CKS(cudaMemsetAsync(s->arena, 0, s->arena_bytes, st));
   CKS(cudaMemcpyAsync(s->K_ptr, row_ptr, 4 * (M + 1), cudaMemcpyHostToDevice, st));
   if (nnz) {
-    CKS(cudaMemcpyAsync(s->K_idx, col_idx, 4 * Z, cudaMemcpyHostToDevice, st));
-    CKS(cudaMemcpyAsync(s->K_val, val, 8 * Z, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(s->K_idx, col_idx, 4 * Z, entry_kind, st));
+    CKS(cudaMemcpyAsync(s->K_val, val, 8 * Z, entry_kind, st));
   }
-  CKS(cudaMemcpyAsync(Ktl, tilesK.data(), sizeof(int2) * tilesK.size(), cudaMemcpyHostToDevice, st));
+  if (m) CKS(cudaMemcpyAsync(s->perm_r, LK.perm.data(), 4 * M, cudaMemcpyHostToDevice, st));
 
   // ---- K' on the device: row starts from K's column counts, then the
   // stable transpose (the threaded host counting sort when a column is
-  // longer than the device's per-column sort takes); its tile schedule on
-  // the host from the row starts ----
+  // longer than the device's per-column sort takes) ----
   std::vector<int32_t> tp((size_t)n + 1, 0);
   int32_t longest = 0;
   // scratch of the row starts, then of the transpose; the transpose leaves
@@ -422,13 +434,13 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
   // after the scaling)
   const size_t wcs = col_starts_work_ints(n);
   struct ScratchBuffer {  // an error exit releases it (synchronously: the stream may be gone)
-    int32_t *p = nullptr;
+    void *p = nullptr;
     ~ScratchBuffer() {
       if (p) cudaFree(p);
     }
-  } tw;
-  CKS(cudaMallocAsync((void **)&tw.p, sizeof(int32_t) * (wcs + transpose_work_ints(n, nnz)), st));
-  int32_t *const twork = tw.p;
+  } tw, lw;
+  CKS(cudaMallocAsync(&tw.p, sizeof(int32_t) * (wcs + transpose_work_ints(n, nnz)), st));
+  int32_t *const twork = static_cast<int32_t *>(tw.p);
   CKS(setup_col_starts(n, nnz, s->K_idx, s->T_ptr, twork, st));
   CKS(cudaMemcpyAsync(tp.data(), s->T_ptr, 4 * (N + 1), cudaMemcpyDeviceToHost, st));
   CKS(cudaMemcpyAsync(&longest, twork, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -437,26 +449,43 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
     CKS(setup_transpose(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, twork + wcs, st));
   const bool have_perm = nnz && longest <= transpose_max_segment();
   if (nnz && longest > transpose_max_segment()) {
-    std::vector<int32_t> tp_h((size_t)n + 1), ti((size_t)nnz);
-    std::vector<double> tv((size_t)nnz);
-    csr_transpose(m, n, row_ptr, col_idx, val, tp_h.data(), ti.data(), tv.data());
+    std::vector<int32_t> tp_h((size_t)n + 1), ti((size_t)nnz), ci_h;
+    std::vector<double> tv((size_t)nnz), v_h;
+    const int32_t *ci = col_idx;
+    const double *v = val;
+    if (dev_entries) {  // the host sort needs the entries on the host
+      ci_h.resize(Z);
+      v_h.resize(Z);
+      CKS(cudaMemcpyAsync(ci_h.data(), s->K_idx, 4 * Z, cudaMemcpyDeviceToHost, st));
+      CKS(cudaMemcpyAsync(v_h.data(), s->K_val, 8 * Z, cudaMemcpyDeviceToHost, st));
+      CKS(cudaStreamSynchronize(st));
+      ci = ci_h.data();
+      v = v_h.data();
+    }
+    csr_transpose(m, n, row_ptr, ci, v, tp_h.data(), ti.data(), tv.data());
     CKS(cudaMemcpyAsync(s->T_idx, ti.data(), 4 * Z, cudaMemcpyHostToDevice, st));
     CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
     CKS(cudaStreamSynchronize(st));  // the host arrays go out of scope
   }
-  std::vector<int2> tilesT = build_tiles(tp.data(), n);
-  CKS(cudaMemcpyAsync(Ttl, tilesT.data(), sizeof(int2) * tilesT.size(), cudaMemcpyHostToDevice, st));
-  s->gridA = capped(gridA_max, (int)tilesT.size() - 1);
-  s->gridR1 = capped(gridR1_max, (int)tilesT.size() - 1);
+  // the layout of K' (one group: every column of K) while the device works
+  SellLayout LT = sell_layout(tp.data(), n, n);
+  if (LK.total >= ((int64_t)1 << 31) || LT.total >= ((int64_t)1 << 31)) {
+    free_solver(s);
+    return fail(PDLP_ERR_INVALID, "the sliced-ELL copy of K needs 2^31 or more stored entries");
+  }
+  s->gridA = capped(gridA_max, (int)LT.items.size());
+  s->gridR1 = capped(gridR1_max, (int)LT.items.size());
   V.gridA = s->gridA;
   V.gridR1 = s->gridR1;
-  s->KT = Csr{n, (int32_t)tilesT.size() - 1, s->T_ptr, s->T_idx, s->T_val, s->T_val32, Ttl};
-  CKS(cudaMemcpyAsync(s->l0, l, 8 * N, cudaMemcpyHostToDevice, st));
-  CKS(cudaMemcpyAsync(s->u0, u, 8 * N, cudaMemcpyHostToDevice, st));
-  CKS(cudaMemcpyAsync(V.xout, c, 8 * N, cudaMemcpyHostToDevice, st));  // original c, consumed below
+  CKS(cudaMemcpyAsync(s->perm_c, LT.perm.data(), 4 * N, cudaMemcpyHostToDevice, st));
+  // original c, q, l, u into spare vectors, consumed below
+  CKS(cudaMemcpyAsync(V.xout, c, 8 * N, cudaMemcpyHostToDevice, st));
   if (m) CKS(cudaMemcpyAsync(V.yout, q, 8 * M, cudaMemcpyHostToDevice, st));
+  double *const l_orig = VN(9), *const u_orig = VN(10);
+  CKS(cudaMemcpyAsync(l_orig, l, 8 * N, cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(u_orig, u, 8 * N, cudaMemcpyHostToDevice, st));
 
-  // ---- Sec. 2.2 scaling on the device ----
+  // ---- Sec. 2.2 scaling on the device (original order) ----
   {
     cudaError_t e;
     if (have_perm) {
@@ -472,14 +501,70 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
     tw.p = nullptr;
     CKS(ef);
   }
-  CKS(setup_vectors(m, n, V.xout, V.yout, s->l0, s->u0, s->D1, s->D2, s->c, s->q, s->l, s->u, st));
-  CKS(setup_recip(n, s->D2, VN(17), st));
-  CKS(setup_recip(m, s->D1, VM(13), st));
-  if (f32) {
-    CKS(setup_f32(nnz, s->K_val, s->K_val32, st));
-    CKS(setup_f32(nnz, s->T_val, s->T_val32, st));
+  // scaled vectors in the original order (spare slots), their scalars
+  double *const c_s = VN(6), *const l_s = VN(7), *const u_s = VN(8), *const q_s = VM(2);
+  CKS(setup_vectors(m, n, V.xout, V.yout, l_orig, u_orig, s->D1, s->D2, c_s, q_s, l_s, u_s, st));
+  CKS(setup_scalars(m, n, nnz, c_s, q_s, s->K_val, s->d_scal, s->d_scal + 8, st));
+
+  // ---- sliced-ELL copies of the scaled K and K', columns renumbered ----
+  {
+    Layout SL;
+    const size_t ZK = (size_t)LK.total, ZT = (size_t)LT.total;
+    const size_t o_ki = SL.take(4 * ZK), o_kv = SL.take(8 * ZK), o_kf = f32 ? SL.take(4 * ZK) : 0;
+    const size_t o_ti = SL.take(4 * ZT), o_tv = SL.take(8 * ZT), o_tf = f32 ? SL.take(4 * ZT) : 0;
+    const size_t o_kit = SL.take(sizeof(int4) * LK.items.size()), o_tit = SL.take(sizeof(int4) * LT.items.size());
+    s->sell_bytes = SL.off;
+    CKS(cudaMalloc((void **)&s->sell_arena, s->sell_bytes));
+    char *B = s->sell_arena;
+    s->K = SellMat{m, (int32_t)LK.items.size(), (const int4 *)(B + o_kit), (const int32_t *)(B + o_ki),
+                   (const double *)(B + o_kv), f32 ? (const float *)(B + o_kf) : nullptr};
+    s->KT = SellMat{n, (int32_t)LT.items.size(), (const int4 *)(B + o_tit), (const int32_t *)(B + o_ti),
+                    (const double *)(B + o_tv), f32 ? (const float *)(B + o_tf) : nullptr};
+    if (!LK.items.empty())
+      CKS(cudaMemcpyAsync(B + o_kit, LK.items.data(), sizeof(int4) * LK.items.size(), cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(B + o_tit, LT.items.data(), sizeof(int4) * LT.items.size(), cudaMemcpyHostToDevice, st));
+    // scratch: inverse permutations, entry bases and strides of both layouts
+    Layout WL;
+    const size_t o_ir = WL.take(4 * (M + 1)), o_ic = WL.take(4 * N), o_bk = WL.take(4 * (M + 1)),
+                 o_bt = WL.take(4 * N), o_lk = WL.take(M + 1), o_lt = WL.take(N);
+    CKS(cudaMallocAsync(&lw.p, WL.off, st));
+    char *W = static_cast<char *>(lw.p);
+    int32_t *inv_r = (int32_t *)(W + o_ir), *inv_c = (int32_t *)(W + o_ic);
+    if (m) {
+      CKS(cudaMemcpyAsync(W + o_bk, LK.base.data(), 4 * M, cudaMemcpyHostToDevice, st));
+      CKS(cudaMemcpyAsync(W + o_lk, LK.lane.data(), M, cudaMemcpyHostToDevice, st));
+    }
+    CKS(cudaMemcpyAsync(W + o_bt, LT.base.data(), 4 * N, cudaMemcpyHostToDevice, st));
+    CKS(cudaMemcpyAsync(W + o_lt, LT.lane.data(), N, cudaMemcpyHostToDevice, st));
+    CKS(setup_invert(m, s->perm_r, inv_r, st));
+    CKS(setup_invert(n, s->perm_c, inv_c, st));
+    CKS(setup_sell_fill(m, LK.total, s->perm_r, (const int32_t *)(W + o_bk), (const uint8_t *)(W + o_lk), s->K_ptr,
+                        s->K_idx, s->K_val, inv_c, (int32_t *)s->K.idx, (double *)s->K.val, st));
+    CKS(setup_sell_fill(n, LT.total, s->perm_c, (const int32_t *)(W + o_bt), (const uint8_t *)(W + o_lt), s->T_ptr,
+                        s->T_idx, s->T_val, inv_r, (int32_t *)s->KT.idx, (double *)s->KT.val, st));
+    if (f32) {
+      CKS(setup_f32(LK.total, s->K.val, (float *)s->K.val32, st));
+      CKS(setup_f32(LT.total, s->KT.val, (float *)s->KT.val32, st));
+    }
+    // the host layouts go out of scope: wait for their uploads
+    CKS(cudaStreamSynchronize(st));
+    const cudaError_t ef = cudaFreeAsync(lw.p, st);
+    lw.p = nullptr;
+    CKS(ef);
   }
-  CKS(setup_scalars(m, n, nnz, s->c, s->q, s->K_val, s->d_scal, s->d_scal + 8, st));
+  s->h_perm_r.swap(LK.perm);
+  s->h_perm_c.swap(LT.perm);
+  // ---- vectors in the internal order ----
+  CKS(setup_permute(n, s->perm_c, c_s, s->c, st));
+  CKS(setup_permute(n, s->perm_c, l_s, s->l, st));
+  CKS(setup_permute(n, s->perm_c, u_s, s->u, st));
+  CKS(setup_permute(n, s->perm_c, s->D2, VN(3), st));
+  CKS(setup_permute(n, s->perm_c, l_orig, s->l0, st));
+  CKS(setup_permute(n, s->perm_c, u_orig, s->u0, st));
+  CKS(setup_permute(m, s->perm_r, q_s, s->q, st));
+  CKS(setup_permute(m, s->perm_r, s->D1, VM(1), st));
+  CKS(setup_recip(n, VN(3), VN(17), st));
+  CKS(setup_recip(m, VM(1), VM(13), st));
   CKS(setup_pow_table((double *)(A + o_pw), npw, st));
   CKS(cudaMemcpyAsync(s->h_scal, s->d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CKS(cudaStreamSynchronize(st));
@@ -491,6 +576,52 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
 #undef CKS
   *out = s;
   return PDLP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pdlp_create_device(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c,
+                       const int32_t *row_ptr, const int32_t *col_idx, const double *val, const double *q,
+                       const double *l, const double *u, const pdlp_params *params, void *stream) {
+  g_err.clear();
+  if (!out) return fail(PDLP_ERR_INVALID, "out is NULL");
+  pdlp_params prm;
+  if (params)
+    prm = *params;
+  else
+    pdlp_default_params(&prm);
+  int rc = check_params(prm);
+  if (rc) return rc;
+  if (m < 0 || n < 1 || n_eq < 0 || n_eq > m) return fail(PDLP_ERR_INVALID, "dimensions: need m >= 0, n >= 1, 0 <= n_eq <= m");
+  if (!c || !row_ptr || !l || !u || (m > 0 && !q)) return fail(PDLP_ERR_INVALID, "null input array");
+  const double t_start = now_ms();
+  cudaStream_t st = (cudaStream_t)stream;
+  // the row starts and the vectors come to the host (the layout and the
+  // checks need them; the norms are taken by the same host code as in
+  // pdlp_create_ex); the entries stay on the device
+  std::vector<int32_t> rp((size_t)m + 1);
+  std::vector<double> hc((size_t)n), hl((size_t)n), hu((size_t)n), hq((size_t)m);
+  CK(cudaMemcpyAsync(rp.data(), row_ptr, 4 * ((size_t)m + 1), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hc.data(), c, 8 * (size_t)n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hl.data(), l, 8 * (size_t)n, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hu.data(), u, 8 * (size_t)n, cudaMemcpyDeviceToHost, st));
+  if (m) CK(cudaMemcpyAsync(hq.data(), q, 8 * (size_t)m, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  rc = validate_vectors(m, n, n_eq, hc.data(), rp.data(), hq.data(), hl.data(), hu.data());
+  if (rc) return rc;
+  const int64_t nnz = rp[m];
+  if (nnz >= ((int64_t)1 << 31)) return fail(PDLP_ERR_INVALID, "nnz must be < 2^31");
+  if (nnz > 0) {
+    if (!col_idx || !val) return fail(PDLP_ERR_INVALID, "null col_idx / val");
+    int64_t first = nnz;
+    int col_bad = 0;
+    CK(setup_check_entries(nnz, col_idx, val, n, &first, &col_bad, st));
+    if (first < nnz) return bad_entry(first, col_bad != 0);
+  }
+  return create_common(out, m, n, n_eq, hc.data(), rp.data(), col_idx, val, hq.data(), hl.data(), hu.data(), prm,
+                       stream, true, t_start);
 }
 
 int pdlp_create(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *row_ptr,
@@ -517,7 +648,8 @@ int pdlp_begin(pdlp_solver *s, const double *x0, const double *y0, double tol, i
   const size_t N = (size_t)s->n, M = (size_t)s->m;
   if (x0) CK(cudaMemcpyAsync(V.xout, x0, 8 * N, cudaMemcpyHostToDevice, st));
   if (y0 && M) CK(cudaMemcpyAsync(V.yout, y0, 8 * M, cudaMemcpyHostToDevice, st));
-  CK(setup_warm(s->m, s->n, x0 ? V.xout : nullptr, (y0 && M) ? V.yout : nullptr, s->D1, s->D2, V.x[0], V.y[0], st));
+  CK(setup_warm_perm(s->m, s->n, x0 ? V.xout : nullptr, (y0 && M) ? V.yout : nullptr, s->perm_r, s->perm_c, V.D1,
+                     V.D2, V.x[0], V.y[0], st));
   CK(cudaMemsetAsync(V.sx[0], 0, 8 * N, st));
   CK(cudaMemsetAsync(V.sx[1], 0, 8 * N, st));
   CK(cudaMemcpyAsync(V.xlast, V.x[0], 8 * N, cudaMemcpyDeviceToDevice, st));
@@ -604,10 +736,10 @@ int pdlp_finish(pdlp_solver *s, double *x_out, double *y_out, int *status, int64
   return PDLP_OK;
 }
 
-int pdlp_solve_warm(pdlp_solver *s, const double *x0, const double *y0, double tol, int64_t max_iter, double *x_out,
-                    double *y_out, int *status, int64_t *iters) {
-  int rc = pdlp_begin(s, x0, y0, tol, max_iter);
-  if (rc) return rc;
+// Replays the graph until the device state leaves RUNNING (or the time
+// limit), polling a pinned copy of the state one period behind, then writes
+// the outputs (pdlp_finish).
+static int drive(pdlp_solver *s, double *x_out, double *y_out, int *status, int64_t *iters) {
   cudaStream_t st = s->stream;
   const double limit_ms = s->prm.time_limit_s > 0.0 ? 1000.0 * s->prm.time_limit_s : INFINITY;
   // one period in flight ahead of the one being polled
@@ -631,6 +763,23 @@ int pdlp_solve_warm(pdlp_solver *s, const double *x0, const double *y0, double t
     slot = nxt;
   }
   return pdlp_finish(s, x_out, y_out, status, iters);
+}
+
+int pdlp_solve_warm(pdlp_solver *s, const double *x0, const double *y0, double tol, int64_t max_iter, double *x_out,
+                    double *y_out, int *status, int64_t *iters) {
+  int rc = pdlp_begin(s, x0, y0, tol, max_iter);
+  if (rc) return rc;
+  return drive(s, x_out, y_out, status, iters);
+}
+
+int pdlp_resume(pdlp_solver *s, double *x_out, double *y_out, int *status, int64_t *iters) {
+  g_err.clear();
+  if (!s || !s->gexec) return fail(PDLP_ERR_INVALID, "pdlp_resume: call pdlp_begin or pdlp_set_state first");
+  CK(cudaSetDevice(s->device));
+  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpy(s->h_st, s->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  if (s->h_st->status != ST_RUNNING) return pdlp_finish(s, x_out, y_out, status, iters);
+  return drive(s, x_out, y_out, status, iters);
 }
 
 int pdlp_solve(pdlp_solver *s, double tol, int64_t max_iter, double *x_out, double *y_out, int *status,
@@ -756,8 +905,130 @@ int pdlp_get_scaling(const pdlp_solver *s, double *D1, double *D2, double *val_s
   return PDLP_OK;
 }
 
+// ---- solver state (checkpoint / resume) ----
+//
+// Blob: StateHeader, the DevState bytes, then the scaled-space vectors in the
+// ORIGINAL order of rows and columns (exact: a permutation moves bits, it
+// rounds nothing): n-vectors x, sum eta x, K'y, x at the last restart, K'y at
+// the epoch start, K'y of the previous accepted iterate; m-vectors y,
+// sum eta y, Kx, y at the last restart, Kx at the epoch start.  Together with
+// the LP and the parameters these fix every later step (Algorithm 1's
+// z^{n,t}, the epoch sums behind z-bar, eta, omega, k, t, n, the KKT
+// references and the restart candidate); the other buffers are rewritten
+// before they are read again.
+namespace {
+struct StateHeader {
+  uint64_t magic;
+  uint32_t version;
+  int32_t m, n, check_period, value_bits, pad;
+  int64_t nnz;
+  uint64_t devstate_bytes;
+};
+constexpr uint64_t STATE_MAGIC = 0x3154535050444c50ull;  // "PLDPPST1" little-endian
+constexpr int STATE_NV_N = 6, STATE_NV_M = 5;
+
+size_t state_bytes(const pdlp_solver *s) {
+  return sizeof(StateHeader) + sizeof(DevState) + 8 * ((size_t)STATE_NV_N * s->n + (size_t)STATE_NV_M * s->m);
+}
+
+void state_vectors(const pdlp_solver *s, int cur, double *(&vn)[STATE_NV_N], double *(&vm)[STATE_NV_M]) {
+  const Vecs &V = s->V;
+  double *const n_vecs[STATE_NV_N] = {V.x[cur], V.sx[cur], V.g, V.xlast, V.g0, V.gprev};
+  double *const m_vecs[STATE_NV_M] = {V.y[cur], V.sy[cur], V.Kx[cur], V.ylast, V.kx0};
+  for (int i = 0; i < STATE_NV_N; ++i) vn[i] = n_vecs[i];
+  for (int i = 0; i < STATE_NV_M; ++i) vm[i] = m_vecs[i];
+}
+}  // namespace
+
+int pdlp_get_state(const pdlp_solver *s, void *buf, size_t cap, size_t *bytes) {
+  g_err.clear();
+  if (!s) return fail(PDLP_ERR_INVALID, "solver is NULL");
+  const size_t need = state_bytes(s);
+  if (bytes) *bytes = need;
+  if (!buf) return PDLP_OK;
+  if (cap < need) return fail(PDLP_ERR_INVALID, "pdlp_get_state: buffer smaller than the state");
+  CK(cudaSetDevice(s->device));
+  CK(cudaStreamSynchronize(s->stream));
+  char *out = static_cast<char *>(buf);
+  StateHeader h{};
+  h.magic = STATE_MAGIC;
+  h.version = 1;
+  h.m = s->m;
+  h.n = s->n;
+  h.check_period = s->prm.check_period;
+  h.value_bits = s->prm.value_bits;
+  h.nnz = s->nnz;
+  h.devstate_bytes = sizeof(DevState);
+  std::memcpy(out, &h, sizeof(h));
+  DevState d;
+  CK(cudaMemcpy(&d, s->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  std::memcpy(out + sizeof(h), &d, sizeof(d));
+  double *vn[STATE_NV_N], *vm[STATE_NV_M];
+  state_vectors(s, d.cur, vn, vm);
+  double *dst = reinterpret_cast<double *>(out + sizeof(h) + sizeof(d));
+  std::vector<double> tmp((size_t)std::max(s->n, s->m));
+  auto pull = [&](const double *src, int32_t count, const std::vector<int32_t> &perm) -> int {
+    if (count == 0) return PDLP_OK;
+    CK(cudaMemcpy(tmp.data(), src, 8 * (size_t)count, cudaMemcpyDeviceToHost));
+    for (int32_t r = 0; r < count; ++r) dst[perm[r]] = tmp[r];
+    dst += count;
+    return PDLP_OK;
+  };
+  for (int i = 0; i < STATE_NV_N; ++i)
+    if (int rc = pull(vn[i], s->n, s->h_perm_c)) return rc;
+  for (int i = 0; i < STATE_NV_M; ++i)
+    if (int rc = pull(vm[i], s->m, s->h_perm_r)) return rc;
+  return PDLP_OK;
+}
+
+int pdlp_set_state(pdlp_solver *s, const void *buf, size_t bytes) {
+  g_err.clear();
+  if (!s || !buf) return fail(PDLP_ERR_INVALID, "null argument");
+  if (bytes != state_bytes(s)) return fail(PDLP_ERR_INVALID, "pdlp_set_state: size does not match this solver's state");
+  const char *in = static_cast<const char *>(buf);
+  StateHeader h;
+  std::memcpy(&h, in, sizeof(h));
+  if (h.magic != STATE_MAGIC || h.version != 1 || h.devstate_bytes != sizeof(DevState))
+    return fail(PDLP_ERR_INVALID, "pdlp_set_state: not a state of this library version");
+  if (h.m != s->m || h.n != s->n || h.nnz != s->nnz || h.check_period != s->prm.check_period ||
+      h.value_bits != s->prm.value_bits)
+    return fail(PDLP_ERR_INVALID, "pdlp_set_state: the state belongs to another LP or other parameters");
+  DevState d;
+  std::memcpy(&d, in + sizeof(h), sizeof(d));
+  if ((d.cur != 0 && d.cur != 1) || d.check_pending != 0)
+    return fail(PDLP_ERR_INVALID, "pdlp_set_state: the state was not taken between check periods");
+  CK(cudaSetDevice(s->device));
+  int rc = build_graph(s);
+  if (rc) return rc;
+  double *vn[STATE_NV_N], *vm[STATE_NV_M];
+  state_vectors(s, d.cur, vn, vm);
+  const double *src = reinterpret_cast<const double *>(in + sizeof(h) + sizeof(d));
+  std::vector<double> tmp((size_t)std::max(s->n, s->m));
+  cudaStream_t st = s->stream;
+  CK(cudaStreamSynchronize(st));
+  auto push = [&](double *dst, int32_t count, const std::vector<int32_t> &perm) -> int {
+    if (count == 0) return PDLP_OK;
+    for (int32_t r = 0; r < count; ++r) tmp[r] = src[perm[r]];
+    CK(cudaMemcpy(dst, tmp.data(), 8 * (size_t)count, cudaMemcpyHostToDevice));
+    src += count;
+    return PDLP_OK;
+  };
+  for (int i = 0; i < STATE_NV_N; ++i)
+    if ((rc = push(vn[i], s->n, s->h_perm_c))) return rc;
+  for (int i = 0; i < STATE_NV_M; ++i)
+    if ((rc = push(vm[i], s->m, s->h_perm_r))) return rc;
+  std::memset(d.cnt, 0, sizeof(d.cnt));
+  *s->h_st = d;
+  CK(cudaMemcpy(s->st, s->h_st, sizeof(DevState), cudaMemcpyHostToDevice));
+  s->launches = 0;
+  s->have_result = false;
+  s->last_status = d.status;
+  s->t0 = now_ms();
+  return PDLP_OK;
+}
+
 void *pdlp_get_stream(const pdlp_solver *s) { return s ? (void *)s->stream : nullptr; }
 
-size_t pdlp_device_bytes(const pdlp_solver *s) { return s ? s->arena_bytes : 0; }
+size_t pdlp_device_bytes(const pdlp_solver *s) { return s ? s->arena_bytes + s->sell_bytes : 0; }
 
 }  // extern "C"

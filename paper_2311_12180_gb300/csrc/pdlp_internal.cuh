@@ -6,15 +6,32 @@
 
 namespace pdlp {
 
-// Tile-SpMV geometry (see pdlp_kernels.cu).  A tile is a run of consecutive
-// CSR rows holding at most TILE_NNZ nonzeros and TILE_ROWS rows, or a single
-// row longer than TILE_NNZ.  One CTA of NT threads processes one tile at a
-// time, one row per thread in the epilogue.
+// Thread-block geometry of the step and check kernels (see pdlp_kernels.cu).
 constexpr int NT = 256;
 constexpr int NW = NT / 32;
-constexpr int EPT = 8;                   // consecutive entries per thread
-constexpr int TILE_NNZ = NT * EPT - EPT;  // 2040: the EPT-aligned span of a tile fits NT * EPT
-constexpr int TILE_ROWS = 256;
+
+// Sliced-ELL storage of K and K' (see pdlp_kernels.cu and pdlp_sell.h).
+// Rows are renumbered (the solver's internal order): within each group
+// (the equality rows of K, then its ">=" rows; all rows of K') by length,
+// longest first.  Rows of at most SELL_LONG entries are stored in slices of
+// 32 consecutive internal rows, entry k of the slice's lane-th row at
+// off + 32 k + lane (L = the slice's longest row; shorter rows padded); a
+// longer row is stored contiguously from off, padded to a multiple of 32.
+// Padding entries hold column -1 and value 0.  Every item starts at a
+// multiple of 32 entries.
+constexpr int SELL_LONG = 128;
+constexpr int SELL_U = 4;  // strides of 32 entries loaded per batch
+
+// One unit of work for one warp: a slice {first row, rows (1..32), L, off}
+// or a long row {row, -1, length, off}.
+struct SellMat {
+  int32_t rows;
+  int32_t nitems;
+  const int4 *items;    // in schedule order (cost, longest first)
+  const int32_t *idx;   // internal column of each stored entry, -1 for padding
+  const double *val;    // FP64 values (scaled)
+  const float *val32;   // FP32 copy of val (or null)
+};
 
 constexpr int ST_RUNNING = -1;
 constexpr int ST_OPTIMAL = 0;
@@ -41,16 +58,6 @@ constexpr int NV_R3 = 2;  // ||x_new - x_last||^2, ||y_new - y_last||^2
 // ||(K_E xr, min(K_G xr, 0))||^2, q'yr, ||min(yr_G, 0)||^2.
 constexpr int NV_I1 = 7;
 constexpr int NV_I = 2 * NV_I1;
-
-struct Csr {
-  int32_t rows;
-  int32_t ntiles;
-  const int32_t *ptr;    // rows + 1
-  const int32_t *idx;    // nnz
-  const double *val;     // nnz, FP64 (scaled)
-  const float *val32;    // nnz, FP32 copy of val (or null)
-  const int2 *tmeta;     // ntiles + 1: {first row, first nonzero} of each tile; last = {rows, nnz}
-};
 
 // Device-resident solver state: read by every kernel at entry, written only
 // by one thread of the last block of a kernel (or by the host between solves).
@@ -112,6 +119,9 @@ struct Vecs {
   // (k + 2)^-0.3 at pw[k] and (k + 2)^-0.6 at pw[npw + k] for k < npw
   const double *pw;
   long long npw;
+  // internal -> original row of K (m) and column (n); every vector above is
+  // in the internal order, k_output writes the original order
+  const int32_t *perm_r, *perm_c;
 };
 
 // ---- kernel launchers (pdlp_kernels.cu) ----
@@ -124,10 +134,10 @@ struct LaunchCfg {
   int gridA, gridB, gridR1, gridR2, gridR3;
 };
 
-cudaError_t launch_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s);
-cudaError_t launch_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cudaStream_t s);
-cudaError_t launch_check_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s);
-cudaError_t launch_check_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cudaStream_t s);
+cudaError_t launch_primal(const SellMat &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s);
+cudaError_t launch_dual(const SellMat &K, const Vecs &V, DevState *st, int grid, cudaStream_t s);
+cudaError_t launch_check_primal(const SellMat &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s);
+cudaError_t launch_check_dual(const SellMat &K, const Vecs &V, DevState *st, int grid, cudaStream_t s);
 cudaError_t launch_restart(const Vecs &V, DevState *st, int grid, cudaStream_t s);
 cudaError_t launch_infeas(const Vecs &V, DevState *st, int grid, cudaStream_t s);
 cudaError_t launch_output(const Vecs &V, DevState *st, cudaStream_t s);

@@ -28,29 +28,24 @@
 // has nothing to do, so a fixed CUDA graph of P + E trial slots followed by the
 // check kernels advances the solve by exactly one check period.
 //
-// SpMV ("tile_direct"): a tile is a run of consecutive rows with <= TILE_NNZ
-// nonzeros and <= TILE_ROWS rows (or one longer row).  Thread t of the CTA
-// owns the EPT consecutive entries starting at a + EPT t, where a is the
-// tile's first nonzero rounded down to a multiple of EPT; it loads their
-// column indices and values with 16-byte streaming vector loads (coalesced
-// across the warp, evict-first: read once per SpMV), masks entries outside
-// the tile, and issues its EPT random gathers of x / y at once into
-// registers.  The random gathers are the binding resource on GB300 (each is
-// a distinct cache line for the SM's L1TEX tag stage, ~0.9 lines per clock
-// per SM measured), so the kernel keeps per-entry instruction counts low and
-// relies on occupancy (no matrix staging in shared memory) for many gathers
-// in flight.  The reduction keeps every lane busy -- GB300 issues FP64 at
-// ~1.6 DFMA per clock per SM and a warp-wide FP64 instruction costs the same
-// however many lanes are active: each thread sums its entries with FMA,
-// writing rows that start and end in its range directly, and rows that cross
-// thread boundaries are completed from per-thread carries (serially for up to
-// CHAIN_MAX threads, else by a warp-strided sum).  The epilogue runs one row
-// per thread on operands prefetched into registers before the reduction.
-// As soon as a thread's own sums are done, it issues the loads of its chunk
-// of the CTA's next tile into the registers just freed, so that HBM latency
-// overlaps the carries, barriers and epilogue of the current tile.
-// Reductions are deterministic: fixed per-thread order, fixed shuffle trees,
-// fixed block order in the last CTA.  No atomics touch floating point.
+// SpMV (sliced ELL, see SellMat): rows are renumbered by length within
+// their group at create, so that 32 consecutive internal rows have nearly
+// equal lengths; such a slice is stored column-major (entry k of lane l at
+// off + 32 k + l) and one warp computes it with one row per lane: coalesced
+// 4-byte index loads, 8-byte value loads, random gathers of x / y straight
+// into registers, FMAs in the row's own order, and the row's epilogue in the
+// same lane -- no shared memory, no barriers, no cross-lane reduction.  The
+// random gathers bind on GB300 (about 0.85 per clock per SM whatever the
+// cache qualifier; 2e7 of them take ~74 us), then the narrow FP64 pipe
+// (~1.6 DFMA per clock per SM), so the layout spends one FMA per stored
+// entry and one epilogue per 32 rows.  Rows longer than SELL_LONG are stored
+// contiguously and taken by a whole warp (lane-strided partial sums); their
+// totals come out of a butterfly over 32 such rows at a time, followed by
+// one vectorised epilogue.  Warps walk a cost-sorted item list in a snake
+// order, independently: every warp keeps its own loads and gathers in
+// flight.  Reductions are deterministic: fixed per-lane order, fixed
+// butterfly and shuffle trees, fixed block order in the last CTA.  No
+// atomics touch floating point.
 
 #include <math.h>
 #include <math_constants.h>
@@ -137,36 +132,8 @@ __device__ __forceinline__ void sum_partials(const double *part, int count, doub
   block_sum<NV>(tot, s_red);
 }
 
-// ---------------------------------------------------------------- IEEE-bit helpers
+// ---------------------------------------------------------------- sliced-ELL SpMV
 
-// ---------------------------------------------------------------- tile SpMV
-
-constexpr int CHAIN_MAX = 8;
-static_assert(EPT == 8, "load_chunk() loads 8 entries");
-
-template <int NV>
-struct TileSmem {
-  int off[TILE_ROWS + 1];  // row starts relative to the tile's aligned base
-  double rowsum[NV][TILE_ROWS];
-  double carry[NV][NT];
-  double red[16 * NW];
-  int flag;
-};
-
-__device__ __forceinline__ void load_chunk(const int32_t *p, int (&c)[EPT]) {
-  const int4 a = __ldcs(reinterpret_cast<const int4 *>(p));
-  const int4 b = __ldcs(reinterpret_cast<const int4 *>(p) + 1);
-  c[0] = a.x; c[1] = a.y; c[2] = a.z; c[3] = a.w;
-  c[4] = b.x; c[5] = b.y; c[6] = b.z; c[7] = b.w;
-}
-__device__ __forceinline__ void load_chunk(const double *p, double (&v)[EPT]) {
-#pragma unroll
-  for (int k = 0; k < EPT / 2; ++k) {
-    const double2 a = __ldcs(reinterpret_cast<const double2 *>(p) + k);
-    v[2 * k] = a.x;
-    v[2 * k + 1] = a.y;
-  }
-}
 // float -> double from the IEEE bits with integer operations (exact for
 // every normal float: the exponent is re-biased by 1023 - 127 = 896 and the
 // 23-bit mantissa moved to the top of the 52-bit one), keeping the widening
@@ -181,224 +148,166 @@ __device__ __forceinline__ double f2d(float f) {
                                ((unsigned long long)(b & 0x7fffffu) << 29);
   return __longlong_as_double((long long)d);
 }
-__device__ __forceinline__ void load_chunk(const float *p, float (&v)[EPT]) {
-#pragma unroll
-  for (int k = 0; k < EPT / 4; ++k) {
-    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p) + k);
-    v[4 * k] = a.x;
-    v[4 * k + 1] = a.y;
-    v[4 * k + 2] = a.z;
-    v[4 * k + 3] = a.w;
-  }
-}
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double widen(float v) { return f2d(v); }
-__device__ __forceinline__ void load_chunk(const float *p, double (&v)[EPT]) {
-#pragma unroll
-  for (int k = 0; k < EPT / 4; ++k) {
-    const float4 a = __ldcs(reinterpret_cast<const float4 *>(p) + k);
-    v[4 * k] = f2d(a.x);
-    v[4 * k + 1] = f2d(a.y);
-    v[4 * k + 2] = f2d(a.z);
-    v[4 * k + 3] = f2d(a.w);
-  }
-}
-__device__ __forceinline__ double ld_val(const double *p) { return __ldcs(p); }
-__device__ __forceinline__ double ld_val(const float *p) { return f2d(__ldcs(p)); }
 
-// Loads a regular tile's column indices and values into this thread's
-// registers (a tile holding one row longer than a tile loads as it strides).
-template <typename VT>
-__device__ __forceinline__ void tile_load(const Csr &A, const VT *__restrict__ val, int2 m0, int2 m1,
-                                          int (&col)[EPT], VT (&v)[EPT]) {
-  const int e0 = m0.y, e1 = m1.y;
-  if (e1 - e0 > TILE_NNZ) return;
-  const int base = e0 & ~(EPT - 1), c0 = EPT * threadIdx.x;
-  if (base + c0 < e1) {
-    load_chunk(A.idx + base + c0, col);
-    load_chunk(val + base + c0, v);
-  } else {
+// Sum over `cnt` strides of 32 stored entries, this lane's entry of each
+// stride: acc[a] += val * xs[a][col] in stride order (FMA), padding (column
+// -1) skipped.  SELL_U strides are loaded (streaming, coalesced across the
+// warp) before their gathers are issued, and all gathers before the FMAs.
+template <typename VT, int NV, bool SCALED>
+__device__ __forceinline__ void strided_dot(const int32_t *__restrict__ ip, const VT *__restrict__ vp, int cnt,
+                                            const double *const (&xs)[NV], const double (&sc)[NV],
+                                            double (&acc)[NV]) {
+  int k = 0;
+  for (; k + SELL_U <= cnt; k += SELL_U) {
+    int c[SELL_U];
+    VT v[SELL_U];
 #pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      col[i] = 0;
-      v[i] = VT(0);
+    for (int u = 0; u < SELL_U; ++u) {
+      c[u] = __ldcs(ip + 32 * (k + u));
+      v[u] = __ldcs(vp + 32 * (k + u));
     }
-  }
-}
-
-// One tile of y = A x for NV (1 or 2) gathered vectors, followed by the
-// epilogue ep.finish(row, sums) for row r0 + threadIdx.x.  With SCALED,
-// vector a is multiplied by sc[a] entry by entry (the epoch average 1/W sum).
-template <typename VT, int NV, bool SCALED, int NVS, class Epi>
-__device__ __forceinline__ void tile_direct(const Csr &A, const VT *__restrict__ val,
-                                            const double *const (&xs)[NV], const double (&sc)[NV], int2 m0, int2 m1,
-                                            TileSmem<NVS> &sm, Epi &ep, int (&col)[EPT], VT (&v)[EPT],
-                                            const int2 *next) {
-  static_assert(NV == 1 || NV == 2, "one or two gathered vectors");
-  static_assert(NV <= NVS, "tile shared memory holds fewer vectors");
-  const int tid = threadIdx.x;
-  const int r0 = m0.x, e0 = m0.y, e1 = m1.y;
-  const int nrows = m1.x - m0.x;
-  if (e1 - e0 > TILE_NNZ) {  // one row longer than a tile: the whole CTA strides over it
-    if (tid == 0) ep.prefetch(r0);
-    double acc[NV];
+    double g[NV][SELL_U];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-    for (int e = e0 + tid; e < e1; e += NT) {
-      const int col = __ldcs(A.idx + e);
-      const double v = ld_val(val + e);
+    for (int u = 0; u < SELL_U; ++u)
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
-        const double xv = __ldg(xs[a] + col);
-        acc[a] = fma(v, SCALED ? sc[a] * xv : xv, acc[a]);
+        const double xv = c[u] >= 0 ? __ldg(xs[a] + c[u]) : 0.0;
+        g[a][u] = SCALED ? sc[a] * xv : xv;
       }
-    }
-    block_sum<NV>(acc, sm.red);
-    if (next) tile_load(A, val, next[0], next[1], col, v);
-    if (tid == 0) ep.finish(r0, acc);
-    return;
-  }
-  // ---- loads and gathers (registers) ----
-  const int base = e0 & ~(EPT - 1);
-  const int c0 = EPT * tid;  // this thread's chunk, relative to base (col, v loaded by tile_load)
-  double xv[NV][EPT];
-  const int lo = e0 - base, hi = e1 - base;  // tile entries, relative to base
 #pragma unroll
-  for (int i = 0; i < EPT; ++i) {
-    const bool in = c0 + i >= lo && c0 + i < hi;
+    for (int u = 0; u < SELL_U; ++u)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) acc[a] = fma(widen(v[u]), g[a][u], acc[a]);
+  }
+  for (; k < cnt; ++k) {
+    const int c = __ldcs(ip + 32 * k);
+    const VT v = __ldcs(vp + 32 * k);
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
-      double g = 0.0;
-      if (in) g = __ldg(xs[a] + col[i]);
-      xv[a][i] = SCALED ? sc[a] * g : g;
+      const double xv = c >= 0 ? __ldg(xs[a] + c) : 0.0;
+      acc[a] = fma(widen(v), SCALED ? sc[a] * xv : xv, acc[a]);
     }
   }
-  if (tid < nrows) {
-    ep.prefetch(r0 + tid);
-    sm.off[tid] = A.ptr[r0 + tid] - base;
-  }
-  if (tid == 0) sm.off[nrows] = hi;
-  __syncthreads();
-  // ---- per-thread consecutive sums ----
-  const int s0 = max(c0, lo), s1 = min(c0 + EPT, hi);
-  double acc[NV], carry[NV], head[NV];
+}
+
+// One butterfly level: lanes with the `off` bit clear keep row a's pair sum,
+// lanes with it set keep row b's.
+__device__ __forceinline__ double bfly(double a, double b, int off, int lane) {
+  const bool hi = (lane & off) != 0;
+  const double recv = __shfl_xor_sync(0xffffffffu, hi ? a : b, off);
+  return (hi ? b : a) + recv;
+}
+
+// Long rows (whole warp per row) are reduced 32 at a time: the per-lane
+// partial sums of the batch's rows go through a five-level butterfly
+// (31 additions per lane for 32 rows instead of 5 per row), after which
+// lane l holds the total of the batch's row rev5(l), and one vectorised
+// epilogue finishes all 32 rows.  The tree is fixed, so the sums are too.
+template <int NV>
+struct LongRows {
+  double buf[5][NV];
+  int t;       // rows in the current batch (warp-uniform)
+  int *rows;   // this warp's 32 row slots in shared memory
+};
+
+template <int NV, class Epi>
+__device__ __forceinline__ void long_push(LongRows<NV> &lr, const double (&p)[NV], int row, Epi &ep) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) lr.rows[lr.t] = row;
+  const int t = lr.t;
+  double v[NV];
 #pragma unroll
-  for (int a = 0; a < NV; ++a) acc[a] = carry[a] = head[a] = 0.0;
-  bool has_head = false;
-  int head_row = 0;
-  if (s0 < s1) {
-    int lo_r = 0, hi_r = nrows;  // largest row with start <= s0: the nonempty row holding entry s0
-    while (hi_r - lo_r > 1) {
-      const int mid = (lo_r + hi_r) >> 1;
-      if (sm.off[mid] <= s0)
-        lo_r = mid;
-      else
-        hi_r = mid;
-    }
-    int r = lo_r, rstart = sm.off[lo_r], rend = sm.off[lo_r + 1];
+  for (int a = 0; a < NV; ++a) v[a] = p[a];
+  bool done = false;
+  if (!(t & 1)) {
 #pragma unroll
-    for (int i = 0; i < EPT; ++i) {
-      const int e = c0 + i;
-      if (e >= s0 && e < s1) {
+    for (int a = 0; a < NV; ++a) lr.buf[0][a] = v[a];
+  } else {
 #pragma unroll
-        for (int a = 0; a < NV; ++a) acc[a] = fma(widen(v[i]), xv[a][i], acc[a]);
-        if (e + 1 == rend) {
-          if (rstart >= s0) {
+    for (int a = 0; a < NV; ++a) v[a] = bfly(lr.buf[0][a], v[a], 16, lane);
+    if (!(t & 2)) {
 #pragma unroll
-            for (int a = 0; a < NV; ++a) sm.rowsum[a][r] = acc[a];
+      for (int a = 0; a < NV; ++a) lr.buf[1][a] = v[a];
+    } else {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) v[a] = bfly(lr.buf[1][a], v[a], 8, lane);
+      if (!(t & 4)) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) lr.buf[2][a] = v[a];
+      } else {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) v[a] = bfly(lr.buf[2][a], v[a], 4, lane);
+        if (!(t & 8)) {
+#pragma unroll
+          for (int a = 0; a < NV; ++a) lr.buf[3][a] = v[a];
+        } else {
+#pragma unroll
+          for (int a = 0; a < NV; ++a) v[a] = bfly(lr.buf[3][a], v[a], 2, lane);
+          if (!(t & 16)) {
+#pragma unroll
+            for (int a = 0; a < NV; ++a) lr.buf[4][a] = v[a];
           } else {
-            has_head = true;
-            head_row = r;
 #pragma unroll
-            for (int a = 0; a < NV; ++a) head[a] = acc[a];
-          }
-#pragma unroll
-          for (int a = 0; a < NV; ++a) acc[a] = 0.0;
-          if (e + 1 < hi) {
-            do {
-              ++r;
-            } while (sm.off[r + 1] == e + 1);
-            rstart = e + 1;
-            rend = sm.off[r + 1];
+            for (int a = 0; a < NV; ++a) v[a] = bfly(lr.buf[4][a], v[a], 1, lane);
+            done = true;
           }
         }
       }
     }
-    if (rend > s1) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) carry[a] = acc[a];
-    }
   }
-  // the next tile's indices and values stream in while this one's carries,
-  // barriers and epilogue run
-  if (next) tile_load(A, val, next[0], next[1], col, v);
-#pragma unroll
-  for (int a = 0; a < NV; ++a) sm.carry[a][tid] = carry[a];
-  __syncthreads();
-  // ---- rows that crossed thread boundaries ----
-  bool longchain = false;
-  int ts = 0;
-  if (has_head) {
-    ts = sm.off[head_row] / EPT;  // thread holding the row's first entry
-    if (tid - ts <= CHAIN_MAX) {
-      double sum[NV];
-#pragma unroll
-      for (int a = 0; a < NV; ++a) sum[a] = head[a];
-      for (int t2 = tid - 1; t2 >= ts; --t2) {
-#pragma unroll
-        for (int a = 0; a < NV; ++a) sum[a] += sm.carry[a][t2];
-      }
-#pragma unroll
-      for (int a = 0; a < NV; ++a) sm.rowsum[a][head_row] = sum[a];
-    } else {
-      longchain = true;
+  lr.t = t + 1;
+  if (done) {
+    __syncwarp();
+    const int r = lr.rows[__brev(lane) >> 27];
+    __syncwarp();
+    if (r >= 0) {
+      ep.prefetch(r);
+      ep.finish(r, v);
     }
+    lr.t = 0;
   }
-  const int lane = tid & 31;
-  unsigned int msk = __ballot_sync(0xffffffffu, longchain);
-  while (msk) {
-    const int src = __ffs(msk) - 1;
-    msk &= msk - 1;
-    const int row = __shfl_sync(0xffffffffu, head_row, src);
-    const int t0 = __shfl_sync(0xffffffffu, ts, src);
-    const int tend = (tid & ~31) + src;
-    double sum[NV];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) sum[a] = 0.0;
-    for (int t2 = t0 + lane; t2 < tend; t2 += 32) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) sum[a] += sm.carry[a][t2];
-    }
-#pragma unroll
-    for (int a = 0; a < NV; ++a) sum[a] = warp_sum(sum[a]);
-    if (lane == src) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) sm.rowsum[a][row] = sum[a] + head[a];
-    }
-  }
-  __syncthreads();
-  double out[NV];
-  const bool has_row = tid < nrows;
-  if (has_row) {
-    const bool empty = sm.off[tid] == sm.off[tid + 1];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) out[a] = empty ? 0.0 : sm.rowsum[a][tid];
-  }
-  __syncthreads();  // the next tile rewrites off / rowsum
-  if (has_row) ep.finish(r0 + tid, out);
 }
 
-// Persistent loop over this CTA's tiles.
-template <typename VT, int NV, bool SCALED, int NVS, class Epi>
-__device__ __forceinline__ void spmv_tiles(const Csr &A, const VT *__restrict__ val, const double *const (&xs)[NV],
-                                           const double (&sc)[NV], TileSmem<NVS> &sm, Epi &ep) {
-  int col[EPT];
-  VT v[EPT];  // values as stored (FP32 values widen at use)
-  if (blockIdx.x < A.ntiles) tile_load(A, val, A.tmeta[blockIdx.x], A.tmeta[blockIdx.x + 1], col, v);
-  for (int t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
-    const int tn = t + gridDim.x;
-    tile_direct<VT, NV, SCALED>(A, val, xs, sc, A.tmeta[t], A.tmeta[t + 1], sm, ep, col, v,
-                                tn < A.ntiles ? A.tmeta + tn : nullptr);
+// y = A x for NV (1 or 2) gathered vectors, each finished row r passed to
+// ep.finish(r, sums) after ep.prefetch(r).  With SCALED, gathered entries of
+// vector a are multiplied by sc[a] (the epoch average (1/W) sum).  Warp w of
+// the grid takes items w, 2G - 1 - w, 2G + w, ... of the schedule (G warps):
+// a snake over the cost-sorted items, so every warp gets about the same work.
+template <typename VT, int NV, bool SCALED, class Epi>
+__device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict__ val,
+                                          const double *const (&xs)[NV], const double (&sc)[NV], Epi &ep,
+                                          int *warp_rows) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)((gridDim.x * (unsigned)NT) >> 5);
+  const int gw = (int)((blockIdx.x * (unsigned)NT + threadIdx.x) >> 5);
+  LongRows<NV> lr;
+  lr.t = 0;
+  lr.rows = warp_rows;
+  for (int b = 0;; ++b) {
+    const long long first = (long long)b * nw;
+    if (first >= A.nitems) break;
+    const long long it = first + ((b & 1) ? nw - 1 - gw : gw);
+    if (it >= A.nitems) continue;
+    const int4 d = __ldg(A.items + it);
+    double acc[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) acc[a] = 0.0;
+    if (d.y > 0) {  // slice: one row per lane
+      const bool has = lane < d.y;
+      const int row = d.x + lane;
+      if (has) ep.prefetch(row);
+      strided_dot<VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, d.z, xs, sc, acc);
+      if (has) ep.finish(row, acc);
+    } else {  // long row: the whole warp
+      strided_dot<VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, (d.z + 31) >> 5, xs, sc, acc);
+      long_push(lr, acc, d.x, ep);
+    }
+  }
+  if (lr.t > 0) {  // complete the last batch with empty rows
+    const double z[NV] = {};
+    while (lr.t > 0) long_push(lr, z, -1, ep);
   }
 }
 
@@ -428,8 +337,9 @@ struct PrimalEpi {
 };
 
 // 64 registers: four CTAs (32 warps) per SM for gathers in flight
-__global__ void __launch_bounds__(NT, 4) k_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem<1> sm;
+__global__ void __launch_bounds__(NT, 4) k_primal(SellMat KT, Vecs V, DevState *__restrict__ st) {
+  __shared__ double s_red[16 * NW];
+  __shared__ int s_rows[NW][32];
   if (st->status != ST_RUNNING || st->check_pending) return;
   const int cur = st->cur, nxt = cur ^ 1, need_g = st->need_g, f32 = st->use_f32;
   const double eta = st->eta, omega = st->omega;
@@ -449,9 +359,9 @@ __global__ void __launch_bounds__(NT, 4) k_primal(Csr KT, Vecs V, DevState *__re
     const double *const xs[1] = {V.y[cur]};
     const double sc[1] = {1.0};
     if (f32)
-      spmv_tiles<float, 1, false>(KT, KT.val32, xs, sc, sm, ep);
+      spmv_sell<float, 1, false>(KT, KT.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
     else
-      spmv_tiles<double, 1, false>(KT, KT.val, xs, sc, sm, ep);
+      spmv_sell<double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else {
     // rejected trial: g = K'y is unchanged, only the projection reruns
     for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += gridDim.x * NT) {
@@ -460,7 +370,7 @@ __global__ void __launch_bounds__(NT, 4) k_primal(Csr KT, Vecs V, DevState *__re
     }
   }
   double acc[1] = {ep.dx2};
-  block_sum<1>(acc, sm.red);
+  block_sum<1>(acc, s_red);
   if (threadIdx.x == 0) V.partA[blockIdx.x] = acc[0];
 }
 
@@ -525,8 +435,10 @@ __device__ void step_test(DevState *st, const Vecs &V, double dx2, double dy2, d
   }
 }
 
-__global__ void __launch_bounds__(NT, 4) k_dual(Csr K, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem<1> sm;
+__global__ void __launch_bounds__(NT, 4) k_dual(SellMat K, Vecs V, DevState *__restrict__ st) {
+  __shared__ double s_red[16 * NW];
+  __shared__ int s_flag;
+  __shared__ int s_rows[NW][32];
   if (st->status != ST_RUNNING || st->check_pending) return;
   const int cur = st->cur, nxt = cur ^ 1, f32 = st->use_f32;
   const double eta = st->eta, omega = st->omega;
@@ -546,14 +458,14 @@ __global__ void __launch_bounds__(NT, 4) k_dual(Csr K, Vecs V, DevState *__restr
   const double *const xs[1] = {V.x[nxt]};
   const double sc[1] = {1.0};
   if (f32)
-    spmv_tiles<float, 1, false>(K, K.val32, xs, sc, sm, ep);
+    spmv_sell<float, 1, false>(K, K.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   else
-    spmv_tiles<double, 1, false>(K, K.val, xs, sc, sm, ep);
+    spmv_sell<double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   double acc[2] = {ep.dy2, ep.cross};
   double tot[2];
-  if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], sm.red, &sm.flag, tot)) return;
+  if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], s_red, &s_flag, tot)) return;
   double dx[1];
-  sum_partials<1>(V.partA, V.gridA, sm.red, dx);
+  sum_partials<1>(V.partA, V.gridA, s_red, dx);
   if (threadIdx.x == 0) step_test(st, V, dx[0], tot[0], tot[1]);
 }
 
@@ -625,11 +537,10 @@ struct CheckPrimalEpi {
   }
 };
 
-// three CTAs per SM (80 registers): the two-vector tile SpMV then spills ~100
-// bytes, which costs less than running two CTAs per SM (498 vs 560 us on the
-// 1e6 x 2e6 LP)
-__global__ void __launch_bounds__(NT, 3) k_check_primal(Csr KT, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem<2> sm;
+// three CTAs per SM (80 registers) for the two-vector SpMV of a check
+__global__ void __launch_bounds__(NT, 3) k_check_primal(SellMat KT, Vecs V, DevState *__restrict__ st) {
+  __shared__ double s_red[16 * NW];
+  __shared__ int s_rows[NW][32];
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur, need_g = st->need_g;
   const bool check = mode == MODE_CHECK;
@@ -652,17 +563,17 @@ __global__ void __launch_bounds__(NT, 3) k_check_primal(Csr KT, Vecs V, DevState
   if (ep.kind == 0) {
     const double *const xs[1] = {V.y[cur]};
     const double sc[1] = {1.0};
-    spmv_tiles<double, 1, false>(KT, KT.val, xs, sc, sm, ep);
+    spmv_sell<double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else if (ep.kind == 1) {
     const double *const xs[2] = {V.y[cur], V.sy[cur]};
     const double sc[2] = {1.0, ep.invW};
-    spmv_tiles<double, 2, true>(KT, KT.val, xs, sc, sm, ep);
+    spmv_sell<double, 2, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else {
     const double *const xs[1] = {V.sy[cur]};
     const double sc[1] = {ep.invW};
-    spmv_tiles<double, 1, true>(KT, KT.val, xs, sc, sm, ep);
+    spmv_sell<double, 1, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   }
-  block_sum<NV_R1>(ep.acc, sm.red);
+  block_sum<NV_R1>(ep.acc, s_red);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int a = 0; a < NV_R1; ++a) V.partR1[(size_t)blockIdx.x * NV_R1 + a] = ep.acc[a];
@@ -855,8 +766,10 @@ struct CheckDualEpi {
   }
 };
 
-__global__ void __launch_bounds__(NT) k_check_dual(Csr K, Vecs V, DevState *__restrict__ st) {
-  __shared__ TileSmem<1> sm;
+__global__ void __launch_bounds__(NT) k_check_dual(SellMat K, Vecs V, DevState *__restrict__ st) {
+  __shared__ double s_red[16 * NW];
+  __shared__ int s_flag;
+  __shared__ int s_rows[NW][32];
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur;
   const bool check = mode == MODE_CHECK;
@@ -877,19 +790,19 @@ __global__ void __launch_bounds__(NT) k_check_dual(Csr K, Vecs V, DevState *__re
   if (!check) {
     const double *const xs[1] = {V.x[cur]};
     const double sc[1] = {1.0};
-    spmv_tiles<double, 1, false>(K, K.val, xs, sc, sm, ep);
+    spmv_sell<double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else {
     const double *const xs[1] = {V.sx[cur]};
     const double sc[1] = {ep.invW};
-    spmv_tiles<double, 1, true>(K, K.val, xs, sc, sm, ep);
+    spmv_sell<double, 1, true>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   }
   double tot[NV_R2];
-  if (!grid_finish<NV_R2>(ep.acc, V.partR2, &st->cnt[CNT_R2], sm.red, &sm.flag, tot)) return;
+  if (!grid_finish<NV_R2>(ep.acc, V.partR2, &st->cnt[CNT_R2], s_red, &s_flag, tot)) return;
   double p[NV_R1];
-  sum_partials<NV_R1>(V.partR1, V.gridR1, sm.red, p);
+  sum_partials<NV_R1>(V.partR1, V.gridR1, s_red, p);
   double inf[NV_I];
   const bool infeas = check && st->eps_infeas > 0.0;
-  if (infeas) sum_partials<NV_I>(V.partI, V.gridI, sm.red, inf);
+  if (infeas) sum_partials<NV_I>(V.partI, V.gridI, s_red, inf);
   if (threadIdx.x == 0) check_decide(st, V.trace, p, tot, infeas ? inf : nullptr);
 }
 
@@ -1045,8 +958,9 @@ __global__ void __launch_bounds__(NT) k_restart(Vecs V, DevState *__restrict__ s
 
 // ---------------------------------------------------------------- output
 
-// Original-space output: the current iterate or the average (projected onto
-// X), or, for an infeasibility status, the certificate ray in place of the
+// Original-space output, written in the original order of rows and
+// columns: the current iterate or the average (projected onto X), or, for an
+// infeasibility status, the certificate ray in place of the
 // iterate it concerns (y for primal infeasibility, x for dual
 // infeasibility; unprojected).
 __global__ void __launch_bounds__(NT) k_output(Vecs V, DevState *__restrict__ st) {
@@ -1057,22 +971,22 @@ __global__ void __launch_bounds__(NT) k_output(Vecs V, DevState *__restrict__ st
   const int stride = gridDim.x * NT;
   for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += stride) {
     if (xray) {
-      V.xout[j] = V.D2[j] * (V.x[cur][j] - (which == 2 ? V.x[prv][j] : V.xlast[j]));
+      V.xout[V.perm_c[j]] = V.D2[j] * (V.x[cur][j] - (which == 2 ? V.x[prv][j] : V.xlast[j]));
       continue;
     }
     const double xs = avg ? invW * V.sx[cur][j] : V.x[cur][j];
     double v = V.D2[j] * xs;
     if (v < V.l0[j]) v = V.l0[j];
     if (v > V.u0[j]) v = V.u0[j];
-    V.xout[j] = v;
+    V.xout[V.perm_c[j]] = v;
   }
   for (int i = blockIdx.x * NT + threadIdx.x; i < V.m; i += stride) {
     if (yray) {
-      V.yout[i] = V.D1[i] * (V.y[cur][i] - (which == 2 ? V.y[prv][i] : V.ylast[i]));
+      V.yout[V.perm_r[i]] = V.D1[i] * (V.y[cur][i] - (which == 2 ? V.y[prv][i] : V.ylast[i]));
       continue;
     }
     const double ys = avg ? invW * V.sy[cur][i] : V.y[cur][i];
-    V.yout[i] = V.D1[i] * ys;
+    V.yout[V.perm_r[i]] = V.D1[i] * ys;
   }
 }
 
@@ -1104,19 +1018,19 @@ int occupancy_grid(int kc, int num_sms) {
 }
 
 cudaError_t kernels_init() { return cudaSuccess; }
-cudaError_t launch_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
+cudaError_t launch_primal(const SellMat &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
   k_primal<<<grid, NT, 0, s>>>(KT, V, st);
   return cudaGetLastError();
 }
-cudaError_t launch_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
+cudaError_t launch_dual(const SellMat &K, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
   k_dual<<<grid, NT, 0, s>>>(K, V, st);
   return cudaGetLastError();
 }
-cudaError_t launch_check_primal(const Csr &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
+cudaError_t launch_check_primal(const SellMat &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
   k_check_primal<<<grid, NT, 0, s>>>(KT, V, st);
   return cudaGetLastError();
 }
-cudaError_t launch_check_dual(const Csr &K, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
+cudaError_t launch_check_dual(const SellMat &K, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
   k_check_dual<<<grid, NT, 0, s>>>(K, V, st);
   return cudaGetLastError();
 }

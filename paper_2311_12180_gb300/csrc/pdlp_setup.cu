@@ -547,6 +547,119 @@ cudaError_t setup_pow_table(double *pw, long long count, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- sliced-ELL layout
+
+namespace {
+
+// inv[perm[r]] = r
+__global__ void k_invert(int32_t rows, const int32_t *__restrict__ perm, int32_t *__restrict__ inv) {
+  for (int32_t r = blockIdx.x * ST + threadIdx.x; r < rows; r += gridDim.x * ST) inv[perm[r]] = r;
+}
+
+// One warp per internal row r: entry k of original row perm[r] goes to
+// base[r] + k (long row) or base[r] + 32 k (slice row), its column renumbered
+// through inv.  Padding was set beforehand (column -1, value 0).
+__global__ void k_sell_fill(int32_t rows, const int32_t *__restrict__ perm, const int32_t *__restrict__ base,
+                            const uint8_t *__restrict__ lane, const int32_t *__restrict__ ptr,
+                            const int32_t *__restrict__ idx, const double *__restrict__ val,
+                            const int32_t *__restrict__ inv, int32_t *__restrict__ sidx,
+                            double *__restrict__ sval) {
+  const int ln = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * ST + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * ST) >> 5;
+  for (long long r = warp; r < rows; r += nwarps) {
+    const int32_t i = perm[r], e0 = ptr[i], e1 = ptr[i + 1];
+    const int64_t b = base[r], step = lane[r] ? 32 : 1;
+    for (int32_t e = e0 + ln; e < e1; e += 32) {
+      const int64_t d = b + (int64_t)(e - e0) * step;
+      sidx[d] = inv[idx[e]];
+      sval[d] = val[e];
+    }
+  }
+}
+
+__global__ void k_warm_perm(int32_t m, int32_t n, const double *__restrict__ x0, const double *__restrict__ y0,
+                            const int32_t *__restrict__ perm_r, const int32_t *__restrict__ perm_c,
+                            const double *__restrict__ D1, const double *__restrict__ D2, double *__restrict__ x,
+                            double *__restrict__ y) {
+  for (int j = blockIdx.x * ST + threadIdx.x; j < n; j += gridDim.x * ST) x[j] = x0 ? x0[perm_c[j]] / D2[j] : 0.0;
+  for (int i = blockIdx.x * ST + threadIdx.x; i < m; i += gridDim.x * ST) y[i] = y0 ? y0[perm_r[i]] / D1[i] : 0.0;
+}
+
+// first[0] = min index e with a column outside [0, n) or a non-finite value
+// (unchanged when there is none)
+__global__ void k_check_entries(int64_t nnz, const int32_t *__restrict__ idx, const double *__restrict__ val,
+                                int32_t n, unsigned long long *__restrict__ first) {
+  for (int64_t e = (int64_t)blockIdx.x * ST + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * ST) {
+    const int32_t c = idx[e];
+    const unsigned long long b = (unsigned long long)__double_as_longlong(val[e]);
+    if (c < 0 || c >= n || (b & 0x7ff0000000000000ull) == 0x7ff0000000000000ull) atomicMin(first, (unsigned long long)e);
+  }
+}
+
+// dst[r] = src[perm[r]]
+__global__ void k_permute(int32_t count, const int32_t *__restrict__ perm, const double *__restrict__ src,
+                          double *__restrict__ dst) {
+  for (int32_t r = blockIdx.x * ST + threadIdx.x; r < count; r += gridDim.x * ST) dst[r] = src[perm[r]];
+}
+
+}  // namespace
+
+cudaError_t setup_invert(int32_t rows, const int32_t *perm, int32_t *inv, cudaStream_t s) {
+  if (rows > 0) k_invert<<<grid_for(rows), ST, 0, s>>>(rows, perm, inv);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_sell_fill(int32_t rows, int64_t total, const int32_t *perm, const int32_t *base,
+                            const uint8_t *lane, const int32_t *ptr, const int32_t *idx, const double *val,
+                            const int32_t *inv, int32_t *sidx, double *sval, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sidx, 0xff, sizeof(int32_t) * (size_t)total, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(sval, 0, sizeof(double) * (size_t)total, s);
+  if (e != cudaSuccess) return e;
+  if (rows > 0)
+    k_sell_fill<<<grid_for((long long)rows * 32), ST, 0, s>>>(rows, perm, base, lane, ptr, idx, val, inv, sidx,
+                                                              sval);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_warm_perm(int32_t m, int32_t n, const double *x0, const double *y0, const int32_t *perm_r,
+                            const int32_t *perm_c, const double *D1, const double *D2, double *x, double *y,
+                            cudaStream_t s) {
+  k_warm_perm<<<grid_for(n > m ? n : m), ST, 0, s>>>(m, n, x0, y0, perm_r, perm_c, D1, D2, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t setup_check_entries(int64_t nnz, const int32_t *idx, const double *val, int32_t n, int64_t *first,
+                                int *col_bad, cudaStream_t s) {
+  *first = nnz;
+  *col_bad = 0;
+  unsigned long long *d = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&d, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  unsigned long long h = ~0ull;
+  int32_t c = 0;
+  e = cudaMemsetAsync(d, 0xff, sizeof(unsigned long long), s);
+  if (e == cudaSuccess) {
+    k_check_entries<<<grid_for(nnz), ST, 0, s>>>(nnz, idx, val, n, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && h < (unsigned long long)nnz) {
+    e = cudaMemcpyAsync(&c, idx + h, sizeof(c), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    *first = (int64_t)h;
+    *col_bad = (c < 0 || c >= n) ? 1 : 0;
+  }
+  const cudaError_t ef = cudaFreeAsync(d, s);
+  return e != cudaSuccess ? e : ef;
+}
+
+cudaError_t setup_permute(int32_t count, const int32_t *perm, const double *src, double *dst, cudaStream_t s) {
+  if (count > 0) k_permute<<<grid_for(count), ST, 0, s>>>(count, perm, src, dst);
+  return cudaGetLastError();
+}
+
 }  // namespace pdlp
 
 // ---------------------------------------------------------------------------

@@ -58,4 +58,25 @@ size_t scalars_work_doubles();
 cudaError_t setup_warm(int32_t m, int32_t n, const double *x0, const double *y0, const double *D1,
                        const double *D2, double *x, double *y, cudaStream_t s);
 
+// Sliced-ELL copy of a CSR matrix (layout from sell_layout, pdlp_sell.h):
+// inv[perm[r]] = r; then every stored entry is set to column -1 / value 0
+// and internal row r's entries (original row perm[r], columns renumbered
+// through inv) are written from base[r], 32 apart when lane[r] is 1.
+cudaError_t setup_invert(int32_t rows, const int32_t *perm, int32_t *inv, cudaStream_t s);
+cudaError_t setup_sell_fill(int32_t rows, int64_t total, const int32_t *perm, const int32_t *base,
+                            const uint8_t *lane, const int32_t *ptr, const int32_t *idx, const double *val,
+                            const int32_t *inv, int32_t *sidx, double *sval, cudaStream_t s);
+// Entries of a CSR matrix on the device: *first = the first nonzero whose
+// column lies outside [0, n) or whose value is not finite (nnz if none),
+// *col_bad = 1 when that entry's column is the fault; waits for the result.
+cudaError_t setup_check_entries(int64_t nnz, const int32_t *idx, const double *val, int32_t n, int64_t *first,
+                                int *col_bad, cudaStream_t s);
+// dst[r] = src[perm[r]] for r < count (original order -> internal order)
+cudaError_t setup_permute(int32_t count, const int32_t *perm, const double *src, double *dst, cudaStream_t s);
+// Warm start in the internal order: x[j] = x0[perm_c[j]] / D2[j] (0 without
+// x0), y[i] = y0[perm_r[i]] / D1[i], with D1, D2 in the internal order.
+cudaError_t setup_warm_perm(int32_t m, int32_t n, const double *x0, const double *y0, const int32_t *perm_r,
+                            const int32_t *perm_c, const double *D1, const double *D2, double *x, double *y,
+                            cudaStream_t s);
+
 }  // namespace pdlp
