@@ -41,6 +41,7 @@ __all__ = [
     "large_lp",
     "random_boxed_lp",
     "batch_lps",
+    "batch_lp",
     "infeasible_lp",
 ]
 
@@ -405,23 +406,39 @@ def infeasible_lp(seed: int, kind: str, m_eq: int = 30, m_ineq: int = 30, n: int
               meta=dict(kind="infeasible-dual", seed=seed, ray_x=ray_x, ray_y=None))
 
 
+def _batch_shapes(count: int, seed: int, m_lo: int, m_hi: int, dens_lo: float, dens_hi: float):
+    rng = np.random.default_rng([0xBA7C, seed])
+    for _ in range(count):
+        m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
+        n = int(round(math.exp(rng.uniform(math.log(2 * m / 3), math.log(2.5 * m)))))
+        d = float(rng.uniform(dens_lo, dens_hi))
+        yield m, n, d
+
+
+def _batch_member(i: int, seed: int, m: int, n: int, d: float) -> LP:
+    n_eq = m // 2
+    sub = np.random.default_rng([0xBA7C, seed, i])
+    row_ptr, cols = uniform_pattern(sub, m, n, d, cover=True)
+    val = sub.standard_normal(cols.size)
+    return plant(sub, m, n, n_eq, row_ptr, cols, val, np.zeros(n), np.full(n, 10.0),
+                 meta=dict(kind="batch", seed=seed, index=i, density=d))
+
+
 def batch_lps(count: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,
               dens_lo: float = 0.005, dens_hi: float = 0.05) -> list[LP]:
     """Uneven batch: m ~ logU[m_lo, m_hi], n ~ logU[2m/3, 2.5m], density ~
     U[dens_lo, dens_hi], N(0,1) values, half equality rows, 0 <= x <= 10."""
-    rng = np.random.default_rng([0xBA7C, seed])
-    out = []
-    for i in range(count):
-        m = int(round(math.exp(rng.uniform(math.log(m_lo), math.log(m_hi)))))
-        n = int(round(math.exp(rng.uniform(math.log(2 * m / 3), math.log(2.5 * m)))))
-        d = float(rng.uniform(dens_lo, dens_hi))
-        n_eq = m // 2
-        sub = np.random.default_rng([0xBA7C, seed, i])
-        row_ptr, cols = uniform_pattern(sub, m, n, d, cover=True)
-        val = sub.standard_normal(cols.size)
-        out.append(plant(sub, m, n, n_eq, row_ptr, cols, val, np.zeros(n), np.full(n, 10.0),
-                         meta=dict(kind="batch", seed=seed, index=i, density=d)))
-    return out
+    return [_batch_member(i, seed, m, n, d)
+            for i, (m, n, d) in enumerate(_batch_shapes(count, seed, m_lo, m_hi, dens_lo, dens_hi))]
+
+
+def batch_lp(index: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,
+             dens_lo: float = 0.005, dens_hi: float = 0.05) -> LP:
+    """Member `index` of batch_lps(count > index, seed, ...), built alone."""
+    for i, (m, n, d) in enumerate(_batch_shapes(index + 1, seed, m_lo, m_hi, dens_lo, dens_hi)):
+        if i == index:
+            return _batch_member(i, seed, m, n, d)
+    raise IndexError(index)
 
 
 # ----------------------------------------------------------------------------

@@ -68,6 +68,8 @@ class _Params(C.Structure):
         ("beta_nec", C.c_double),
         ("beta_art", C.c_double),
         ("eps_infeas", C.c_double),
+        ("restart_metric", C.c_int32),
+        ("pad_", C.c_int32),
     ]
 
 
@@ -139,6 +141,8 @@ def lib():
         L.orc_restart_mask.restype = i32
         L.orc_pdhg_step.argtypes = [vp, vp, vp, d, d, vp, vp]
         L.orc_pdhg_step.restype = C.c_int
+        L.orc_normalized_gap.argtypes = [vp, vp, vp, d, d]
+        L.orc_normalized_gap.restype = d
         L.orc_kkt_standard.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, vp]
         L.orc_kkt_standard.restype = d
         L.orc_alg3.argtypes = [i32, i32, vp, vp, vp, vp, vp, d, d, i64, vp, vp, vp, vp, i32]
@@ -191,11 +195,12 @@ class Params:
     beta_nec: float = 0.8
     beta_art: float = 0.36
     eps_infeas: float = 1e-8
+    restart_metric: int = 0  # 0: KKT error (Sec. 3.4); 1: normalized duality gap (ablation only)
 
     def struct(self):
         return _Params(self.tol, self.max_iter, self.check_period, self.ruiz_iters, self.pc_alpha,
                        self.theta, self.eps_zero, self.beta_suff, self.beta_nec, self.beta_art,
-                       self.eps_infeas)
+                       self.eps_infeas, self.restart_metric, 0)
 
 
 @dataclass
@@ -256,6 +261,18 @@ def precondition(lp, ruiz_iters: int = 10, pc_alpha: float = 1.0):
         ci = np.zeros(1, dtype=np.int32)
     lib().orc_precondition(lp.m, lp.n, _p(rp), _p(ci), _p(sv), ruiz_iters, pc_alpha, _p(D1), _p(D2))
     return sv[: lp.nnz], D1[: lp.m], D2[: lp.n]
+
+
+def normalized_gap(lp, x, y, omega, r):
+    """rho_r(z): the normalized duality gap of (x, y) on `lp` as given (no
+    scaling) over the omega-norm ball of radius r cut by X x Y (restart-metric
+    ablation; see normalized_gap in pdlp_oracle.c)."""
+    h = _holder(lp)
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    ya = np.ascontiguousarray(y, dtype=np.float64)
+    xa = xa if xa.size else np.zeros(1)
+    ya = ya if ya.size else np.zeros(1)
+    return lib().orc_normalized_gap(h.ref, _p(xa), _p(ya), float(omega), float(r))
 
 
 def kkt_terms(lp, x, y):

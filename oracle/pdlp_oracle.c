@@ -23,6 +23,10 @@
  *     Sec. 2.2, relative-KKT termination on the ORIGINAL LP (Sec. 4.1).
  *   Restarted PDHG for standard-form LP with fixed step and uniform average
  *     (Algorithm 3, Appendix A) as a separate test-only routine.
+ *   Restart-metric ablation (orc_params.restart_metric = 1, not the paper's
+ *     method): the same restart scheme driven by the normalized duality gap
+ *     of the CPU PDLP restart scheme the paper replaces (normalized_gap),
+ *     with the readings listed there.
  *
  * Readings where the paper is silent or garbled (each also used by the CUDA
  * path, which implements them independently):
@@ -106,6 +110,9 @@ typedef struct {
   double eps_zero;
   double beta_suff, beta_nec, beta_art;
   double eps_infeas; /* relative tolerance of the infeasibility certificates; 0 = off */
+  int32_t restart_metric; /* 0: KKT error, eq. (kkt) (Sec. 3.4); 1: normalized duality gap
+                             (the restart metric of CPU PDLP the paper compares against) */
+  int32_t pad_;
 } orc_params;
 
 typedef struct {
@@ -466,6 +473,106 @@ int orc_pdhg_step(const orc_lp *lp, const double *x, const double *y, double tau
 }
 
 /* ------------------------------------------------------------------------ */
+/* normalized duality gap (restart-metric ablation, not the paper's metric)  */
+/* ------------------------------------------------------------------------ */
+
+/* Normalized duality gap of z = (x, y) on the scaled LP with radius r in the
+ * primal-weight norm ||(dx, dy)||_omega^2 = omega ||dx||^2 + ||dy||^2 / omega:
+ *   rho_r(z) = (1/r) max { L(x, y^) - L(x^, y) : z^ in X x Y, ||z^ - z||_omega <= r },
+ * the restart metric of the CPU PDLP restart scheme that Sec. 3.4 replaces
+ * by the KKT error (Sec. 2.2 "Adaptive restarts"; Appendix A).  With
+ * L(x, y) = c'x - y'Kx + q'y the objective is linear in d = z^ - z:
+ *   L(x, y^) - L(x^, y) = -(c - K'y)'dx + (q - Kx)'dy   (zero at d = 0).
+ * In e = (sqrt(omega) dx, dy / sqrt(omega)) the ball is ||e|| <= r, the
+ * objective is h'e with h = (-(c - K'y) / sqrt(omega), sqrt(omega)(q - Kx)),
+ * and X x Y becomes a box B around 0 (lower bound -y / sqrt(omega) on ">="
+ * rows).  A linear function over a ball cut by a box is maximised by
+ * e(t) = proj_B(t h) with t >= 0 the largest at which ||e(t)|| <= r
+ * (||e(t)|| does not decrease in t); t is found by bisection.  r = 0 or
+ * h = 0 gives 0.  Kx = K x, KTy = K' y. */
+static double box_step(double t, double h, double lo, double hi) {
+  double v = t * h;
+  if (v < lo) v = lo;
+  if (v > hi) v = hi;
+  return v;
+}
+
+/* ||e(t)||^2 and h'e(t) at the multiplier t (one pass over the coordinates). */
+static void gap_eval(double t, int32_t m, int32_t n, int32_t n_eq, const double *c, const double *q,
+                     const double *l, const double *u, const double *x, const double *y, const double *Kx,
+                     const double *KTy, double so, double *norm2, double *value) {
+  double n2 = 0.0, v = 0.0;
+  for (int32_t j = 0; j < n; ++j) {
+    const double h = -(c[j] - KTy[j]) / so;
+    const double e = box_step(t, h, so * (l[j] - x[j]), so * (u[j] - x[j]));
+    n2 += e * e;
+    v += h * e;
+  }
+  for (int32_t i = 0; i < m; ++i) {
+    const double h = so * (q[i] - Kx[i]);
+    const double e = box_step(t, h, i >= n_eq ? -y[i] / so : -INFINITY, INFINITY);
+    n2 += e * e;
+    v += h * e;
+  }
+  *norm2 = n2;
+  *value = v;
+}
+
+static double normalized_gap(int32_t m, int32_t n, int32_t n_eq, const double *c, const double *q,
+                             const double *l, const double *u, const double *x, const double *y,
+                             const double *Kx, const double *KTy, double omega, double r) {
+  if (!(r > 0.0)) return 0.0;
+  const double so = sqrt(omega);
+  double n2, val, prev = -1.0, hi = 1.0;
+  gap_eval(hi, m, n, n_eq, c, q, l, u, x, y, Kx, KTy, so, &n2, &val);
+  /* grow t until the ball binds, or until the box alone bounds e */
+  while (n2 < r * r) {
+    if (n2 == prev || !(hi < 1e300)) return val / r; /* every coordinate at its bound */
+    prev = n2;
+    hi *= 2.0;
+    gap_eval(hi, m, n, n_eq, c, q, l, u, x, y, Kx, KTy, so, &n2, &val);
+  }
+  double lo = 0.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    gap_eval(mid, m, n, n_eq, c, q, l, u, x, y, Kx, KTy, so, &n2, &val);
+    if (n2 <= r * r)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  gap_eval(lo, m, n, n_eq, c, q, l, u, x, y, Kx, KTy, so, &n2, &val);
+  return val / r;
+}
+
+/* rho_r(z) for the tests, on the LP as given (no scaling). */
+double orc_normalized_gap(const orc_lp *lp, const double *x, const double *y, double omega, double r) {
+  double *Kx = (double *)calloc((size_t)lp->m + 1, sizeof(double));
+  double *KTy = (double *)calloc((size_t)lp->n + 1, sizeof(double));
+  if (!Kx || !KTy) {
+    free(Kx);
+    free(KTy);
+    return NAN;
+  }
+  spmv(lp->m, lp->row_ptr, lp->col_idx, lp->val, x, Kx);
+  for (int32_t i = 0; i < lp->m; ++i)
+    for (int32_t e = lp->row_ptr[i]; e < lp->row_ptr[i + 1]; ++e) KTy[lp->col_idx[e]] += lp->val[e] * y[i];
+  const double g = normalized_gap(lp->m, lp->n, lp->n_eq, lp->c, lp->q, lp->l, lp->u, x, y, Kx, KTy, omega, r);
+  free(Kx);
+  free(KTy);
+  return g;
+}
+
+/* ||(x - xr, y - yr)||_omega */
+static double wdist(int32_t m, int32_t n, const double *x, const double *y, const double *xr, const double *yr,
+                    double omega) {
+  double a = 0.0, b = 0.0;
+  for (int32_t j = 0; j < n; ++j) a += (x[j] - xr[j]) * (x[j] - xr[j]);
+  for (int32_t i = 0; i < m; ++i) b += (y[i] - yr[i]) * (y[i] - yr[i]);
+  return sqrt(omega * a + b / omega);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Algorithm 1 + Algorithm 2 (restarted PDHG with adaptive steps)            */
 /* ------------------------------------------------------------------------ */
 
@@ -614,6 +721,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
   double terms[6] = {0, 0, 0, 0, 0, 0};
   double ray[2] = {0.0, 0.0};
   int32_t ntrace = 0;
+  int gap_start_pending = p->restart_metric == 1;
 
   while (status < 0) {
     /* ---- Algorithm 2: AdaptiveStepPDHG(z, omega, eta_hat, k) ---- */
@@ -719,6 +827,24 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     kkt_pieces(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.xb, w.yb, w.Kxb, w.KTyb, &rpa, &rda, &pa, &da);
     double kc = kkt_omega_from(rpc, rdc, pc, dc, omega);
     double ka = kkt_omega_from(rpa, rda, pa, da, omega);
+    if (p->restart_metric == 1) {
+      /* the normalized duality gap of each point over the ball reaching back
+       * to the epoch's restart point z^{n,0} (kept in x_last, y_last) */
+      const double rc = wdist(m, n, w.x, w.y, w.x_last, w.y_last, omega);
+      const double ra = wdist(m, n, w.xb, w.yb, w.x_last, w.y_last, omega);
+      kc = normalized_gap(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.x, w.y, w.Kx, w.KTy, omega, rc);
+      ka = normalized_gap(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.xb, w.yb, w.Kxb, w.KTyb, omega, ra);
+      if (restarts == 0 && gap_start_pending) {
+        /* z^{0,0} has no earlier restart point: its gap is taken over the
+         * first candidate's radius */
+        const double r0 = !(kc < ka) ? ra : rc;
+        spmv(m, rp, ci, w.sv, w.x_last, w.Kv);
+        spmv(n, w.tp, w.ti, w.tv, w.y_last, w.v);
+        kkt_start = normalized_gap(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.x_last, w.y_last, w.Kv, w.v, omega, r0);
+        kkt_prev = kkt_start;
+        gap_start_pending = 0;
+      }
+    }
     int cand_avg = !(kc < ka);
     double kcand = cand_avg ? ka : kc;
     int32_t mask = orc_restart_mask(kcand, kkt_start, kkt_prev, t, k, p->beta_suff, p->beta_nec, p->beta_art);
@@ -740,7 +866,10 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
       W = 0.0;
       t = 0;
       ++restarts;
-      if (cand_avg)
+      if (p->restart_metric == 1)
+        kkt_start = normalized_gap(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.x, w.y, w.Kx, w.KTy, omega,
+                                   sqrt(omega * ddx + ddy / omega));
+      else if (cand_avg)
         kkt_start = kkt_omega_from(rpa, rda, pa, da, omega);
       else
         kkt_start = kkt_omega_from(rpc, rdc, pc, dc, omega);

@@ -363,3 +363,25 @@ def test_iteration_limit_below_one_is_rejected():
     # the iteration limit counts accepted steps and must allow at least one
     with pytest.raises(ValueError):
         oracle.solve(lpgen.tiny_lp(0), tol=1e-6, max_iter=0)
+
+
+def test_oracle_stalls_on_batch_lp_2581_by_primal_weight_runaway():
+    """Member 2581 of the 4096-LP batch workload (147 x 120, planted, so
+    feasible and bounded) ends at the iteration limit in the batched GPU
+    solver; the oracle does the same.  After k ~ 1.5e3 every restart raises
+    the primal weight (Sec. 2.2 PrimalWeightUpdate: the dual iterate moves
+    far more than the primal one between restart points), omega passes 1e5,
+    the primal step eta / omega all but vanishes, and from k ~ 1.6e4 only
+    the artificial criterion (iii) restarts: a limit of the method as read
+    (unbounded omega), not of the GPU path."""
+    lp = lpgen.batch_lp(2581)
+    assert (lp.m, lp.n, lp.nnz) == (147, 120, 399)
+    r = oracle.solve(lp, tol=1e-6, max_iter=1_000_000, check_period=64)
+    assert r.status == oracle.ITER_LIMIT and r.iters == 1_000_000
+    restarts = r.trace[r.trace["restart"] != 0]
+    assert restarts["omega"][-1] > 1e5
+    late = restarts[restarts["k"] > 20000]
+    assert len(late) >= 3 and np.all(late["restart"] == 4)  # only criterion (iii)
+    assert np.all(np.diff(late["omega"]) > 0)
+    # still near the optimum: the objective is off by a few 1e-6 relative
+    assert abs(float(lp.c @ r.x) - lp.obj_star) < 1e-5 * abs(lp.obj_star)
