@@ -42,6 +42,7 @@ __all__ = [
     "random_boxed_lp",
     "batch_lps",
     "batch_lp",
+    "planted_qp",
     "infeasible_lp",
 ]
 
@@ -65,6 +66,7 @@ class LP:
     lam_star: np.ndarray | None = None
     obj_star: float | None = None
     meta: dict = field(default_factory=dict)
+    qdiag: np.ndarray | None = None  # QP extension: objective x'Qx/2 + c'x with Q = diag(qdiag)
 
     @property
     def nnz(self) -> int:
@@ -439,6 +441,22 @@ def batch_lp(index: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,
         if i == index:
             return _batch_member(i, seed, m, n, d)
     raise IndexError(index)
+
+
+def planted_qp(lp: LP, seed: int = 0, frac: float = 0.6, lo: float = 0.0, hi: float = 2.0) -> LP:
+    """The QP min x'Qx/2 + c'x over the planted LP's feasible set, Q =
+    diag(qdiag) with a fraction `frac` of its entries ~ U(lo, hi), the rest 0,
+    and c shifted by -Q x* so that the LP's planted pair (x*, y*, lambda*)
+    satisfies the QP's KKT system (stationarity c + Q x* - K'y* - lambda* = 0,
+    the same complementarity): x* is optimal with value x*'Qx*/2 + c'x*."""
+    rng = np.random.default_rng([0x0D1A, seed])
+    qd = np.where(rng.random(lp.n) < frac, rng.uniform(lo, hi, lp.n), 0.0)
+    c = lp.c - qd * lp.x_star
+    obj = float(0.5 * np.dot(qd * lp.x_star, lp.x_star) + np.dot(c, lp.x_star))
+    out = LP(m=lp.m, n=lp.n, n_eq=lp.n_eq, c=c, row_ptr=lp.row_ptr, col_idx=lp.col_idx, val=lp.val, q=lp.q,
+             l=lp.l, u=lp.u, x_star=lp.x_star, y_star=lp.y_star, lam_star=lp.lam_star, obj_star=obj,
+             meta=dict(lp.meta, qp=True, qp_seed=seed), qdiag=qd)
+    return out
 
 
 # ----------------------------------------------------------------------------

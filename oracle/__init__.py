@@ -52,6 +52,7 @@ class _LPStruct(C.Structure):
         ("q", C.c_void_p),
         ("l", C.c_void_p),
         ("u", C.c_void_p),
+        ("qd", C.c_void_p),
     ]
 
 
@@ -158,7 +159,7 @@ def _p(a):
 class _Holder:
     """Keeps the arrays behind an _LPStruct alive."""
 
-    def __init__(self, m, n, n_eq, c, row_ptr, col_idx, val, q, l, u):
+    def __init__(self, m, n, n_eq, c, row_ptr, col_idx, val, q, l, u, qd=None):
         self.arrs = [
             np.ascontiguousarray(row_ptr, dtype=np.int32),
             np.ascontiguousarray(col_idx, dtype=np.int32),
@@ -171,7 +172,10 @@ class _Holder:
         # keep zero-length arrays addressable
         self.arrs = [a if a.size else np.zeros(1, dtype=a.dtype) for a in self.arrs]
         rp, ci, v, cc, qq, ll, uu = self.arrs
-        self.s = _LPStruct(m, n, n_eq, 0, _p(rp), _p(ci), _p(v), _p(cc), _p(qq), _p(ll), _p(uu))
+        self.qd = None if qd is None else np.ascontiguousarray(qd, dtype=np.float64)
+        if self.qd is not None and self.qd.size == 0:
+            self.qd = np.zeros(1)
+        self.s = _LPStruct(m, n, n_eq, 0, _p(rp), _p(ci), _p(v), _p(cc), _p(qq), _p(ll), _p(uu), _p(self.qd))
 
     @property
     def ref(self):
@@ -179,7 +183,10 @@ class _Holder:
 
 
 def _holder(lp):
-    return _Holder(lp.m, lp.n, lp.n_eq, lp.c, lp.row_ptr, lp.col_idx, lp.val, lp.q, lp.l, lp.u)
+    """The LP (or, with a `qdiag` field that is not None, the QP with
+    objective x'Qx/2 + c'x, Q = diag(qdiag)) as the C structure."""
+    return _Holder(lp.m, lp.n, lp.n_eq, lp.c, lp.row_ptr, lp.col_idx, lp.val, lp.q, lp.l, lp.u,
+                   getattr(lp, "qdiag", None))
 
 
 @dataclass

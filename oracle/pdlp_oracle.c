@@ -23,6 +23,12 @@
  *     Sec. 2.2, relative-KKT termination on the ORIGINAL LP (Sec. 4.1).
  *   Restarted PDHG for standard-form LP with fixed step and uniform average
  *     (Algorithm 3, Appendix A) as a separate test-only routine.
+ *   QP extension (orc_lp.qd != NULL; the introduction names the extension
+ *     to quadratic programs): objective x'Qx/2 + c'x with Q diagonal; the
+ *     primal step is the exact proximal step x' = proj_X((x - tau(c - K'y)) /
+ *     (1 + tau Q)) (per coordinate), the KKT pieces use the objective's
+ *     gradient c + Qx and the QP's objectives (kkt_pieces), Q is scaled as
+ *     D2 Q D2, and infeasibility detection is off.
  *   Restart-metric ablation (orc_params.restart_metric = 1, not the paper's
  *     method): the same restart scheme driven by the normalized duality gap
  *     of the CPU PDLP restart scheme the paper replaces (normalized_gap),
@@ -98,6 +104,7 @@ typedef struct {
   const int32_t *col_idx;
   const double *val;
   const double *c, *q, *l, *u;
+  const double *qd; /* diagonal of Q for the QP extension (objective 1/2 x'Qx + c'x), NULL for an LP */
 } orc_lp;
 
 typedef struct {
@@ -248,9 +255,13 @@ int orc_precondition(int32_t m, int32_t n, const int32_t *rp, const int32_t *ci,
  * (x, y), given Kx = K x and KTy = K' y:
  *   rp2 = ||(Ax - b, [h - Gx]^+)||^2
  *   rd2 = ||c - K'y - lambda||^2
- *   pobj = c'x,  dobj = q'y + l'lambda^+ - u'lambda^-                        */
+ *   pobj = c'x,  dobj = q'y + l'lambda^+ - u'lambda^-
+ * With a diagonal Q (qd != NULL, the QP extension) the gradient of the
+ * objective replaces c: lambda = proj_Lambda(c + Qx - K'y),
+ * rd2 = ||c + Qx - K'y - lambda||^2, pobj = c'x + x'Qx / 2 and
+ * dobj = q'y + l'lambda^+ - u'lambda^- - x'Qx / 2 (the QP's dual objective). */
 static void kkt_pieces(int32_t m, int32_t n, int32_t n_eq, const double *c, const double *q,
-                       const double *l, const double *u, const double *x, const double *y,
+                       const double *l, const double *u, const double *qd, const double *x, const double *y,
                        const double *Kx, const double *KTy, double *rp2, double *rd2, double *pobj,
                        double *dobj) {
   double sp = 0.0;
@@ -259,19 +270,20 @@ static void kkt_pieces(int32_t m, int32_t n, int32_t n_eq, const double *c, cons
     if (i >= n_eq) r = r > 0.0 ? r : 0.0;
     sp += r * r;
   }
-  double sd = 0.0, lu = 0.0;
+  double sd = 0.0, lu = 0.0, xqx = 0.0;
   for (int32_t j = 0; j < n; ++j) {
-    double d = c[j] - KTy[j];
+    double d = qd ? c[j] + qd[j] * x[j] - KTy[j] : c[j] - KTy[j];
     double lam = proj_lambda(d, l[j], u[j]);
     double r = d - lam;
     sd += r * r;
     if (lam > 0.0) lu += l[j] * lam;
     if (lam < 0.0) lu -= u[j] * (-lam);
+    if (qd) xqx += qd[j] * x[j] * x[j];
   }
   *rp2 = sp;
   *rd2 = sd;
-  *pobj = dot(n, c, x);
-  *dobj = dot(m, q, y) + lu;
+  *pobj = dot(n, c, x) + 0.5 * xqx;
+  *dobj = dot(m, q, y) + lu - 0.5 * xqx;
 }
 
 /* eq. (kkt): KKT_omega from its pieces. */
@@ -296,7 +308,7 @@ int orc_kkt_terms(const orc_lp *lp, const double *x, const double *y, double *ou
   for (int32_t i = 0; i < m; ++i)
     for (int32_t e = lp->row_ptr[i]; e < lp->row_ptr[i + 1]; ++e) KTy[lp->col_idx[e]] += lp->val[e] * y[i];
   double rp2, rd2, pobj, dobj;
-  kkt_pieces(m, n, lp->n_eq, lp->c, lp->q, lp->l, lp->u, x, y, Kx, KTy, &rp2, &rd2, &pobj, &dobj);
+  kkt_pieces(m, n, lp->n_eq, lp->c, lp->q, lp->l, lp->u, lp->qd, x, y, Kx, KTy, &rp2, &rd2, &pobj, &dobj);
   out[0] = pobj;
   out[1] = dobj;
   out[2] = sqrt(rp2);
@@ -579,6 +591,7 @@ static double wdist(int32_t m, int32_t n, const double *x, const double *y, cons
 typedef struct {
   /* scaled problem */
   double *sv, *D1, *D2, *sc, *sq, *sl, *su;
+  double *sqd; /* QP: the scaled diagonal D2 Q D2 (NULL for an LP) */
   int32_t *tp, *ti;
   double *tv;
   int64_t *perm;
@@ -593,7 +606,7 @@ static void free_work(orc_work *w) {
   double **d[] = {&w->sv, &w->D1, &w->D2, &w->sc, &w->sq, &w->sl, &w->su, &w->tv,
                   &w->x, &w->y, &w->Kx, &w->KTy, &w->xp, &w->yp, &w->v, &w->Kv,
                   &w->dxv, &w->Kdx, &w->sum_x, &w->sum_y, &w->xb, &w->yb, &w->Kxb,
-                  &w->KTyb, &w->x_last, &w->y_last, &w->xo, &w->yo, &w->x_prev, &w->y_prev};
+                  &w->KTyb, &w->x_last, &w->y_last, &w->xo, &w->yo, &w->x_prev, &w->y_prev, &w->sqd};
   for (size_t i = 0; i < sizeof(d) / sizeof(d[0]); ++i) {
     free(*d[i]);
     *d[i] = NULL;
@@ -617,6 +630,9 @@ static int validate(const orc_lp *lp) {
       return ORC_ERR_INVALID;
   for (int32_t i = 0; i < lp->m; ++i)
     if (!isfinite(lp->q[i])) return ORC_ERR_INVALID;
+  if (lp->qd)
+    for (int32_t j = 0; j < lp->n; ++j)
+      if (!isfinite(lp->qd[j]) || lp->qd[j] < 0.0) return ORC_ERR_INVALID;
   return ORC_OK;
 }
 
@@ -693,6 +709,14 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     w.su[j] = lp->u[j] / w.D2[j];
   }
   for (int32_t i = 0; i < m; ++i) w.sq[i] = w.D1[i] * lp->q[i];
+  if (lp->qd) { /* QP: x = D2 x~ turns x'Qx into x~'(D2 Q D2)x~ */
+    w.sqd = (double *)calloc(N, sizeof(double));
+    if (!w.sqd) {
+      free_work(&w);
+      return ORC_ERR_NOMEM;
+    }
+    for (int32_t j = 0; j < n; ++j) w.sqd[j] = w.D2[j] * lp->qd[j] * w.D2[j];
+  }
   if (transpose_pattern(m, n, rp, ci, w.tp, w.ti, w.perm) != ORC_OK) {
     free_work(&w);
     return ORC_ERR_NOMEM;
@@ -712,7 +736,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
   memcpy(w.x_last, w.x, sizeof(double) * (size_t)n);
   memcpy(w.y_last, w.y, sizeof(double) * (size_t)m);
   double rp2, rd2, pobj, dobj;
-  kkt_pieces(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.x, w.y, w.Kx, w.KTy, &rp2, &rd2, &pobj, &dobj);
+  kkt_pieces(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.sqd, w.x, w.y, w.Kx, w.KTy, &rp2, &rd2, &pobj, &dobj);
   double kkt_start = kkt_omega_from(rp2, rd2, pobj, dobj, omega);
   double kkt_prev = kkt_start;
   double W = 0.0;
@@ -729,7 +753,11 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     for (;;) {
       ++attempts;
       double tau = eta / omega, sigma = eta * omega;
-      for (int32_t j = 0; j < n; ++j) w.xp[j] = clamp(w.x[j] - tau * (w.sc[j] - w.KTy[j]), w.sl[j], w.su[j]);
+      if (w.sqd) /* QP: the exact proximal step of x'Qx/2 + (c - K'y)'x over X (Q diagonal) */
+        for (int32_t j = 0; j < n; ++j)
+          w.xp[j] = clamp((w.x[j] - tau * (w.sc[j] - w.KTy[j])) / (1.0 + tau * w.sqd[j]), w.sl[j], w.su[j]);
+      else
+        for (int32_t j = 0; j < n; ++j) w.xp[j] = clamp(w.x[j] - tau * (w.sc[j] - w.KTy[j]), w.sl[j], w.su[j]);
       for (int32_t j = 0; j < n; ++j) w.v[j] = 2.0 * w.xp[j] - w.x[j];
       spmv(m, rp, ci, w.sv, w.v, w.Kv);
       for (int32_t i = 0; i < m; ++i) {
@@ -792,7 +820,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     }
     /* Sec. 2.2 infeasibility detection: difference ray, then normalised-
      * iterate ray, both unscaled to the original LP */
-    if (p->eps_infeas > 0.0) {
+    if (p->eps_infeas > 0.0 && !lp->qd) { /* LP only: the certificates below are the LP's */
       for (int seq = 0; seq < 2 && status < 0; ++seq) {
         const double *xr0 = seq == 0 ? w.x_prev : w.x_last, *yr0 = seq == 0 ? w.y_prev : w.y_last;
         for (int32_t j = 0; j < n; ++j) w.xo[j] = w.D2[j] * (w.x[j] - xr0[j]);
@@ -823,8 +851,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     }
     /* Sec. 3.4 GetRestartCandidate on the scaled LP */
     double rpc, rdc, pc, dc, rpa, rda, pa, da;
-    kkt_pieces(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.x, w.y, w.Kx, w.KTy, &rpc, &rdc, &pc, &dc);
-    kkt_pieces(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.xb, w.yb, w.Kxb, w.KTyb, &rpa, &rda, &pa, &da);
+    kkt_pieces(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.sqd, w.x, w.y, w.Kx, w.KTy, &rpc, &rdc, &pc, &dc);
+    kkt_pieces(m, n, n_eq, w.sc, w.sq, w.sl, w.su, w.sqd, w.xb, w.yb, w.Kxb, w.KTyb, &rpa, &rda, &pa, &da);
     double kc = kkt_omega_from(rpc, rdc, pc, dc, omega);
     double ka = kkt_omega_from(rpa, rda, pa, da, omega);
     if (p->restart_metric == 1) {

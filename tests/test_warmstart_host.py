@@ -65,3 +65,20 @@ def test_baselines_and_init():
     assert p.dtype == np.float32 and p.size == 4 * 8 + 8 + 8 * 8 + 8 + 8 * 3 + 3
     assert np.all(p[32:40] == 0) and np.abs(p[:32]).max() <= np.sqrt(6 / 4)
     assert np.array_equal(p, W.init_params(4, 8, 3, seed=0))
+
+
+def test_leave_one_out_neighbour_and_residual_inputs():
+    import numpy as np
+
+    from paper_2311_12180_gb300 import warmstart as W
+
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((300, 5))
+    nn = W.nearest_index(X, X, exclude_self=True, chunk=64)
+    d = ((X[:, None, :] - X[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d, np.inf)
+    assert np.array_equal(nn, d.argmin(1))
+    assert np.all(nn != np.arange(300))
+    assert np.array_equal(W.nearest_index(X, X[:7]), np.arange(7))  # itself when not excluded
+    R = W.residual_inputs(X[:3], X[nn[:3]])
+    assert R.shape == (3, 10) and np.allclose(R[:, 5:], X[nn[:3]] - X[:3], atol=1e-6)
