@@ -1,7 +1,7 @@
 """Benchmark: restarted-PDHG iterations per second on the GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large|tiny] [--ttt]
+                    [--workload large|tiny|batch|warmstart|sweep] [--no-ttt] [--lp-scale S]
 
 Workload (default): the planted-optimum LP with m = 1e6 rows (4e5
 equalities), n = 2e6 variables, nnz = 2e7 with Zipf(1.5) row lengths and
@@ -18,7 +18,13 @@ e2e    = the same metric through the C ABI with (page-locked) host buffers:
          number of iterations + device -> host copy of (x, y);
 roofline = the dominant kernel's algorithmic HBM bytes per launch over its
          CUDA-event-timed average duration, against the measured copy
-         bandwidth in MEASURED_PEAKS.json;
+         bandwidth in MEASURED_PEAKS.json; `roofs` adds, per step kernel, the
+         random-gather ceiling (one gather per nonzero) and the FP64-pipe
+         ceiling (FP64 instructions counted from the source), both measured
+         on the GPU by pdlp_probe_rates, and names the binding one;
+time_to_tol = after the timed region, a solve from zero to each --ttt-tols
+         tolerance (default 1e-4): seconds, iterations, objective error
+         against the planted optimum;
 cpu_baseline = the FP64 CPU oracle (single thread) on a bounded sample of
          the same LP.
 
@@ -170,13 +176,14 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(name: str, seed: int = 0):
+def make_workload(name: str, seed: int = 0, scale: float = 1.0):
     import lpgen
 
     if name == "large":
-        lp = lpgen.large_lp(seed)
-        desc = ("planted LP m=1e6 (4e5 eq) n=2e6 nnz=%d, Zipf(1.5) row lengths (max %d), lognormal(0,2) values, "
-                "bounds 50%% [0,inf) 30%% [l,u] 20%% free" % (lp.nnz, lp.meta["max_row"]))
+        m, n, nnz = int(round(1e6 * scale)), int(round(2e6 * scale)), int(round(2e7 * scale))
+        lp = lpgen.large_lp(seed, m=m, n=n, nnz=nnz)
+        desc = ("planted LP m=%d (40%% eq) n=%d nnz=%d, Zipf(1.5) row lengths (max %d), lognormal(0,2) values, "
+                "bounds 50%% [0,inf) 30%% [l,u] 20%% free" % (m, n, lp.nnz, lp.meta["max_row"]))
     elif name == "tiny":
         lp = lpgen.tiny_lp(seed)
         desc = "planted LP m=200 (100 eq) n=500 nnz=%d, 2%% density, N(0,1), 0<=x<=10" % lp.nnz
@@ -200,6 +207,24 @@ def algorithmic_bytes(lp, kernel: str, value_bytes: int = 8) -> float:
     if kernel == "k_primal_reuse_g":
         return 9 * 8.0 * n
     raise KeyError(kernel)
+
+
+def fp64_warp_instructions(layout: dict, kernel: str) -> float:
+    """FP64 warp instructions one launch issues, counted from the kernels'
+    source: one FMA per stored entry (a warp instruction covers 32 stored
+    entries), one epilogue per slice (k_dual 8 FP64 operations per row:
+    2 FMA + 1 subtraction for the extrapolated dual step, 1 FMA for the
+    running sum, 1 subtraction + 2 FMA + 1 subtraction for the two partial
+    sums; k_primal 5: 1 subtraction + 1 FMA for the step, 1 FMA for the
+    running sum, 1 subtraction + 1 FMA for ||x' - x||^2), and per 32 long
+    rows a 31-addition butterfly plus one epilogue."""
+    if kernel == "k_dual":
+        stored, slices, longs, epi = layout["K_stored"], layout["K_slices"], layout["K_long_rows"], 8
+    elif kernel == "k_primal":
+        stored, slices, longs, epi = layout["KT_stored"], layout["KT_slices"], layout["KT_long_rows"], 5
+    else:
+        raise KeyError(kernel)
+    return stored / 32.0 + epi * slices + (31 + epi) * ((longs + 31) // 32)
 
 
 def cpu_baseline(lp, budget_s: float = 20.0):
@@ -237,7 +262,7 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
-    lp, desc = make_workload(args.workload)
+    lp, desc = make_workload(args.workload, seed=args.seed, scale=args.lp_scale)
 
     def timed(k):
         t = time.perf_counter()
@@ -351,11 +376,12 @@ def run_batch(args, rank, world):
 
 def run_sweep(args, rank, world):
     """Size sweep: planted LPs of the large recipe (Zipf(1.5) row lengths,
-    lognormal(0,2) values, m = nnz/20, n = nnz/10) from 1e5 to 5e7 nonzeros;
+    lognormal(0,2) values, m = nnz/20, n = nnz/10) from 1e5 to 1e8 nonzeros;
     per size the device-timed PDHG iteration rate (as the large workload:
     warm-up periods, then timed check periods) and the FP64 oracle's rate on
     a bounded sample, and their ratio (the paper reports the GPU's advantage
-    growing with the LP's size)."""
+    growing with the LP's size), with the step kernels' event-timed durations
+    and their HBM roofline fraction per size."""
     if rank != 0:
         return
     import numpy as np
@@ -391,8 +417,15 @@ def run_sweep(args, rank, world):
                     break
                 periods = int(periods * max(2.0, 250.0 / max(ms, 1e-3)))
             gpu = (k1 - k0) / (ms / 1000.0)
+            kt = s.time_kernels(2)
+        peak, _ = measured_peaks()
+        t_p = kt["k_primal"][0] / max(kt["k_primal"][1], 1) / 1000.0
+        t_d = kt["k_dual"][0] / max(kt["k_dual"][1], 1) / 1000.0
+        pair_bytes = algorithmic_bytes(lp, "k_primal") + algorithmic_bytes(lp, "k_dual")
         cpu = None if args.no_cpu else cpu_baseline(lp, budget_s=args.sweep_cpu_s)
         rows.append({"nnz": lp.nnz, "m": lp.m, "n": lp.n, "gpu_iters_per_s": gpu, "periods_timed": periods,
+                     "k_primal_us": 1e6 * t_p, "k_dual_us": 1e6 * t_d,
+                     "hbm_frac_step_kernels": pair_bytes / (t_p + t_d) / (peak * 1e9),
                      "cpu_iters_per_s": cpu["value"] if cpu else None,
                      "gpu_over_cpu": gpu / cpu["value"] if cpu else None,
                      "cpu_sample": cpu["sample"] if cpu else None})
@@ -412,7 +445,9 @@ def run_warmstart(args, rank, world):
     solutions; the BF16 MLP theta -> (x, y) is trained by the library's
     kernels; the held-out thetas are then solved to tol from the cold start,
     from the MLP's prediction (with cold fallback), and from two naive starts
-    (mean training solution; solution of the nearest training theta)."""
+    (mean training solution; solution of the nearest training theta) and two
+    hybrids: a second MLP (theta, theta_nn - theta) -> T - T_nn that corrects
+    the nearest training solution, and the neighbour's x with the MLP's y."""
     if rank != 0:
         return
     import numpy as np
@@ -449,11 +484,21 @@ def run_warmstart(args, rank, world):
     t = time.perf_counter()
     net, losses = W.train(th_tr, T, hidden=256, schedule=sched, batch=256, seed=0)
     train_s = time.perf_counter() - t
+    # neighbour-residual model: (theta, theta_nn - theta) -> T - T_nn with the
+    # leave-one-out neighbour inside the training set
+    nn_tr = W.nearest_index(th_tr, th_tr, exclude_self=True)
+    t = time.perf_counter()
+    net_r, losses_r = W.train(W.residual_inputs(th_tr, th_tr[nn_tr]), T - T[nn_tr], hidden=256, schedule=sched,
+                              batch=256, seed=1)
+    train_r_s = time.perf_counter() - t
     flops_step = 6.0 * 256 * (16 * 256 + 256 * 256 + 256 * (n + m))
+    near = W.nearest_index(th_tr, th_te)
     t = time.perf_counter()
     Yp = net.predict(th_te).astype(np.float64)
     predict_s = time.perf_counter() - t
     net.close()
+    Yr = T[near].astype(np.float64) + net_r.predict(W.residual_inputs(th_te, th_tr[near])).astype(np.float64)
+    net_r.close()
 
     Tc = np.empty((args.ws_test, n + m))
 
@@ -466,10 +511,13 @@ def run_warmstart(args, rank, world):
     arms["cold"] = {"solve_s": cold_s, "optimal": int(np.sum(st_c == 0)), "iters_median": float(np.median(it_c)),
                     "iters_mean": float(np.mean(it_c))}
     mx, my = W.mean_start(T, n)
-    near = W.nearest_index(th_tr, th_te)
+    Ymix = np.concatenate([T[near][:, :n].astype(np.float64), Yp[:, n:]], axis=1)
     starts = {"mlp": lambda i: (Yp[i, :n], Yp[i, n:]), "mean": lambda i: (mx, my),
-              "nearest": lambda i: (T[near[i], :n], T[near[i], n:])}
-    preds = {"mlp": Yp, "mean": np.tile(np.concatenate([mx, my]), (args.ws_test, 1)), "nearest": T[near]}
+              "nearest": lambda i: (T[near[i], :n], T[near[i], n:]),
+              "mlp_nn_residual": lambda i: (Yr[i, :n], Yr[i, n:]),
+              "nearest_x_mlp_y": lambda i: (Ymix[i, :n], Ymix[i, n:])}
+    preds = {"mlp": Yp, "mean": np.tile(np.concatenate([mx, my]), (args.ws_test, 1)), "nearest": T[near],
+             "mlp_nn_residual": Yr, "nearest_x_mlp_y": Ymix}
     for name, fn in starts.items():
         r = W.solve_with_fallback(mk_te, args.ws_test, tol, fn)
         P_ = preds[name]
@@ -491,7 +539,10 @@ def run_warmstart(args, rank, world):
             "data_generation_s": data_s, "data_solve_s": data_solve_s, "data_optimal": int(np.sum(st == 0)),
             "data_iters_median": float(np.median(it)), "train_s": train_s,
             "train_tflops": flops_step * steps / train_s / 1e12,
-            "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean()), "arms": arms}
+            "loss_first": float(losses[:10].mean()), "loss_last": float(losses[-50:].mean()),
+            "residual_model": {"train_s": train_r_s, "loss_first": float(losses_r[:10].mean()),
+                               "loss_last": float(losses_r[-50:].mean())},
+            "arms": arms}
     print(json.dumps(line), flush=True)
 
 
@@ -502,7 +553,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=["large", "tiny", "batch", "warmstart", "sweep"])
-    ap.add_argument("--sweep-nnz", default="1e5,1e6,1e7,5e7", help="comma-separated nonzero counts (sweep)")
+    ap.add_argument("--sweep-nnz", default="1e5,1e6,1e7,5e7,1e8", help="comma-separated nonzero counts (sweep)")
     ap.add_argument("--sweep-cpu-s", type=float, default=5.0, help="oracle sample budget per size (sweep)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-tol", type=float, default=1e-6)
@@ -516,10 +567,13 @@ def main():
     ap.add_argument("--ws-test", type=int, default=1000)
     ap.add_argument("--ws-steps", type=int, default=4000)
     ap.add_argument("--ws-tol", type=float, default=1e-6)
-    ap.add_argument("--ws-data-tol", type=float, default=1e-4)
-    ap.add_argument("--ttt", action="store_true", help="also time full solves to 1e-4 and 1e-8 KKT")
-    ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per --ttt solve (s)")
-    ap.add_argument("--ttt-tols", default="1e-4,1e-8", help="comma-separated tolerances for --ttt")
+    ap.add_argument("--ws-data-tol", type=float, default=1e-6)
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves after the timed region")
+    ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per time-to-tolerance solve (s)")
+    ap.add_argument("--ttt-tols", default="1e-4", help="comma-separated tolerances of the time-to-tolerance solves")
+    ap.add_argument("--seed", type=int, default=0, help="generator seed of the large / tiny workload")
+    ap.add_argument("--lp-scale", type=float, default=1.0,
+                    help="large workload: m, n and nnz scaled by this factor (1 = the 1e6 x 2e6 LP)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--value-bits", type=int, default=64, choices=[64, 32],
                     help="32: step kernels read an FP32 copy of K (FP64 gathers, accumulation, iterates)")
@@ -557,7 +611,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
 
-    lp, desc = make_workload(args.workload)
+    lp, desc = make_workload(args.workload, seed=args.seed, scale=args.lp_scale)
     stream = torch.cuda.Stream()
     solver = P.Solver(lp, stream=stream.cuda_stream, value_bits=args.value_bits)
     period = P.pdlp_default_params().check_period
@@ -600,7 +654,27 @@ def main():
     dom_bytes = algorithmic_bytes(lp, dom, vb)
     achieved = dom_bytes / (dom_ms / 1000.0) / 1e9
     sha = kernel_source_sha()
-    tr = NCU_TRAFFIC.get((dom, sha, args.value_bits)) if args.workload == "large" else None
+    tr = NCU_TRAFFIC.get((dom, sha, args.value_bits)) if args.workload == "large" and args.lp_scale == 1.0 else None
+    # the on-chip ceilings next to HBM: random gathers (one per nonzero) and
+    # the FP64 pipe (FP64 instructions counted from the kernels' source)
+    g_rate, f_rate = P.probe_rates()
+    lay = solver.layout()
+    roofs = {}
+    for k in ("k_primal", "k_dual"):
+        if k not in cands:
+            continue
+        t_k = cands[k][0] / cands[k][1] / 1000.0
+        wi = fp64_warp_instructions(lay, k)
+        roofs[k] = {
+            "seconds": t_k,
+            "hbm": {"floor_s": algorithmic_bytes(lp, k, vb) / (peak * 1e9),
+                    "frac": algorithmic_bytes(lp, k, vb) / t_k / (peak * 1e9)},
+            "gather": {"per_launch": lp.nnz, "peak_per_s": g_rate, "floor_s": lp.nnz / g_rate,
+                       "frac": lp.nnz / t_k / g_rate},
+            "fp64": {"warp_instructions": wi, "lane_ops": 32 * wi, "peak_lane_ops_per_s": f_rate,
+                     "floor_s": 32 * wi / f_rate, "frac": 32 * wi / t_k / f_rate},
+        }
+        roofs[k]["binding"] = max(("hbm", "gather", "fp64"), key=lambda r: roofs[k][r]["frac"])
     solver.finish()
     info = solver.info()
 
@@ -616,13 +690,13 @@ def main():
     e2e_setup_ms = s2.info()["setup_ms"]
     s2.close()
     # in: K (row starts, columns, values), c, l, u, q (K' is built on the device);
-    # out: K''s row starts (read back at create for its tile schedule), x, y
+    # out: K''s row starts (read back at create for its sliced-ELL layout), x, y
     h2d = (4 * (lp.m + 1) + 12 * lp.nnz + 8 * 3 * lp.n + 8 * lp.m)
     d2h = 4 * (lp.n + 1) + 4 + 8 * (lp.n + lp.m)
     e2e_val = it2 / e2e_s * world
 
     ttt = None
-    if args.ttt:
+    if not args.no_ttt:
         ttt = {}
         with P.Solver(lp, time_limit_s=args.ttt_limit, value_bits=args.value_bits) as s3:
             for tol in [float(v) for v in args.ttt_tols.split(",")]:
@@ -631,7 +705,7 @@ def main():
                 stt, itt = _[2], _[3]
                 x_t, y_t = _[0], _[1]
                 ttt["%g" % tol] = {"seconds": time.perf_counter() - t, "status": P.STATUS_NAMES.get(stt, stt),
-                                   "iters": itt, "setup_excluded": True,
+                                   "iters": itt, "setup_excluded": True, "objective": float(np.dot(lp.c, x_t)),
                                    "obj_rel_err_vs_planted": abs(float(np.dot(lp.c, x_t)) - lp.obj_star)
                                    / abs(lp.obj_star)}
                 inf = s3.info()
@@ -672,7 +746,11 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": tr, "traffic_unit": "bytes per launch (ncu)",
                      "algorithmic_bytes_per_launch": dom_bytes, "avg_launch_ms": dom_ms,
-                     "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in times.items()}},
+                     "kernel_ms": {k: (v[0] / v[1] if v[1] else None) for k, v in times.items()},
+                     "roofs": roofs, "binding": roofs[dom]["binding"],
+                     "binding_frac": roofs[dom][roofs[dom]["binding"]]["frac"],
+                     "roofs_note": "gather and FP64 peaks measured on this GPU by pdlp_probe_rates (random "
+                                   "8-byte gathers of a 16 MB vector; FP64 FMA lane operations)"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "iters": it2, "seconds": e2e_s, "create_ms": e2e_setup_ms, "note": "one step = create + solve(%d iterations) + outputs" % it2},

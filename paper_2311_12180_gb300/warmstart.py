@@ -108,9 +108,25 @@ def mean_start(T, n):
     return mu[:n], mu[n:]
 
 
-def nearest_index(train_X, X):
-    """Index of the nearest training parameter for each row of X."""
+def nearest_index(train_X, X, exclude_self: bool = False, chunk: int = 2048):
+    """Index of the nearest training parameter for each row of X (with
+    exclude_self, X is the training set itself and each row's own index is
+    skipped: the leave-one-out neighbour)."""
     A = np.asarray(train_X, dtype=np.float64)
     B = np.asarray(X, dtype=np.float64)
-    d = (B * B).sum(1)[:, None] - 2 * B @ A.T + (A * A).sum(1)[None, :]
-    return np.argmin(d, axis=1)
+    a2 = (A * A).sum(1)
+    out = np.empty(B.shape[0], dtype=np.int64)
+    for c0 in range(0, B.shape[0], chunk):
+        Bc = B[c0:c0 + chunk]
+        d = (Bc * Bc).sum(1)[:, None] - 2 * Bc @ A.T + a2[None, :]
+        if exclude_self:
+            d[np.arange(Bc.shape[0]), np.arange(c0, c0 + Bc.shape[0])] = np.inf
+        out[c0:c0 + chunk] = np.argmin(d, axis=1)
+    return out
+
+
+def residual_inputs(theta, theta_nn):
+    """Inputs of the neighbour-residual model: the parameter and its offset
+    from the neighbour whose solution the prediction corrects."""
+    theta = np.asarray(theta, dtype=np.float32)
+    return np.concatenate([theta, np.asarray(theta_nn, dtype=np.float32) - theta], axis=1)
