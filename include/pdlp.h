@@ -158,6 +158,25 @@ int pdlp_create_ex(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const 
 int pdlp_solve(pdlp_solver *s, double tol, int64_t max_iter, double *x_out, double *y_out, int *status,
                int64_t *iters);
 
+/* pdlp_create_ex for an LP whose arrays are already in DEVICE memory (the
+ * same layout and meaning as pdlp_create's host arrays: c, l, u of n; q of m;
+ * CSR row_ptr m+1, col_idx / val nnz; all on the current device).  The
+ * caller keeps ownership; the solver copies what it needs into its own
+ * memory, so the arrays may be freed or reused once the call returns.  The
+ * row starts and the n- and m-vectors are read back to the host (the layout
+ * of K and the input checks need them); the nonzeros are checked and copied
+ * on the device and never cross to the host, except for an LP with a column
+ * of more than 4096 nonzeros, whose K' is then built on the host.  Work is
+ * ordered on `stream` (cudaStream_t as void*, NULL = a new stream), which
+ * becomes the solver's stream as in pdlp_create_ex.  The solver is the one
+ * pdlp_create_ex builds from the same values: every later result is bitwise
+ * the same.  Errors: PDLP_ERR_INVALID for the input faults pdlp_create
+ * rejects (found on the host or by the device check, before any solver
+ * memory is allocated), PDLP_ERR_CUDA / PDLP_ERR_OOM as pdlp_create_ex. */
+int pdlp_create_device(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c,
+                       const int32_t *row_ptr, const int32_t *col_idx, const double *val, const double *q,
+                       const double *l, const double *u, const pdlp_params *params, void *stream);
+
 /* As pdlp_solve but starting from (x0, y0) given in the ORIGINAL space
  * (host arrays of n and m; either may be NULL = zeros).  The point is used as
  * given (the first PDHG step projects it). */
@@ -177,6 +196,33 @@ int pdlp_run_periods(pdlp_solver *s, int32_t n_periods);
 int pdlp_poll(pdlp_solver *s, int *status, int64_t *iters);
 int pdlp_finish(pdlp_solver *s, double *x_out, double *y_out, int *status, int64_t *iters);
 
+/* Checkpoint and resume of a solve: the state of Algorithm 1 (the iterate
+ * z^{n,t}, the epoch's step-weighted sums behind the average z-bar^{n,t},
+ * the restart point z^{n,0}, the step size eta-hat, the primal weight
+ * omega^n, the counters k, t, n, the KKT references of the Sec. 3.4
+ * criteria, the restart candidate) together with the cached products K x and
+ * K'y the steps reuse and the infeasibility-detection references (Sec. 2.2).
+ * The vectors are the scaled-space values in the ORIGINAL order of rows and
+ * columns (stored exactly, nothing is rounded).
+ *   pdlp_get_state: with buf = NULL, writes the blob's size to *bytes;
+ *   otherwise copies the state into buf (cap bytes available) once the
+ *   solver's stream is idle.  Take it between check periods: after
+ *   pdlp_begin, pdlp_run_periods + pdlp_poll, or a finished solve.
+ *   pdlp_set_state: loads a blob from pdlp_get_state of a solver built from
+ *   the same LP with the same parameters (possibly another solver object,
+ *   in another process, on a GPU with the same number of SMs), replacing
+ *   the current state; the check trace is not part of the state.
+ *   pdlp_resume: continues the loaded (or begun) solve like pdlp_solve,
+ *   to the tolerance, iteration limit and time limit of the original solve
+ *   (the time limit counts from pdlp_set_state).
+ * Solving N + M steps equals solving N, moving the state, and resuming, bit
+ * for bit.  Errors: PDLP_ERR_INVALID for a too-small buffer, a blob of
+ * another size, library version, LP or parameter set, or one not taken
+ * between check periods; PDLP_ERR_CUDA for CUDA failures. */
+int pdlp_get_state(const pdlp_solver *s, void *buf, size_t cap, size_t *bytes);
+int pdlp_set_state(pdlp_solver *s, const void *buf, size_t bytes);
+int pdlp_resume(pdlp_solver *s, double *x_out, double *y_out, int *status, int64_t *iters);
+
 /* Enqueues n_periods periods like pdlp_run_periods but launches each kernel
  * directly (no graph) between CUDA events on the solver's stream, then waits
  * and adds each kernel class's event-measured device time to ms[i] and its
@@ -195,6 +241,28 @@ int pdlp_get_trace(const pdlp_solver *s, pdlp_check *trace, int32_t cap, int32_t
  * values of K~ = D1 K D2 in the input's CSR order (nnz).  Any pointer may be
  * NULL. */
 int pdlp_get_scaling(const pdlp_solver *s, double *D1, double *D2, double *val_scaled);
+
+/* Shapes of the sliced-ELL copies of K and K' the step and check kernels
+ * read (pdlp_get_layout).  Rows are renumbered by length inside their group
+ * (equality rows of K first); rows of at most long_threshold entries sit in
+ * slices of 32 rows padded to the slice's longest row, longer rows are stored
+ * whole, padded to a multiple of 32 entries.  Every stored entry costs one
+ * FMA per SpMV, each slice one epilogue per SpMV. */
+typedef struct {
+  int64_t K_stored, K_slices, K_long_rows;    /* stored entries (padding included), slices, long rows */
+  int64_t KT_stored, KT_slices, KT_long_rows; /* the same for K' */
+  int32_t long_threshold, pad_;
+} pdlp_layout_info;
+int pdlp_get_layout(const pdlp_solver *s, pdlp_layout_info *info);
+
+/* Measures this GPU's rate of random 8-byte gathers from a 16 MB vector
+ * (2e7 gathers with coalesced 32-bit indices, 8 in flight per thread) and
+ * of FP64 fused multiply-adds (lane operations per second), with CUDA
+ * events on a private stream: the ceilings of the two on-chip resources an
+ * SpMV half-step uses besides HBM (one gather and one FMA per nonzero).  Not
+ * part of the method; allocates ~100 MB for the duration of the call.
+ * Errors: PDLP_ERR_INVALID for null arguments, PDLP_ERR_CUDA. */
+int pdlp_probe_rates(double *gathers_per_s, double *dfma_per_s);
 
 /* The CUDA stream (cudaStream_t as void*) all work of `s` is ordered on. */
 void *pdlp_get_stream(const pdlp_solver *s);
@@ -235,8 +303,11 @@ typedef struct {
   double setup_ms;         /* create: validation, transposes, copies, batched scaling */
   double tune_ms;          /* create: schedule autotuning */
   double solve_ms;         /* last pdlp_batch_solve call, wall time */
-  double entries_per_lane; /* autotuned SpMV schedule: lanes per row = smallest power of two g <= 32
-                              with (mean row length) / g <= entries_per_lane */
+  double entries_per_lane; /* the SpMV schedule most LPs were given by the per-LP autotuner: lanes
+                              per row = smallest power of two g <= 32 with (mean row length) / g <=
+                              entries_per_lane, from {4, 8, 16}; each LP's own choice is in
+                              pdlp_batch_lanes.  Row sums have one order for every choice, so the
+                              results do not depend on it */
   size_t device_bytes;
   int32_t resident;        /* LPs small enough to be solved from the CTA's shared memory */
   int32_t resident_max_bytes; /* shared-memory budget per CTA for such an LP */
@@ -272,7 +343,10 @@ int pdlp_batch_info(const pdlp_batch *b, pdlp_batch_stats *stats);
  * global timer), in seconds after the earliest start (count entries each;
  * NULL ok): the schedule behind the batch's makespan. */
 int pdlp_batch_times(const pdlp_batch *b, double *start_s, double *end_s);
-/* Lanes per row chosen for each LP's K and K' (count entries each; NULL ok). */
+/* Lanes per row chosen for each LP's K and K' (count entries each; NULL ok):
+ * 32 is a warp per row, smaller values put 32 / g rows on a warp.  The
+ * autotuner at create times each candidate schedule on the whole batch and
+ * keeps, per LP, the fastest; it changes speed, not results. */
 int pdlp_batch_lanes(const pdlp_batch *b, int32_t *lanes_K, int32_t *lanes_KT);
 void pdlp_batch_destroy(pdlp_batch *b);
 

@@ -10,9 +10,11 @@
 // size, primal weight, restart, termination and infeasibility state in
 // registers (identical in every thread: all of them read the same
 // block-reduced sums).  Its SpMVs
-// map G lanes to a row (G a power of two <= 32, chosen per instance from its
-// mean row length by the autotuned rule in pdlp_batch_create), with a fixed
-// lane order and fixed shuffle trees, so a solve is deterministic.
+// map G lanes to a row (G a power of two <= 32: autotuned per instance in
+// pdlp_batch_create for the LPs solved by teams, a fixed rule for the
+// others); a team LP's row sums have one order whatever G is and its sums
+// over rows are taken by element passes (rows_spmv), so results are the same
+// for every schedule and every create.
 //
 // Arithmetic matches the single-instance kernels in pdlp_kernels.cu (same
 // formulas and readings of the paper); only the summation order differs.
@@ -60,7 +62,8 @@ enum { VN_C = 0, VN_L, VN_U, VN_D2, VN_L0, VN_U0, VN_X0, VN_X1, VN_SX0, VN_SX1, 
 constexpr int VM_RES = VM_KXS, VN_RES = VN_GS;
 
 struct Inst {
-  int m, n, n_eq, gk, gt;  // gk / gt: lanes per row for K / K'
+  int m, n, n_eq, gk, gt;  // gk / gt: lanes per row for K / K' (the schedule)
+  int sk, st;              // sk / st: slots of the canonical row-sum order for K / K'
   int pad;
   long long kp, ke, tp, te;  // offsets of K row_ptr / nonzeros, K' row_ptr / nonzeros
   long long om, on;          // offsets of the m- and n-vector blocks
@@ -237,6 +240,9 @@ struct TeamState {
 constexpr int TEAM = 4;                 // CTAs per team
 constexpr int BACK_CTAS = 16;           // CTAs that start from the small end of the queue
 constexpr long long TEAM_MIN_NNZ = 32768;  // LPs at least this large are solved by a team
+// lanes-per-row rule of an LP solved by one CTA: the smallest power of two G
+// with (mean row length) / G <= SOLO_TARGET
+constexpr double SOLO_TARGET = 8.0;
 constexpr unsigned long long TEAM_WAIT_NS = 2000000000ull;
 
 // An LP solved by TEAM CTAs (one per SM): rows and vector entries are dealt
@@ -345,35 +351,76 @@ struct Team {
 
 // Rows of a CSR block with G lanes per row: for each row, f(row, sums) runs
 // in the group's first lane.  Every lane of a warp takes part in each round,
-// so the shuffles are always full-warp.
-template <int NV, bool SCALED, bool CG = false, class F>
-__device__ __forceinline__ void rows_spmv(const int *__restrict__ ptr, const int *__restrict__ idx,
-                                          const double *__restrict__ val, int rows, int G,
-                                          const double *const (&xs)[NV], const double (&sc)[NV], F &f,
-                                          int part = 0, int parts = 1) {
-  const int gid = threadIdx.x / G, li = threadIdx.x % G, ngroups = NTB / G;
+// so the shuffles are always full-warp.  For an LP solved by a team, f only
+// stores: its sums over rows (step-test and KKT pieces) are taken afterwards
+// by an elementwise pass with a fixed thread per element, so which thread
+// finished a row never matters and the autotuned G cannot change them.  On
+// one CTA (fixed G) f also keeps those sums, saving the pass.
+//
+// A row's sum has one order whatever G is (G a power of two dividing S, S / G
+// in {1, 2, 4}): S slots, slot s taking the row's entries e with
+// e mod S = s in increasing order (an FMA chain), and the slots added by the
+// xor butterfly S/2, S/4, ..., 1.  Lane li of a group holds the R = S / G
+// slots li + G j: slot pairs at offsets >= G are added in registers (in
+// butterfly order), the rest by shuffles.  So the schedule (G) changes
+// speed, never results: the autotuner may pick any G per LP.
+template <int R, int NV, bool SCALED, bool CG, class F>
+__device__ __forceinline__ void rows_spmv_r(const int *__restrict__ ptr, const int *__restrict__ idx,
+                                            const double *__restrict__ val, int rows, int G,
+                                            const double *const (&xs)[NV], const double (&sc)[NV], F &f, int part,
+                                            int parts) {
+  const int gid = threadIdx.x / G, li = threadIdx.x % G, ngroups = NTB / G, S = G * R;
   for (int base = part * ngroups; base < rows; base += parts * ngroups) {
     const int r = base + gid;
-    double s[NV];
+    double s[R][NV];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) s[a] = 0.0;
+    for (int j = 0; j < R; ++j)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s[j][a] = 0.0;
     if (r < rows) {
-      for (int e = ptr[r] + li; e < ptr[r + 1]; e += G) {
-        const double v = val[e];
-        const int c = idx[e];
+      const int e1 = ptr[r + 1];
+      for (int b0 = ptr[r] + li; b0 < e1; b0 += S) {
 #pragma unroll
-        for (int a = 0; a < NV; ++a) {
-          const double xv = ldv<CG>(xs[a] + c);
-          s[a] = fma(v, SCALED ? sc[a] * xv : xv, s[a]);
+        for (int j = 0; j < R; ++j) {
+          const int e = b0 + G * j;
+          if (e < e1) {
+            const double v = val[e];
+            const int c = idx[e];
+#pragma unroll
+            for (int a = 0; a < NV; ++a) {
+              const double xv = ldv<CG>(xs[a] + c);
+              s[j][a] = fma(v, SCALED ? sc[a] * xv : xv, s[j][a]);
+            }
+          }
         }
       }
     }
+#pragma unroll
+    for (int b = R / 2; b >= 1; b >>= 1)
+#pragma unroll
+      for (int j = 0; j < b; ++j)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) s[j][a] += s[j + b][a];
     for (int o = G >> 1; o > 0; o >>= 1) {
 #pragma unroll
-      for (int a = 0; a < NV; ++a) s[a] += __shfl_xor_sync(0xffffffffu, s[a], o, G);
+      for (int a = 0; a < NV; ++a) s[0][a] += __shfl_xor_sync(0xffffffffu, s[0][a], o, G);
     }
-    if (r < rows && li == 0) f(r, s);
+    if (r < rows && li == 0) f(r, s[0]);
   }
+}
+
+template <int NV, bool SCALED, bool CG = false, class F>
+__device__ __forceinline__ void rows_spmv(const int *__restrict__ ptr, const int *__restrict__ idx,
+                                          const double *__restrict__ val, int rows, int G, int S,
+                                          const double *const (&xs)[NV], const double (&sc)[NV], F &f,
+                                          int part, int parts) {
+  const int R = S / G;
+  if (R == 1)
+    rows_spmv_r<1, NV, SCALED, CG>(ptr, idx, val, rows, G, xs, sc, f, part, parts);
+  else if (R == 2)
+    rows_spmv_r<2, NV, SCALED, CG>(ptr, idx, val, rows, G, xs, sc, f, part, parts);
+  else
+    rows_spmv_r<4, NV, SCALED, CG>(ptr, idx, val, rows, G, xs, sc, f, part, parts);
 }
 
 __device__ __forceinline__ double proj_lambda(double d, double l, double u) {
@@ -473,8 +520,9 @@ template <bool CG>
 struct PrimalRow {
   const double *c, *l, *u, *x, *sx;
   double *g, *xn, *sxn;
-  double tau, eta, dx2;
+  double tau, eta;
   bool store_g;
+  double dx2 = 0.0;  // one CTA per LP (fixed schedule): ||x' - x||^2 kept here
   __device__ __forceinline__ void operator()(int j, const double (&s)[1]) { apply(j, s[0]); }
   __device__ __forceinline__ void apply(int j, double gj) {
     if (store_g) g[j] = gj;
@@ -482,8 +530,10 @@ struct PrimalRow {
     const double v = clamp_bits(fma(-tau, c[j] - gj, xj), l[j], u[j]);  // integer compares, off the FP64 pipe
     xn[j] = v;
     sxn[j] = fma(eta, v, ldv<CG>(sx + j));
-    const double d = v - xj;
-    dx2 = fma(d, d, dx2);
+    if (!CG) {
+      const double d = v - xj;
+      dx2 = fma(d, d, dx2);
+    }
   }
 };
 
@@ -491,8 +541,9 @@ template <bool CG>
 struct DualRow {
   const double *q, *y, *kx, *sy;
   double *yn, *kxn, *syn;
-  double sigma, eta, dy2, cross;
+  double sigma, eta;
   int n_eq;
+  double dy2 = 0.0, cross = 0.0;  // one CTA per LP: the step-test pieces kept here
   __device__ __forceinline__ void operator()(int i, const double (&s)[1]) {
     const double kn = s[0], kxi = ldv<CG>(kx + i), yi = ldv<CG>(y + i);
     double v = fma(sigma, q[i] - fma(2.0, kn, -kxi), yi);
@@ -500,9 +551,11 @@ struct DualRow {
     yn[i] = v;
     kxn[i] = kn;
     syn[i] = fma(eta, v, ldv<CG>(sy + i));
-    const double d = v - yi;
-    dy2 = fma(d, d, dy2);
-    cross = fma(d, kn - kxi, cross);
+    if (!CG) {
+      const double d = v - yi;
+      dy2 = fma(d, d, dy2);
+      cross = fma(d, kn - kxi, cross);
+    }
   }
 };
 
@@ -544,11 +597,16 @@ struct CheckT {
     } else {
       gb = s[0];
     }
-    piece(c[j], gj, l[j], u[j], d2[j], ldv<CG>(x + j), acc);
-    if (kind) {
-      gbar[j] = gb;
-      piece(c[j], gb, l[j], u[j], d2[j], invW * ldv<CG>(sx + j), acc + 4);
+    if (kind) gbar[j] = gb;
+    if (!CG) {  // one CTA per LP: the pieces here (a team takes them in sums())
+      piece(c[j], gj, l[j], u[j], d2[j], ldv<CG>(x + j), acc);
+      if (kind) piece(c[j], gb, l[j], u[j], d2[j], invW * ldv<CG>(sx + j), acc + 4);
     }
+  }
+  // this element's pieces, from the stored K'y (and K'ybar)
+  __device__ __forceinline__ void sums(int j) {
+    piece(c[j], ldv<CG>(g + j), l[j], u[j], d2[j], ldv<CG>(x + j), acc);
+    if (kind) piece(c[j], ldv<CG>(gbar + j), l[j], u[j], d2[j], invW * ldv<CG>(sx + j), acc + 4);
   }
 };
 
@@ -571,17 +629,23 @@ struct CheckK {
     a[2] = fma(qi, yi, a[2]);
   }
   __device__ __forceinline__ void operator()(int i, const double (&s)[1]) {
-    const bool ineq = i >= n_eq;
-    double kxi = check ? ldv<CG>(kx + i) : s[0];
     if (!check) {
-      kx[i] = kxi;
-      if (keep) kxs[i] = kxi;
-    }
-    piece(q[i], kxi, ineq, d1[i], ldv<CG>(y + i), acc);
-    if (check) {
+      kx[i] = s[0];
+      if (keep) kxs[i] = s[0];
+    } else {
       kxbar[i] = s[0];
-      piece(q[i], s[0], ineq, d1[i], invW * ldv<CG>(sy + i), acc + 3);
     }
+    if (!CG) {  // one CTA per LP: the pieces here (a team takes them in sums())
+      const bool ineq = i >= n_eq;
+      piece(q[i], check ? ldv<CG>(kx + i) : s[0], ineq, d1[i], ldv<CG>(y + i), acc);
+      if (check) piece(q[i], s[0], ineq, d1[i], invW * ldv<CG>(sy + i), acc + 3);
+    }
+  }
+  // this element's pieces, from the stored K x (and K xbar)
+  __device__ __forceinline__ void sums(int i) {
+    const bool ineq = i >= n_eq;
+    piece(q[i], ldv<CG>(kx + i), ineq, d1[i], ldv<CG>(y + i), acc);
+    if (check) piece(q[i], ldv<CG>(kxbar + i), ineq, d1[i], invW * ldv<CG>(sy + i), acc + 3);
   }
 };
 
@@ -687,12 +751,17 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     ct.gs = VNK(VN_GS);
     const double *const xs[1] = {y[0]};
     const double sc[1] = {1.0};
-    rows_spmv<1, false, CG>(tp, ti, tv, n, I.gt, xs, sc, ct, part, parts);
+    rows_spmv<1, false, CG>(tp, ti, tv, n, I.gt, I.st, xs, sc, ct, part, parts);
     CheckK<CG> ck{q, D1, y[0], sy[0], kx[0], kxb, 0.0, 0, I.n_eq, {0, 0, 0, 0, 0, 0}};
     ck.keep = keep;
     ck.kxs = VMK(VM_KXS);
     const double *const xs2[1] = {x[0]};
-    rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, xs2, sc, ck, part, parts);
+    rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, I.sk, xs2, sc, ck, part, parts);
+    if (CG) {  // a team: the stored products, then their pieces element by element
+      ok = grp.sync() && ok;
+      for (int j = e0; j < n; j += es) ct.sums(j);
+      for (int i = e0; i < m; i += es) ck.sums(i);
+    }
     double s[5] = {ct.acc[0], ct.acc[2], ct.acc[3], ck.acc[0], ck.acc[2]};
     ok = grp.template reduce<5>(s, red) && ok;
     if (!ok) status = ST_NUMERICAL;
@@ -702,11 +771,11 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
   while (status == ST_RUNNING) {
     const int nxt = cur ^ 1;
     // ---- Algorithm 2 trial: primal half-step ----
-    PrimalRow<CG> pr{c, l, u, x[cur], sx[cur], g, x[nxt], sx[nxt], tau, eta, 0.0, need_g != 0};
+    PrimalRow<CG> pr{c, l, u, x[cur], sx[cur], g, x[nxt], sx[nxt], tau, eta, need_g != 0};
     if (need_g) {
       const double *const xs[1] = {y[cur]};
       const double sc[1] = {1.0};
-      rows_spmv<1, false, CG>(tp, ti, tv, n, I.gt, xs, sc, pr, part, parts);
+      rows_spmv<1, false, CG>(tp, ti, tv, n, I.gt, I.st, xs, sc, pr, part, parts);
     } else {
       for (int j = e0; j < n; j += es) pr.apply(j, ldv<CG>(g + j));
     }
@@ -715,13 +784,30 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
       break;
     }
     // ---- dual half-step ----
-    DualRow<CG> dr{q, y[cur], kx[cur], sy[cur], y[nxt], kx[nxt], sy[nxt], sigma, eta, 0.0, 0.0, I.n_eq};
+    DualRow<CG> dr{q, y[cur], kx[cur], sy[cur], y[nxt], kx[nxt], sy[nxt], sigma, eta, I.n_eq};
     {
       const double *const xs[1] = {x[nxt]};
       const double sc[1] = {1.0};
-      rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, xs, sc, dr, part, parts);
+      rows_spmv<1, false, CG>(kp, ki, kv, m, I.gk, I.sk, xs, sc, dr, part, parts);
     }
     double s3[3] = {pr.dx2, dr.dy2, dr.cross};
+    if (CG) {
+      // a team (autotuned schedule): ||x' - x||^2, ||y' - y||^2 and
+      // (y' - y)'(Kx' - Kx) from the stored vectors, one fixed thread per element
+      if (!grp.sync()) {
+        status = ST_NUMERICAL;
+        break;
+      }
+      for (int j = e0; j < n; j += es) {
+        const double d = ldv<CG>(x[nxt] + j) - ldv<CG>(x[cur] + j);
+        s3[0] = fma(d, d, s3[0]);
+      }
+      for (int i = e0; i < m; i += es) {
+        const double kn = ldv<CG>(kx[nxt] + i), d = ldv<CG>(y[nxt] + i) - ldv<CG>(y[cur] + i);
+        s3[1] = fma(d, d, s3[1]);
+        s3[2] = fma(d, kn - ldv<CG>(kx[cur] + i), s3[2]);
+      }
+    }
     // ---- step-size test (eq. step-size with |interaction|; exponent base k + 2) ----
     // one thread evaluates it and broadcasts: the FP64 divisions and powers,
     // run by every warp, would cost more than the whole iteration of a small
@@ -773,7 +859,7 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     {
       const double *const xs[2] = {y[cur], sy[cur]};
       const double sc[2] = {1.0, invW};
-      rows_spmv<2, true, CG>(tp, ti, tv, n, I.gt, xs, sc, ct, part, parts);
+      rows_spmv<2, true, CG>(tp, ti, tv, n, I.gt, I.st, xs, sc, ct, part, parts);
     }
     CheckK<CG> ck{q, D1, y[cur], sy[cur], kx[cur], kxb, invW, 1, I.n_eq, {0, 0, 0, 0, 0, 0}};
     ck.keep = keep;
@@ -781,9 +867,17 @@ __device__ void solve_instance(const Arrays &A, const Inst &I, const Params &p, 
     {
       const double *const xs[1] = {sx[cur]};
       const double sc[1] = {invW};
-      rows_spmv<1, true, CG>(kp, ki, kv, m, I.gk, xs, sc, ck, part, parts);
+      rows_spmv<1, true, CG>(kp, ki, kv, m, I.gk, I.sk, xs, sc, ck, part, parts);
     }
     need_g = 0;
+    if (CG) {
+      if (!grp.sync()) {
+        status = ST_NUMERICAL;
+        break;
+      }
+      for (int j = e0; j < n; j += es) ct.sums(j);
+      for (int i = e0; i < m; i += es) ck.sums(i);
+    }
     double s[14];
 #pragma unroll
     for (int a = 0; a < 8; ++a) s[a] = ct.acc[a];
@@ -1404,21 +1498,47 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   BCKS(cudaMemcpyAsync(b->h_inst.data(), b->d_inst, sizeof(Inst) * count, cudaMemcpyDeviceToHost, st));
   BCKS(cudaStreamSynchronize(st));
   b->setup_ms = now_ms() - t0;
-  // ---- schedule: lanes per row from the mean row length; the entries-per-lane
-  // target is autotuned by timing short solves of the whole batch ----
-  auto set_lanes = [&](double target) -> int {
-    for (int i = 0; i < count; ++i) {
-      Inst &I = b->h_inst[i];
-      const double nnz = (double)lps[i].row_ptr[lps[i].m];
-      I.gk = lanes_for(I.m ? nnz / I.m : 0.0, target);
-      I.gt = lanes_for(nnz / I.n, target);
+  // ---- schedule: lanes per row (G) for each LP's K and K'.  An LP solved
+  // by a team is autotuned: candidates are the rules "smallest power of two
+  // G <= 32 with mean row length / G <= t" for t in {4, 8, 16} (warp-per-row
+  // for the longest rows, several rows per warp for short ones); every
+  // candidate is timed on short solves of the whole batch (2P iterations)
+  // and each LP keeps the one under which it finished fastest.  Its row sums
+  // do not depend on G (the slot order of rows_spmv, S = the t = 4 rule) and
+  // its sums over rows are taken by element passes, so the choice, and any
+  // timing noise behind it, changes speed only, never results.  An LP on one
+  // CTA (latency-bound: an element pass would cost it more than tuning
+  // gains) keeps the fixed rule t = SOLO_TARGET. ----
+  std::vector<double> mean_k(count), mean_t(count);
+  std::vector<char> team(count);
+  for (int i = 0; i < count; ++i) {
+    Inst &I = b->h_inst[i];
+    const double nnz = (double)lps[i].row_ptr[lps[i].m];
+    mean_k[i] = I.m ? nnz / I.m : 0.0;
+    mean_t[i] = nnz / I.n;
+    team[i] = nnz >= (double)TEAM_MIN_NNZ;
+    // a team's rows may take any tuned G (S from the t = 4 rule); an LP on
+    // one CTA keeps the fixed rule t = SOLO_TARGET (S = G: the plain order)
+    I.sk = lanes_for(mean_k[i], team[i] ? 4.0 : SOLO_TARGET);
+    I.st = lanes_for(mean_t[i], team[i] ? 4.0 : SOLO_TARGET);
+  }
+  const double cands[3] = {4.0, 8.0, 16.0};
+  auto lanes_of = [&](int i, double target, int *gk, int *gt) {
+    const Inst &I = b->h_inst[i];
+    if (!team[i]) {
+      *gk = I.sk;
+      *gt = I.st;
+      return;
     }
+    *gk = std::max(lanes_for(mean_k[i], target), std::max(1, I.sk / 4));
+    *gt = std::max(lanes_for(mean_t[i], target), std::max(1, I.st / 4));
+  };
+  auto set_lanes = [&](const std::vector<int> &choice) -> int {
+    for (int i = 0; i < count; ++i) lanes_of(i, cands[choice[i]], &b->h_inst[i].gk, &b->h_inst[i].gt);
     cudaError_t e3 = cudaMemcpyAsync(b->d_inst, b->h_inst.data(), sizeof(Inst) * count, cudaMemcpyHostToDevice, st);
     return e3 == cudaSuccess ? PDLP_OK : set_error(PDLP_ERR_CUDA, cudaGetErrorString(e3));
   };
   const double t1 = now_ms();
-  const double cands[4] = {2.0, 4.0, 8.0, 16.0};
-  double best = INFINITY, best_t = 4.0;
   Params tp{};
   tp.tol = 0.0;
   tp.theta = prm.theta;
@@ -1430,39 +1550,47 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
   tp.max_iter = 2 * prm.check_period;
   tp.P = prm.check_period;
   tp.warm = 0;
-  cudaEvent_t ea, eb;
-  BCKS(cudaEventCreate(&ea));
-  BCKS(cudaEventCreate(&eb));
-  for (double c : cands) {
-    int rc = set_lanes(c);
+  std::vector<int> choice(count, 0);
+  std::vector<double> best(count, INFINITY);
+  std::vector<unsigned long long> stamps(2 * (size_t)count);
+  for (int ci = -1; ci < 3; ++ci) {  // ci = -1: an untimed warm-up launch
+    std::vector<int> all(count, ci < 0 ? 0 : ci);
+    int rc = set_lanes(all);
+    if (!rc) rc = launch_solve(b, b->A, tp, st);
     if (rc) {
       free_batch(b);
       return rc;
     }
-    BCKS(cudaEventRecord(ea, st));
-    rc = launch_solve(b, b->A, tp, st);
-    if (rc) {
-      free_batch(b);
-      return rc;
-    }
-    BCKS(cudaEventRecord(eb, st));
-    BCKS(cudaEventSynchronize(eb));
-    float ms = 0.f;
-    BCKS(cudaEventElapsedTime(&ms, ea, eb));
-    if (ms < best) {
-      best = ms;
-      best_t = c;
+    BCKS(cudaMemcpyAsync(stamps.data(), b->A.t_start, 16 * (size_t)count, cudaMemcpyDeviceToHost, st));
+    BCKS(cudaStreamSynchronize(st));
+    if (ci < 0) continue;
+    for (int i = 0; i < count; ++i) {
+      const double d = (double)(stamps[count + i] - stamps[i]);
+      if (d < best[i]) {
+        best[i] = d;
+        choice[i] = ci;
+      }
     }
   }
-  cudaEventDestroy(ea);
-  cudaEventDestroy(eb);
-  int rc = set_lanes(best_t);
+  // test hook (environment PDLP_TEST_BATCH_TARGET = 4, 8 or 16): every LP
+  // gets that candidate, so tests can compare results across schedules
+  if (const char *force = std::getenv("PDLP_TEST_BATCH_TARGET")) {
+    const double f = std::atof(force);
+    for (int k = 0; k < 3; ++k)
+      if (f == cands[k]) std::fill(choice.begin(), choice.end(), k);
+  }
+  int rc = set_lanes(choice);
   if (rc) {
     free_batch(b);
     return rc;
   }
   BCKS(cudaStreamSynchronize(st));
-  b->lanes_target = best_t;
+  {
+    int votes[3] = {0, 0, 0};
+    for (int i = 0; i < count; ++i) votes[choice[i]]++;
+    const int top = (int)(std::max_element(votes, votes + 3) - votes);
+    b->lanes_target = cands[top];
+  }
   b->tune_ms = now_ms() - t1;
 #undef BCKS
   *out = b;

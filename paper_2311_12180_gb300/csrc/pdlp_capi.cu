@@ -81,6 +81,7 @@ struct pdlp_solver {
   double *D1 = nullptr, *D2 = nullptr, *work_m = nullptr, *work_n = nullptr;  // D1, D2: original order
   int32_t *perm_r = nullptr, *perm_c = nullptr;  // internal -> original row / column
   std::vector<int32_t> h_perm_r, h_perm_c;        // the same on the host (state export / import)
+  pdlp_layout_info layout{};                      // sliced-ELL shapes of K and K'
   double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr, *l0 = nullptr, *u0 = nullptr;
   int gridA = 1, gridB = 1, gridR1 = 1, gridR2 = 1, gridR3 = 1, gridI = 1;
   int slots = 0;
@@ -552,6 +553,13 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
     lw.p = nullptr;
     CKS(ef);
   }
+  s->layout.K_stored = LK.total;
+  s->layout.K_slices = LK.nslices;
+  s->layout.K_long_rows = LK.nlong;
+  s->layout.KT_stored = LT.total;
+  s->layout.KT_slices = LT.nslices;
+  s->layout.KT_long_rows = LT.nlong;
+  s->layout.long_threshold = SELL_LONG;
   s->h_perm_r.swap(LK.perm);
   s->h_perm_c.swap(LT.perm);
   // ---- vectors in the internal order ----
@@ -923,9 +931,27 @@ struct StateHeader {
   int32_t m, n, check_period, value_bits, pad;
   int64_t nnz;
   uint64_t devstate_bytes;
+  uint64_t fingerprint;  // of the LP as the solver holds it (see lp_fingerprint)
 };
 constexpr uint64_t STATE_MAGIC = 0x3154535050444c50ull;  // "PLDPPST1" little-endian
 constexpr int STATE_NV_N = 6, STATE_NV_M = 5;
+
+// FNV-1a over the internal row and column orders and the norms and start
+// scalars derived from c, q and the scaled K: two LPs that differ in these
+// cannot exchange states.
+uint64_t lp_fingerprint(const pdlp_solver *s) {
+  uint64_t h = 0xcbf29ce484222325ull;
+  auto mix = [&h](const void *p, size_t bytes) {
+    const unsigned char *b = static_cast<const unsigned char *>(p);
+    for (size_t i = 0; i < bytes; ++i) h = (h ^ b[i]) * 0x100000001b3ull;
+  };
+  mix(s->h_perm_r.data(), 4 * s->h_perm_r.size());
+  mix(s->h_perm_c.data(), 4 * s->h_perm_c.size());
+  const double sc[4] = {s->q_norm, s->c_norm, s->eta_hat0, s->omega0};
+  mix(sc, sizeof(sc));
+  mix(&s->n_eq, sizeof(s->n_eq));
+  return h;
+}
 
 size_t state_bytes(const pdlp_solver *s) {
   return sizeof(StateHeader) + sizeof(DevState) + 8 * ((size_t)STATE_NV_N * s->n + (size_t)STATE_NV_M * s->m);
@@ -959,6 +985,7 @@ int pdlp_get_state(const pdlp_solver *s, void *buf, size_t cap, size_t *bytes) {
   h.value_bits = s->prm.value_bits;
   h.nnz = s->nnz;
   h.devstate_bytes = sizeof(DevState);
+  h.fingerprint = lp_fingerprint(s);
   std::memcpy(out, &h, sizeof(h));
   DevState d;
   CK(cudaMemcpy(&d, s->st, sizeof(DevState), cudaMemcpyDeviceToHost));
@@ -991,7 +1018,7 @@ int pdlp_set_state(pdlp_solver *s, const void *buf, size_t bytes) {
   if (h.magic != STATE_MAGIC || h.version != 1 || h.devstate_bytes != sizeof(DevState))
     return fail(PDLP_ERR_INVALID, "pdlp_set_state: not a state of this library version");
   if (h.m != s->m || h.n != s->n || h.nnz != s->nnz || h.check_period != s->prm.check_period ||
-      h.value_bits != s->prm.value_bits)
+      h.value_bits != s->prm.value_bits || h.fingerprint != lp_fingerprint(s))
     return fail(PDLP_ERR_INVALID, "pdlp_set_state: the state belongs to another LP or other parameters");
   DevState d;
   std::memcpy(&d, in + sizeof(h), sizeof(d));
@@ -1024,6 +1051,13 @@ int pdlp_set_state(pdlp_solver *s, const void *buf, size_t bytes) {
   s->have_result = false;
   s->last_status = d.status;
   s->t0 = now_ms();
+  return PDLP_OK;
+}
+
+int pdlp_get_layout(const pdlp_solver *s, pdlp_layout_info *info) {
+  g_err.clear();
+  if (!s || !info) return fail(PDLP_ERR_INVALID, "null argument");
+  *info = s->layout;
   return PDLP_OK;
 }
 

@@ -19,8 +19,17 @@ constexpr int NW = NT / 32;
 // longer row is stored contiguously from off, padded to a multiple of 32.
 // Padding entries hold column -1 and value 0.  Every item starts at a
 // multiple of 32 entries.
-constexpr int SELL_LONG = 128;
-constexpr int SELL_U = 4;  // strides of 32 entries loaded per batch
+constexpr int SELL_LONG = 48;
+// strides of 32 entries loaded per batch: primal step (K'), dual step (K),
+// check passes
+constexpr int SELL_U_P = 2;
+constexpr int SELL_U_D = 2;
+constexpr int SELL_U_C = 4;
+// bulk L2 prefetch of the warp's next work item (and of the rest of the
+// current one) when an item starts
+constexpr bool SELL_PREFETCH = false;
+// CTAs per SM the two-vector check pass over K' is compiled for
+constexpr int CHECK_MINB = 2;
 
 // One unit of work for one warp: a slice {first row, rows (1..32), L, off}
 // or a long row {row, -1, length, off}.

@@ -153,31 +153,31 @@ __device__ __forceinline__ double widen(float v) { return f2d(v); }
 
 // Sum over `cnt` strides of 32 stored entries, this lane's entry of each
 // stride: acc[a] += val * xs[a][col] in stride order (FMA), padding (column
-// -1) skipped.  SELL_U strides are loaded (streaming, coalesced across the
+// -1) skipped.  U strides are loaded (streaming, coalesced across the
 // warp) before their gathers are issued, and all gathers before the FMAs.
-template <typename VT, int NV, bool SCALED>
+template <int U, typename VT, int NV, bool SCALED>
 __device__ __forceinline__ void strided_dot(const int32_t *__restrict__ ip, const VT *__restrict__ vp, int cnt,
                                             const double *const (&xs)[NV], const double (&sc)[NV],
                                             double (&acc)[NV]) {
   int k = 0;
-  for (; k + SELL_U <= cnt; k += SELL_U) {
-    int c[SELL_U];
-    VT v[SELL_U];
+  for (; k + U <= cnt; k += U) {
+    int c[U];
+    VT v[U];
 #pragma unroll
-    for (int u = 0; u < SELL_U; ++u) {
+    for (int u = 0; u < U; ++u) {
       c[u] = __ldcs(ip + 32 * (k + u));
       v[u] = __ldcs(vp + 32 * (k + u));
     }
-    double g[NV][SELL_U];
+    double g[NV][U];
 #pragma unroll
-    for (int u = 0; u < SELL_U; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
         const double xv = c[u] >= 0 ? __ldg(xs[a] + c[u]) : 0.0;
         g[a][u] = SCALED ? sc[a] * xv : xv;
       }
 #pragma unroll
-    for (int u = 0; u < SELL_U; ++u)
+    for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int a = 0; a < NV; ++a) acc[a] = fma(widen(v[u]), g[a][u], acc[a]);
   }
@@ -190,6 +190,17 @@ __device__ __forceinline__ void strided_dot(const int32_t *__restrict__ ip, cons
       acc[a] = fma(widen(v), SCALED ? sc[a] * xv : xv, acc[a]);
     }
   }
+}
+
+// Bulk L2 prefetch of `count` stored entries from `off` (indices and
+// values; count a multiple of 32, so both ranges are multiples of 16 bytes
+// and start 128-byte aligned).
+template <typename VT>
+__device__ __forceinline__ void prefetch_item(const SellMat &A, const VT *val, int off, int count) {
+  if (count <= 0) return;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.idx + off), "r"(4 * count) : "memory");
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(val + off), "r"((int)sizeof(VT) * count)
+               : "memory");
 }
 
 // One butterfly level: lanes with the `off` bit clear keep row a's pair sum,
@@ -270,12 +281,43 @@ __device__ __forceinline__ void long_push(LongRows<NV> &lr, const double (&p)[NV
   }
 }
 
+// Finishes a partial batch of t < 32 long rows without padding it: buf[k]
+// (present when bit k of t is set) holds slots [t & ~(2^(k+1) - 1), +2^k)
+// after k butterfly levels, lane l carrying a partial of the block's slot
+// rev_k(l >> (5 - k)); the remaining 5 - k levels are a plain xor reduction,
+// after which the first lane of every group of 32 >> k finishes its row.
+template <int NV, class Epi>
+__device__ __forceinline__ void long_flush(LongRows<NV> &lr, Epi &ep) {
+  const int lane = threadIdx.x & 31, t = lr.t;
+  __syncwarp();
+#pragma unroll
+  for (int k = 4; k >= 0; --k) {
+    if (!(t & (1 << k))) continue;
+    const int start = t & ~((2 << k) - 1);
+    double v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = lr.buf[k][a];
+#pragma unroll
+    for (int off = 16 >> k; off >= 1; off >>= 1)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
+    if ((lane & ((32 >> k) - 1)) == 0) {
+      const int slot = start + (k ? (int)(__brev((unsigned)(lane >> (5 - k))) >> (32 - k)) : 0);
+      const int r = lr.rows[slot];
+      ep.prefetch(r);
+      ep.finish(r, v);
+    }
+  }
+  __syncwarp();
+  lr.t = 0;
+}
+
 // y = A x for NV (1 or 2) gathered vectors, each finished row r passed to
 // ep.finish(r, sums) after ep.prefetch(r).  With SCALED, gathered entries of
 // vector a are multiplied by sc[a] (the epoch average (1/W) sum).  Warp w of
 // the grid takes items w, 2G - 1 - w, 2G + w, ... of the schedule (G warps):
 // a snake over the cost-sorted items, so every warp gets about the same work.
-template <typename VT, int NV, bool SCALED, class Epi>
+template <int U, typename VT, int NV, bool SCALED, class Epi>
 __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict__ val,
                                           const double *const (&xs)[NV], const double (&sc)[NV], Epi &ep,
                                           int *warp_rows) {
@@ -291,6 +333,18 @@ __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict
     const long long it = first + ((b & 1) ? nw - 1 - gw : gw);
     if (it >= A.nitems) continue;
     const int4 d = __ldg(A.items + it);
+    if (SELL_PREFETCH && lane == 0) {
+      // the rest of this item, and the warp's next item, stream into L2
+      // while this one's first loads and gathers are in flight
+      const int nstr = d.y > 0 ? d.z : (d.z + 31) >> 5;
+      if (nstr > U) prefetch_item(A, val, d.w + 32 * U, 32 * (nstr - U));
+      const long long nb = first + nw;
+      const long long itn = nb + (((b + 1) & 1) ? nw - 1 - gw : gw);
+      if (nb < A.nitems && itn < A.nitems) {
+        const int4 dn = __ldg(A.items + itn);
+        prefetch_item(A, val, dn.w, 32 * (dn.y > 0 ? dn.z : (dn.z + 31) >> 5));
+      }
+    }
     double acc[NV];
 #pragma unroll
     for (int a = 0; a < NV; ++a) acc[a] = 0.0;
@@ -298,17 +352,14 @@ __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict
       const bool has = lane < d.y;
       const int row = d.x + lane;
       if (has) ep.prefetch(row);
-      strided_dot<VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, d.z, xs, sc, acc);
+      strided_dot<U, VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, d.z, xs, sc, acc);
       if (has) ep.finish(row, acc);
     } else {  // long row: the whole warp
-      strided_dot<VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, (d.z + 31) >> 5, xs, sc, acc);
+      strided_dot<U, VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, (d.z + 31) >> 5, xs, sc, acc);
       long_push(lr, acc, d.x, ep);
     }
   }
-  if (lr.t > 0) {  // complete the last batch with empty rows
-    const double z[NV] = {};
-    while (lr.t > 0) long_push(lr, z, -1, ep);
-  }
+  if (lr.t > 0) long_flush(lr, ep);
 }
 
 // ---------------------------------------------------------------- primal step
@@ -359,9 +410,9 @@ __global__ void __launch_bounds__(NT, 4) k_primal(SellMat KT, Vecs V, DevState *
     const double *const xs[1] = {V.y[cur]};
     const double sc[1] = {1.0};
     if (f32)
-      spmv_sell<float, 1, false>(KT, KT.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+      spmv_sell<SELL_U_P, float, 1, false>(KT, KT.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
     else
-      spmv_sell<double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+      spmv_sell<SELL_U_P, double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else {
     // rejected trial: g = K'y is unchanged, only the projection reruns
     for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += gridDim.x * NT) {
@@ -458,9 +509,9 @@ __global__ void __launch_bounds__(NT, 4) k_dual(SellMat K, Vecs V, DevState *__r
   const double *const xs[1] = {V.x[nxt]};
   const double sc[1] = {1.0};
   if (f32)
-    spmv_sell<float, 1, false>(K, K.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_D, float, 1, false>(K, K.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   else
-    spmv_sell<double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_D, double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   double acc[2] = {ep.dy2, ep.cross};
   double tot[2];
   if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], s_red, &s_flag, tot)) return;
@@ -537,8 +588,7 @@ struct CheckPrimalEpi {
   }
 };
 
-// three CTAs per SM (80 registers) for the two-vector SpMV of a check
-__global__ void __launch_bounds__(NT, 3) k_check_primal(SellMat KT, Vecs V, DevState *__restrict__ st) {
+__global__ void __launch_bounds__(NT, CHECK_MINB) k_check_primal(SellMat KT, Vecs V, DevState *__restrict__ st) {
   __shared__ double s_red[16 * NW];
   __shared__ int s_rows[NW][32];
   if (st->status != ST_RUNNING || !st->check_pending) return;
@@ -563,15 +613,15 @@ __global__ void __launch_bounds__(NT, 3) k_check_primal(SellMat KT, Vecs V, DevS
   if (ep.kind == 0) {
     const double *const xs[1] = {V.y[cur]};
     const double sc[1] = {1.0};
-    spmv_sell<double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else if (ep.kind == 1) {
     const double *const xs[2] = {V.y[cur], V.sy[cur]};
     const double sc[2] = {1.0, ep.invW};
-    spmv_sell<double, 2, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 2, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else {
     const double *const xs[1] = {V.sy[cur]};
     const double sc[1] = {ep.invW};
-    spmv_sell<double, 1, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   }
   block_sum<NV_R1>(ep.acc, s_red);
   if (threadIdx.x == 0) {
@@ -790,11 +840,11 @@ __global__ void __launch_bounds__(NT) k_check_dual(SellMat K, Vecs V, DevState *
   if (!check) {
     const double *const xs[1] = {V.x[cur]};
     const double sc[1] = {1.0};
-    spmv_sell<double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   } else {
     const double *const xs[1] = {V.sx[cur]};
     const double sc[1] = {ep.invW};
-    spmv_sell<double, 1, true>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, true>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
   }
   double tot[NV_R2];
   if (!grid_finish<NV_R2>(ep.acc, V.partR2, &st->cnt[CNT_R2], s_red, &s_flag, tot)) return;

@@ -91,10 +91,17 @@ EXPORTS = (
     "pdlp_run_periods", "pdlp_poll", "pdlp_finish", "pdlp_time_kernels", "pdlp_kernel_count",
     "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
     "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error", "pdlp_scale_device_noalloc",
+    "pdlp_create_device", "pdlp_get_state", "pdlp_set_state", "pdlp_resume", "pdlp_get_layout",
+    "pdlp_probe_rates",
     "pdlp_batch_create", "pdlp_batch_solve", "pdlp_batch_info", "pdlp_batch_lanes", "pdlp_batch_times", "pdlp_batch_destroy",
     "pdlp_mlp_create", "pdlp_mlp_param_count", "pdlp_mlp_set_params", "pdlp_mlp_get_params", "pdlp_mlp_set_data",
     "pdlp_mlp_train", "pdlp_mlp_predict", "pdlp_mlp_gradients", "pdlp_mlp_stats", "pdlp_mlp_destroy",
 )
+
+
+class pdlp_layout_info(C.Structure):
+    _fields_ = [(f, C.c_int64) for f in ("K_stored", "K_slices", "K_long_rows", "KT_stored", "KT_slices",
+                                          "KT_long_rows")] + [("long_threshold", C.c_int32), ("pad_", C.c_int32)]
 
 
 class pdlp_lp(C.Structure):
@@ -157,6 +164,18 @@ def lib():
     L.pdlp_create.restype = C.c_int
     L.pdlp_create_ex.argtypes = [P(vp), i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, P(pdlp_params), vp]
     L.pdlp_create_ex.restype = C.c_int
+    L.pdlp_create_device.argtypes = [P(vp), i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, P(pdlp_params), vp]
+    L.pdlp_create_device.restype = C.c_int
+    L.pdlp_get_state.argtypes = [vp, vp, sz, P(sz)]
+    L.pdlp_get_state.restype = C.c_int
+    L.pdlp_set_state.argtypes = [vp, vp, sz]
+    L.pdlp_set_state.restype = C.c_int
+    L.pdlp_resume.argtypes = [vp, vp, vp, P(C.c_int), P(i64)]
+    L.pdlp_resume.restype = C.c_int
+    L.pdlp_get_layout.argtypes = [vp, P(pdlp_layout_info)]
+    L.pdlp_get_layout.restype = C.c_int
+    L.pdlp_probe_rates.argtypes = [P(d), P(d)]
+    L.pdlp_probe_rates.restype = C.c_int
     L.pdlp_solve.argtypes = [vp, d, i64, vp, vp, P(C.c_int), P(i64)]
     L.pdlp_solve.restype = C.c_int
     L.pdlp_solve_warm.argtypes = [vp, vp, vp, d, i64, vp, vp, P(C.c_int), P(i64)]
@@ -275,6 +294,16 @@ def pdlp_create(m, n, n_eq, c, row_ptr, col_idx, val, q, l, u, params=None, stre
     return h
 
 
+def pdlp_create_device(m, n, n_eq, c, row_ptr, col_idx, val, q, l, u, params=None, stream=None):
+    """pdlp_create_device: every array argument is a DEVICE address (int,
+    e.g. a torch tensor's data_ptr()); returns the opaque handle."""
+    h = C.c_void_p()
+    _check(lib().pdlp_create_device(C.byref(h), m, n, n_eq, c, row_ptr, col_idx, val, q, l, u,
+                                    C.byref(params) if params is not None else None,
+                                    C.c_void_p(stream) if stream else None))
+    return h
+
+
 def pdlp_solve_warm(h, x0, y0, tol, max_iter, n, m):
     x = np.empty(n)
     y = np.empty(max(m, 1))
@@ -302,6 +331,14 @@ def pdlp_scale_device_noalloc(m, n, K_ptr, K_idx, K_val, KT_ptr, KT_idx, KT_val,
                                            float(pc_alpha), D1, D2, stream))
 
 
+def probe_rates():
+    """(random 8-byte gathers per second, FP64 FMA lane operations per second)
+    measured on the current GPU (pdlp_probe_rates)."""
+    g, f = C.c_double(0), C.c_double(0)
+    _check(lib().pdlp_probe_rates(C.byref(g), C.byref(f)))
+    return g.value, f.value
+
+
 def kernel_names():
     L = lib()
     return [L.pdlp_kernel_name(i).decode() for i in range(L.pdlp_kernel_count())]
@@ -314,15 +351,23 @@ class Solver:
     """One LP on the GPU.  `lp` is anything with fields m, n, n_eq, c,
     row_ptr, col_idx, val, q, l, u (e.g. lpgen.LP)."""
 
-    def __init__(self, lp, params: pdlp_params | None = None, stream: int | None = None, **kw):
+    def __init__(self, lp, params: pdlp_params | None = None, stream: int | None = None, device=None, **kw):
+        """device: None for host arrays in `lp`; otherwise a dict of DEVICE
+        addresses with keys c, row_ptr, col_idx, val, q, l, u (and `lp` only
+        supplies m, n, n_eq, nnz): pdlp_create_device."""
         if kw:
             params = params or pdlp_default_params()
             for k, v in kw.items():
                 setattr(params, k, v)
         self.m, self.n, self.n_eq = int(lp.m), int(lp.n), int(lp.n_eq)
-        self.nnz = int(lp.row_ptr[-1])
-        self.h = pdlp_create(self.m, self.n, self.n_eq, lp.c, lp.row_ptr, lp.col_idx, lp.val, lp.q, lp.l, lp.u,
-                             params=params, stream=stream)
+        self.nnz = int(lp.row_ptr[-1]) if device is None else int(lp.nnz)
+        if device is None:
+            self.h = pdlp_create(self.m, self.n, self.n_eq, lp.c, lp.row_ptr, lp.col_idx, lp.val, lp.q, lp.l,
+                                 lp.u, params=params, stream=stream)
+        else:
+            d = device
+            self.h = pdlp_create_device(self.m, self.n, self.n_eq, d["c"], d["row_ptr"], d["col_idx"], d["val"],
+                                        d["q"], d["l"], d["u"], params=params, stream=stream)
 
     def close(self):
         if getattr(self, "h", None):
@@ -366,6 +411,27 @@ class Solver:
         _check(lib().pdlp_finish(self.h, _ptr(x), _ptr(y), C.byref(st), C.byref(it)))
         return x, y[: self.m], st.value, it.value
 
+    # checkpoint / resume
+    def get_state(self) -> bytes:
+        need = C.c_size_t(0)
+        _check(lib().pdlp_get_state(self.h, None, 0, C.byref(need)))
+        buf = (C.c_char * need.value)()
+        _check(lib().pdlp_get_state(self.h, buf, need.value, C.byref(need)))
+        return bytes(buf)
+
+    def set_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib().pdlp_set_state(self.h, buf, len(blob)))
+
+    def resume(self):
+        """Continues a begun or loaded solve to its end: (x, y, status, iters)."""
+        x = np.empty(self.n)
+        y = np.empty(max(self.m, 1))
+        st = C.c_int(-9)
+        it = C.c_int64(0)
+        _check(lib().pdlp_resume(self.h, _ptr(x), _ptr(y), C.byref(st), C.byref(it)))
+        return x, y[: self.m], st.value, it.value
+
     def time_kernels(self, n_periods):
         k = lib().pdlp_kernel_count()
         ms = np.zeros(k)
@@ -390,6 +456,11 @@ class Solver:
         v = np.zeros(max(self.nnz, 1))
         _check(lib().pdlp_get_scaling(self.h, _ptr(D1), _ptr(D2), _ptr(v)))
         return D1[: self.m], D2, v[: self.nnz]
+
+    def layout(self) -> dict:
+        info = pdlp_layout_info()
+        _check(lib().pdlp_get_layout(self.h, C.byref(info)))
+        return {f: int(getattr(info, f)) for f, _ in pdlp_layout_info._fields_ if f != "pad_"}
 
     @property
     def stream(self) -> int:
