@@ -176,7 +176,7 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(name: str, seed: int = 0, scale: float = 1.0):
+def make_workload(name: str, seed: int = 0, scale: float = 1.0, permute: int = -1):
     import lpgen
 
     if name == "large":
@@ -184,6 +184,9 @@ def make_workload(name: str, seed: int = 0, scale: float = 1.0):
         lp = lpgen.large_lp(seed, m=m, n=n, nnz=nnz)
         desc = ("planted LP m=%d (40%% eq) n=%d nnz=%d, Zipf(1.5) row lengths (max %d), lognormal(0,2) values, "
                 "bounds 50%% [0,inf) 30%% [l,u] 20%% free" % (m, n, lp.nnz, lp.meta["max_row"]))
+        if permute >= 0:
+            lp = lpgen.permuted(lp, permute)
+            desc += ", rows and columns permuted (seed %d)" % permute
     elif name == "tiny":
         lp = lpgen.tiny_lp(seed)
         desc = "planted LP m=200 (100 eq) n=500 nnz=%d, 2%% density, N(0,1), 0<=x<=10" % lp.nnz
@@ -262,7 +265,7 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
-    lp, desc = make_workload(args.workload, seed=args.seed, scale=args.lp_scale)
+    lp, desc = make_workload(args.workload, seed=args.seed, scale=args.lp_scale, permute=args.permute_seed)
 
     def timed(k):
         t = time.perf_counter()
@@ -572,6 +575,8 @@ def main():
     ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per time-to-tolerance solve (s)")
     ap.add_argument("--ttt-tols", default="1e-4", help="comma-separated tolerances of the time-to-tolerance solves")
     ap.add_argument("--seed", type=int, default=0, help="generator seed of the large / tiny workload")
+    ap.add_argument("--permute-seed", type=int, default=-1,
+                    help="large workload: the same LP with rows (within their group) and columns permuted")
     ap.add_argument("--lp-scale", type=float, default=1.0,
                     help="large workload: m, n and nnz scaled by this factor (1 = the 1e6 x 2e6 LP)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
@@ -611,7 +616,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
 
-    lp, desc = make_workload(args.workload, seed=args.seed, scale=args.lp_scale)
+    lp, desc = make_workload(args.workload, seed=args.seed, scale=args.lp_scale, permute=args.permute_seed)
     stream = torch.cuda.Stream()
     solver = P.Solver(lp, stream=stream.cuda_stream, value_bits=args.value_bits)
     period = P.pdlp_default_params().check_period

@@ -132,9 +132,11 @@ void pdlp_default_params(pdlp_params *p);
 
 /* Builds a solver for the LP: validates the CSR (row_ptr[0] = 0,
  * non-decreasing, 0 <= col_idx < n, finite values / c / q, no NaN bounds,
- * l <= u, l != +inf, u != -inf), copies everything to the GPU, builds K' and
- * the SpMV tile schedules, and runs the Sec. 2.2 Ruiz + Pock-Chambolle
- * scaling on the device.
+ * l <= u, l != +inf, u != -inf), copies everything to the GPU, builds K',
+ * runs the Sec. 2.2 Ruiz + Pock-Chambolle scaling on the device, and stores
+ * the scaled K and K' a second time in the sliced-ELL layout the iteration
+ * reads (rows renumbered by length; see pdlp_get_layout).  The sliced-ELL
+ * copy needs fewer than 2^31 stored entries (padding included).
  *   m >= 0 rows, n >= 1 columns, 0 <= n_eq <= m, nnz = row_ptr[m] < 2^31.
  *   c: n, row_ptr: m+1, col_idx / val: nnz (int32 / float64), q: m, l / u: n.
  * Errors: PDLP_ERR_INVALID (bad input; *out untouched), PDLP_ERR_CUDA,
@@ -176,6 +178,21 @@ int pdlp_solve(pdlp_solver *s, double tol, int64_t max_iter, double *x_out, doub
 int pdlp_create_device(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const double *c,
                        const int32_t *row_ptr, const int32_t *col_idx, const double *val, const double *q,
                        const double *l, const double *u, const pdlp_params *params, void *stream);
+
+/* QP extension (the paper's introduction names the extension of the method
+ * to quadratic programs; this is the case of a diagonal Hessian): from the
+ * next solve on, the objective is x'Qx/2 + c'x with Q = diag(qdiag), qdiag a
+ * HOST array of n finite, non-negative entries in the original column order
+ * (copied; NULL returns to the LP).  The primal step becomes the exact
+ * proximal step x' = proj_X((x - tau (c - K'y)) / (1 + tau Q_jj)), the KKT
+ * error and Sec. 4.1 termination use the objective's gradient c + Qx in the
+ * reduced cost and the QP's objectives (primal c'x + x'Qx/2, dual
+ * q'y + l'lambda+ - u'lambda- - x'Qx/2), Q is scaled with the columns
+ * (D2 Q D2), and infeasibility detection is off (its certificates are the
+ * LP's).  Everything else (Algorithms 1-2, restarts, primal weight) is
+ * unchanged.  Errors: PDLP_ERR_INVALID for a null solver or a negative or
+ * non-finite entry; PDLP_ERR_CUDA. */
+int pdlp_set_quadratic(pdlp_solver *s, const double *qdiag);
 
 /* As pdlp_solve but starting from (x0, y0) given in the ORIGINAL space
  * (host arrays of n and m; either may be NULL = zeros).  The point is used as

@@ -43,6 +43,7 @@ __all__ = [
     "batch_lps",
     "batch_lp",
     "planted_qp",
+    "permuted",
     "infeasible_lp",
 ]
 
@@ -457,6 +458,32 @@ def planted_qp(lp: LP, seed: int = 0, frac: float = 0.6, lo: float = 0.0, hi: fl
              l=lp.l, u=lp.u, x_star=lp.x_star, y_star=lp.y_star, lam_star=lp.lam_star, obj_star=obj,
              meta=dict(lp.meta, qp=True, qp_seed=seed), qdiag=qd)
     return out
+
+
+def permuted(lp: LP, seed: int) -> LP:
+    """The same LP with its columns permuted and its rows permuted within the
+    equality and the ">=" groups (and the planted pair with them): another
+    summation order for every solver, nothing else changed."""
+    rng = np.random.default_rng([0x9E57, seed])
+    pc = rng.permutation(lp.n)
+    pr = np.concatenate([rng.permutation(lp.n_eq), lp.n_eq + rng.permutation(lp.m - lp.n_eq)])
+    inv_c = np.empty(lp.n, dtype=np.int64)
+    inv_c[pc] = np.arange(lp.n)
+    lens = np.diff(lp.row_ptr)[pr]
+    row_ptr = np.zeros(lp.m + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    starts = np.asarray(lp.row_ptr)[pr]
+    src = np.repeat(starts - row_ptr[:-1], lens) + np.arange(int(row_ptr[-1]))
+    cols = inv_c[np.asarray(lp.col_idx)[src]]
+    vals = np.asarray(lp.val)[src]
+    rows = np.repeat(np.arange(lp.m), lens)
+    order = np.lexsort((cols, rows))  # columns increasing inside each row
+    return LP(m=lp.m, n=lp.n, n_eq=lp.n_eq, c=lp.c[pc], row_ptr=row_ptr.astype(np.int32),
+              col_idx=cols[order].astype(np.int32), val=vals[order], q=lp.q[pr], l=lp.l[pc], u=lp.u[pc],
+              x_star=None if lp.x_star is None else lp.x_star[pc],
+              y_star=None if lp.y_star is None else lp.y_star[pr],
+              lam_star=None if lp.lam_star is None else lp.lam_star[pc], obj_star=lp.obj_star,
+              meta=dict(lp.meta, permuted=seed), qdiag=None if lp.qdiag is None else lp.qdiag[pc])
 
 
 # ----------------------------------------------------------------------------

@@ -240,9 +240,13 @@ struct TeamState {
 constexpr int TEAM = 4;                 // CTAs per team
 constexpr int BACK_CTAS = 16;           // CTAs that start from the small end of the queue
 constexpr long long TEAM_MIN_NNZ = 32768;  // LPs at least this large are solved by a team
-// lanes-per-row rule of an LP solved by one CTA: the smallest power of two G
-// with (mean row length) / G <= SOLO_TARGET
-constexpr double SOLO_TARGET = 8.0;
+// lanes-per-row rule of an LP solved by one CTA: SOLO_FILL = false: the
+// smallest power of two G with (mean row length) / G <= SOLO_TARGET;
+// SOLO_FILL = true: the largest power of two G <= 32 with rows * G <= the
+// CTA's threads (one round of rows fills the CTA), at most the rule's G for
+// SOLO_TARGET = 1
+constexpr double SOLO_TARGET = 4.0;
+constexpr bool SOLO_FILL = false;
 constexpr unsigned long long TEAM_WAIT_NS = 2000000000ull;
 
 // An LP solved by TEAM CTAs (one per SM): rows and vector entries are dealt
@@ -1241,6 +1245,14 @@ int lanes_for(double mean_len, double target) {
   return g;
 }
 
+// the fixed lanes-per-row rule of an LP solved by one CTA (SOLO_FILL)
+int solo_lanes(int rows, double mean_len) {
+  if (!SOLO_FILL) return lanes_for(mean_len, SOLO_TARGET);
+  int g = 1;
+  while (g < 32 && (long long)rows * (2 * g) <= NTB) g <<= 1;
+  return std::min(g, lanes_for(mean_len, 1.0));
+}
+
 void free_batch(pdlp_batch *b) {
   if (!b) return;
   if (b->gexec) cudaGraphExecDestroy(b->gexec);
@@ -1519,8 +1531,8 @@ int pdlp_batch_create(pdlp_batch **out, int32_t count, const pdlp_lp *lps, const
     team[i] = nnz >= (double)TEAM_MIN_NNZ;
     // a team's rows may take any tuned G (S from the t = 4 rule); an LP on
     // one CTA keeps the fixed rule t = SOLO_TARGET (S = G: the plain order)
-    I.sk = lanes_for(mean_k[i], team[i] ? 4.0 : SOLO_TARGET);
-    I.st = lanes_for(mean_t[i], team[i] ? 4.0 : SOLO_TARGET);
+    I.sk = team[i] ? lanes_for(mean_k[i], 4.0) : solo_lanes(I.m, mean_k[i]);
+    I.st = team[i] ? lanes_for(mean_t[i], 4.0) : solo_lanes(I.n, mean_t[i]);
   }
   const double cands[3] = {4.0, 8.0, 16.0};
   auto lanes_of = [&](int i, double target, int *gk, int *gt) {

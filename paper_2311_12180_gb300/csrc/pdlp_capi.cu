@@ -82,6 +82,8 @@ struct pdlp_solver {
   int32_t *perm_r = nullptr, *perm_c = nullptr;  // internal -> original row / column
   std::vector<int32_t> h_perm_r, h_perm_c;        // the same on the host (state export / import)
   pdlp_layout_info layout{};                      // sliced-ELL shapes of K and K'
+  double *qd = nullptr;                           // QP: scaled Hessian diagonal (internal order), or null
+  std::vector<double> h_qdiag;                    // QP: the caller's diagonal (state fingerprint)
   double *c = nullptr, *q = nullptr, *l = nullptr, *u = nullptr, *l0 = nullptr, *u0 = nullptr;
   int gridA = 1, gridB = 1, gridR1 = 1, gridR2 = 1, gridR3 = 1, gridI = 1;
   int slots = 0;
@@ -159,6 +161,7 @@ void free_solver(pdlp_solver *s) {
     if (e) cudaEventDestroy(e);
   if (s->arena) cudaFree(s->arena);
   if (s->sell_arena) cudaFree(s->sell_arena);
+  if (s->qd) cudaFree(s->qd);
   if (s->h_st) cudaFreeHost(s->h_st);
   if (s->h_poll) cudaFreeHost(s->h_poll);
   if (s->h_scal) cudaFreeHost(s->h_scal);
@@ -692,7 +695,7 @@ int pdlp_begin(pdlp_solver *s, const double *x0, const double *y0, double tol, i
   h.trace_cap = TRACE_CAP;
   h.use_f32 = s->prm.value_bits == 32 ? 1 : 0;
   h.polish = s->prm.f32_polish ? 1 : 0;
-  h.eps_infeas = s->prm.eps_infeas;
+  h.eps_infeas = s->V.qd ? 0.0 : s->prm.eps_infeas;  // the certificates are the LP's
   CK(cudaMemcpyAsync(s->st, s->h_st, sizeof(DevState), cudaMemcpyHostToDevice, st));
   // KKT(z^{0,0}): K'y, Kx and the pieces of eq. (kkt) at the start point
   CK(launch_check_primal(s->KT, V, s->st, s->gridR1, st));
@@ -950,6 +953,7 @@ uint64_t lp_fingerprint(const pdlp_solver *s) {
   const double sc[4] = {s->q_norm, s->c_norm, s->eta_hat0, s->omega0};
   mix(sc, sizeof(sc));
   mix(&s->n_eq, sizeof(s->n_eq));
+  mix(s->h_qdiag.data(), 8 * s->h_qdiag.size());
   return h;
 }
 
@@ -1051,6 +1055,39 @@ int pdlp_set_state(pdlp_solver *s, const void *buf, size_t bytes) {
   s->have_result = false;
   s->last_status = d.status;
   s->t0 = now_ms();
+  return PDLP_OK;
+}
+
+int pdlp_set_quadratic(pdlp_solver *s, const double *qdiag) {
+  g_err.clear();
+  if (!s) return fail(PDLP_ERR_INVALID, "solver is NULL");
+  if (qdiag)
+    for (int32_t j = 0; j < s->n; ++j)
+      if (!std::isfinite(qdiag[j]) || qdiag[j] < 0.0)
+        return fail(PDLP_ERR_INVALID, "pdlp_set_quadratic: need finite, non-negative diagonal entries (variable " +
+                                          std::to_string(j) + ")");
+  CK(cudaSetDevice(s->device));
+  CK(cudaStreamSynchronize(s->stream));
+  // the captured graph holds the kernels' arguments: rebuilt at the next begin
+  if (s->gexec) {
+    cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+  }
+  if (s->graph) {
+    cudaGraphDestroy(s->graph);
+    s->graph = nullptr;
+  }
+  if (!qdiag) {
+    s->V.qd = nullptr;
+    s->h_qdiag.clear();
+    return PDLP_OK;
+  }
+  s->h_qdiag.assign(qdiag, qdiag + s->n);
+  if (!s->qd) CK(cudaMalloc((void **)&s->qd, 8 * (size_t)s->n));
+  CK(cudaMemcpyAsync(s->V.xout, qdiag, 8 * (size_t)s->n, cudaMemcpyHostToDevice, s->stream));
+  CK(setup_qp_diag(s->n, s->perm_c, s->V.D2, s->V.xout, s->qd, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->V.qd = s->qd;
   return PDLP_OK;
 }
 

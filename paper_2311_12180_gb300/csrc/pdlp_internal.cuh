@@ -30,6 +30,14 @@ constexpr int SELL_U_C = 4;
 constexpr bool SELL_PREFETCH = false;
 // CTAs per SM the two-vector check pass over K' is compiled for
 constexpr int CHECK_MINB = 2;
+// CTAs per SM the step kernels are compiled for (registers per thread:
+// 65536 / (256 x this))
+constexpr int STEP_MINB = 4;
+// k_dual: load the next batch of indices and values before the current
+// batch's FMAs (software pipelining of the strided loop)
+constexpr bool SELL_PIPE_D = false;
+// load the warp's next work-item descriptor at the start of the current item
+constexpr bool SELL_NEXT_DESC = false;
 
 // One unit of work for one warp: a slice {first row, rows (1..32), L, off}
 // or a long row {row, -1, length, off}.
@@ -131,6 +139,9 @@ struct Vecs {
   // internal -> original row of K (m) and column (n); every vector above is
   // in the internal order, k_output writes the original order
   const int32_t *perm_r, *perm_c;
+  // QP extension: the scaled diagonal D2 Q D2 of the objective's Hessian
+  // (n, internal order), or null for an LP
+  const double *qd;
 };
 
 // ---- kernel launchers (pdlp_kernels.cu) ----

@@ -155,11 +155,49 @@ __device__ __forceinline__ double widen(float v) { return f2d(v); }
 // stride: acc[a] += val * xs[a][col] in stride order (FMA), padding (column
 // -1) skipped.  U strides are loaded (streaming, coalesced across the
 // warp) before their gathers are issued, and all gathers before the FMAs.
-template <int U, typename VT, int NV, bool SCALED>
+template <int U, typename VT, int NV, bool SCALED, bool PIPE = false>
 __device__ __forceinline__ void strided_dot(const int32_t *__restrict__ ip, const VT *__restrict__ vp, int cnt,
                                             const double *const (&xs)[NV], const double (&sc)[NV],
                                             double (&acc)[NV]) {
   int k = 0;
+  if (PIPE && cnt >= U) {
+    // batch k's indices and values are in registers when its gathers issue;
+    // batch k + 1's loads go out before batch k's FMAs
+    int c[U];
+    VT v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = __ldcs(ip + 32 * u);
+      v[u] = __ldcs(vp + 32 * u);
+    }
+    for (; k + U <= cnt; k += U) {
+      double g[NV][U];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) {
+          const double xv = c[u] >= 0 ? __ldg(xs[a] + c[u]) : 0.0;
+          g[a][u] = SCALED ? sc[a] * xv : xv;
+        }
+      const bool more = k + 2 * U <= cnt;
+      int cn[U];
+      VT vn[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        cn[u] = more ? __ldcs(ip + 32 * (k + U + u)) : -1;
+        vn[u] = more ? __ldcs(vp + 32 * (k + U + u)) : VT(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int a = 0; a < NV; ++a) acc[a] = fma(widen(v[u]), g[a][u], acc[a]);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        c[u] = cn[u];
+        v[u] = vn[u];
+      }
+    }
+  }
   for (; k + U <= cnt; k += U) {
     int c[U];
     VT v[U];
@@ -219,8 +257,9 @@ __device__ __forceinline__ double bfly(double a, double b, int off, int lane) {
 template <int NV>
 struct LongRows {
   double buf[5][NV];
-  int t;       // rows in the current batch (warp-uniform)
-  int *rows;   // this warp's 32 row slots in shared memory
+  int t;        // rows in the current batch (warp-uniform)
+  int *rows;    // this warp's 32 row slots in shared memory
+  double *tot;  // this warp's 32 x NV totals in shared memory (partial batch)
 };
 
 template <int NV, class Epi>
@@ -285,7 +324,9 @@ __device__ __forceinline__ void long_push(LongRows<NV> &lr, const double (&p)[NV
 // (present when bit k of t is set) holds slots [t & ~(2^(k+1) - 1), +2^k)
 // after k butterfly levels, lane l carrying a partial of the block's slot
 // rev_k(l >> (5 - k)); the remaining 5 - k levels are a plain xor reduction,
-// after which the first lane of every group of 32 >> k finishes its row.
+// after which the first lane of every group of 32 >> k holds its row's
+// total.  The totals go through shared memory so that lane s finishes slot
+// s: one epilogue (one round of operand loads) for the whole batch.
 template <int NV, class Epi>
 __device__ __forceinline__ void long_flush(LongRows<NV> &lr, Epi &ep) {
   const int lane = threadIdx.x & 31, t = lr.t;
@@ -303,10 +344,18 @@ __device__ __forceinline__ void long_flush(LongRows<NV> &lr, Epi &ep) {
       for (int a = 0; a < NV; ++a) v[a] += __shfl_xor_sync(0xffffffffu, v[a], off);
     if ((lane & ((32 >> k) - 1)) == 0) {
       const int slot = start + (k ? (int)(__brev((unsigned)(lane >> (5 - k))) >> (32 - k)) : 0);
-      const int r = lr.rows[slot];
-      ep.prefetch(r);
-      ep.finish(r, v);
+#pragma unroll
+      for (int a = 0; a < NV; ++a) lr.tot[slot * NV + a] = v[a];
     }
+  }
+  __syncwarp();
+  if (lane < t) {
+    const int r = lr.rows[lane];
+    double v[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) v[a] = lr.tot[lane * NV + a];
+    ep.prefetch(r);
+    ep.finish(r, v);
   }
   __syncwarp();
   lr.t = 0;
@@ -317,33 +366,38 @@ __device__ __forceinline__ void long_flush(LongRows<NV> &lr, Epi &ep) {
 // vector a are multiplied by sc[a] (the epoch average (1/W) sum).  Warp w of
 // the grid takes items w, 2G - 1 - w, 2G + w, ... of the schedule (G warps):
 // a snake over the cost-sorted items, so every warp gets about the same work.
-template <int U, typename VT, int NV, bool SCALED, class Epi>
+template <int U, typename VT, int NV, bool SCALED, class Epi, bool PIPE = false>
 __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict__ val,
                                           const double *const (&xs)[NV], const double (&sc)[NV], Epi &ep,
-                                          int *warp_rows) {
+                                          int *warp_rows, double *warp_tot) {
   const int lane = threadIdx.x & 31;
   const int nw = (int)((gridDim.x * (unsigned)NT) >> 5);
   const int gw = (int)((blockIdx.x * (unsigned)NT + threadIdx.x) >> 5);
   LongRows<NV> lr;
   lr.t = 0;
   lr.rows = warp_rows;
-  for (int b = 0;; ++b) {
+  lr.tot = warp_tot;
+  // the warp's b-th item of the snake order (-1: none)
+  auto item_of = [&](int b) -> long long {
     const long long first = (long long)b * nw;
-    if (first >= A.nitems) break;
+    if (first >= A.nitems) return -1;
     const long long it = first + ((b & 1) ? nw - 1 - gw : gw);
-    if (it >= A.nitems) continue;
-    const int4 d = __ldg(A.items + it);
+    return it < A.nitems ? it : -1;
+  };
+  long long it = item_of(0);
+  int4 d = it >= 0 ? __ldg(A.items + it) : make_int4(0, 0, 0, 0);
+  for (int b = 0; it >= 0; ++b) {
+    // with SELL_NEXT_DESC the next item's descriptor is loaded while this
+    // item runs (its latency hidden, four more live registers)
+    const long long itn = item_of(b + 1);
+    int4 dn = make_int4(0, 0, 0, 0);
+    if (SELL_NEXT_DESC && itn >= 0) dn = __ldg(A.items + itn);
     if (SELL_PREFETCH && lane == 0) {
       // the rest of this item, and the warp's next item, stream into L2
       // while this one's first loads and gathers are in flight
       const int nstr = d.y > 0 ? d.z : (d.z + 31) >> 5;
       if (nstr > U) prefetch_item(A, val, d.w + 32 * U, 32 * (nstr - U));
-      const long long nb = first + nw;
-      const long long itn = nb + (((b + 1) & 1) ? nw - 1 - gw : gw);
-      if (nb < A.nitems && itn < A.nitems) {
-        const int4 dn = __ldg(A.items + itn);
-        prefetch_item(A, val, dn.w, 32 * (dn.y > 0 ? dn.z : (dn.z + 31) >> 5));
-      }
+      if (SELL_NEXT_DESC && itn >= 0) prefetch_item(A, val, dn.w, 32 * (dn.y > 0 ? dn.z : (dn.z + 31) >> 5));
     }
     double acc[NV];
 #pragma unroll
@@ -352,34 +406,44 @@ __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict
       const bool has = lane < d.y;
       const int row = d.x + lane;
       if (has) ep.prefetch(row);
-      strided_dot<U, VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, d.z, xs, sc, acc);
+      strided_dot<U, VT, NV, SCALED, PIPE>(A.idx + d.w + lane, val + d.w + lane, d.z, xs, sc, acc);
       if (has) ep.finish(row, acc);
     } else {  // long row: the whole warp
-      strided_dot<U, VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, (d.z + 31) >> 5, xs, sc, acc);
+      strided_dot<U, VT, NV, SCALED, PIPE>(A.idx + d.w + lane, val + d.w + lane, (d.z + 31) >> 5, xs, sc, acc);
       long_push(lr, acc, d.x, ep);
     }
+    if (!SELL_NEXT_DESC && itn >= 0) dn = __ldg(A.items + itn);
+    it = itn;
+    d = dn;
   }
   if (lr.t > 0) long_flush(lr, ep);
 }
 
 // ---------------------------------------------------------------- primal step
 
+// QP: qd (the scaled diagonal of Q) non-null, and the primal step is the
+// exact proximal step of x'Qx/2 + (c - K'y)'x over X, coordinate by
+// coordinate: x' = proj_X((x - tau (c - g)) / (1 + tau Q_jj)).
+template <bool QP>
 struct PrimalEpi {
   const double *__restrict__ c, *__restrict__ l, *__restrict__ u, *__restrict__ x, *__restrict__ sx;
+  const double *__restrict__ qd;
   double *__restrict__ g, *__restrict__ xn, *__restrict__ sxn;
   double tau, eta, dx2;
-  double pc, pl, pu, px, psx;
+  double pc, pl, pu, px, psx, pq;
   __device__ __forceinline__ void prefetch(int j) {
     pc = c[j];
     pl = l[j];
     pu = u[j];
     px = x[j];
     psx = sx[j];
+    if (QP) pq = qd[j];
   }
   __device__ __forceinline__ void finish(int j, const double (&gs)[1]) { apply(j, gs[0], true); }
   __device__ __forceinline__ void apply(int j, double gj, bool store_g) {
     if (store_g) g[j] = gj;
-    const double v = clamp_bits(fma(-tau, pc - gj, px), pl, pu);
+    const double v = QP ? clamp_bits(fma(-tau, pc - gj, px) / fma(tau, pq, 1.0), pl, pu)
+                        : clamp_bits(fma(-tau, pc - gj, px), pl, pu);
     xn[j] = v;
     sxn[j] = fma(eta, v, psx);
     const double d = v - px;
@@ -387,17 +451,16 @@ struct PrimalEpi {
   }
 };
 
-// 64 registers: four CTAs (32 warps) per SM for gathers in flight
-__global__ void __launch_bounds__(NT, 4) k_primal(SellMat KT, Vecs V, DevState *__restrict__ st) {
-  __shared__ double s_red[16 * NW];
-  __shared__ int s_rows[NW][32];
-  if (st->status != ST_RUNNING || st->check_pending) return;
+template <bool QP>
+__device__ __forceinline__ void primal_step(const SellMat &KT, const Vecs &V, const DevState *st, double *s_red,
+                                            int (*s_rows)[32], double (*s_tot)[64]) {
   const int cur = st->cur, nxt = cur ^ 1, need_g = st->need_g, f32 = st->use_f32;
   const double eta = st->eta, omega = st->omega;
-  PrimalEpi ep;
+  PrimalEpi<QP> ep;
   ep.c = V.c;
   ep.l = V.l;
   ep.u = V.u;
+  ep.qd = V.qd;
   ep.x = V.x[cur];
   ep.sx = V.sx[cur];
   ep.g = V.g;
@@ -410,9 +473,9 @@ __global__ void __launch_bounds__(NT, 4) k_primal(SellMat KT, Vecs V, DevState *
     const double *const xs[1] = {V.y[cur]};
     const double sc[1] = {1.0};
     if (f32)
-      spmv_sell<SELL_U_P, float, 1, false>(KT, KT.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+      spmv_sell<SELL_U_P, float, 1, false>(KT, KT.val32, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
     else
-      spmv_sell<SELL_U_P, double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+      spmv_sell<SELL_U_P, double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   } else {
     // rejected trial: g = K'y is unchanged, only the projection reruns
     for (int j = blockIdx.x * NT + threadIdx.x; j < V.n; j += gridDim.x * NT) {
@@ -423,6 +486,25 @@ __global__ void __launch_bounds__(NT, 4) k_primal(SellMat KT, Vecs V, DevState *
   double acc[1] = {ep.dx2};
   block_sum<1>(acc, s_red);
   if (threadIdx.x == 0) V.partA[blockIdx.x] = acc[0];
+}
+
+// STEP_MINB CTAs per SM: as many warps (gathers in flight) as the registers allow
+__global__ void __launch_bounds__(NT, STEP_MINB) k_primal(SellMat KT, Vecs V, DevState *__restrict__ st) {
+  __shared__ double s_red[16 * NW];
+  __shared__ int s_rows[NW][32];
+  __shared__ double s_tot[NW][64];
+  if (st->status != ST_RUNNING || st->check_pending) return;
+  primal_step<false>(KT, V, st, s_red, s_rows, s_tot);
+}
+
+// The QP's primal step (V.qd set), a kernel of its own so that the LP's
+// keeps its register budget.
+__global__ void __launch_bounds__(NT, STEP_MINB) k_primal_qp(SellMat KT, Vecs V, DevState *__restrict__ st) {
+  __shared__ double s_red[16 * NW];
+  __shared__ int s_rows[NW][32];
+  __shared__ double s_tot[NW][64];
+  if (st->status != ST_RUNNING || st->check_pending) return;
+  primal_step<true>(KT, V, st, s_red, s_rows, s_tot);
 }
 
 // ---------------------------------------------------------------- dual step + Algorithm 2 test
@@ -486,10 +568,11 @@ __device__ void step_test(DevState *st, const Vecs &V, double dx2, double dy2, d
   }
 }
 
-__global__ void __launch_bounds__(NT, 4) k_dual(SellMat K, Vecs V, DevState *__restrict__ st) {
+__global__ void __launch_bounds__(NT, STEP_MINB) k_dual(SellMat K, Vecs V, DevState *__restrict__ st) {
   __shared__ double s_red[16 * NW];
   __shared__ int s_flag;
   __shared__ int s_rows[NW][32];
+  __shared__ double s_tot[NW][64];
   if (st->status != ST_RUNNING || st->check_pending) return;
   const int cur = st->cur, nxt = cur ^ 1, f32 = st->use_f32;
   const double eta = st->eta, omega = st->omega;
@@ -509,9 +592,9 @@ __global__ void __launch_bounds__(NT, 4) k_dual(SellMat K, Vecs V, DevState *__r
   const double *const xs[1] = {V.x[nxt]};
   const double sc[1] = {1.0};
   if (f32)
-    spmv_sell<SELL_U_D, float, 1, false>(K, K.val32, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_D, float, 1, false, DualEpi, SELL_PIPE_D>(K, K.val32, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   else
-    spmv_sell<SELL_U_D, double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_D, double, 1, false, DualEpi, SELL_PIPE_D>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   double acc[2] = {ep.dy2, ep.cross};
   double tot[2];
   if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], s_red, &s_flag, tot)) return;
@@ -531,9 +614,12 @@ __device__ __forceinline__ double proj_lambda(double d, double l, double u) {
 }
 
 // Dual-side pieces of eq. (kkt) / Sec. 4.1 for one variable.
+// With qp (Q_jj = qdj), the objective's gradient c + Qx replaces c in the
+// reduced cost, and x'Qx/2 is added to the primal objective c'x and taken
+// from the dual one (the QP's objectives).
 __device__ __forceinline__ void dual_piece(double c, double g, double l, double u, double d2, double x,
-                                           double *acc) {
-  const double d = c - g;
+                                           double *acc, bool qp = false, double qdj = 0.0) {
+  const double d = qp ? fma(qdj, x, c) - g : c - g;
   const double lam = proj_lambda(d, l, u);
   const double r = d - lam;
   acc[0] = fma(r, r, acc[0]);
@@ -542,6 +628,11 @@ __device__ __forceinline__ void dual_piece(double c, double g, double l, double 
   acc[2] = fma(c, x, acc[2]);
   if (lam > 0.0) acc[3] = fma(l, lam, acc[3]);
   if (lam < 0.0) acc[3] = acc[3] - u * (-lam);
+  if (qp) {
+    const double h = 0.5 * qdj * x * x;
+    acc[2] += h;
+    acc[3] -= h;
+  }
 }
 
 // Epilogue of the dual-side check pass.  kind 0: start point (sums = {K'y});
@@ -552,10 +643,11 @@ struct CheckPrimalEpi {
       *__restrict__ sx;
   double *__restrict__ g, *__restrict__ gbar;
   double *__restrict__ g0, *__restrict__ gprev;  // kept for infeasibility detection when keep
+  const double *__restrict__ qd;                 // QP: the scaled diagonal of Q (else null)
   double invW;
   int kind, keep;
   double acc[NV_R1];
-  double pc, pl, pu, pd2, px, psx, pg;
+  double pc, pl, pu, pd2, px, psx, pg, pq;
   __device__ __forceinline__ void prefetch(int j) {
     pc = c[j];
     pl = l[j];
@@ -564,6 +656,7 @@ struct CheckPrimalEpi {
     px = x[j];
     psx = kind ? sx[j] : 0.0;
     pg = (kind == 2 || (kind == 1 && keep)) ? g[j] : 0.0;
+    pq = qd ? qd[j] : 0.0;
   }
   template <int NV>
   __device__ __forceinline__ void finish(int j, const double (&s)[NV]) {
@@ -580,10 +673,11 @@ struct CheckPrimalEpi {
     } else {
       gb = s[0];
     }
-    dual_piece(pc, gj, pl, pu, pd2, px, acc);
+    const bool qp = qd != nullptr;
+    dual_piece(pc, gj, pl, pu, pd2, px, acc, qp, pq);
     if (kind) {
       gbar[j] = gb;
-      dual_piece(pc, gb, pl, pu, pd2, invW * psx, acc + 4);
+      dual_piece(pc, gb, pl, pu, pd2, invW * psx, acc + 4, qp, pq);
     }
   }
 };
@@ -591,6 +685,7 @@ struct CheckPrimalEpi {
 __global__ void __launch_bounds__(NT, CHECK_MINB) k_check_primal(SellMat KT, Vecs V, DevState *__restrict__ st) {
   __shared__ double s_red[16 * NW];
   __shared__ int s_rows[NW][32];
+  __shared__ double s_tot[NW][64];
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur, need_g = st->need_g;
   const bool check = mode == MODE_CHECK;
@@ -605,6 +700,7 @@ __global__ void __launch_bounds__(NT, CHECK_MINB) k_check_primal(SellMat KT, Vec
   ep.gbar = V.gbar;
   ep.g0 = V.g0;
   ep.gprev = V.gprev;
+  ep.qd = V.qd;
   ep.invW = check ? 1.0 / st->W : 0.0;
   ep.kind = !check ? 0 : (need_g ? 1 : 2);
   ep.keep = st->eps_infeas > 0.0;
@@ -613,15 +709,15 @@ __global__ void __launch_bounds__(NT, CHECK_MINB) k_check_primal(SellMat KT, Vec
   if (ep.kind == 0) {
     const double *const xs[1] = {V.y[cur]};
     const double sc[1] = {1.0};
-    spmv_sell<SELL_U_C, double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, false>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   } else if (ep.kind == 1) {
     const double *const xs[2] = {V.y[cur], V.sy[cur]};
     const double sc[2] = {1.0, ep.invW};
-    spmv_sell<SELL_U_C, double, 2, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 2, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   } else {
     const double *const xs[1] = {V.sy[cur]};
     const double sc[1] = {ep.invW};
-    spmv_sell<SELL_U_C, double, 1, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, true>(KT, KT.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   }
   block_sum<NV_R1>(ep.acc, s_red);
   if (threadIdx.x == 0) {
@@ -820,6 +916,7 @@ __global__ void __launch_bounds__(NT) k_check_dual(SellMat K, Vecs V, DevState *
   __shared__ double s_red[16 * NW];
   __shared__ int s_flag;
   __shared__ int s_rows[NW][32];
+  __shared__ double s_tot[NW][64];
   if (st->status != ST_RUNNING || !st->check_pending) return;
   const int mode = st->mode, cur = st->cur;
   const bool check = mode == MODE_CHECK;
@@ -840,11 +937,11 @@ __global__ void __launch_bounds__(NT) k_check_dual(SellMat K, Vecs V, DevState *
   if (!check) {
     const double *const xs[1] = {V.x[cur]};
     const double sc[1] = {1.0};
-    spmv_sell<SELL_U_C, double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, false>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   } else {
     const double *const xs[1] = {V.sx[cur]};
     const double sc[1] = {ep.invW};
-    spmv_sell<SELL_U_C, double, 1, true>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_C, double, 1, true>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   }
   double tot[NV_R2];
   if (!grid_finish<NV_R2>(ep.acc, V.partR2, &st->cnt[CNT_R2], s_red, &s_flag, tot)) return;
@@ -1069,7 +1166,10 @@ int occupancy_grid(int kc, int num_sms) {
 
 cudaError_t kernels_init() { return cudaSuccess; }
 cudaError_t launch_primal(const SellMat &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
-  k_primal<<<grid, NT, 0, s>>>(KT, V, st);
+  if (V.qd)
+    k_primal_qp<<<grid, NT, 0, s>>>(KT, V, st);
+  else
+    k_primal<<<grid, NT, 0, s>>>(KT, V, st);
   return cudaGetLastError();
 }
 cudaError_t launch_dual(const SellMat &K, const Vecs &V, DevState *st, int grid, cudaStream_t s) {

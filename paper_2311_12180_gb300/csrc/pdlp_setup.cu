@@ -597,6 +597,13 @@ __global__ void k_check_entries(int64_t nnz, const int32_t *__restrict__ idx, co
   }
 }
 
+// QP: qd[j] = (D2[j] * q0[perm_c[j]]) * D2[j], the internal-order diagonal of
+// D2 Q D2 (D2 internal, q0 the caller's diagonal in the original order)
+__global__ void k_qp_diag(int32_t n, const int32_t *__restrict__ perm_c, const double *__restrict__ D2,
+                          const double *__restrict__ q0, double *__restrict__ qd) {
+  for (int32_t j = blockIdx.x * ST + threadIdx.x; j < n; j += gridDim.x * ST) qd[j] = D2[j] * q0[perm_c[j]] * D2[j];
+}
+
 // dst[r] = src[perm[r]]
 __global__ void k_permute(int32_t count, const int32_t *__restrict__ perm, const double *__restrict__ src,
                           double *__restrict__ dst) {
@@ -653,6 +660,12 @@ cudaError_t setup_check_entries(int64_t nnz, const int32_t *idx, const double *v
   }
   const cudaError_t ef = cudaFreeAsync(d, s);
   return e != cudaSuccess ? e : ef;
+}
+
+cudaError_t setup_qp_diag(int32_t n, const int32_t *perm_c, const double *D2, const double *q0, double *qd,
+                          cudaStream_t s) {
+  k_qp_diag<<<grid_for(n), ST, 0, s>>>(n, perm_c, D2, q0, qd);
+  return cudaGetLastError();
 }
 
 cudaError_t setup_permute(int32_t count, const int32_t *perm, const double *src, double *dst, cudaStream_t s) {

@@ -71,6 +71,10 @@ cudaError_t setup_sell_fill(int32_t rows, int64_t total, const int32_t *perm, co
 // *col_bad = 1 when that entry's column is the fault; waits for the result.
 cudaError_t setup_check_entries(int64_t nnz, const int32_t *idx, const double *val, int32_t n, int64_t *first,
                                 int *col_bad, cudaStream_t s);
+// QP extension: qd[j] = D2[j] q0[perm_c[j]] D2[j] (scaled Hessian diagonal,
+// internal order; q0 in the original order).
+cudaError_t setup_qp_diag(int32_t n, const int32_t *perm_c, const double *D2, const double *q0, double *qd,
+                          cudaStream_t s);
 // dst[r] = src[perm[r]] for r < count (original order -> internal order)
 cudaError_t setup_permute(int32_t count, const int32_t *perm, const double *src, double *dst, cudaStream_t s);
 // Warm start in the internal order: x[j] = x0[perm_c[j]] / D2[j] (0 without

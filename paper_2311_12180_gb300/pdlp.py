@@ -92,7 +92,7 @@ EXPORTS = (
     "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
     "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error", "pdlp_scale_device_noalloc",
     "pdlp_create_device", "pdlp_get_state", "pdlp_set_state", "pdlp_resume", "pdlp_get_layout",
-    "pdlp_probe_rates",
+    "pdlp_probe_rates", "pdlp_set_quadratic",
     "pdlp_batch_create", "pdlp_batch_solve", "pdlp_batch_info", "pdlp_batch_lanes", "pdlp_batch_times", "pdlp_batch_destroy",
     "pdlp_mlp_create", "pdlp_mlp_param_count", "pdlp_mlp_set_params", "pdlp_mlp_get_params", "pdlp_mlp_set_data",
     "pdlp_mlp_train", "pdlp_mlp_predict", "pdlp_mlp_gradients", "pdlp_mlp_stats", "pdlp_mlp_destroy",
@@ -172,6 +172,8 @@ def lib():
     L.pdlp_set_state.restype = C.c_int
     L.pdlp_resume.argtypes = [vp, vp, vp, P(C.c_int), P(i64)]
     L.pdlp_resume.restype = C.c_int
+    L.pdlp_set_quadratic.argtypes = [vp, vp]
+    L.pdlp_set_quadratic.restype = C.c_int
     L.pdlp_get_layout.argtypes = [vp, P(pdlp_layout_info)]
     L.pdlp_get_layout.restype = C.c_int
     L.pdlp_probe_rates.argtypes = [P(d), P(d)]
@@ -368,6 +370,14 @@ class Solver:
             d = device
             self.h = pdlp_create_device(self.m, self.n, self.n_eq, d["c"], d["row_ptr"], d["col_idx"], d["val"],
                                         d["q"], d["l"], d["u"], params=params, stream=stream)
+        qd = getattr(lp, "qdiag", None)
+        if qd is not None:  # a QP (objective x'Qx/2 + c'x, Q = diag(qdiag))
+            self.set_quadratic(qd)
+
+    def set_quadratic(self, qdiag):
+        """pdlp_set_quadratic: Q = diag(qdiag) from the next solve on (None: LP)."""
+        arr = None if qdiag is None else _f64(qdiag, self.n)
+        _check(lib().pdlp_set_quadratic(self.h, _ptr(arr)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -14,3 +14,16 @@ def test_batch_lp_equals_the_member_of_its_batch():
         assert (one.m, one.n, one.n_eq) == (ref.m, ref.n, ref.n_eq)
         for f in ("row_ptr", "col_idx", "val", "c", "q", "l", "u", "x_star", "y_star"):
             assert np.array_equal(getattr(one, f), getattr(ref, f)), f
+
+
+def test_permuted_lp_is_the_same_lp():
+    import oracle
+
+    lp = lpgen.tiny_lp(3)
+    p = lpgen.permuted(lp, 1)
+    assert p.nnz == lp.nnz and np.all(np.diff(p.row_ptr) >= 0)
+    assert sorted(p.val.tolist()) == sorted(lp.val.tolist())
+    t = oracle.kkt_terms(p, p.x_star, p.y_star)  # the planted pair, permuted, is still optimal
+    assert t["rp"] < 1e-12 and t["rd"] < 1e-12 and abs(t["pobj"] - lp.obj_star) < 1e-10 * (1 + abs(lp.obj_star))
+    # equality rows stay first
+    assert p.n_eq == lp.n_eq and np.array_equal(np.sort(p.q[: p.n_eq]), np.sort(lp.q[: lp.n_eq]))
