@@ -59,3 +59,52 @@ def test_warm_start_from_the_solution_is_immediate():
     r = W.solve_with_fallback(lambda i: lpgen.transport_lp(fam, th[i], i), 16, 1e-6, lambda i: sols[i])
     assert np.all(r["status"] == P.OPTIMAL) and r["fallbacks"] == 0
     assert np.all(r["iters"] <= 64)
+
+
+def test_noisy_transport_family_neighbour_x_with_mlp_y():
+    # the 200 x 300 transportation family with N(0, 0.1) cost noise at
+    # reduced counts (2000 training solutions to 1e-6, 200 held out): no
+    # theta -> x regression pays here; the MLP predicts the duals better than
+    # the nearest training solution does, and paired with the neighbour's x
+    # it starts well ahead of cold and level with the neighbour.  Measured on
+    # a GB300 with these seeds: median iterations cold 4512, nearest 4032,
+    # nearest x + MLP y 4096; median y error MLP 0.723, nearest 0.813.
+    fam = lpgen.transport_family(0, sources=200, sinks=300, dim=16, noise=0.1, cost_scale=1.0)
+    n, m = fam.n, fam.m
+    ntr, nte = 2000, 200
+    th_tr, th_te = lpgen.transport_thetas(ntr, 1), lpgen.transport_thetas(nte, 2)
+    T = np.empty((ntr, n + m), np.float32)
+
+    def keep(i, x, y):
+        T[i, :n], T[i, n:] = x, y
+
+    st, _, _, _ = W.solve_many(lambda i: lpgen.transport_lp(fam, th_tr[i], i), ntr, 1e-6, on_solution=keep)
+    assert np.all(st == P.OPTIMAL)
+    net, losses = W.train(th_tr, T, hidden=256, schedule=((900, 1e-3), (450, 3e-4), (150, 1e-4)), batch=256)
+    Yp = net.predict(th_te).astype(np.float64)
+    net.close()
+    near = W.nearest_index(th_tr, th_te)
+
+    def mk(i):
+        return lpgen.transport_lp(fam, th_te[i], 10_000_000 + i)
+
+    Tc = np.empty((nte, n + m))
+
+    def keep_c(i, x, y):
+        Tc[i, :n], Tc[i, n:] = x, y
+
+    st_c, it_c, _, _ = W.solve_many(mk, nte, 1e-6, on_solution=keep_c)
+    nb = W.solve_with_fallback(mk, nte, 1e-6, lambda i: (T[near[i], :n], T[near[i], n:]))
+    hy = W.solve_with_fallback(mk, nte, 1e-6, lambda i: (T[near[i], :n], Yp[i, n:]))
+    assert np.all(st_c == P.OPTIMAL) and np.all(nb["status"] == P.OPTIMAL) and np.all(hy["status"] == P.OPTIMAL)
+
+    def rel_y(Y):
+        return np.median(np.linalg.norm(Y - Tc[:, n:], axis=1) / np.linalg.norm(Tc[:, n:], axis=1))
+
+    ey_mlp, ey_nb = rel_y(Yp[:, n:]), rel_y(T[near][:, n:].astype(np.float64))
+    med_c, med_n, med_h = np.median(it_c), np.median(nb["iters"]), np.median(hy["iters"])
+    print("median iterations: cold %d, nearest %d, nearest x + MLP y %d; y error MLP %.3f nearest %.3f"
+          % (med_c, med_n, med_h, ey_mlp, ey_nb))
+    assert ey_mlp < 0.95 * ey_nb
+    assert med_h <= 0.95 * med_c and med_n <= 0.95 * med_c
+    assert med_h <= 1.05 * med_n
