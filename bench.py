@@ -24,7 +24,8 @@ roofline = the dominant kernel's algorithmic HBM bytes per launch over its
          on the GPU by pdlp_probe_rates, and names the binding one;
 time_to_tol = after the timed region, a solve from zero to each --ttt-tols
          tolerance (default 1e-4): seconds, iterations, objective error
-         against the planted optimum;
+         against the planted optimum (--trace-out FILE writes each of these
+         solves' per-check records as JSON lines);
 cpu_baseline = the FP64 CPU oracle (single thread) on a bounded sample of
          the same LP.
 
@@ -228,6 +229,20 @@ def fp64_warp_instructions(layout: dict, kernel: str) -> float:
     else:
         raise KeyError(kernel)
     return stored / 32.0 + epi * slices + (31 + epi) * ((longs + 31) // 32)
+
+
+def write_trace(path: str, trace, tol: float, recorded: int) -> None:
+    """Appends the check records of one solve (the device ring's, copied
+    once after the solve) to `path` as JSON lines."""
+    import numpy as np
+
+    with open(path, "a") as f:
+        for r in trace:
+            rec = {"tol": tol, "checks_recorded": recorded}
+            for name in trace.dtype.names:
+                v = r[name]
+                rec[name] = int(v) if np.issubdtype(trace.dtype[name], np.integer) else float(v)
+            f.write(json.dumps(rec) + "\n")
 
 
 def cpu_baseline(lp, budget_s: float = 20.0):
@@ -574,6 +589,9 @@ def main():
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-tolerance solves after the timed region")
     ap.add_argument("--ttt-limit", type=float, default=600.0, help="time limit per time-to-tolerance solve (s)")
     ap.add_argument("--ttt-tols", default="1e-4", help="comma-separated tolerances of the time-to-tolerance solves")
+    ap.add_argument("--trace-out", default="", help="append each time-to-tolerance solve's per-check records "
+                                                    "(k, trials, restarts, KKT, omega, step, Sec. 4.1 measures) "
+                                                    "to this file as JSON lines")
     ap.add_argument("--seed", type=int, default=0, help="generator seed of the large / tiny workload")
     ap.add_argument("--permute-seed", type=int, default=-1,
                     help="large workload: the same LP with rows (within their group) and columns permuted")
@@ -719,6 +737,8 @@ def main():
                     "rel_gap": abs(inf["pobj"] - inf["dobj"]) / (1 + abs(inf["pobj"]) + abs(inf["dobj"])),
                     "rel_primal_res": inf["rp_norm"] / (1 + inf["q_norm"]),
                     "rel_dual_res": inf["rd_norm"] / (1 + inf["c_norm"])})
+                if args.trace_out and rank == 0:
+                    write_trace(args.trace_out, s3.trace(), tol, s3.checks_recorded())
 
     if rank != 0:
         if pg is not None:

@@ -115,16 +115,23 @@ typedef struct {
   double ray_obj, ray_res;
 } pdlp_info;
 
-/* One restart / termination check (pdlp_get_trace), values on the scaled LP. */
+/* One restart / termination check that did not end the solve
+ * (pdlp_get_trace): the Sec. 3.4 quantities on the scaled LP and the
+ * Sec. 4.1 measures of the current iterate on the original LP. */
 typedef struct {
-  int64_t k;        /* accepted steps when the check ran */
-  int32_t restart;  /* bit 0: criterion (i), bit 1: (ii), bit 2: (iii); 0 = no restart */
-  int32_t cand_avg; /* 1 if GetRestartCandidate picked the average */
-  double kkt_cur;   /* KKT_omega(current iterate), eq. (kkt) */
-  double kkt_avg;   /* KKT_omega(average iterate) */
-  double kkt_start; /* KKT_omega(z^{n,0}) after the check (recomputed with the new omega) */
-  double omega;     /* primal weight after the check */
-  double eta_hat;   /* next trial step size */
+  int64_t k;          /* accepted steps when the check ran */
+  int64_t attempts;   /* Algorithm 2 trials so far (rejected steps = attempts - k) */
+  int64_t restarts;   /* restarts so far (n in Algorithm 1), this check's included */
+  int32_t restart;    /* bit 0: criterion (i), bit 1: (ii), bit 2: (iii); 0 = no restart */
+  int32_t cand_avg;   /* 1 if GetRestartCandidate picked the average */
+  double kkt_cur;     /* KKT_omega(current iterate), eq. (kkt) */
+  double kkt_avg;     /* KKT_omega(average iterate) */
+  double kkt_start;   /* KKT_omega(z^{n,0}) after the check (recomputed with the new omega) */
+  double omega;       /* primal weight after the check */
+  double eta_hat;     /* next trial step size */
+  double rel_gap;     /* |c'x - dual objective| / (1 + |c'x| + |dual objective|) */
+  double rel_primal;  /* primal residual / (1 + ||q||) */
+  double rel_dual;    /* dual residual / (1 + ||c||) */
 } pdlp_check;
 
 /* Fills *p with the defaults listed above.  p must be non-NULL. */
@@ -249,8 +256,12 @@ int pdlp_time_kernels(pdlp_solver *s, int32_t n_periods, double *ms, int64_t *la
 int32_t pdlp_kernel_count(void);
 const char *pdlp_kernel_name(int32_t i);
 
-/* Reports on the last solve.  info: see pdlp_info.  trace: up to cap check
- * records (in order) and their total count in *count. */
+/* Reports on the last solve.  info: see pdlp_info.  trace: the solver keeps
+ * the records of the last 65536 checks in a device ring buffer (written by
+ * the check kernel, no per-check transfer); pdlp_get_trace copies up to cap
+ * of the retained records, oldest first, into trace and stores the number
+ * of checks recorded since the solve began (which may exceed 65536) in
+ * *count. */
 int pdlp_get_info(const pdlp_solver *s, pdlp_info *info);
 int pdlp_get_trace(const pdlp_solver *s, pdlp_check *trace, int32_t cap, int32_t *count);
 

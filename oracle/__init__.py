@@ -98,6 +98,8 @@ class _Info(C.Structure):
 CHECK_DTYPE = np.dtype(
     [
         ("k", np.int64),
+        ("attempts", np.int64),
+        ("restarts", np.int64),
         ("restart", np.int32),
         ("cand_avg", np.int32),
         ("kkt_cur", np.float64),
@@ -105,6 +107,9 @@ CHECK_DTYPE = np.dtype(
         ("kkt_start", np.float64),
         ("omega", np.float64),
         ("eta_hat", np.float64),
+        ("rel_gap", np.float64),
+        ("rel_primal", np.float64),
+        ("rel_dual", np.float64),
     ]
 )
 

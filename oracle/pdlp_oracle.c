@@ -137,10 +137,15 @@ typedef struct {
 
 typedef struct {
   int64_t k;
+  int64_t attempts; /* Algorithm 2 trials so far */
+  int64_t restarts; /* restarts so far, this check's included */
   int32_t restart;  /* bit0 (i) sufficient, bit1 (ii) necessary, bit2 (iii) artificial */
   int32_t cand_avg; /* 1 if the restart candidate is the average */
   double kkt_cur, kkt_avg, kkt_start;
   double omega, eta_hat;
+  /* Sec. 4.1 relative measures of the current iterate on the original LP:
+   * |pobj - dobj| / (1 + |pobj| + |dobj|), ||rp|| / (1 + ||q||), ||rd|| / (1 + ||c||) */
+  double rel_gap, rel_primal, rel_dual;
 } orc_check;
 
 /* ------------------------------------------------------------------------ */
@@ -813,6 +818,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
       which = 0;
       break;
     }
+    const double rel_gap = fabs(terms[0] - terms[1]) / (1.0 + fabs(terms[0]) + fabs(terms[1]));
+    const double rel_primal = terms[2] / (1.0 + terms[4]), rel_dual = terms[3] / (1.0 + terms[5]);
     if (check_original(lp, &w, w.xb, w.yb, p->tol, terms)) {
       status = ORC_OPTIMAL;
       which = 1;
@@ -908,6 +915,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     if (trace && ntrace < trace_cap) {
       orc_check *r = &trace[ntrace++];
       r->k = k;
+      r->attempts = attempts;
+      r->restarts = restarts;
       r->restart = mask;
       r->cand_avg = cand_avg;
       r->kkt_cur = kc;
@@ -915,6 +924,9 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
       r->kkt_start = kkt_start;
       r->omega = omega;
       r->eta_hat = eta_hat;
+      r->rel_gap = rel_gap;
+      r->rel_primal = rel_primal;
+      r->rel_dual = rel_dual;
     }
   }
 

@@ -888,19 +888,27 @@ int pdlp_get_trace(const pdlp_solver *s, pdlp_check *trace, int32_t cap, int32_t
   CK(cudaSetDevice(s->device));
   const int nt = s->h_st->ntrace;
   if (count) *count = nt;
-  const int ncopy = nt < cap ? nt : cap;
+  // retained: the last TRACE_CAP records, the oldest at index first % TRACE_CAP
+  const int kept = nt < TRACE_CAP ? nt : TRACE_CAP, first = nt - kept;
+  const int ncopy = kept < cap ? kept : cap;
   if (ncopy <= 0) return PDLP_OK;
-  std::vector<TraceRec> tmp(ncopy);
-  CK(cudaMemcpy(tmp.data(), s->V.trace, sizeof(TraceRec) * ncopy, cudaMemcpyDeviceToHost));
+  std::vector<TraceRec> tmp(kept);
+  CK(cudaMemcpy(tmp.data(), s->V.trace, sizeof(TraceRec) * kept, cudaMemcpyDeviceToHost));
   for (int i = 0; i < ncopy; ++i) {
-    trace[i].k = tmp[i].k;
-    trace[i].restart = tmp[i].restart;
-    trace[i].cand_avg = tmp[i].cand_avg;
-    trace[i].kkt_cur = tmp[i].kkt_cur;
-    trace[i].kkt_avg = tmp[i].kkt_avg;
-    trace[i].kkt_start = tmp[i].kkt_start;
-    trace[i].omega = tmp[i].omega;
-    trace[i].eta_hat = tmp[i].eta_hat;
+    const TraceRec &r = tmp[(first + i) % TRACE_CAP];
+    trace[i].k = r.k;
+    trace[i].attempts = r.attempts;
+    trace[i].restarts = r.restarts;
+    trace[i].restart = r.restart;
+    trace[i].cand_avg = r.cand_avg;
+    trace[i].kkt_cur = r.kkt_cur;
+    trace[i].kkt_avg = r.kkt_avg;
+    trace[i].kkt_start = r.kkt_start;
+    trace[i].omega = r.omega;
+    trace[i].eta_hat = r.eta_hat;
+    trace[i].rel_gap = r.rel_gap;
+    trace[i].rel_primal = r.rel_primal;
+    trace[i].rel_dual = r.rel_dual;
   }
   return PDLP_OK;
 }

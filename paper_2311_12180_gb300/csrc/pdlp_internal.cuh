@@ -108,11 +108,16 @@ struct DevState {
   unsigned int cnt[CNT_NUM];
 };
 
+// One check's record in the device ring (trace_cap records, written at
+// ntrace mod trace_cap; ntrace counts every record ever written).
 struct TraceRec {
   long long k;
+  long long attempts;  // Algorithm 2 trials so far (rejections = attempts - k)
+  long long restarts;  // restarts so far, this check's included
   int restart;
   int cand_avg;
   double kkt_cur, kkt_avg, kkt_start, omega, eta_hat;
+  double rel_gap, rel_primal, rel_dual;  // Sec. 4.1 measures of the current iterate, original LP
 };
 
 struct Vecs {

@@ -866,9 +866,11 @@ __device__ void check_decide(DevState *st, TraceRec *trace, const double *p, con
     st->kkt_prev = kcand;
     st->check_pending = 0;
   }
-  if (st->ntrace < st->trace_cap) {
-    TraceRec &r = trace[st->ntrace];
+  {  // the check's record, into the ring
+    TraceRec &r = trace[st->ntrace % st->trace_cap];
     r.k = st->k;
+    r.attempts = st->attempts;
+    r.restarts = st->restarts + (mask ? 1 : 0);
     r.restart = mask;
     r.cand_avg = cand_avg;
     r.kkt_cur = kc;
@@ -876,6 +878,9 @@ __device__ void check_decide(DevState *st, TraceRec *trace, const double *p, con
     r.kkt_start = st->kkt_start;
     r.omega = omega;
     r.eta_hat = st->eta;
+    r.rel_gap = fabs(pc - dc) / (1.0 + fabs(pc) + fabs(dc));
+    r.rel_primal = rpc / (1.0 + qn);
+    r.rel_dual = rdc / (1.0 + cn);
     st->ntrace += 1;
   }
 }
@@ -1096,9 +1101,9 @@ __global__ void __launch_bounds__(NT) k_restart(Vecs V, DevState *__restrict__ s
     st->kkt_prev = k0;
     st->restart_to = 0;
     st->check_pending = 0;
-    if (st->ntrace > 0 && V.trace[st->ntrace - 1].k == st->k) {
-      V.trace[st->ntrace - 1].omega = omega;
-      V.trace[st->ntrace - 1].kkt_start = k0;
+    if (st->ntrace > 0 && V.trace[(st->ntrace - 1) % st->trace_cap].k == st->k) {
+      V.trace[(st->ntrace - 1) % st->trace_cap].omega = omega;
+      V.trace[(st->ntrace - 1) % st->trace_cap].kkt_start = k0;
     }
   }
 }

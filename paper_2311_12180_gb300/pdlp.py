@@ -72,9 +72,14 @@ class pdlp_info(C.Structure):
     ]
 
 
+# check records the device ring keeps (pdlp_get_trace)
+TRACE_RETAINED = 1 << 16
+
 CHECK_DTYPE = np.dtype(
     [
         ("k", np.int64),
+        ("attempts", np.int64),
+        ("restarts", np.int64),
         ("restart", np.int32),
         ("cand_avg", np.int32),
         ("kkt_cur", np.float64),
@@ -82,6 +87,9 @@ CHECK_DTYPE = np.dtype(
         ("kkt_start", np.float64),
         ("omega", np.float64),
         ("eta_hat", np.float64),
+        ("rel_gap", np.float64),
+        ("rel_primal", np.float64),
+        ("rel_dual", np.float64),
     ]
 )
 
@@ -454,11 +462,19 @@ class Solver:
         _check(lib().pdlp_get_info(self.h, C.byref(inf)))
         return {f: getattr(inf, f) for f, _ in pdlp_info._fields_}
 
-    def trace(self, cap=1 << 16):
+    def trace(self, cap=TRACE_RETAINED):
+        """Check records of the last solve, oldest retained first (the device
+        ring keeps the last TRACE_RETAINED); checks_recorded() gives the total."""
         out = np.zeros(cap, dtype=CHECK_DTYPE)
         cnt = C.c_int32(0)
         _check(lib().pdlp_get_trace(self.h, _ptr(out), cap, C.byref(cnt)))
-        return out[: min(cnt.value, cap)].copy()
+        self._checks_recorded = cnt.value
+        return out[: min(cnt.value, cap, TRACE_RETAINED)].copy()
+
+    def checks_recorded(self) -> int:
+        cnt = C.c_int32(0)
+        _check(lib().pdlp_get_trace(self.h, None, 0, C.byref(cnt)))
+        return cnt.value
 
     def scaling(self):
         D1 = np.zeros(max(self.m, 1))

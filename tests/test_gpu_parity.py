@@ -77,13 +77,15 @@ def test_iterates_match_oracle(case, P_, N):
     assert len(tr) == len(r.trace)
     np.testing.assert_array_equal(tr["k"], r.trace["k"])
     np.testing.assert_array_equal(tr["restart"], r.trace["restart"])
+    np.testing.assert_array_equal(tr["attempts"], r.trace["attempts"])
+    np.testing.assert_array_equal(tr["restarts"], r.trace["restarts"])
     # GetRestartCandidate is decided by KKT(current) < KKT(average); where the
     # two agree to rounding (e.g. t = 1, when the average is the current
     # iterate up to (1/eta)(eta x)), both candidates are the same point and
     # either choice is correct, so only distinguishable cases are compared
     tie = np.abs(r.trace["kkt_cur"] - r.trace["kkt_avg"]) <= 1e-12 * np.maximum(r.trace["kkt_cur"], r.trace["kkt_avg"])
     np.testing.assert_array_equal(tr["cand_avg"][~tie], r.trace["cand_avg"][~tie])
-    for f in ("kkt_cur", "kkt_avg", "kkt_start", "omega", "eta_hat"):
+    for f in ("kkt_cur", "kkt_avg", "kkt_start", "omega", "eta_hat", "rel_gap", "rel_primal", "rel_dual"):
         np.testing.assert_allclose(tr[f], r.trace[f], rtol=1e-9, err_msg=f)
     np.testing.assert_allclose(x, r.x, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.x).max()))
     np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))

@@ -313,6 +313,30 @@ def test_iteration_limit_and_trace():
     assert r.trace["restart"][0] & 4
 
 
+def test_trace_metrics_match_a_solve_stopped_at_the_check():
+    """Each check record's Sec. 4.1 measures are those of the current iterate
+    on the original LP: a solve stopped by the iteration limit at that k
+    returns that iterate, whose measures kkt_terms evaluates independently;
+    its trial count is the record's, and the restart count is the running
+    number of restart masks."""
+    lp = lpgen.tiny_lp(1)
+    r = oracle.solve(lp, tol=1e-12, max_iter=640, check_period=64)
+    tr = r.trace
+    assert len(tr) == 9
+    assert np.array_equal(tr["restarts"], np.cumsum(tr["restart"] != 0))
+    assert np.all(np.diff(tr["attempts"]) >= 64) and np.all(tr["attempts"] >= tr["k"])
+    for rec in tr[[0, 3, 8]]:
+        k = int(rec["k"])
+        s = oracle.solve(lp, tol=1e-12, max_iter=k, check_period=64)
+        assert s.status == oracle.ITER_LIMIT and s.iters == k and s.attempts == rec["attempts"]
+        t = oracle.kkt_terms(lp, s.x, s.y)
+        gap = abs(t["pobj"] - t["dobj"]) / (1.0 + abs(t["pobj"]) + abs(t["dobj"]))
+        want = [gap, t["rp"] / (1.0 + t["q_norm"]), t["rd"] / (1.0 + t["c_norm"])]
+        got = [rec["rel_gap"], rec["rel_primal"], rec["rel_dual"]]
+        np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-15)
+        assert max(got) > 1e-12  # the check did not end the solve
+
+
 def test_invalid_inputs_rejected():
     lp = lpgen.tiny_lp(0)
     bad = lpgen.tiny_lp(0)
