@@ -1169,7 +1169,24 @@ int occupancy_grid(int kc, int num_sms) {
   return nb * num_sms;
 }
 
-cudaError_t kernels_init() { return cudaSuccess; }
+// Preferred shared-memory carveout of the step kernels, in percent of the
+// largest configuration: 8 % is the smallest that holds four CTAs' static
+// shared memory, so the L1 keeps the rest.  Every in-flight gather of x or y
+// holds an L1 line until it returns, so the L1's size bounds the gathers in
+// flight (measured on the 1e6 x 2e6 LP: 8 % 83.5 / 117.9 us per k_primal /
+// k_dual launch, the driver's default 86.2 / 119.0, 28 % 92.1 / 120.4,
+// 58 % 112.5 / 132.9).
+#ifndef PDLP_STEP_CARVEOUT
+#define PDLP_STEP_CARVEOUT 8
+#endif
+cudaError_t kernels_init() {
+  if (PDLP_STEP_CARVEOUT < 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_primal, cudaFuncAttributePreferredSharedMemoryCarveout, PDLP_STEP_CARVEOUT);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_primal_qp, cudaFuncAttributePreferredSharedMemoryCarveout, PDLP_STEP_CARVEOUT);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_dual, cudaFuncAttributePreferredSharedMemoryCarveout, PDLP_STEP_CARVEOUT);
+  return e;
+}
 cudaError_t launch_primal(const SellMat &KT, const Vecs &V, DevState *st, int grid, cudaStream_t s) {
   if (V.qd)
     k_primal_qp<<<grid, NT, 0, s>>>(KT, V, st);
