@@ -605,11 +605,21 @@ __global__ void __launch_bounds__(NT, STEP_MINB) k_dual(SellMat K, Vecs V, DevSt
 
 // ---------------------------------------------------------------- restart / termination check
 
+// IEEE-bit tests (integer pipe): sign of a nonzero, finiteness
+__device__ __forceinline__ bool neg_bits(double v) { return __double_as_longlong(v) < 0; }
+__device__ __forceinline__ bool pos_bits(double v) { return __double_as_longlong(v) > 0; }
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
+}
+
+// proj_Lambda (reading 5 of the paper's lambda): every test on the IEEE
+// bits, so GB300's narrow FP64 pipe does none of it.  -0.0 maps to -0.0 or
+// +0.0, which no sum below can tell from 0.
 __device__ __forceinline__ double proj_lambda(double d, double l, double u) {
-  const bool lf = isfinite(l), uf = isfinite(u);
+  const bool lf = finite_bits(l), uf = finite_bits(u);
   if (lf && uf) return d;
-  if (lf) return d > 0.0 ? d : 0.0;
-  if (uf) return d < 0.0 ? d : 0.0;
+  if (lf) return pos_bits(d) ? d : 0.0;
+  if (uf) return neg_bits(d) ? d : 0.0;
   return 0.0;
 }
 
@@ -617,17 +627,19 @@ __device__ __forceinline__ double proj_lambda(double d, double l, double u) {
 // With qp (Q_jj = qdj), the objective's gradient c + Qx replaces c in the
 // reduced cost, and x'Qx/2 is added to the primal objective c'x and taken
 // from the dual one (the QP's objectives).
-__device__ __forceinline__ void dual_piece(double c, double g, double l, double u, double d2, double x,
+// The original-space residual is r / D2, taken as r times the stored 1/D2
+// (rd2): no FP64 division on the hot check path.
+__device__ __forceinline__ void dual_piece(double c, double g, double l, double u, double rd2, double x,
                                            double *acc, bool qp = false, double qdj = 0.0) {
   const double d = qp ? fma(qdj, x, c) - g : c - g;
   const double lam = proj_lambda(d, l, u);
   const double r = d - lam;
   acc[0] = fma(r, r, acc[0]);
-  const double ro = r / d2;
+  const double ro = r * rd2;
   acc[1] = fma(ro, ro, acc[1]);
   acc[2] = fma(c, x, acc[2]);
-  if (lam > 0.0) acc[3] = fma(l, lam, acc[3]);
-  if (lam < 0.0) acc[3] = acc[3] - u * (-lam);
+  if (pos_bits(lam)) acc[3] = fma(l, lam, acc[3]);
+  if (neg_bits(lam) && (__double_as_longlong(lam) << 1) != 0) acc[3] = acc[3] - u * (-lam);
   if (qp) {
     const double h = 0.5 * qdj * x * x;
     acc[2] += h;
@@ -639,7 +651,7 @@ __device__ __forceinline__ void dual_piece(double c, double g, double l, double 
 // kind 1: check with stale g (sums = {K'y, K'ybar}); kind 2: check with g
 // current (sums = {K'ybar}, g loaded).
 struct CheckPrimalEpi {
-  const double *__restrict__ c, *__restrict__ l, *__restrict__ u, *__restrict__ d2, *__restrict__ x,
+  const double *__restrict__ c, *__restrict__ l, *__restrict__ u, *__restrict__ rd2, *__restrict__ x,
       *__restrict__ sx;
   double *__restrict__ g, *__restrict__ gbar;
   double *__restrict__ g0, *__restrict__ gprev;  // kept for infeasibility detection when keep
@@ -652,7 +664,7 @@ struct CheckPrimalEpi {
     pc = c[j];
     pl = l[j];
     pu = u[j];
-    pd2 = d2[j];
+    pd2 = rd2[j];
     px = x[j];
     psx = kind ? sx[j] : 0.0;
     pg = (kind == 2 || (kind == 1 && keep)) ? g[j] : 0.0;
@@ -693,7 +705,7 @@ __global__ void __launch_bounds__(NT, CHECK_MINB) k_check_primal(SellMat KT, Vec
   ep.c = V.c;
   ep.l = V.l;
   ep.u = V.u;
-  ep.d2 = V.D2;
+  ep.rd2 = V.rD2;
   ep.x = V.x[cur];
   ep.sx = V.sx[cur];
   ep.g = V.g;
@@ -726,11 +738,12 @@ __global__ void __launch_bounds__(NT, CHECK_MINB) k_check_primal(SellMat KT, Vec
   }
 }
 
-__device__ __forceinline__ void primal_piece(double q, double kx, bool ineq, double d1, double y, double *acc) {
+// The original-space residual is r / D1, taken as r times the stored 1/D1.
+__device__ __forceinline__ void primal_piece(double q, double kx, bool ineq, double rd1, double y, double *acc) {
   double r = q - kx;
-  if (ineq && r < 0.0) r = 0.0;
+  if (ineq && neg_bits(r)) r = 0.0;
   acc[0] = fma(r, r, acc[0]);
-  const double ro = r / d1;
+  const double ro = r * rd1;
   acc[1] = fma(ro, ro, acc[1]);
   acc[2] = fma(q, y, acc[2]);
 }
@@ -888,7 +901,7 @@ __device__ void check_decide(DevState *st, TraceRec *trace, const double *p, con
 // Epilogue of the primal-side check pass.  check = 0: start point (sums =
 // {Kx}, stored as Kx); check = 1: sums = {K xbar}.
 struct CheckDualEpi {
-  const double *__restrict__ q, *__restrict__ d1, *__restrict__ y, *__restrict__ sy;
+  const double *__restrict__ q, *__restrict__ rd1, *__restrict__ y, *__restrict__ sy;
   double *__restrict__ kx, *__restrict__ kxbar, *__restrict__ kx0;
   double invW;
   int check, n_eq, keep;
@@ -896,7 +909,7 @@ struct CheckDualEpi {
   double pq, pd1, py, psy, pkx;
   __device__ __forceinline__ void prefetch(int i) {
     pq = q[i];
-    pd1 = d1[i];
+    pd1 = rd1[i];
     py = y[i];
     psy = check ? sy[i] : 0.0;
     pkx = check ? kx[i] : 0.0;
@@ -927,7 +940,7 @@ __global__ void __launch_bounds__(NT) k_check_dual(SellMat K, Vecs V, DevState *
   const bool check = mode == MODE_CHECK;
   CheckDualEpi ep;
   ep.q = V.q;
-  ep.d1 = V.D1;
+  ep.rd1 = V.rD1;
   ep.y = V.y[cur];
   ep.sy = V.sy[cur];
   ep.kx = V.Kx[cur];
@@ -972,12 +985,6 @@ __global__ void __launch_bounds__(NT) k_check_dual(SellMat K, Vecs V, DevState *
 // bits (integer pipe); GB300's FP64 pipe does only the arithmetic.  Runs
 // between k_check_primal (which refreshed g = K'y) and k_check_dual, whose
 // last CTA sums the block partials and decides.
-__device__ __forceinline__ bool neg_bits(double v) { return __double_as_longlong(v) < 0; }
-__device__ __forceinline__ bool pos_bits(double v) { return __double_as_longlong(v) > 0; }
-__device__ __forceinline__ bool finite_bits(double v) {
-  return ((unsigned long long)__double_as_longlong(v) & 0x7ff0000000000000ull) != 0x7ff0000000000000ull;
-}
-
 __global__ void __launch_bounds__(NT) k_infeas(Vecs V, DevState *__restrict__ st) {
   __shared__ double s_red[16 * NW];
   if (st->status != ST_RUNNING || !st->check_pending || st->mode != MODE_CHECK || !(st->eps_infeas > 0.0)) return;
