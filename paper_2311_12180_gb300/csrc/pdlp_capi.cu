@@ -14,6 +14,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pdlp.h"
@@ -255,10 +256,18 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
   const int64_t nnz = row_ptr[m];
   const cudaMemcpyKind entry_kind = dev_entries ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
 
-  // ---- host: the sliced-ELL layout of K (row lengths are known here); K'
-  // (row starts, entries) is built on the device after the upload, and its
-  // layout from the row starts ----
-  SellLayout LK = sell_layout(row_ptr, m, n_eq);
+  // ---- host: the sliced-ELL layout of K (row lengths are known here) on a
+  // host thread while the device takes the upload, builds K' and scales;
+  // K''s layout comes from its row starts, on this thread while the device
+  // scales ----
+  SellLayout LK;
+  struct Joiner {  // every exit waits for the layout thread
+    std::thread t;
+    ~Joiner() {
+      if (t.joinable()) t.join();
+    }
+  } lk_thread;
+  lk_thread.t = std::thread([&LK, row_ptr, m, n_eq] { LK = sell_layout(row_ptr, m, n_eq); });
   double qn = 0.0, cn = 0.0;
   for (int32_t i = 0; i < m; ++i) qn += q[i] * q[i];
   for (int32_t j = 0; j < n; ++j) cn += c[j] * c[j];
@@ -310,10 +319,11 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
     return std::max(1, std::min(g, need));
   };
   const int gridA_max = occupancy_grid(KC_PRIMAL, s->num_sms), gridR1_max = occupancy_grid(KC_R1, s->num_sms);
+  const int gridB_max = occupancy_grid(KC_DUAL, s->num_sms), gridR2_max = occupancy_grid(KC_R2, s->num_sms);
   s->gridA = gridA_max;
-  s->gridB = capped(occupancy_grid(KC_DUAL, s->num_sms), (int)LK.items.size());
+  s->gridB = gridB_max;  // capped by K's work items once its layout is known
   s->gridR1 = gridR1_max;
-  s->gridR2 = capped(occupancy_grid(KC_R2, s->num_sms), (int)LK.items.size());
+  s->gridR2 = gridR2_max;
   {
     const int64_t mx = n > m ? n : m;
     int g = occupancy_grid(KC_R3, s->num_sms);
@@ -426,7 +436,6 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
     CKS(cudaMemcpyAsync(s->K_idx, col_idx, 4 * Z, entry_kind, st));
     CKS(cudaMemcpyAsync(s->K_val, val, 8 * Z, entry_kind, st));
   }
-  if (m) CKS(cudaMemcpyAsync(s->perm_r, LK.perm.data(), 4 * M, cudaMemcpyHostToDevice, st));
 
   // ---- K' on the device: row starts from K's column counts, then the
   // stable transpose (the threaded host counting sort when a column is
@@ -471,17 +480,6 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
     CKS(cudaMemcpyAsync(s->T_val, tv.data(), 8 * Z, cudaMemcpyHostToDevice, st));
     CKS(cudaStreamSynchronize(st));  // the host arrays go out of scope
   }
-  // the layout of K' (one group: every column of K) while the device works
-  SellLayout LT = sell_layout(tp.data(), n, n);
-  if (LK.total >= ((int64_t)1 << 31) || LT.total >= ((int64_t)1 << 31)) {
-    free_solver(s);
-    return fail(PDLP_ERR_INVALID, "the sliced-ELL copy of K needs 2^31 or more stored entries");
-  }
-  s->gridA = capped(gridA_max, (int)LT.items.size());
-  s->gridR1 = capped(gridR1_max, (int)LT.items.size());
-  V.gridA = s->gridA;
-  V.gridR1 = s->gridR1;
-  CKS(cudaMemcpyAsync(s->perm_c, LT.perm.data(), 4 * N, cudaMemcpyHostToDevice, st));
   // original c, q, l, u into spare vectors, consumed below
   CKS(cudaMemcpyAsync(V.xout, c, 8 * N, cudaMemcpyHostToDevice, st));
   if (m) CKS(cudaMemcpyAsync(V.yout, q, 8 * M, cudaMemcpyHostToDevice, st));
@@ -510,6 +508,21 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
   CKS(setup_vectors(m, n, V.xout, V.yout, l_orig, u_orig, s->D1, s->D2, c_s, q_s, l_s, u_s, st));
   CKS(setup_scalars(m, n, nnz, c_s, q_s, s->K_val, s->d_scal, s->d_scal + 8, st));
 
+  // the layout of K' (one group: every column of K) while the device scales
+  SellLayout LT = sell_layout(tp.data(), n, n);
+  lk_thread.t.join();
+  s->gridB = capped(gridB_max, (int)LK.items.size());
+  s->gridR2 = capped(gridR2_max, (int)LK.items.size());
+  if (m) CKS(cudaMemcpyAsync(s->perm_r, LK.perm.data(), 4 * M, cudaMemcpyHostToDevice, st));
+  if (LK.total >= ((int64_t)1 << 31) || LT.total >= ((int64_t)1 << 31)) {
+    free_solver(s);
+    return fail(PDLP_ERR_INVALID, "the sliced-ELL copy of K needs 2^31 or more stored entries");
+  }
+  s->gridA = capped(gridA_max, (int)LT.items.size());
+  s->gridR1 = capped(gridR1_max, (int)LT.items.size());
+  V.gridA = s->gridA;
+  V.gridR1 = s->gridR1;
+  CKS(cudaMemcpyAsync(s->perm_c, LT.perm.data(), 4 * N, cudaMemcpyHostToDevice, st));
   // ---- sliced-ELL copies of the scaled K and K', columns renumbered ----
   {
     Layout SL;
