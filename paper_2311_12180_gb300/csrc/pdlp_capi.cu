@@ -492,8 +492,9 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
     cudaError_t e;
     if (have_perm) {
       const int32_t *perm = twork + wcs + n, *rowid = perm + nnz;
+      // reciprocal scratch: the x_last / y_last slots, unused until a solve begins
       e = setup_scale_perm(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_val, rowid, perm, s->D1, s->D2,
-                           s->work_m, s->work_n, prm.ruiz_iters, prm.pc_alpha, st);
+                           s->work_m, s->work_n, VM(9), VN(12), prm.ruiz_iters, prm.pc_alpha, st);
     } else {
       e = setup_scale(m, n, nnz, s->K_ptr, s->K_idx, s->K_val, s->T_ptr, s->T_idx, s->T_val, s->D1, s->D2,
                       s->work_m, s->work_n, prm.ruiz_iters, prm.pc_alpha, st);

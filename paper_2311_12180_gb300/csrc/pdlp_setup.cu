@@ -97,13 +97,43 @@ __global__ void k_entry_max(const int32_t *__restrict__ idx, const int32_t *__re
   }
 }
 
+// rD[i] = 1 / D[i], correctly rounded (IEEE division).
+__global__ void k_recip(int32_t count, const double *D, double *rD) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) rD[i] = 1.0 / D[i];
+}
+
+// RN(a / b) from y = RN(1 / b) by one correction step (Markstein, IBM J. Res.
+// Dev. 34(1), 1990; Handbook of Floating-Point Arithmetic, the theorem on
+// division by an FMA correction): q = RN(a y) is within one ulp of a / b,
+// the remainder a - b q is exact with an FMA, and RN(q + (a - b q) y) is the
+// correctly rounded quotient when nothing underflows or overflows.  Where a
+// or q is outside [2^-900, 2^900] (or zero, or not finite) the plain
+// division runs instead.  Three FP64 operations instead of a division
+// routine: the Ruiz passes divide every entry twice, on GB300's narrow FP64
+// pipe.
+__device__ __forceinline__ unsigned int exp_bits(double v) {
+  return (unsigned int)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu;
+}
+__device__ __forceinline__ double div_rn(double a, double b, double y) {
+  const double q = a * y;
+  const unsigned int ea = exp_bits(a), eq = exp_bits(q);
+  if (ea < 1023u - 900u || ea > 1023u + 900u || eq < 1023u - 900u || eq > 1023u + 900u) return a / b;
+  const double r = fma(-b, q, a);
+  return fma(r, y, q);
+}
+
 // K's entries in storage order: val[e] = (val[e] / r[row]) / s[column], the
-// same two divisions in the same order as the row-wise k_scale.
+// same two correctly rounded divisions in the same order as the row-wise
+// k_scale (the reciprocals rr, rs of the factors make each one three FP64
+// operations, div_rn).
 __global__ void k_scale_entries(const int32_t *__restrict__ idx, const int32_t *__restrict__ rowid,
                                 double *__restrict__ val, int64_t nnz, const double *__restrict__ r,
-                                const double *__restrict__ s) {
-  for (int64_t e = (int64_t)blockIdx.x * ST + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * ST)
-    val[e] = val[e] / r[rowid[e]] / s[idx[e]];
+                                const double *__restrict__ s, const double *__restrict__ rr,
+                                const double *__restrict__ rs) {
+  for (int64_t e = (int64_t)blockIdx.x * ST + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * ST) {
+    const int32_t i = rowid[e], j = idx[e];
+    val[e] = div_rn(div_rn(val[e], r[i], rr[i]), s[j], rs[j]);
+  }
 }
 
 // K' values as a copy of K's through the transpose permutation.
@@ -248,7 +278,7 @@ cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32
 cudaError_t setup_scale_perm(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
                              double *K_val, const int32_t *T_ptr, double *T_val, const int32_t *rowid,
                              const int32_t *perm, double *D1, double *D2, double *work_m, double *work_n,
-                             int ruiz_iters, double pc_alpha, cudaStream_t s) {
+                             double *rcp_m, double *rcp_n, int ruiz_iters, double pc_alpha, cudaStream_t s) {
   if (m > 0) k_fill<<<grid_for(m), ST, 0, s>>>(D1, m, 1.0);
   k_fill<<<grid_for(n), ST, 0, s>>>(D2, n, 1.0);
   const int eg = grid_for(nnz);
@@ -261,7 +291,9 @@ cudaError_t setup_scale_perm(int32_t m, int32_t n, int64_t nnz, const int32_t *K
                                     reinterpret_cast<unsigned long long *>(work_n));
     if (m > 0) k_factor<<<grid_for(m), ST, 0, s>>>(work_m, m);
     k_factor<<<grid_for(n), ST, 0, s>>>(work_n, n);
-    if (nnz > 0) k_scale_entries<<<eg, ST, 0, s>>>(K_idx, rowid, K_val, nnz, work_m, work_n);
+    if (m > 0) k_recip<<<grid_for(m), ST, 0, s>>>(m, work_m, rcp_m);
+    k_recip<<<grid_for(n), ST, 0, s>>>(n, work_n, rcp_n);
+    if (nnz > 0) k_scale_entries<<<eg, ST, 0, s>>>(K_idx, rowid, K_val, nnz, work_m, work_n, rcp_m, rcp_n);
     if (m > 0) k_div<<<grid_for(m), ST, 0, s>>>(D1, work_m, m);
     k_div<<<grid_for(n), ST, 0, s>>>(D2, work_n, n);
   }
@@ -271,7 +303,9 @@ cudaError_t setup_scale_perm(int32_t m, int32_t n, int64_t nnz, const int32_t *K
     k_row_norm<<<grid_for((long long)n * 32), ST, 0, s>>>(T_ptr, T_val, n, work_n, 1, pc_alpha);
     if (m > 0) k_factor<<<grid_for(m), ST, 0, s>>>(work_m, m);
     k_factor<<<grid_for(n), ST, 0, s>>>(work_n, n);
-    if (nnz > 0) k_scale_entries<<<eg, ST, 0, s>>>(K_idx, rowid, K_val, nnz, work_m, work_n);
+    if (m > 0) k_recip<<<grid_for(m), ST, 0, s>>>(m, work_m, rcp_m);
+    k_recip<<<grid_for(n), ST, 0, s>>>(n, work_n, rcp_n);
+    if (nnz > 0) k_scale_entries<<<eg, ST, 0, s>>>(K_idx, rowid, K_val, nnz, work_m, work_n, rcp_m, rcp_n);
     if (m > 0) k_div<<<grid_for(m), ST, 0, s>>>(D1, work_m, m);
     k_div<<<grid_for(n), ST, 0, s>>>(D2, work_n, n);
     if (nnz > 0) k_copy_perm<<<eg, ST, 0, s>>>(perm, K_val, nnz, T_val);
@@ -284,10 +318,6 @@ cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *
                           double *u, cudaStream_t s) {
   k_vectors<<<grid_for(n > m ? n : m), ST, 0, s>>>(m, n, c0, q0, l0, u0, D1, D2, c, q, l, u);
   return cudaGetLastError();
-}
-
-__global__ void k_recip(int32_t count, const double *D, double *rD) {
-  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) rD[i] = 1.0 / D[i];
 }
 
 cudaError_t setup_recip(int32_t count, const double *D, double *rD, cudaStream_t s) {

@@ -43,7 +43,7 @@ cudaError_t setup_scale(int32_t m, int32_t n, int64_t nnz, int32_t *K_ptr, int32
 cudaError_t setup_scale_perm(int32_t m, int32_t n, int64_t nnz, const int32_t *K_ptr, const int32_t *K_idx,
                              double *K_val, const int32_t *T_ptr, double *T_val, const int32_t *rowid,
                              const int32_t *perm, double *D1, double *D2, double *work_m, double *work_n,
-                             int ruiz_iters, double pc_alpha, cudaStream_t s);
+                             double *rcp_m, double *rcp_n, int ruiz_iters, double pc_alpha, cudaStream_t s);
 cudaError_t setup_vectors(int32_t m, int32_t n, const double *c0, const double *q0, const double *l0,
                           const double *u0, const double *D1, const double *D2, double *c, double *q, double *l,
                           double *u, cudaStream_t s);

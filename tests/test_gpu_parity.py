@@ -53,8 +53,12 @@ def test_scaling_matches_oracle(seed):
     np.testing.assert_allclose(v, sv, rtol=1e-13)
 
 
-def test_ruiz_only_scaling_is_bitwise():
-    lp = lpgen.tiny_lp(3)
+@pytest.mark.parametrize("case", ["tiny", "powerlaw"])
+def test_ruiz_only_scaling_is_bitwise(case):
+    """Ten Ruiz passes: every entry divided twice per pass, on the GPU by a
+    reciprocal and one correction step (correctly rounded) and in the oracle by
+    plain division: bitwise equal on 2e3 and on 4e5 lognormal entries."""
+    lp = lpgen.tiny_lp(3) if case == "tiny" else lpgen.large_lp(4, m=20000, n=40000, nnz=400000)
     with _solver(lp, pc_alpha=-1.0) as s:
         D1, D2, v = s.scaling()
     sv, oD1, oD2 = oracle.precondition(lp, ruiz_iters=10, pc_alpha=-1.0)
