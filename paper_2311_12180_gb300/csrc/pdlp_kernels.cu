@@ -134,19 +134,19 @@ __device__ __forceinline__ void sum_partials(const double *part, int count, doub
 
 // ---------------------------------------------------------------- sliced-ELL SpMV
 
-// float -> double from the IEEE bits with integer operations (exact for
-// every normal float: the exponent is re-biased by 1023 - 127 = 896 and the
-// 23-bit mantissa moved to the top of the 52-bit one), keeping the widening
-// off GB300's narrow FP64 pipe; zero, subnormals, inf and NaN take the
-// hardware conversion.
+// float -> double from the IEEE bits with integer operations, exact for
+// every normal float and for zero: with t the magnitude bits, the high word
+// is the sign | ((t >> 3) + (896 << 20)) (exponent re-biased by 1023 - 127,
+// top 20 mantissa bits), the low word the last 3 mantissa bits << 29, and
+// t = 0 gives the signed zero.  The FP32 copies the step kernels read hold
+// only normal floats and zeros (setup_f32 flushes the subnormals, and the
+// scaled matrix is finite), so no hardware conversion and no branch: the
+// widening stays off GB300's narrow FP64 pipe.
 __device__ __forceinline__ double f2d(float f) {
   const unsigned int b = __float_as_uint(f);
-  const unsigned int ex = (b >> 23) & 0xffu;
-  if (ex == 0u || ex == 0xffu) return (double)f;
-  const unsigned long long d = ((unsigned long long)(b & 0x80000000u) << 32) |
-                               ((unsigned long long)(ex + 896u) << 52) |
-                               ((unsigned long long)(b & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)d);
+  const unsigned int t = b & 0x7fffffffu;
+  const unsigned int hi = (b ^ t) | (t ? (t >> 3) + 0x38000000u : 0u);
+  return __hiloint2double((int)hi, (int)(b << 29));
 }
 __device__ __forceinline__ double widen(double v) { return v; }
 __device__ __forceinline__ double widen(float v) { return f2d(v); }

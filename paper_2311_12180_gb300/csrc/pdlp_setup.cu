@@ -159,9 +159,14 @@ __global__ void k_vectors(int32_t m, int32_t n, const double *__restrict__ c0, c
   for (int i = blockIdx.x * ST + threadIdx.x; i < m; i += gridDim.x * ST) q[i] = D1[i] * q0[i];
 }
 
+// FP32 copy of the scaled values (round to nearest); a value below the
+// smallest normal float is stored as a signed zero, so the step kernels'
+// integer widening sees only normal floats and zeros.
 __global__ void k_f32(long long nnz, const double *__restrict__ v, float *__restrict__ f) {
-  for (long long e = (long long)blockIdx.x * ST + threadIdx.x; e < nnz; e += (long long)gridDim.x * ST)
-    f[e] = (float)v[e];
+  for (long long e = (long long)blockIdx.x * ST + threadIdx.x; e < nnz; e += (long long)gridDim.x * ST) {
+    const float x = (float)v[e];
+    f[e] = (__float_as_uint(x) & 0x7f800000u) ? x : __uint_as_float(__float_as_uint(x) & 0x80000000u);
+  }
 }
 
 // out = {sum c^2, sum q^2, max |val|} in two steps with a fixed order for a
