@@ -527,7 +527,7 @@ def run_warmstart(args, rank, world):
     arms = {}
     st_c, it_c, cold_s, _ = W.solve_many(mk_te, args.ws_test, tol, on_solution=keep_c)
     arms["cold"] = {"solve_s": cold_s, "optimal": int(np.sum(st_c == 0)), "iters_median": float(np.median(it_c)),
-                    "iters_mean": float(np.mean(it_c))}
+                    "iters_p90": float(np.percentile(it_c, 90)), "iters_mean": float(np.mean(it_c))}
     mx, my = W.mean_start(T, n)
     Ymix = np.concatenate([T[near][:, :n].astype(np.float64), Yp[:, n:]], axis=1)
     starts = {"mlp": lambda i: (Yp[i, :n], Yp[i, n:]), "mean": lambda i: (mx, my),
@@ -542,7 +542,8 @@ def run_warmstart(args, rank, world):
         ex = np.linalg.norm(P_[:, :n] - Tc[:, :n], axis=1) / np.maximum(np.linalg.norm(Tc[:, :n], axis=1), 1e-30)
         ey = np.linalg.norm(P_[:, n:] - Tc[:, n:], axis=1) / np.maximum(np.linalg.norm(Tc[:, n:], axis=1), 1e-30)
         arms[name] = {"solve_s": r["solve_s"], "optimal": int(np.sum(r["status"] == 0)), "fallbacks": r["fallbacks"],
-                      "iters_median": float(np.median(r["iters"])), "iters_mean": float(np.mean(r["iters"])),
+                      "iters_median": float(np.median(r["iters"])), "iters_p90": float(np.percentile(r["iters"], 90)),
+                      "iters_mean": float(np.mean(r["iters"])),
                       "iters_ratio_vs_cold_median": float(np.median(r["iters"] / np.maximum(it_c, 1))),
                       "rel_err_x_median": float(np.median(ex)), "rel_err_y_median": float(np.median(ey))}
     warm_total = arms["mlp"]["solve_s"] + predict_s
@@ -732,6 +733,7 @@ def main():
                                    "obj_rel_err_vs_planted": abs(float(np.dot(lp.c, x_t)) - lp.obj_star)
                                    / abs(lp.obj_star)}
                 inf = s3.info()
+                ttt["%g" % tol]["seconds_with_setup"] = ttt["%g" % tol]["seconds"] + inf["setup_ms"] / 1000.0
                 ttt["%g" % tol].update({
                     "restarts": inf["restarts"], "f64_switch_iter": inf["f64_switch_iter"],
                     "rel_gap": abs(inf["pobj"] - inf["dobj"]) / (1 + abs(inf["pobj"]) + abs(inf["dobj"])),
