@@ -538,6 +538,17 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
                    (const double *)(B + o_kv), f32 ? (const float *)(B + o_kf) : nullptr};
     s->KT = SellMat{n, (int32_t)LT.items.size(), (const int4 *)(B + o_tit), (const int32_t *)(B + o_ti),
                     (const double *)(B + o_tv), f32 ? (const float *)(B + o_tf) : nullptr};
+    // the solve's CUDA graph (one check period) is captured and instantiated
+    // now, on the host, while the device is still scaling: it needs only the
+    // pointers and grids, all known here
+    s->slots = prm.check_period + (prm.check_period / 8 > 4 ? prm.check_period / 8 : 4);
+    {
+      const int grc = build_graph(s);
+      if (grc) {
+        free_solver(s);
+        return grc;
+      }
+    }
     if (!LK.items.empty())
       CKS(cudaMemcpyAsync(B + o_kit, LK.items.data(), sizeof(int4) * LK.items.size(), cudaMemcpyHostToDevice, st));
     CKS(cudaMemcpyAsync(B + o_tit, LT.items.data(), sizeof(int4) * LT.items.size(), cudaMemcpyHostToDevice, st));
@@ -596,7 +607,6 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
   const double cc = std::sqrt(s->h_scal[0]), qq = std::sqrt(s->h_scal[1]), kmax = s->h_scal[2];
   s->eta_hat0 = kmax > 0.0 ? 1.0 / kmax : 1.0;                                        // Algorithm 1
   s->omega0 = (cc > prm.eps_zero && qq > prm.eps_zero) ? cc / qq : 1.0;              // InitializePrimalWeight
-  s->slots = prm.check_period + (prm.check_period / 8 > 4 ? prm.check_period / 8 : 4);
   s->setup_ms = now_ms() - t_start;
 #undef CKS
   *out = s;
