@@ -103,21 +103,46 @@ struct pdlp_solver {
 
 namespace {
 
-// Dimensions, row starts and the vectors (host arrays).
+// Dimensions, row starts and the vectors (host arrays).  The scans run in
+// parallel chunks; the report names the first bad index of each kind.
 int validate_vectors(int32_t m, int32_t n, int32_t n_eq, const double *c, const int32_t *rp, const double *q,
                      const double *l, const double *u) {
   if (m < 0 || n < 1 || n_eq < 0 || n_eq > m) return fail(PDLP_ERR_INVALID, "dimensions: need m >= 0, n >= 1, 0 <= n_eq <= m");
   if (!c || !rp || !l || !u || (m > 0 && !q)) return fail(PDLP_ERR_INVALID, "null input array");
   if (rp[0] != 0) return fail(PDLP_ERR_INVALID, "row_ptr[0] must be 0");
-  for (int32_t i = 0; i < m; ++i)
-    if (rp[i + 1] < rp[i]) return fail(PDLP_ERR_INVALID, "row_ptr is not non-decreasing at row " + std::to_string(i));
-  for (int32_t j = 0; j < n; ++j) {
-    if (!std::isfinite(c[j])) return fail(PDLP_ERR_INVALID, "non-finite c at " + std::to_string(j));
-    if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY)
-      return fail(PDLP_ERR_INVALID, "bad bounds at variable " + std::to_string(j));
-  }
-  for (int32_t i = 0; i < m; ++i)
-    if (!std::isfinite(q[i])) return fail(PDLP_ERR_INVALID, "non-finite q at row " + std::to_string(i));
+  const int T = host_threads((int64_t)m + n);
+  std::vector<int32_t> bad_row(T, m), bad_c(T, n), bad_b(T, n), bad_q(T, m);
+  parallel_for(T, [&](int t) {
+    const int32_t i0 = (int32_t)((int64_t)m * t / T), i1 = (int32_t)((int64_t)m * (t + 1) / T);
+    for (int32_t i = i0; i < i1; ++i)
+      if (rp[i + 1] < rp[i]) {
+        bad_row[t] = i;
+        break;
+      }
+    for (int32_t i = i0; i < i1; ++i)
+      if (!std::isfinite(q[i])) {
+        bad_q[t] = i;
+        break;
+      }
+    const int32_t j0 = (int32_t)((int64_t)n * t / T), j1 = (int32_t)((int64_t)n * (t + 1) / T);
+    for (int32_t j = j0; j < j1; ++j)
+      if (!std::isfinite(c[j])) {
+        bad_c[t] = j;
+        break;
+      }
+    for (int32_t j = j0; j < j1; ++j)
+      if (std::isnan(l[j]) || std::isnan(u[j]) || l[j] > u[j] || l[j] == INFINITY || u[j] == -INFINITY) {
+        bad_b[t] = j;
+        break;
+      }
+  });
+  const int32_t br = *std::min_element(bad_row.begin(), bad_row.end());
+  if (br < m) return fail(PDLP_ERR_INVALID, "row_ptr is not non-decreasing at row " + std::to_string(br));
+  const int32_t bc = *std::min_element(bad_c.begin(), bad_c.end()), bb = *std::min_element(bad_b.begin(), bad_b.end());
+  if (bc < n && bc <= bb) return fail(PDLP_ERR_INVALID, "non-finite c at " + std::to_string(bc));
+  if (bb < n) return fail(PDLP_ERR_INVALID, "bad bounds at variable " + std::to_string(bb));
+  const int32_t bq = *std::min_element(bad_q.begin(), bad_q.end());
+  if (bq < m) return fail(PDLP_ERR_INVALID, "non-finite q at row " + std::to_string(bq));
   return PDLP_OK;
 }
 
@@ -267,10 +292,12 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
       if (t.joinable()) t.join();
     }
   } lk_thread;
-  lk_thread.t = std::thread([&LK, row_ptr, m, n_eq] { LK = sell_layout(row_ptr, m, n_eq); });
-  double qn = 0.0, cn = 0.0;
-  for (int32_t i = 0; i < m; ++i) qn += q[i] * q[i];
-  for (int32_t j = 0; j < n; ++j) cn += c[j] * c[j];
+  double qn = 0.0, cn = 0.0;  // ||q||^2, ||c||^2 of the original LP (Sec. 4.1), on the same thread
+  lk_thread.t = std::thread([&LK, &qn, &cn, row_ptr, q, c, m, n, n_eq] {
+    LK = sell_layout(row_ptr, m, n_eq);
+    for (int32_t i = 0; i < m; ++i) qn += q[i] * q[i];
+    for (int32_t j = 0; j < n; ++j) cn += c[j] * c[j];
+  });
 
   pdlp_solver *s = new pdlp_solver();
   s->m = m;
@@ -278,8 +305,6 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
   s->n_eq = n_eq;
   s->nnz = nnz;
   s->prm = prm;
-  s->q_norm = std::sqrt(qn);
-  s->c_norm = std::sqrt(cn);
 #define CKS(call)                                                                                              \
   do {                                                                                                         \
     cudaError_t e_ = (call);                                                                                   \
@@ -512,6 +537,8 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
   // the layout of K' (one group: every column of K) while the device scales
   SellLayout LT = sell_layout(tp.data(), n, n);
   lk_thread.t.join();
+  s->q_norm = std::sqrt(qn);
+  s->c_norm = std::sqrt(cn);
   s->gridB = capped(gridB_max, (int)LK.items.size());
   s->gridR2 = capped(gridR2_max, (int)LK.items.size());
   if (m) CKS(cudaMemcpyAsync(s->perm_r, LK.perm.data(), 4 * M, cudaMemcpyHostToDevice, st));
