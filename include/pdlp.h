@@ -422,10 +422,12 @@ void pdlp_mlp_destroy(pdlp_mlp *net);
 
 /* Allocation-free Ruiz + Pock-Chambolle scaling of a matrix the caller keeps
  * in DEVICE memory.  This entry point has no counterpart in the paper; it is
- * the same scaling pdlp_create applies, with the same divisions in the same
- * order (row by row here, entry by entry in pdlp_create; l_inf maxima and the
- * fixed-order Pock-Chambolle row sums do not depend on that), so D1, D2 and
- * the scaled values are bitwise equal to pdlp_get_scaling's.  It is offered
+ * the same scaling pdlp_create applies, with the same correctly rounded
+ * divisions in the same order (row by row here, entry by entry in
+ * pdlp_create, where each quotient comes from the factor's reciprocal and one
+ * exact correction step; l_inf maxima and the fixed-order Pock-Chambolle row
+ * sums do not depend on that), so D1, D2 and the scaled values are bitwise
+ * equal to pdlp_get_scaling's.  It is offered
  * for callers
  * that cannot call cudaMalloc or cudaFree: code that must take every byte of
  * device memory from its own pool (a framework's caching allocator, a
