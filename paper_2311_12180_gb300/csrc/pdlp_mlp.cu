@@ -303,6 +303,7 @@ struct EpiOut : EpiBase {
 // FP32 over a thread's 16 columns, FP64 across chunks and threads).
 struct EpiLoss {
   const float *bias, *t, *mu, *sigma;
+  const int *rows;  // batch row m's target is row rows[m] of the data set t
   float *dy;
   bf16 *dyh, *dyhT;
   double *part;
@@ -312,11 +313,12 @@ struct EpiLoss {
   double acc;
   __device__ __forceinline__ void chunk(int m, int n, const float (&v)[16], int cnt, int) {
     float tv[16];
+    const float *tr = t + (size_t)rows[m] * ldt;
     if (vec && cnt == 16) {
-      ld16_f32(t + (size_t)m * ldt + n, tv);
+      ld16_f32(tr + n, tv);
     } else {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) tv[j] = j < cnt ? t[(size_t)m * ldt + n + j] : 0.0f;
+      for (int j = 0; j < 16; ++j) tv[j] = j < cnt ? tr[n + j] : 0.0f;
     }
     float g[16];
     __align__(16) bf16 gh[16];
@@ -406,20 +408,16 @@ __global__ void k_splitk_relu_grad(const float *__restrict__ part, int splits, i
 
 // Mini-batch gather: inputs to BF16 in both layouts, targets (FP32) of the
 // sampled rows.
-__global__ void k_gather(const float *__restrict__ X, const float *__restrict__ T, const int *__restrict__ idx,
-                         int batch, int in_dim, int out_dim, bf16 *__restrict__ xb, int ldx, bf16 *__restrict__ xbT,
-                         int ldT, float *__restrict__ tb) {
-  const int b = blockIdx.y;
+__global__ void k_gather(const float *__restrict__ X, const int *__restrict__ idx, int batch, int in_dim,
+                         bf16 *__restrict__ xb, int ldx, bf16 *__restrict__ xbT, int ldT) {
+  const int b = blockIdx.x;
   if (b >= batch) return;
   const size_t row = (size_t)idx[b];
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < out_dim; i += gridDim.x * blockDim.x)
-    tb[(size_t)b * out_dim + i] = T[row * out_dim + i];
-  if (blockIdx.x == 0)
-    for (int i = threadIdx.x; i < in_dim; i += blockDim.x) {
-      const bf16 v = __float2bfloat16(X[row * in_dim + i]);
-      xb[(size_t)b * ldx + i] = v;
-      xbT[(size_t)i * ldT + b] = v;
-    }
+  for (int i = threadIdx.x; i < in_dim; i += blockDim.x) {
+    const bf16 v = __float2bfloat16(X[row * in_dim + i]);
+    xb[(size_t)b * ldx + i] = v;
+    xbT[(size_t)i * ldT + b] = v;
+  }
 }
 
 // prediction input: X (count x in, FP32) -> BF16 rows
@@ -447,11 +445,27 @@ __global__ void k_loss_finish(const double *__restrict__ part, int nparts, size_
 }
 
 // out[c] = sum over rows of X[rows x cols] (fixed row order): bias gradients.
+// Column sums of X (rows x cols, FP32): a block of 32 columns x 8 row
+// groups; group g adds rows g, g + 8, ... in order, then the eight partial
+// sums are added in group order (a fixed order, whatever the grid).
+constexpr int COLSUM_GROUPS = 8;
 __global__ void k_colsum(const float *__restrict__ X, int rows, int cols, float *__restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < cols; c += gridDim.x * blockDim.x) {
+  __shared__ float part[COLSUM_GROUPS][32];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  for (int c0 = blockIdx.x * 32; c0 < cols; c0 += gridDim.x * 32) {
+    const int c = c0 + lane;
     float s = 0.0f;
-    for (int r = 0; r < rows; ++r) s += X[(size_t)r * cols + c];
-    out[c] = s;
+    if (c < cols)
+      for (int r = grp; r < rows; r += COLSUM_GROUPS) s += X[(size_t)r * cols + c];
+    part[grp][lane] = s;
+    __syncthreads();
+    if (grp == 0 && c < cols) {
+      float t = 0.0f;
+#pragma unroll
+      for (int g = 0; g < COLSUM_GROUPS; ++g) t += part[g][lane];
+      out[c] = t;
+    }
+    __syncthreads();
   }
 }
 
@@ -537,6 +551,8 @@ int grid1(size_t n, int bs = 256) {
   if (g > 65535 * 4) g = 65535 * 4;
   return (int)(g < 1 ? 1 : g);
 }
+// k_colsum: one block per 32 columns
+int colsum_grid(int cols) { return cols > 0 ? (cols + 31) / 32 : 1; }
 
 }  // namespace mlp
 }  // namespace pdlp
@@ -601,7 +617,7 @@ struct pdlp_mlp {
   // one mini-batch: BF16 GEMM operands in both layouts, FP32 loss path
   bf16 *xb = nullptr, *xbT = nullptr, *h1 = nullptr, *h1T = nullptr, *h2 = nullptr, *h2T = nullptr;
   bf16 *dyh = nullptr, *dyhT = nullptr, *dz2h = nullptr, *dz2hT = nullptr, *dz1hT = nullptr;
-  float *xin = nullptr, *tb = nullptr, *y = nullptr, *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr, *dh1 = nullptr,
+  float *xin = nullptr, *y = nullptr, *dy = nullptr, *dz2 = nullptr, *dz1 = nullptr, *dh1 = nullptr,
         *part = nullptr;
   double *lpart = nullptr;
   int lparts = 0;
@@ -689,21 +705,21 @@ int forward_hidden(pdlp_mlp *M, int B) {
 
 // loss (fused into the output layer) and every gradient into M->g for the
 // batch in xb / tb
-int forward_backward(pdlp_mlp *M, int B) {
+int forward_backward(pdlp_mlp *M, int B, const int *rows) {
   cudaStream_t s = M->stream;
   int rc = forward_hidden(M, B);
   if (rc) return rc;
   const size_t BO = (size_t)B * M->out, BH = (size_t)B * M->hid;
   const int tiles = ((M->out + TBN - 1) / TBN) * ((B + TBM - 1) / TBM);
-  EpiLoss el{M->p + M->ob3, M->tb, M->mu, M->sigma, M->dy, M->dyh, M->dyhT, M->lpart, 2.0f / (float)BO,
-             M->out, M->ldo, M->ldb, vec4(M->tb, M->out) && vec4(M->dy, M->out), 0.0};
+  EpiLoss el{M->p + M->ob3, M->T, M->mu, M->sigma, rows, M->dy, M->dyh, M->dyhT, M->lpart, 2.0f / (float)BO,
+             M->out, M->ldo, M->ldb, vec4(M->T, M->out) && vec4(M->dy, M->out), 0.0};
   rc = gemm(M, B, M->out, M->hid, 1, M->h2, M->ldh, M->w3t, M->ldh, el);
   if (rc) return rc;
   k_loss_finish<<<1, 256, 0, s>>>(M->lpart, tiles, BO, M->loss_dev);
   // output layer: gW3 = H2' dY, gb3 = column sums of dY, dH2 = dY W3'
   rc = gemm(M, M->hid, M->out, B, 1, M->h2T, M->ldb, M->dyhT, M->ldb, EpiStore{{}, M->g + M->oW3, M->out, vec4(M->g + M->oW3, M->out)});
   if (rc) return rc;
-  k_colsum<<<grid1(M->out), 256, 0, s>>>(M->dy, B, M->out, M->g + M->ob3);
+  k_colsum<<<colsum_grid(M->out), 256, 0, s>>>(M->dy, B, M->out, M->g + M->ob3);
   rc = gemm(M, B, M->hid, M->out, M->splits, M->dyh, M->ldo, M->w3, M->ldo, EpiPartial{{}, M->part, M->hid, BH, vec4(M->part, M->hid) && BH % 4 == 0});
   if (rc) return rc;
   k_splitk_relu_grad<<<grid1(BH), 256, 0, s>>>(M->part, M->splits, B, M->hid, M->h2, M->ldh, M->dz2, M->dz2h,
@@ -711,14 +727,14 @@ int forward_backward(pdlp_mlp *M, int B) {
   // second layer
   rc = gemm(M, M->hid, M->hid, B, 1, M->h1T, M->ldb, M->dz2hT, M->ldb, EpiStore{{}, M->g + M->oW2, M->hid, vec4(M->g + M->oW2, M->hid)});
   if (rc) return rc;
-  k_colsum<<<grid1(M->hid), 256, 0, s>>>(M->dz2, B, M->hid, M->g + M->ob2);
+  k_colsum<<<colsum_grid(M->hid), 256, 0, s>>>(M->dz2, B, M->hid, M->g + M->ob2);
   rc = gemm(M, B, M->hid, M->hid, 1, M->dz2h, M->ldh, M->w2, M->ldh, EpiStore{{}, M->dh1, M->hid, vec4(M->dh1, M->hid)});
   if (rc) return rc;
   k_relu_grad<<<grid1(BH), 256, 0, s>>>(M->dh1, B, M->hid, M->h1, M->ldh, M->dz1, M->dz1hT, M->ldb);
   // first layer
   rc = gemm(M, M->in, M->hid, B, 1, M->xbT, M->ldb, M->dz1hT, M->ldb, EpiStore{{}, M->g + M->oW1, M->hid, vec4(M->g + M->oW1, M->hid)});
   if (rc) return rc;
-  k_colsum<<<grid1(M->hid), 256, 0, s>>>(M->dz1, B, M->hid, M->g + M->ob1);
+  k_colsum<<<colsum_grid(M->hid), 256, 0, s>>>(M->dz1, B, M->hid, M->g + M->ob1);
   MCK(cudaGetLastError());
   return PDLP_OK;
 }
@@ -830,7 +846,6 @@ int pdlp_mlp_create(pdlp_mlp **out, int32_t in_dim, int32_t hidden, int32_t out_
   rc = rc ? rc : dalloc(M, &M->dz2hT, (size_t)hidden * LB);
   rc = rc ? rc : dalloc(M, &M->dz1hT, (size_t)hidden * LB);
   rc = rc ? rc : dalloc(M, &M->xin, B * in_dim);
-  rc = rc ? rc : dalloc(M, &M->tb, BO);
   rc = rc ? rc : dalloc(M, &M->y, BO);
   rc = rc ? rc : dalloc(M, &M->dy, BO);
   rc = rc ? rc : dalloc(M, &M->dz2, BH);
@@ -919,11 +934,10 @@ int pdlp_mlp_train(pdlp_mlp *M, int32_t steps, int32_t batch, const int32_t *idx
   cudaStream_t s = M->stream;
   MCK(cudaMemcpyAsync(M->idx, idx, sizeof(int) * (size_t)steps * batch, cudaMemcpyHostToDevice, s));
   for (int st = 0; st < steps; ++st) {
-    dim3 gg((M->out + 255) / 256 < 64 ? (M->out + 255) / 256 : 64, batch);
-    k_gather<<<gg, 256, 0, s>>>(M->X, M->T, M->idx + (size_t)st * batch, batch, M->in, M->out, M->xb, M->ldi, M->xbT,
-                                M->ldb, M->tb);
+    const int *rows = M->idx + (size_t)st * batch;
+    k_gather<<<batch, 64, 0, s>>>(M->X, rows, batch, M->in, M->xb, M->ldi, M->xbT, M->ldb);
     MCK(cudaGetLastError());
-    rc = forward_backward(M, batch);
+    rc = forward_backward(M, batch, rows);
     if (rc) return rc;
     MCK(cudaMemcpyAsync(dloss + st, M->loss_dev, sizeof(float), cudaMemcpyDeviceToDevice, s));
     ++M->adam_t;
@@ -977,9 +991,8 @@ int pdlp_mlp_gradients(pdlp_mlp *M, int32_t batch, const int32_t *idx, float *lo
   if (rc) return rc;
   cudaStream_t s = M->stream;
   MCK(cudaMemcpyAsync(M->idx, idx, sizeof(int) * batch, cudaMemcpyHostToDevice, s));
-  dim3 gg((M->out + 255) / 256 < 64 ? (M->out + 255) / 256 : 64, batch);
-  k_gather<<<gg, 256, 0, s>>>(M->X, M->T, M->idx, batch, M->in, M->out, M->xb, M->ldi, M->xbT, M->ldb, M->tb);
-  rc = forward_backward(M, batch);
+  k_gather<<<batch, 64, 0, s>>>(M->X, M->idx, batch, M->in, M->xb, M->ldi, M->xbT, M->ldb);
+  rc = forward_backward(M, batch, M->idx);
   if (rc) return rc;
   if (loss) MCK(cudaMemcpyAsync(loss, M->loss_dev, sizeof(float), cudaMemcpyDeviceToHost, s));
   if (grads) MCK(cudaMemcpyAsync(grads, M->g, sizeof(float) * M->nparam, cudaMemcpyDeviceToHost, s));
