@@ -170,6 +170,35 @@ def aggregate_replicas(ms: float, iters: float, pg=None, device: str = "cpu"):
     return float(ms_t.item()), float(it_t.item())
 
 
+def batch_shard(work, rank: int, world: int):
+    """This rank's members of a batch sharded over `world` ranks: members in
+    decreasing expected work dealt out in a snake order (ranks 0 .. world - 1,
+    then world - 1 .. 0, ...), so every rank gets a near-equal share;
+    disjoint, covering, deterministic."""
+    import numpy as np
+
+    order = np.argsort(-np.asarray(work, dtype=np.float64), kind="stable")
+    mine = []
+    for k, i in enumerate(order):
+        rnd, pos = divmod(k, world)
+        if (pos if rnd % 2 == 0 else world - 1 - pos) == rank:
+            mine.append(int(i))
+    return sorted(mine)
+
+
+def aggregate_batch(seconds: float, optimal: int, iters: int, count: int, pg=None, device: str = "cpu"):
+    """Whole-job numbers of a sharded batch: the slowest rank's solve time
+    and the summed optimal count, iterations and LP count."""
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    c = torch.tensor([float(optimal), float(iters), float(count)], dtype=torch.float64, device=device)
+    if pg is not None:
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        pg.all_reduce(c, op=pg.ReduceOp.SUM)
+    return float(t.item()), int(c[0].item()), int(c[1].item()), int(c[2].item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -322,10 +351,12 @@ def run_batch(args, rank, world):
     """Batched mode: many uneven planted LPs (m ~ logU[50,4000], n ~ logU[2m/3,
     2.5m], density ~ U[0.5%,5%], N(0,1) values, half equality rows, 0<=x<=10)
     solved to tol in one persistent launch; compared with the single-instance
-    GPU solver run one LP after another on a sample of the same LPs."""
-    if rank != 0:
-        return
+    GPU solver run one LP after another on a sample of the same LPs.  With N
+    ranks the LPs are sharded by expected work (batch_shard), each rank solves
+    its share in its own launch with no collective on the data path, and the
+    job's time is the slowest rank's (aggregate_batch)."""
     import numpy as np
+    import torch
 
     import lpgen
     from paper_2311_12180_gb300 import _build
@@ -333,17 +364,47 @@ def run_batch(args, rank, world):
     from paper_2311_12180_gb300.metrics import shifted_geometric_mean
 
     _build.build()
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(dist_env()[2])
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dist_env()[2]))
+        pg = dist
     tol = args.batch_tol
     t = time.perf_counter()
-    lps = lpgen.batch_lps(args.batch_count, seed=0)
+    if world > 1:
+        mine = batch_shard(lpgen.batch_work(args.batch_count, seed=0), rank, world)
+        lps = lpgen.batch_subset(mine, args.batch_count, seed=0)
+    else:
+        lps = lpgen.batch_lps(args.batch_count, seed=0)
     gen_s = time.perf_counter() - t
     t = time.perf_counter()
     b = P.BatchSolver(lps)
     create_s = time.perf_counter() - t
     b.solve(tol=tol, max_iter=2)  # graph capture outside the timed solve
+    if pg is not None:
+        torch.cuda.synchronize()
+        pg.barrier()
     t = time.perf_counter()
     xs, ys, st, it = b.solve(tol=tol, max_iter=args.batch_max_iter)
     solve_s = time.perf_counter() - t
+    if pg is not None:
+        job_s, job_opt, job_iters, job_count = aggregate_batch(solve_s, int(np.sum(st == P.OPTIMAL)), int(np.sum(it)),
+                                                               len(lps), pg, device="cuda")
+        if rank != 0:
+            b.close()
+            pg.destroy_process_group()
+            return
+        line = {"metric": "batch time-to-%g KKT (s)" % tol, "value": job_s, "unit": "s", "n_gpus": world,
+                "higher_is_better": False, "scaling": "strong", "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "%d planted LPs sharded over %d ranks by expected work" % (job_count, world)},
+                "optimal": job_opt, "count": job_count, "iters_total": job_iters,
+                "agg_iters_per_s": job_iters / job_s, "rank0": {"lps": len(lps), "seconds": solve_s}}
+        b.close()
+        print(json.dumps(line), flush=True)
+        pg.destroy_process_group()
+        return
     stats = b.stats()
     t0s, t1s = b.times()
     b.close()

@@ -42,6 +42,8 @@ __all__ = [
     "random_boxed_lp",
     "batch_lps",
     "batch_lp",
+    "batch_subset",
+    "batch_work",
     "planted_qp",
     "permuted",
     "infeasible_lp",
@@ -442,6 +444,21 @@ def batch_lp(index: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,
         if i == index:
             return _batch_member(i, seed, m, n, d)
     raise IndexError(index)
+
+
+def batch_subset(indices, count: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,
+                 dens_lo: float = 0.005, dens_hi: float = 0.05) -> list[LP]:
+    """Members `indices` of batch_lps(count, seed, ...), each built alone (a
+    rank of a sharded run builds only its own)."""
+    shapes = list(_batch_shapes(count, seed, m_lo, m_hi, dens_lo, dens_hi))
+    return [_batch_member(int(i), seed, *shapes[int(i)]) for i in indices]
+
+
+def batch_work(count: int, seed: int = 0, m_lo: int = 50, m_hi: int = 4000,
+               dens_lo: float = 0.005, dens_hi: float = 0.05) -> np.ndarray:
+    """Expected nonzeros m n density of each member of batch_lps(count, seed),
+    from the shapes alone (no member is built)."""
+    return np.array([m * n * d for m, n, d in _batch_shapes(count, seed, m_lo, m_hi, dens_lo, dens_hi)])
 
 
 def planted_qp(lp: LP, seed: int = 0, frac: float = 0.6, lo: float = 0.0, hi: float = 2.0) -> LP:

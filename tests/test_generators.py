@@ -27,3 +27,15 @@ def test_permuted_lp_is_the_same_lp():
     assert t["rp"] < 1e-12 and t["rd"] < 1e-12 and abs(t["pobj"] - lp.obj_star) < 1e-10 * (1 + abs(lp.obj_star))
     # equality rows stay first
     assert p.n_eq == lp.n_eq and np.array_equal(np.sort(p.q[: p.n_eq]), np.sort(lp.q[: lp.n_eq]))
+
+
+def test_batch_subset_builds_the_same_members():
+    """A rank of a sharded batch builds only its LPs: each equals the member of
+    the whole batch, and the expected work follows the realised nonzeros."""
+    full = lpgen.batch_lps(10, seed=3)
+    sub = lpgen.batch_subset([2, 5, 9], 10, seed=3)
+    for i, lp in zip([2, 5, 9], sub):
+        assert np.array_equal(lp.row_ptr, full[i].row_ptr) and np.array_equal(lp.col_idx, full[i].col_idx)
+        assert np.array_equal(lp.val, full[i].val) and np.array_equal(lp.c, full[i].c)
+    w = lpgen.batch_work(10, seed=3)
+    assert np.corrcoef(w, [lp.nnz for lp in full])[0, 1] > 0.99
