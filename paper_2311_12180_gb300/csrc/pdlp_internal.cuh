@@ -25,19 +25,11 @@ constexpr int SELL_LONG = 48;
 constexpr int SELL_U_P = 2;
 constexpr int SELL_U_D = 2;
 constexpr int SELL_U_C = 4;
-// bulk L2 prefetch of the warp's next work item (and of the rest of the
-// current one) when an item starts
-constexpr bool SELL_PREFETCH = false;
 // CTAs per SM the two-vector check pass over K' is compiled for
 constexpr int CHECK_MINB = 2;
 // CTAs per SM the step kernels are compiled for (registers per thread:
 // 65536 / (256 x this))
 constexpr int STEP_MINB = 4;
-// k_dual: load the next batch of indices and values before the current
-// batch's FMAs (software pipelining of the strided loop)
-constexpr bool SELL_PIPE_D = false;
-// load the warp's next work-item descriptor at the start of the current item
-constexpr bool SELL_NEXT_DESC = false;
 
 // One unit of work for one warp: a slice {first row, rows (1..32), L, off}
 // or a long row {row, -1, length, off}.

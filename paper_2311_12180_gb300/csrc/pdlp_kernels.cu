@@ -155,49 +155,11 @@ __device__ __forceinline__ double widen(float v) { return f2d(v); }
 // stride: acc[a] += val * xs[a][col] in stride order (FMA), padding (column
 // -1) skipped.  U strides are loaded (streaming, coalesced across the
 // warp) before their gathers are issued, and all gathers before the FMAs.
-template <int U, typename VT, int NV, bool SCALED, bool PIPE = false>
+template <int U, typename VT, int NV, bool SCALED>
 __device__ __forceinline__ void strided_dot(const int32_t *__restrict__ ip, const VT *__restrict__ vp, int cnt,
                                             const double *const (&xs)[NV], const double (&sc)[NV],
                                             double (&acc)[NV]) {
   int k = 0;
-  if (PIPE && cnt >= U) {
-    // batch k's indices and values are in registers when its gathers issue;
-    // batch k + 1's loads go out before batch k's FMAs
-    int c[U];
-    VT v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      c[u] = __ldcs(ip + 32 * u);
-      v[u] = __ldcs(vp + 32 * u);
-    }
-    for (; k + U <= cnt; k += U) {
-      double g[NV][U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int a = 0; a < NV; ++a) {
-          const double xv = c[u] >= 0 ? __ldg(xs[a] + c[u]) : 0.0;
-          g[a][u] = SCALED ? sc[a] * xv : xv;
-        }
-      const bool more = k + 2 * U <= cnt;
-      int cn[U];
-      VT vn[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        cn[u] = more ? __ldcs(ip + 32 * (k + U + u)) : -1;
-        vn[u] = more ? __ldcs(vp + 32 * (k + U + u)) : VT(0);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int a = 0; a < NV; ++a) acc[a] = fma(widen(v[u]), g[a][u], acc[a]);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        c[u] = cn[u];
-        v[u] = vn[u];
-      }
-    }
-  }
   for (; k + U <= cnt; k += U) {
     int c[U];
     VT v[U];
@@ -228,17 +190,6 @@ __device__ __forceinline__ void strided_dot(const int32_t *__restrict__ ip, cons
       acc[a] = fma(widen(v), SCALED ? sc[a] * xv : xv, acc[a]);
     }
   }
-}
-
-// Bulk L2 prefetch of `count` stored entries from `off` (indices and
-// values; count a multiple of 32, so both ranges are multiples of 16 bytes
-// and start 128-byte aligned).
-template <typename VT>
-__device__ __forceinline__ void prefetch_item(const SellMat &A, const VT *val, int off, int count) {
-  if (count <= 0) return;
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(A.idx + off), "r"(4 * count) : "memory");
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(val + off), "r"((int)sizeof(VT) * count)
-               : "memory");
 }
 
 // One butterfly level: lanes with the `off` bit clear keep row a's pair sum,
@@ -366,7 +317,7 @@ __device__ __forceinline__ void long_flush(LongRows<NV> &lr, Epi &ep) {
 // vector a are multiplied by sc[a] (the epoch average (1/W) sum).  Warp w of
 // the grid takes items w, 2G - 1 - w, 2G + w, ... of the schedule (G warps):
 // a snake over the cost-sorted items, so every warp gets about the same work.
-template <int U, typename VT, int NV, bool SCALED, class Epi, bool PIPE = false>
+template <int U, typename VT, int NV, bool SCALED, class Epi>
 __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict__ val,
                                           const double *const (&xs)[NV], const double (&sc)[NV], Epi &ep,
                                           int *warp_rows, double *warp_tot) {
@@ -387,18 +338,8 @@ __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict
   long long it = item_of(0);
   int4 d = it >= 0 ? __ldg(A.items + it) : make_int4(0, 0, 0, 0);
   for (int b = 0; it >= 0; ++b) {
-    // with SELL_NEXT_DESC the next item's descriptor is loaded while this
-    // item runs (its latency hidden, four more live registers)
     const long long itn = item_of(b + 1);
     int4 dn = make_int4(0, 0, 0, 0);
-    if (SELL_NEXT_DESC && itn >= 0) dn = __ldg(A.items + itn);
-    if (SELL_PREFETCH && lane == 0) {
-      // the rest of this item, and the warp's next item, stream into L2
-      // while this one's first loads and gathers are in flight
-      const int nstr = d.y > 0 ? d.z : (d.z + 31) >> 5;
-      if (nstr > U) prefetch_item(A, val, d.w + 32 * U, 32 * (nstr - U));
-      if (SELL_NEXT_DESC && itn >= 0) prefetch_item(A, val, dn.w, 32 * (dn.y > 0 ? dn.z : (dn.z + 31) >> 5));
-    }
     double acc[NV];
 #pragma unroll
     for (int a = 0; a < NV; ++a) acc[a] = 0.0;
@@ -406,13 +347,13 @@ __device__ __forceinline__ void spmv_sell(const SellMat &A, const VT *__restrict
       const bool has = lane < d.y;
       const int row = d.x + lane;
       if (has) ep.prefetch(row);
-      strided_dot<U, VT, NV, SCALED, PIPE>(A.idx + d.w + lane, val + d.w + lane, d.z, xs, sc, acc);
+      strided_dot<U, VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, d.z, xs, sc, acc);
       if (has) ep.finish(row, acc);
     } else {  // long row: the whole warp
-      strided_dot<U, VT, NV, SCALED, PIPE>(A.idx + d.w + lane, val + d.w + lane, (d.z + 31) >> 5, xs, sc, acc);
+      strided_dot<U, VT, NV, SCALED>(A.idx + d.w + lane, val + d.w + lane, (d.z + 31) >> 5, xs, sc, acc);
       long_push(lr, acc, d.x, ep);
     }
-    if (!SELL_NEXT_DESC && itn >= 0) dn = __ldg(A.items + itn);
+    if (itn >= 0) dn = __ldg(A.items + itn);  // the next item's descriptor
     it = itn;
     d = dn;
   }
@@ -592,9 +533,9 @@ __global__ void __launch_bounds__(NT, STEP_MINB) k_dual(SellMat K, Vecs V, DevSt
   const double *const xs[1] = {V.x[nxt]};
   const double sc[1] = {1.0};
   if (f32)
-    spmv_sell<SELL_U_D, float, 1, false, DualEpi, SELL_PIPE_D>(K, K.val32, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_D, float, 1, false, DualEpi>(K, K.val32, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   else
-    spmv_sell<SELL_U_D, double, 1, false, DualEpi, SELL_PIPE_D>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
+    spmv_sell<SELL_U_D, double, 1, false, DualEpi>(K, K.val, xs, sc, ep, s_rows[threadIdx.x >> 5], s_tot[threadIdx.x >> 5]);
   double acc[2] = {ep.dy2, ep.cross};
   double tot[2];
   if (!grid_finish<2>(acc, V.partB, &st->cnt[CNT_DUAL], s_red, &s_flag, tot)) return;
