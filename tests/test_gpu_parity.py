@@ -310,6 +310,22 @@ def test_fp32_values_solution_parity(seed):
     assert info["f64_switch_iter"] == -1 or 0 < info["f64_switch_iter"] <= it8
 
 
+def test_fp32_values_with_entries_below_the_float_range():
+    """Entries far below the smallest normal float (1e-42 and -3e-45 next to
+    O(1) ones) become signed zeros in the FP32 copy the step kernels read; the
+    solve still meets tol on the FP64 LP (termination uses the FP64 K) and
+    matches the oracle's objective on the same LP."""
+    lp = lpgen.tiny_lp(6)
+    lp.val = lp.val.copy()
+    lp.val[[5, 17]] = [1e-42, -3e-45]
+    r8 = _oracle(lp, tol=1e-8)
+    with _solver(lp, value_bits=32) as s:
+        x8, y8, st8, _ = s.solve(tol=1e-8)
+    assert st8 == P.OPTIMAL and r8.status == P.OPTIMAL
+    assert oracle.passes(lp, x8, y8, 1e-8)
+    assert abs(float(lp.c @ x8) - r8.pobj) <= 1e-6 * (1 + abs(r8.pobj))
+
+
 def test_fp32_values_first_steps_track_fp64():
     """Before any restart decision can differ, the FP32-valued steps follow
     the FP64 trajectory to within the FP32 rounding of the matrix (2^-24
