@@ -19,9 +19,11 @@ e2e    = the same metric through the C ABI with (page-locked) host buffers:
 roofline = the dominant kernel's algorithmic HBM bytes per launch over its
          CUDA-event-timed average duration, against the measured copy
          bandwidth in MEASURED_PEAKS.json; `roofs` adds, per step kernel, the
-         random-gather ceiling (one gather per nonzero) and the FP64-pipe
-         ceiling (FP64 instructions counted from the source), both measured
-         on the GPU by pdlp_probe_rates, and names the binding one;
+         random-gather ceiling (one gather per nonzero), the same with the
+         SpMV's index and value stream beside the gathers, and the FP64-pipe
+         ceiling (FP64 instructions counted from the source), all measured
+         on the GPU by pdlp_probe_rates / pdlp_probe_stream_gathers, and
+         names the binding one;
 time_to_tol = after the timed region, a solve from zero to each --ttt-tols
          tolerance (default 1e-4): seconds, iterations, objective error
          against the planted optimum (--trace-out FILE writes each of these
@@ -743,6 +745,7 @@ def main():
     # the on-chip ceilings next to HBM: random gathers (one per nonzero) and
     # the FP64 pipe (FP64 instructions counted from the kernels' source)
     g_rate, f_rate = P.probe_rates()
+    gs_rate = P.probe_stream_gathers()
     lay = solver.layout()
     roofs = {}
     for k in ("k_primal", "k_dual"):
@@ -756,10 +759,12 @@ def main():
                     "frac": algorithmic_bytes(lp, k, vb) / t_k / (peak * 1e9)},
             "gather": {"per_launch": lp.nnz, "peak_per_s": g_rate, "floor_s": lp.nnz / g_rate,
                        "frac": lp.nnz / t_k / g_rate},
+            "gather_stream": {"per_launch": lp.nnz, "peak_per_s": gs_rate, "floor_s": lp.nnz / gs_rate,
+                              "frac": lp.nnz / t_k / gs_rate},
             "fp64": {"warp_instructions": wi, "lane_ops": 32 * wi, "peak_lane_ops_per_s": f_rate,
                      "floor_s": 32 * wi / f_rate, "frac": 32 * wi / t_k / f_rate},
         }
-        roofs[k]["binding"] = max(("hbm", "gather", "fp64"), key=lambda r: roofs[k][r]["frac"])
+        roofs[k]["binding"] = max(("hbm", "gather", "gather_stream", "fp64"), key=lambda r: roofs[k][r]["frac"])
     solver.finish()
     info = solver.info()
 
@@ -838,7 +843,9 @@ def main():
                      "roofs": roofs, "binding": roofs[dom]["binding"],
                      "binding_frac": roofs[dom][roofs[dom]["binding"]]["frac"],
                      "roofs_note": "gather and FP64 peaks measured on this GPU by pdlp_probe_rates (random "
-                                   "8-byte gathers of a 16 MB vector; FP64 FMA lane operations)"},
+                                   "8-byte gathers of a 16 MB vector; FP64 FMA lane operations); gather_stream "
+                                   "by pdlp_probe_stream_gathers (the same gathers with a 4-byte index and an "
+                                   "8-byte value streamed per entry, one FMA each: an SpMV's bytes per nonzero)"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "iters": it2, "seconds": e2e_s, "create_ms": e2e_setup_ms, "note": "one step = create + solve(%d iterations) + outputs" % it2},

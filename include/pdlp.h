@@ -292,6 +292,15 @@ int pdlp_get_layout(const pdlp_solver *s, pdlp_layout_info *info);
  * Errors: PDLP_ERR_INVALID for null arguments, PDLP_ERR_CUDA. */
 int pdlp_probe_rates(double *gathers_per_s, double *dfma_per_s);
 
+/* The same random gathers with an SpMV's matrix stream beside them: per
+ * entry a coalesced 4-byte index, a coalesced 8-byte value, the gather and
+ * one FP64 FMA (the bytes a sliced-ELL SpMV moves per stored nonzero), 2e7
+ * entries; gathers per second.  The ceiling a step kernel's SpMV meets on
+ * an LP whose columns give the gathers no reuse.  Not part of the method;
+ * allocates ~260 MB for the duration of the call.  Errors as
+ * pdlp_probe_rates. */
+int pdlp_probe_stream_gathers(double *gathers_per_s);
+
 /* The CUDA stream (cudaStream_t as void*) all work of `s` is ordered on. */
 void *pdlp_get_stream(const pdlp_solver *s);
 

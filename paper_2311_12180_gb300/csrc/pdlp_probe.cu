@@ -50,6 +50,36 @@ __global__ void __launch_bounds__(PT, 4) k_probe_gather(const int32_t *__restric
   out[(size_t)blockIdx.x * PT + threadIdx.x] = h;
 }
 
+// The same gathers with an SpMV's matrix stream beside them: each thread's
+// chunk of 8 entries also streams their 8 FP64 values (4 x 16-byte loads)
+// and multiplies-adds them into one FP64 sum, so per entry it moves what a
+// sliced-ELL row does -- a 4-byte index, an 8-byte value, a 32-byte sector
+// of x -- with one FMA.
+__global__ void __launch_bounds__(PT, 4) k_probe_gather_stream(const int32_t *__restrict__ idx,
+                                                               const double *__restrict__ val, long long chunks,
+                                                               const double *__restrict__ x,
+                                                               double *__restrict__ out) {
+  double acc = 0.0;
+  for (long long ch = (long long)blockIdx.x * PT + threadIdx.x; ch < chunks; ch += (long long)gridDim.x * PT) {
+    const int4 a = __ldcs(reinterpret_cast<const int4 *>(idx) + 2 * ch);
+    const int4 b = __ldcs(reinterpret_cast<const int4 *>(idx) + 2 * ch + 1);
+    const int c[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    double v[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 w = __ldcs(reinterpret_cast<const double2 *>(val) + 4 * ch + k);
+      v[2 * k] = w.x;
+      v[2 * k + 1] = w.y;
+    }
+    double g[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) g[k] = __ldg(x + c[k]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc = fma(v[k], g[k], acc);
+  }
+  out[(size_t)blockIdx.x * PT + threadIdx.x] = acc;
+}
+
 // Eight independent FMA chains per thread.
 __global__ void __launch_bounds__(PT) k_probe_fma(double *out, int iters, double a) {
   double r[8];
@@ -67,6 +97,58 @@ __global__ void __launch_bounds__(PT) k_probe_fma(double *out, int iters, double
 
 }  // namespace
 }  // namespace pdlp
+
+extern "C" int pdlp_probe_stream_gathers(double *gathers_per_s) {
+  using namespace pdlp;
+  if (!gathers_per_s) return set_error(PDLP_ERR_INVALID, "pdlp_probe_stream_gathers: null argument");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
+  const int32_t n = 1 << 21;         // 16 MB of FP64: L2-resident, far beyond L1
+  const long long count = 20000000;  // entries (a multiple of 8)
+  const int ggrid = 4 * sms;
+  int32_t *idx = nullptr;
+  double *x = nullptr, *val = nullptr, *go = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&idx, sizeof(int32_t) * count);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&val, sizeof(double) * count);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&x, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&go, sizeof(double) * ggrid * PT);
+  if (e == cudaSuccess) {
+    k_probe_fill<<<1024, PT, 0, st>>>(idx, count, n, x);
+    e = cudaMemsetAsync(val, 0, sizeof(double) * count, st);
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) {  // warm-up
+      k_probe_gather_stream<<<ggrid, PT, 0, st>>>(idx, val, count / 8, x, go);
+      e = cudaGetLastError();
+    }
+  }
+  const int reps = 10;
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+    k_probe_gather_stream<<<ggrid, PT, 0, st>>>(idx, val, count / 8, x, go);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (st) cudaStreamSynchronize(st);
+  if (idx) cudaFree(idx);
+  if (val) cudaFree(val);
+  if (x) cudaFree(x);
+  if (go) cudaFree(go);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (e != cudaSuccess) return set_error(PDLP_ERR_CUDA, cudaGetErrorString(e));
+  *gathers_per_s = (double)count * reps / (1e-3 * ms);
+  return PDLP_OK;
+}
 
 extern "C" int pdlp_probe_rates(double *gathers_per_s, double *dfma_per_s) {
   using namespace pdlp;

@@ -100,7 +100,7 @@ EXPORTS = (
     "pdlp_kernel_name", "pdlp_get_info", "pdlp_get_trace", "pdlp_get_scaling", "pdlp_get_stream",
     "pdlp_device_bytes", "pdlp_destroy", "pdlp_last_error", "pdlp_scale_device_noalloc",
     "pdlp_create_device", "pdlp_get_state", "pdlp_set_state", "pdlp_resume", "pdlp_get_layout",
-    "pdlp_probe_rates", "pdlp_set_quadratic",
+    "pdlp_probe_rates", "pdlp_probe_stream_gathers", "pdlp_set_quadratic",
     "pdlp_batch_create", "pdlp_batch_solve", "pdlp_batch_info", "pdlp_batch_lanes", "pdlp_batch_times", "pdlp_batch_destroy",
     "pdlp_mlp_create", "pdlp_mlp_param_count", "pdlp_mlp_set_params", "pdlp_mlp_get_params", "pdlp_mlp_set_data",
     "pdlp_mlp_train", "pdlp_mlp_predict", "pdlp_mlp_gradients", "pdlp_mlp_stats", "pdlp_mlp_destroy",
@@ -186,6 +186,8 @@ def lib():
     L.pdlp_get_layout.restype = C.c_int
     L.pdlp_probe_rates.argtypes = [P(d), P(d)]
     L.pdlp_probe_rates.restype = C.c_int
+    L.pdlp_probe_stream_gathers.argtypes = [P(d)]
+    L.pdlp_probe_stream_gathers.restype = C.c_int
     L.pdlp_solve.argtypes = [vp, d, i64, vp, vp, P(C.c_int), P(i64)]
     L.pdlp_solve.restype = C.c_int
     L.pdlp_solve_warm.argtypes = [vp, vp, vp, d, i64, vp, vp, P(C.c_int), P(i64)]
@@ -347,6 +349,14 @@ def probe_rates():
     g, f = C.c_double(0), C.c_double(0)
     _check(lib().pdlp_probe_rates(C.byref(g), C.byref(f)))
     return g.value, f.value
+
+
+def probe_stream_gathers():
+    """Random 8-byte gathers per second with an SpMV's index and value stream
+    beside them (pdlp_probe_stream_gathers)."""
+    g = C.c_double(0)
+    _check(lib().pdlp_probe_stream_gathers(C.byref(g)))
+    return g.value
 
 
 def kernel_names():

@@ -130,3 +130,14 @@ def test_device_create_rejects_bad_input(defect):
     if defect in ("col_range", "nan_val"):
         assert str(17 if defect == "col_range" else 5) in str(e.value)
     del keep
+
+
+def test_probe_rates_are_ordered():
+    """The roofline probes: random gathers alone, and with an SpMV's index and
+    value stream beside them (more bytes per gather, so no faster), and the
+    FP64 FMA rate, all positive and finite on this GPU."""
+    g, f = P.probe_rates()
+    gs = P.probe_stream_gathers()
+    assert np.isfinite(g) and np.isfinite(gs) and np.isfinite(f)
+    assert g > 0 and gs > 0 and f > 0
+    assert gs <= 1.05 * g
