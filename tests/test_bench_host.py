@@ -1,0 +1,54 @@
+"""Host-side helpers of bench.py: the algorithmic byte counts behind the
+roofline, the FP64 instruction count behind the FP64 roof, and the JSON-lines
+export of the per-check metrics.  No GPU needed."""
+
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import lpgen  # noqa: E402
+from paper_2311_12180_gb300 import pdlp as P  # noqa: E402
+
+
+def test_algorithmic_bytes_count_each_array_once():
+    """k_primal: K' row starts, indices and values, the gathered y, and the
+    eight n-vectors it reads or writes; k_dual: K's, the gathered x', and its
+    seven m-vectors; FP32 values save 4 bytes per nonzero."""
+    lp = lpgen.tiny_lp(0)
+    m, n, z = lp.m, lp.n, lp.nnz
+    assert bench.algorithmic_bytes(lp, "k_primal") == 4 * (n + 1) + 12 * z + 8 * m + 64 * n
+    assert bench.algorithmic_bytes(lp, "k_dual") == 4 * (m + 1) + 12 * z + 8 * n + 56 * m
+    assert bench.algorithmic_bytes(lp, "k_dual", 4) == bench.algorithmic_bytes(lp, "k_dual") - 4 * z
+    assert bench.algorithmic_bytes(lp, "k_primal_reuse_g") == 72 * n
+
+
+def test_fp64_instruction_count_follows_the_layout():
+    """One FMA per stored entry (32 per warp instruction), one epilogue per
+    slice (8 FP64 operations per row in k_dual, 5 in k_primal) and, per 32
+    long rows, a 31-addition butterfly plus one epilogue."""
+    lay = {"K_stored": 6400, "K_slices": 10, "K_long_rows": 33, "KT_stored": 3200, "KT_slices": 100,
+           "KT_long_rows": 0}
+    assert bench.fp64_warp_instructions(lay, "k_dual") == 6400 / 32 + 8 * 10 + (31 + 8) * 2
+    assert bench.fp64_warp_instructions(lay, "k_primal") == 3200 / 32 + 5 * 100
+
+
+def test_trace_export_writes_one_json_line_per_check(tmp_path):
+    tr = np.zeros(3, dtype=P.CHECK_DTYPE)
+    tr["k"] = [64, 128, 192]
+    tr["restart"] = [4, 0, 1]
+    tr["rel_gap"] = [1e-2, 5e-3, 1e-3]
+    path = tmp_path / "checks.jsonl"
+    bench.write_trace(str(path), tr, 1e-4, 3)
+    bench.write_trace(str(path), tr[:1], 1e-6, 1)
+    lines = [json.loads(s) for s in path.read_text().splitlines()]
+    assert len(lines) == 4
+    assert [r["k"] for r in lines] == [64, 128, 192, 64]
+    assert lines[0]["restart"] == 4 and lines[2]["rel_gap"] == 1e-3
+    assert lines[3]["tol"] == 1e-6 and lines[3]["checks_recorded"] == 1
+    assert set(lines[0]) == {"tol", "checks_recorded", *P.CHECK_DTYPE.names}
