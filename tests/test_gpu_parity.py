@@ -189,7 +189,8 @@ def test_edge_cases(case):
     elif case == "free_vars":
         lp = lpgen.large_lp(23, m=400, n=800, nnz=6000)  # 20 % free, 50 % [0, inf)
     elif case == "long_rows":
-        # rows much longer than a tile (2048) next to short ones
+        # rows far beyond the 48-entry slice limit (one warp each, up to 157
+        # strides of 32 entries) next to short ones
         m, n = 40, 12000
         lens = np.array([1, 2, 5000, 3, 2500, 1] + [40] * (m - 6))
         row_ptr, cols = lpgen._sample_rows(rng, lens, n)
@@ -205,7 +206,7 @@ def test_edge_cases(case):
         q = np.concatenate([base.q, [-1.0]])
         lp = lpgen.LP(m=m, n=n, n_eq=base.n_eq, c=c, row_ptr=row_ptr, col_idx=base.col_idx, val=base.val, q=q,
                       l=np.concatenate([base.l, np.zeros(7)]), u=np.concatenate([base.u, np.full(7, 3.0)]))
-    else:  # sizes that leave a ragged last tile on both sides
+    else:  # sizes that leave a ragged last slice of 32 rows on both sides
         lp = lpgen.tiny_lp(25, m_eq=257, m_ineq=300, n=2049, density=0.004)
     r = _oracle(lp, tol=1e-8, max_iter=200000)
     assert r.status == oracle.OPTIMAL
