@@ -70,7 +70,7 @@ class _Params(C.Structure):
         ("beta_art", C.c_double),
         ("eps_infeas", C.c_double),
         ("restart_metric", C.c_int32),
-        ("pad_", C.c_int32),
+        ("step_value_bits", C.c_int32),
     ]
 
 
@@ -208,11 +208,14 @@ class Params:
     beta_art: float = 0.36
     eps_infeas: float = 1e-8
     restart_metric: int = 0  # 0: KKT error (Sec. 3.4); 1: normalized duality gap (ablation only)
+    # 64: FP64 K~; 32: Algorithm 2's products with K~ rounded to FP32 (the
+    # FP32-values mode of the steps, up to the first check)
+    step_value_bits: int = 64
 
     def struct(self):
         return _Params(self.tol, self.max_iter, self.check_period, self.ruiz_iters, self.pc_alpha,
                        self.theta, self.eps_zero, self.beta_suff, self.beta_nec, self.beta_art,
-                       self.eps_infeas, self.restart_metric, 0)
+                       self.eps_infeas, self.restart_metric, self.step_value_bits)
 
 
 @dataclass

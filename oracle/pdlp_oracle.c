@@ -83,6 +83,7 @@
  * the results are the same on x86-64 and aarch64).
  */
 
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -119,7 +120,12 @@ typedef struct {
   double eps_infeas; /* relative tolerance of the infeasibility certificates; 0 = off */
   int32_t restart_metric; /* 0: KKT error, eq. (kkt) (Sec. 3.4); 1: normalized duality gap
                              (the restart metric of CPU PDLP the paper compares against) */
-  int32_t pad_;
+  int32_t step_value_bits; /* 64 (or 0): FP64 K~ throughout; 32: the products of Algorithm 2's
+                              trials and of the accepted iterate use K~ rounded to FP32 (values
+                              below the smallest normal float become signed zeros), everything
+                              else stays FP64 -- the FP32-values mode of the steps, followed up to
+                              the first restart / termination check (the GPU's checks then
+                              recompute their products with the FP64 K~) */
 } orc_params;
 
 typedef struct {
@@ -599,6 +605,7 @@ typedef struct {
   double *sqd; /* QP: the scaled diagonal D2 Q D2 (NULL for an LP) */
   int32_t *tp, *ti;
   double *tv;
+  double *sv32, *tv32; /* K~ and K~' rounded to FP32 (step_value_bits = 32) */
   int64_t *perm;
   /* iterates and products */
   double *x, *y, *Kx, *KTy, *xp, *yp, *v, *Kv, *dxv, *Kdx;
@@ -611,7 +618,8 @@ static void free_work(orc_work *w) {
   double **d[] = {&w->sv, &w->D1, &w->D2, &w->sc, &w->sq, &w->sl, &w->su, &w->tv,
                   &w->x, &w->y, &w->Kx, &w->KTy, &w->xp, &w->yp, &w->v, &w->Kv,
                   &w->dxv, &w->Kdx, &w->sum_x, &w->sum_y, &w->xb, &w->yb, &w->Kxb,
-                  &w->KTyb, &w->x_last, &w->y_last, &w->xo, &w->yo, &w->x_prev, &w->y_prev, &w->sqd};
+                  &w->KTyb, &w->x_last, &w->y_last, &w->xo, &w->yo, &w->x_prev, &w->y_prev, &w->sqd,
+                  &w->sv32, &w->tv32};
   for (size_t i = 0; i < sizeof(d) / sizeof(d[0]); ++i) {
     free(*d[i]);
     *d[i] = NULL;
@@ -619,6 +627,14 @@ static void free_work(orc_work *w) {
   free(w->tp);
   free(w->ti);
   free(w->perm);
+}
+
+/* v rounded to the nearest FP32 value; below the smallest normal float the
+ * signed zero (the FP32-values mode's copy of K~). */
+static double round_f32(double v) {
+  float f = (float)v;
+  if (fabsf(f) < FLT_MIN) f = copysignf(0.0f, f);
+  return (double)f;
 }
 
 static int validate(const orc_lp *lp) {
@@ -656,6 +672,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
   if (!lp || !p || !x_out || !y_out || !info) return ORC_ERR_INVALID;
   if (validate(lp) != ORC_OK) return ORC_ERR_INVALID;
   if (p->check_period < 1 || p->max_iter < 1 || !(p->tol >= 0.0) || !(p->eps_infeas >= 0.0)) return ORC_ERR_INVALID;
+  if (p->step_value_bits != 0 && p->step_value_bits != 64 && p->step_value_bits != 32) return ORC_ERR_INVALID;
   const int32_t m = lp->m, n = lp->n, n_eq = lp->n_eq;
   const int32_t *rp = lp->row_ptr, *ci = lp->col_idx;
   const int64_t nnz = m > 0 ? rp[m] : 0;
@@ -727,6 +744,20 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     return ORC_ERR_NOMEM;
   }
   for (int64_t e = 0; e < nnz; ++e) w.tv[e] = w.sv[w.perm[e]];
+  /* the steps' copy of K~ and K~' (FP32 values, widened exactly) */
+  const double *ssv = w.sv, *stv = w.tv;
+  if (p->step_value_bits == 32) {
+    w.sv32 = (double *)calloc(Z, sizeof(double));
+    w.tv32 = (double *)calloc(Z, sizeof(double));
+    if (!w.sv32 || !w.tv32) {
+      free_work(&w);
+      return ORC_ERR_NOMEM;
+    }
+    for (int64_t e = 0; e < nnz; ++e) w.sv32[e] = round_f32(w.sv[e]);
+    for (int64_t e = 0; e < nnz; ++e) w.tv32[e] = round_f32(w.tv[e]);
+    ssv = w.sv32;
+    stv = w.tv32;
+  }
 
   /* ---- Algorithm 1, initialisation ---- */
   double kmax = 0.0;
@@ -764,14 +795,14 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
       else
         for (int32_t j = 0; j < n; ++j) w.xp[j] = clamp(w.x[j] - tau * (w.sc[j] - w.KTy[j]), w.sl[j], w.su[j]);
       for (int32_t j = 0; j < n; ++j) w.v[j] = 2.0 * w.xp[j] - w.x[j];
-      spmv(m, rp, ci, w.sv, w.v, w.Kv);
+      spmv(m, rp, ci, ssv, w.v, w.Kv);
       for (int32_t i = 0; i < m; ++i) {
         double yn = w.y[i] + sigma * (w.sq[i] - w.Kv[i]);
         if (i >= n_eq && yn < 0.0) yn = 0.0;
         w.yp[i] = yn;
       }
       for (int32_t j = 0; j < n; ++j) w.dxv[j] = w.xp[j] - w.x[j];
-      spmv(m, rp, ci, w.sv, w.dxv, w.Kdx);
+      spmv(m, rp, ci, ssv, w.dxv, w.Kdx);
       double dx2 = dot(n, w.dxv, w.dxv);
       double dy2 = 0.0, cross = 0.0;
       for (int32_t i = 0; i < m; ++i) {
@@ -794,8 +825,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     memcpy(w.y_prev, w.y, sizeof(double) * (size_t)m);
     memcpy(w.x, w.xp, sizeof(double) * (size_t)n);
     memcpy(w.y, w.yp, sizeof(double) * (size_t)m);
-    spmv(m, rp, ci, w.sv, w.x, w.Kx);
-    spmv(n, w.tp, w.ti, w.tv, w.y, w.KTy);
+    spmv(m, rp, ci, ssv, w.x, w.Kx);
+    spmv(n, w.tp, w.ti, stv, w.y, w.KTy);
     eta_hat = eta_next;
     /* Algorithm 1, average of the epoch weighted by accepted step sizes */
     for (int32_t j = 0; j < n; ++j) w.sum_x[j] += eta * w.x[j];

@@ -327,6 +327,27 @@ def test_fp32_values_with_entries_below_the_float_range():
     assert abs(float(lp.c @ x8) - r8.pobj) <= 1e-6 * (1 + abs(r8.pobj))
 
 
+@pytest.mark.parametrize("case,N", [("tiny", 60), ("powerlaw", 60)])
+def test_fp32_values_iterates_match_the_oracles_fp32_steps(case, N):
+    """X1 against the oracle's FP32-values mode of the steps (K~ rounded to
+    FP32 in Algorithm 2's products, FP64 everywhere else) before the first
+    restart / termination check: the same trials and the same iterates
+    elementwise, as in the FP64 parity test."""
+    lp = lpgen.tiny_lp(5) if case == "tiny" else lpgen.large_lp(4, m=20000, n=40000, nnz=400000)
+    with _solver(lp, check_period=64, value_bits=32) as s:
+        x, y, st, it = s.solve(tol=1e-14, max_iter=N)
+        info = s.info()
+    r = _oracle(lp, tol=1e-14, max_iter=N, check_period=64, step_value_bits=32)
+    r64 = _oracle(lp, tol=1e-14, max_iter=N, check_period=64)
+    assert st == P.ITER_LIMIT == r.status and it == N == r.iters
+    assert info["attempts"] == r.attempts
+    np.testing.assert_allclose(x, r.x, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.x).max()))
+    np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))
+    # the FP32 rounding of the matrix is visible at this tolerance: the FP64
+    # method's iterates are elsewhere
+    assert np.abs(y - r64.y).max() > 1e-7 * max(1.0, np.abs(r64.y).max())
+
+
 def test_fp32_values_first_steps_track_fp64():
     """Before any restart decision can differ, the FP32-valued steps follow
     the FP64 trajectory to within the FP32 rounding of the matrix (2^-24

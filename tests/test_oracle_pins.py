@@ -409,3 +409,52 @@ def test_oracle_stalls_on_batch_lp_2581_by_primal_weight_runaway():
     assert np.all(np.diff(late["omega"]) > 0)
     # still near the optimum: the objective is off by a few 1e-6 relative
     assert abs(float(lp.c @ r.x) - lp.obj_star) < 1e-5 * abs(lp.obj_star)
+
+
+def test_fp32_step_mode_first_step_uses_float_values(golden):
+    """FP32-values mode of the steps: from a warm start, one accepted step is
+    eq. (pdhg) with the dual step's product taken with K rounded to FP32 (the
+    primal step's K'y0 is the start point's product, taken in FP64 like every
+    check), eta = 1/max|K| from the FP64 values; and the rounding matters."""
+    g = golden["pdhg_step"]
+    lp = DictLP(g["lp"])
+    lp.val = lp.val / 3.0  # not representable in FP32
+    x0, y0 = np.array(g["x"]), np.array(g["y"])
+    r = oracle.solve(lp, tol=0.0, max_iter=1, check_period=1, ruiz_iters=0, pc_alpha=-1.0, x0=x0, y0=y0,
+                     step_value_bits=32)
+    assert r.status == oracle.ITER_LIMIT and r.iters == 1 and r.attempts == 1
+    K = dense(lp)
+    K32 = K.astype(np.float32).astype(np.float64)
+    eta = 1.0 / np.abs(lp.val).max()
+    omega = np.linalg.norm(lp.c) / np.linalg.norm(lp.q)
+    tau, sigma = eta / omega, eta * omega
+    x1 = np.clip(x0 - tau * (lp.c - K.T @ y0), lp.l, lp.u)
+
+    def dual(Km):
+        y1 = y0 + sigma * (lp.q - Km @ (2 * x1 - x0))
+        y1[lp.n_eq:] = np.maximum(y1[lp.n_eq:], 0)
+        return y1
+
+    np.testing.assert_allclose(r.x, x1, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(r.y, dual(K32), rtol=1e-14, atol=1e-15)
+    assert np.abs(dual(K32) - dual(K)).max() > 1e-12 * np.abs(dual(K)).max()
+
+
+def test_fp32_step_mode_equals_fp64_on_float_exact_values():
+    """Without scaling and with every value exactly representable in FP32,
+    the FP32-values mode of the steps is the FP64 method, bit for bit, over
+    several restart periods."""
+    lp = lpgen.tiny_lp(3)
+    lp.val = np.round(lp.val * 8.0) / 8.0
+    lp.val[lp.val == 0] = 0.125
+    kw = dict(tol=0.0, max_iter=400, check_period=16, ruiz_iters=0, pc_alpha=-1.0)
+    a = oracle.solve(lp, step_value_bits=64, **kw)
+    b = oracle.solve(lp, step_value_bits=32, **kw)
+    assert a.iters == b.iters == 400 and a.attempts == b.attempts and a.restarts == b.restarts > 0
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.y, b.y)
+    assert a.trace.tobytes() == b.trace.tobytes()
+
+
+def test_fp32_step_mode_rejects_other_widths():
+    with pytest.raises(ValueError):
+        oracle.solve(lpgen.tiny_lp(0), tol=1e-6, max_iter=10, step_value_bits=16)
