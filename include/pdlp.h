@@ -81,8 +81,9 @@ typedef struct {
   double beta_art;        /* restart criterion (iii) */
   double time_limit_s;    /* wall-clock limit per solve; <= 0 means none */
   int32_t value_bits;     /* 64: K values stored FP64; 32: the PDHG steps read FP32 copies of the
-                             scaled K (FP64 gathers, accumulation and iterates; restart / KKT checks
-                             and termination always use the FP64 K) */
+                             scaled K (FP64 gathers, accumulation and iterates); the restart /
+                             termination checks take their own products (K'y, K'ybar, K xbar) with
+                             the FP64 K and reuse the dual step's K x of the current iterate */
   int32_t f32_polish;     /* with value_bits = 32: switch the steps to the FP64 K when the original-
                              space relative KKT error stalls over two restarts above tol (1 = on) */
   double eps_infeas;      /* relative tolerance of the infeasibility certificates (default 1e-8);
