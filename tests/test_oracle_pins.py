@@ -458,3 +458,32 @@ def test_fp32_step_mode_equals_fp64_on_float_exact_values():
 def test_fp32_step_mode_rejects_other_widths():
     with pytest.raises(ValueError):
         oracle.solve(lpgen.tiny_lp(0), tol=1e-6, max_iter=10, step_value_bits=16)
+
+
+def test_accepted_steps_satisfy_the_step_size_condition():
+    """Algorithm 2's acceptance on a real trajectory: every step accepted at
+    its first trial, from an iterate no restart moved, satisfies eq.
+    (step-size), eta <= (omega ||dx||^2 + ||dy||^2 / omega) / (2 |dy' K dx|),
+    with dx, dy the differences of the iterates the solve returns when it is
+    stopped before and after the step (no scaling, so these are the LP's own
+    iterates) and eta, omega from the check records in between."""
+    lp = lpgen.tiny_lp(2)
+    kw = dict(tol=0.0, check_period=1, ruiz_iters=0, pc_alpha=-1.0)
+    N = 40
+    runs = [oracle.solve(lp, max_iter=k, **kw) for k in range(1, N + 1)]
+    tr = runs[-1].trace  # record i: the check after step i + 1
+    assert np.array_equal(tr["k"], np.arange(1, N))
+    K = dense(lp)
+    checked = 0
+    for k in range(1, N - 1):  # the step from k to k + 1 accepted steps
+        before, after = tr[k - 1], tr[k]
+        if after["attempts"] - before["attempts"] != 1 or before["restart"] != 0:
+            continue
+        dx = runs[k].x - runs[k - 1].x
+        dy = runs[k].y - runs[k - 1].y
+        eta, omega = before["eta_hat"], before["omega"]
+        inter = abs(dy @ (K @ dx))
+        eta_bar = (omega * (dx @ dx) + (dy @ dy) / omega) / (2.0 * inter) if inter > 0 else np.inf
+        assert eta <= eta_bar * (1 + 1e-12), (k, eta, eta_bar)
+        checked += 1
+    assert checked >= 10
