@@ -487,3 +487,33 @@ def test_accepted_steps_satisfy_the_step_size_condition():
         assert eta <= eta_bar * (1 + 1e-12), (k, eta, eta_bar)
         checked += 1
     assert checked >= 10
+
+
+def test_restart_decisions_follow_the_recorded_kkt_values():
+    """Sec. 3.4's bookkeeping on a real trajectory: at every check the
+    recorded restart mask is the three criteria evaluated on the recorded
+    values -- the candidate (the average unless the current KKT is strictly
+    smaller), the epoch start's KKT as left by the previous check (recomputed
+    with the new primal weight after a restart), the previous candidate's KKT
+    (the restart point's right after a restart) and t = k minus the last
+    restart's k (beta = 0.2, 0.8, 0.36)."""
+    lp = lpgen.tiny_lp(1)
+    r = oracle.solve(lp, tol=0.0, max_iter=64 * 60, check_period=64)
+    tr = r.trace
+    assert len(tr) == 59 and (tr["restart"] != 0).sum() >= 3
+    last_restart = tr["k"][0] if tr["restart"][0] else 0
+    bits = set()
+    for i in range(1, len(tr)):
+        prev, cur = tr[i - 1], tr[i]
+        start = prev["kkt_start"]
+        kprev = start if prev["restart"] else (prev["kkt_avg"] if prev["cand_avg"] else prev["kkt_cur"])
+        cand_avg = not (cur["kkt_cur"] < cur["kkt_avg"])
+        assert cur["cand_avg"] == cand_avg
+        cand = cur["kkt_avg"] if cand_avg else cur["kkt_cur"]
+        t = cur["k"] - last_restart
+        mask = (cand <= 0.2 * start) | ((cand <= 0.8 * start and cand > kprev) << 1) | ((t >= 0.36 * cur["k"]) << 2)
+        assert cur["restart"] == mask, (i, cur["restart"], mask)
+        if mask:
+            last_restart = cur["k"]
+            bits |= {b for b in (1, 2, 4) if mask & b}
+    assert len(bits) >= 2  # more than one criterion fired along the way
