@@ -517,3 +517,32 @@ def test_restart_decisions_follow_the_recorded_kkt_values():
             last_restart = cur["k"]
             bits |= {b for b in (1, 2, 4) if mask & b}
     assert len(bits) >= 2  # more than one criterion fired along the way
+
+
+def test_primal_weight_updates_follow_the_restart_points():
+    """PrimalWeightUpdate (Sec. 2.2, read in log space) on a real trajectory:
+    between two restarts to the current iterate, omega moves to
+    exp(theta log(||dy|| / ||dx||) + (1 - theta) log(omega)) with dx, dy the
+    differences of the two restart points, which the test takes from solves
+    stopped at those checks (no scaling, so these are the LP's own iterates);
+    where either distance is below eps_zero omega stays."""
+    lp = lpgen.large_lp(0, m=300, n=600, nnz=3000)
+    kw = dict(tol=0.0, check_period=64, ruiz_iters=0, pc_alpha=-1.0)
+    tr = oracle.solve(lp, max_iter=64 * 60, **kw).trace
+    ks = {int(r["k"]): r for r in tr}
+    restarts = [int(r["k"]) for r in tr if r["restart"]]
+    pairs = [(a, b) for a, b in zip(restarts, restarts[1:]) if not ks[a]["cand_avg"] and not ks[b]["cand_avg"]]
+    moved = 0
+    for a, b in pairs:
+        za, zb = oracle.solve(lp, max_iter=a, **kw), oracle.solve(lp, max_iter=b, **kw)
+        dx, dy = np.linalg.norm(zb.x - za.x), np.linalg.norm(zb.y - za.y)
+        before = ks[b - 64]["omega"]  # unchanged since the restart at a
+        assert before == ks[a]["omega"]
+        if dx > 1e-10 and dy > 1e-10:
+            want = np.exp(0.5 * np.log(dy / dx) + 0.5 * np.log(before))
+            assert ks[b]["omega"] == pytest.approx(want, rel=1e-12)
+            assert abs(ks[b]["omega"] - before) > 1e-6 * before  # the update moved omega
+            moved += 1
+        else:
+            assert ks[b]["omega"] == before
+    assert moved >= 2
