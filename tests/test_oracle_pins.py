@@ -546,3 +546,26 @@ def test_primal_weight_updates_follow_the_restart_points():
         else:
             assert ks[b]["omega"] == before
     assert moved >= 2
+
+
+def test_average_iterate_is_weighted_by_the_accepted_steps():
+    """Algorithm 1's average on a real trajectory: the KKT of the average
+    recorded at the first check equals, to rounding, eq. (kkt) at the average
+    of the first 64 iterates (taken from solves stopped after each step)
+    weighted by their accepted step sizes (eta_1 = 1 / max|K|, then each
+    solve's next trial step, every trial accepted here); the plain mean of the
+    same iterates scores measurably differently."""
+    lp = lpgen.tiny_lp(2)
+    kw = dict(tol=0.0, check_period=64, ruiz_iters=0, pc_alpha=-1.0)
+    runs = [oracle.solve(lp, max_iter=k, **kw) for k in range(1, 65)]
+    assert runs[-1].attempts == 64  # no rejected trial: accepted eta = the trial eta
+    rec = oracle.solve(lp, max_iter=128, **kw).trace[0]
+    assert rec["k"] == 64
+    eta = np.array([1.0 / np.abs(lp.val).max()] + [r.eta_hat for r in runs[:-1]])
+    X, Y = np.array([r.x for r in runs]), np.array([r.y for r in runs])
+    omega = np.linalg.norm(lp.c) / np.linalg.norm(lp.q)
+    xb, yb = eta @ X / eta.sum(), eta @ Y / eta.sum()
+    assert oracle.kkt_omega(lp, xb, yb, omega) == pytest.approx(rec["kkt_avg"], rel=1e-12)
+    assert oracle.kkt_omega(lp, X[-1], Y[-1], omega) == pytest.approx(rec["kkt_cur"], rel=1e-12)
+    plain = oracle.kkt_omega(lp, X.mean(0), Y.mean(0), omega)
+    assert abs(plain - rec["kkt_avg"]) > 1e-6 * rec["kkt_avg"]
