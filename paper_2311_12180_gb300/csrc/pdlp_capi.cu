@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -601,6 +602,24 @@ int create_common(pdlp_solver **out, int32_t m, int32_t n, int32_t n_eq, const d
     if (f32) {
       CKS(setup_f32(LK.total, s->K.val, (float *)s->K.val32, st));
       CKS(setup_f32(LT.total, s->KT.val, (float *)s->KT.val32, st));
+    }
+    // debug mode (environment PDLP_DEBUG_CHECKS=1): every index the step and
+    // check kernels will gather through, and every work item they will walk,
+    // is checked on the device before the first solve
+    const char *dbg = std::getenv("PDLP_DEBUG_CHECKS");
+    if (dbg && dbg[0] == '1') {
+      unsigned int ck[3], ct[3];
+      CKS(setup_check_sell(m, n, LK.total, (int32_t)LK.items.size(), (const int4 *)(B + o_kit), s->K.idx, s->K.val,
+                           s->K.val32, ck, st));
+      CKS(setup_check_sell(n, m, LT.total, (int32_t)LT.items.size(), (const int4 *)(B + o_tit), s->KT.idx,
+                           s->KT.val, s->KT.val32, ct, st));
+      if (ck[0] | ck[1] | ck[2] | ct[0] | ct[1] | ct[2]) {
+        free_solver(s);
+        return fail(PDLP_ERR_INVALID, "debug check of the sliced-ELL copies failed: K entries / items / rows " +
+                                          std::to_string(ck[0]) + " / " + std::to_string(ck[1]) + " / " +
+                                          std::to_string(ck[2]) + ", K' " + std::to_string(ct[0]) + " / " +
+                                          std::to_string(ct[1]) + " / " + std::to_string(ct[2]));
+      }
     }
     // the host layouts go out of scope: wait for their uploads
     CKS(cudaStreamSynchronize(st));

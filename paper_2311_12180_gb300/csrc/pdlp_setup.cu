@@ -697,6 +697,67 @@ cudaError_t setup_check_entries(int64_t nnz, const int32_t *idx, const double *v
   return e != cudaSuccess ? e : ef;
 }
 
+namespace {
+
+// Debug checks of a sliced-ELL copy (PDLP_DEBUG_CHECKS=1 at create): the
+// step and check kernels gather through these indices and walk these items
+// without bounds checks of their own.  Counts go to err[0] (stored entries),
+// err[1] (work items), err[2] (rows not covered exactly once).
+__global__ void k_check_sell_entries(int64_t total, int32_t cols, const int32_t *__restrict__ sidx,
+                                     const double *__restrict__ sval, const float *__restrict__ sval32,
+                                     unsigned int *err) {
+  for (int64_t e = (int64_t)blockIdx.x * ST + threadIdx.x; e < total; e += (int64_t)gridDim.x * ST) {
+    const int32_t c = sidx[e];
+    const bool pad = c == -1;
+    if (c < -1 || c >= cols || (pad && sval[e] != 0.0) || (pad && sval32 && sval32[e] != 0.0f))
+      atomicAdd(err, 1u);
+  }
+}
+
+__global__ void k_check_sell_items(int32_t nitems, const int4 *__restrict__ items, int32_t rows, int64_t total,
+                                   unsigned int *err, unsigned int *cover) {
+  for (int32_t it = blockIdx.x * ST + threadIdx.x; it < nitems; it += gridDim.x * ST) {
+    const int4 d = items[it];
+    bool bad = d.w < 0 || (d.w & 31) != 0 || d.x < 0 || d.z < 0;
+    if (!bad && d.y > 0) {  // slice: d.y rows from d.x, d.z strides of 32 entries
+      bad = d.y > 32 || d.x + d.y > rows || d.z > SELL_LONG || (int64_t)d.w + 32LL * d.z > total;
+      if (!bad)
+        for (int r = 0; r < d.y; ++r) atomicAdd(cover + d.x + r, 1u);
+    } else if (!bad && d.y == -1) {  // long row d.x of d.z entries
+      bad = d.x >= rows || d.z <= SELL_LONG || (int64_t)d.w + 32LL * ((d.z + 31) / 32) > total;
+      if (!bad) atomicAdd(cover + d.x, 1u);
+    } else {
+      bad = true;
+    }
+    if (bad) atomicAdd(err + 1, 1u);
+  }
+}
+
+__global__ void k_check_sell_cover(int32_t rows, const unsigned int *__restrict__ cover, unsigned int *err) {
+  for (int32_t r = blockIdx.x * ST + threadIdx.x; r < rows; r += gridDim.x * ST)
+    if (cover[r] != 1u) atomicAdd(err + 2, 1u);
+}
+
+}  // namespace
+
+cudaError_t setup_check_sell(int32_t rows, int32_t cols, int64_t total, int32_t nitems, const int4 *items,
+                             const int32_t *sidx, const double *sval, const float *sval32, unsigned int counts[3],
+                             cudaStream_t s) {
+  counts[0] = counts[1] = counts[2] = 0;
+  unsigned int *d = nullptr;
+  cudaError_t e = cudaMallocAsync((void **)&d, sizeof(unsigned int) * (3 + (size_t)rows), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(d, 0, sizeof(unsigned int) * (3 + (size_t)rows), s);
+  if (e == cudaSuccess && total > 0) k_check_sell_entries<<<grid_for(total), ST, 0, s>>>(total, cols, sidx, sval, sval32, d);
+  if (e == cudaSuccess && nitems > 0) k_check_sell_items<<<grid_for(nitems), ST, 0, s>>>(nitems, items, rows, total, d, d + 3);
+  if (e == cudaSuccess && rows > 0) k_check_sell_cover<<<grid_for(rows), ST, 0, s>>>(rows, d + 3, d);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(counts, d, sizeof(unsigned int) * 3, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const cudaError_t ef = cudaFreeAsync(d, s);
+  return e != cudaSuccess ? e : ef;
+}
+
 cudaError_t setup_qp_diag(int32_t n, const int32_t *perm_c, const double *D2, const double *q0, double *qd,
                           cudaStream_t s) {
   k_qp_diag<<<grid_for(n), ST, 0, s>>>(n, perm_c, D2, q0, qd);

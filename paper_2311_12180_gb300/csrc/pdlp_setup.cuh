@@ -66,6 +66,14 @@ cudaError_t setup_invert(int32_t rows, const int32_t *perm, int32_t *inv, cudaSt
 cudaError_t setup_sell_fill(int32_t rows, int64_t total, const int32_t *perm, const int32_t *base,
                             const uint8_t *lane, const int32_t *ptr, const int32_t *idx, const double *val,
                             const int32_t *inv, int32_t *sidx, double *sval, cudaStream_t s);
+// Debug check of a sliced-ELL copy (rows internal rows, column indices of
+// the other side in [0, cols)): counts[0] stored entries with a column
+// outside [-1, cols) or padding (column -1) with a nonzero value, counts[1]
+// work items outside the storage or malformed, counts[2] rows that the items
+// do not cover exactly once; waits for the result.
+cudaError_t setup_check_sell(int32_t rows, int32_t cols, int64_t total, int32_t nitems, const int4 *items,
+                             const int32_t *sidx, const double *sval, const float *sval32, unsigned int counts[3],
+                             cudaStream_t s);
 // Entries of a CSR matrix on the device: *first = the first nonzero whose
 // column lies outside [0, n) or whose value is not finite (nnz if none),
 // *col_bad = 1 when that entry's column is the fault; waits for the result.
