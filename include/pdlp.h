@@ -144,7 +144,10 @@ void pdlp_default_params(pdlp_params *p);
  * runs the Sec. 2.2 Ruiz + Pock-Chambolle scaling on the device, and stores
  * the scaled K and K' a second time in the sliced-ELL layout the iteration
  * reads (rows renumbered by length; see pdlp_get_layout).  The sliced-ELL
- * copy needs fewer than 2^31 stored entries (padding included).
+ * copy needs fewer than 2^31 stored entries (padding included).  With the
+ * environment variable PDLP_DEBUG_CHECKS=1 create also checks that copy on
+ * the device (column indices, padding, work items, row coverage) and fails
+ * with PDLP_ERR_INVALID and the violation counts if it is malformed.
  *   m >= 0 rows, n >= 1 columns, 0 <= n_eq <= m, nnz = row_ptr[m] < 2^31.
  *   c: n, row_ptr: m+1, col_idx / val: nnz (int32 / float64), q: m, l / u: n.
  * Errors: PDLP_ERR_INVALID (bad input; *out untouched), PDLP_ERR_CUDA,
