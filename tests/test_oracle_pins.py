@@ -569,3 +569,10 @@ def test_average_iterate_is_weighted_by_the_accepted_steps():
     assert oracle.kkt_omega(lp, X[-1], Y[-1], omega) == pytest.approx(rec["kkt_cur"], rel=1e-12)
     plain = oracle.kkt_omega(lp, X.mean(0), Y.mean(0), omega)
     assert abs(plain - rec["kkt_avg"]) > 1e-6 * rec["kkt_avg"]
+    # this first check restarts to the average (criteria (i) and (iii)): the
+    # new primal weight comes from the distance of the average to the start
+    # point z^{0,0} = 0, and the new epoch's KKT is the average's under it
+    assert rec["restart"] == 5 and rec["cand_avg"] == 1
+    omega1 = np.exp(0.5 * np.log(np.linalg.norm(yb) / np.linalg.norm(xb)) + 0.5 * np.log(omega))
+    assert rec["omega"] == pytest.approx(omega1, rel=1e-12)
+    assert rec["kkt_start"] == pytest.approx(oracle.kkt_omega(lp, xb, yb, omega1), rel=1e-12)
