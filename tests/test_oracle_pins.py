@@ -576,3 +576,22 @@ def test_average_iterate_is_weighted_by_the_accepted_steps():
     omega1 = np.exp(0.5 * np.log(np.linalg.norm(yb) / np.linalg.norm(xb)) + 0.5 * np.log(omega))
     assert rec["omega"] == pytest.approx(omega1, rel=1e-12)
     assert rec["kkt_start"] == pytest.approx(oracle.kkt_omega(lp, xb, yb, omega1), rel=1e-12)
+
+
+def test_solve_stops_at_the_first_check_that_passes():
+    """Sec. 4.1 termination at the first opportunity: every check before the
+    last recorded a current iterate whose relative measures exceed tol, the
+    solve stopped at the next check, and its returned point meets tol on the
+    original LP while the current iterate one check earlier does not."""
+    lp = lpgen.tiny_lp(3)
+    tol = 1e-6
+    r = oracle.solve(lp, tol=tol, check_period=64)
+    assert r.status == oracle.OPTIMAL and r.iters % 64 == 0
+    tr = r.trace
+    assert tr["k"][-1] == r.iters - 64 and len(tr) == r.iters // 64 - 1
+    worst = np.maximum(np.maximum(tr["rel_gap"], tr["rel_primal"]), tr["rel_dual"])
+    assert np.all(worst > tol)
+    assert oracle.passes(lp, r.x, r.y, tol)
+    earlier = oracle.solve(lp, tol=0.0, max_iter=r.iters - 64, check_period=64)
+    assert not oracle.passes(lp, earlier.x, earlier.y, tol)
+    assert oracle.relative_kkt(lp, earlier.x, earlier.y) == pytest.approx(worst[-1], rel=1e-9)
