@@ -239,14 +239,19 @@ int pdlp_finish(pdlp_solver *s, double *x_out, double *y_out, int *status, int64
  *   pdlp_set_state: loads a blob from pdlp_get_state of a solver built from
  *   the same LP with the same parameters (possibly another solver object,
  *   in another process, on a GPU with the same number of SMs), replacing
- *   the current state; the check trace is not part of the state.
+ *   the current state; the check trace is not part of the state (the
+ *   solver's trace restarts: pdlp_get_trace then reports the checks made
+ *   since the load).
  *   pdlp_resume: continues the loaded (or begun) solve like pdlp_solve,
  *   to the tolerance, iteration limit and time limit of the original solve
  *   (the time limit counts from pdlp_set_state).
  * Solving N + M steps equals solving N, moving the state, and resuming, bit
  * for bit.  Errors: PDLP_ERR_INVALID for a too-small buffer, a blob of
- * another size, library version, LP or parameter set, or one not taken
- * between check periods; PDLP_ERR_CUDA for CUDA failures. */
+ * another size, library version, LP or parameter set, one not taken
+ * between check periods, or one whose counters and flags are out of range
+ * (check period, trace position, negative step counts, FP32 values on a
+ * solver without them), all rejected on the host before any device work;
+ * PDLP_ERR_CUDA for CUDA failures. */
 int pdlp_get_state(const pdlp_solver *s, void *buf, size_t cap, size_t *bytes);
 int pdlp_set_state(pdlp_solver *s, const void *buf, size_t bytes);
 int pdlp_resume(pdlp_solver *s, double *x_out, double *y_out, int *status, int64_t *iters);

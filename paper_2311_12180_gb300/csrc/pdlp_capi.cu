@@ -1071,6 +1071,7 @@ int pdlp_get_state(const pdlp_solver *s, void *buf, size_t cap, size_t *bytes) {
   std::memcpy(out, &h, sizeof(h));
   DevState d;
   CK(cudaMemcpy(&d, s->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  d.ntrace = 0;  // the check trace stays with the solver that recorded it
   std::memcpy(out + sizeof(h), &d, sizeof(d));
   double *vn[STATE_NV_N], *vm[STATE_NV_M];
   state_vectors(s, d.cur, vn, vm);
@@ -1106,6 +1107,13 @@ int pdlp_set_state(pdlp_solver *s, const void *buf, size_t bytes) {
   std::memcpy(&d, in + sizeof(h), sizeof(d));
   if ((d.cur != 0 && d.cur != 1) || d.check_pending != 0)
     return fail(PDLP_ERR_INVALID, "pdlp_set_state: the state was not taken between check periods");
+  // the fields the kernels index or divide with: the check period, the
+  // trace ring (its size and write position), the step count (the exponent
+  // table), and the FP32 values, which exist only with value_bits = 32
+  if (d.P != s->prm.check_period || d.trace_cap != TRACE_CAP || d.ntrace != 0 || d.k < 0 || d.t < 0 ||
+      d.attempts < d.k || d.max_iter < 1 || (d.use_f32 != 0 && d.use_f32 != 1) ||
+      (d.use_f32 && s->prm.value_bits != 32) || (d.need_g != 0 && d.need_g != 1))
+    return fail(PDLP_ERR_INVALID, "pdlp_set_state: the state's counters or flags are out of range");
   CK(cudaSetDevice(s->device));
   int rc = build_graph(s);
   if (rc) return rc;

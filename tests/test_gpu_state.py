@@ -2,6 +2,8 @@
 pdlp_resume) and the device-pointer create (pdlp_create_device), through the
 C ABI on the GPU: both must reproduce the plain host path bit for bit."""
 
+import ctypes as C
+
 import numpy as np
 import pytest
 
@@ -36,10 +38,15 @@ def test_resume_after_moving_the_state_is_bitwise():
         c.set_state(blob)
         x, y, st2, it2 = c.resume()
         info = c.info()
+        c_trace = c.trace()
     assert st2 == st_ref and it2 == it_ref
     assert np.array_equal(x, x_ref) and np.array_equal(y, y_ref)
     assert info["restarts"] == info_ref["restarts"] and info["attempts"] == info_ref["attempts"]
     assert info["omega"] == info_ref["omega"] and info["eta_hat"] == info_ref["eta_hat"]
+    # the trace is not part of the state: the new solver holds the checks
+    # made after the load, equal to the uninterrupted solve's
+    tr = trace_ref[trace_ref["k"] > k]
+    assert len(tr) > 0 and c_trace.tobytes() == tr.tobytes()
 
 
 def test_state_round_trip_in_place_and_to_optimality():
@@ -70,6 +77,61 @@ def test_state_rejects_other_lp_and_sizes():
             with pytest.raises(P.PdlpError) as e:
                 target.set_state(data)
             assert e.value.code == P.ERR_INVALID
+
+
+class _Header(C.Structure):
+    """The blob's header as pdlp_get_state writes it (host layout)."""
+
+    _fields_ = [("magic", C.c_uint64), ("version", C.c_uint32), ("m", C.c_int32), ("n", C.c_int32),
+                ("check_period", C.c_int32), ("value_bits", C.c_int32), ("pad", C.c_int32), ("nnz", C.c_int64),
+                ("devstate_bytes", C.c_uint64), ("fingerprint", C.c_uint64)]
+
+
+class _State(C.Structure):
+    """The solver's scalar state that follows the header: 25 doubles
+    (step size, primal weight, epoch sums, KKT references, parameters,
+    candidate and term pieces, certificate), 7 counters, 13 ints of flags
+    and positions, 8 block counters."""
+
+    _fields_ = [("d", C.c_double * 25), ("k", C.c_int64), ("t", C.c_int64), ("attempts", C.c_int64),
+                ("restarts", C.c_int64), ("checks", C.c_int64), ("max_iter", C.c_int64),
+                ("f64_switch_k", C.c_int64), ("cur", C.c_int32), ("need_g", C.c_int32),
+                ("check_pending", C.c_int32), ("status", C.c_int32), ("which", C.c_int32),
+                ("restart_to", C.c_int32), ("mode", C.c_int32), ("P", C.c_int32), ("ntrace", C.c_int32),
+                ("trace_cap", C.c_int32), ("use_f32", C.c_int32), ("polish", C.c_int32), ("stall", C.c_int32),
+                ("cnt", C.c_uint32 * 8)]
+
+
+def test_state_with_out_of_range_counters_is_rejected_on_the_host():
+    """Fields the kernels index or divide with (check period, trace ring
+    size and position, step counts, the FP32 switch) are checked before
+    any device work; the unmodified blob still loads and resumes."""
+    lp = lpgen.tiny_lp(2)
+    with P.Solver(lp, check_period=8) as a:
+        a.begin(tol=1e-6)
+        a.run_periods(3)
+        _, k = a.poll()
+        blob = a.get_state()
+        hdr = _Header.from_buffer_copy(blob)
+        off = C.sizeof(_Header)
+        d = _State.from_buffer_copy(blob, off)
+        # the mirror matches this build's layout
+        assert hdr.devstate_bytes == C.sizeof(_State) and (hdr.m, hdr.n) == (lp.m, lp.n)
+        assert (d.k, d.P, d.trace_cap, d.ntrace, d.check_pending) == (k, 8, P.TRACE_RETAINED, 0, 0)
+        assert d.cur in (0, 1) and d.use_f32 == 0 and d.attempts >= d.k > 0 and d.max_iter >= 1
+        bad_values = dict(P=[0, 9, -8], trace_cap=[0, 1 << 20], ntrace=[5, -1], k=[-1], t=[-1],
+                          attempts=[k - 1], max_iter=[0], use_f32=[1, 2], need_g=[2])
+        for field, values in bad_values.items():
+            for v in values:
+                e = _State.from_buffer_copy(blob, off)
+                setattr(e, field, v)
+                data = blob[:off] + bytes(e) + blob[off + C.sizeof(_State):]
+                with pytest.raises(P.PdlpError) as err:
+                    a.set_state(data)
+                assert err.value.code == P.ERR_INVALID, (field, v)
+        a.set_state(blob)
+        _, _, st, _ = a.resume()
+    assert st == P.OPTIMAL
 
 
 def _device_arrays(lp, torch):
