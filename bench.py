@@ -1,7 +1,7 @@
 """Benchmark: restarted-PDHG iterations per second on the GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large|tiny|batch|warmstart|sweep] [--no-ttt] [--lp-scale S]
+                    [--workload large|qp|tiny|batch|warmstart|sweep] [--no-ttt] [--lp-scale S]
 
 Workload (default): the planted-optimum LP with m = 1e6 rows (4e5
 equalities), n = 2e6 variables, nnz = 2e7 with Zipf(1.5) row lengths and
@@ -30,6 +30,9 @@ time_to_tol = after the timed region, a solve from zero to each --ttt-tols
          solves' per-check records as JSON lines);
 cpu_baseline = the FP64 CPU oracle (single thread) on a bounded sample of
          the same LP.
+
+--workload qp runs the same measurement on a QP: the default LP with a
+diagonal quadratic objective x'Qx/2 + c'x whose planted pair stays optimal.
 
 Multi-GPU: the plain path has an exchange per half-step (Kx', K'y'), so this
 benchmark runs independent replicas, one per rank, and reports the sum.
@@ -73,7 +76,10 @@ def pinned_lp(lp):
     import torch
 
     owners, fields = [], {"m": lp.m, "n": lp.n, "n_eq": lp.n_eq}
-    for f in ("c", "row_ptr", "col_idx", "val", "q", "l", "u"):
+    names = ["c", "row_ptr", "col_idx", "val", "q", "l", "u"]
+    if getattr(lp, "qdiag", None) is not None:
+        names.append("qdiag")
+    for f in names:
         t = torch.from_numpy(np.ascontiguousarray(getattr(lp, f))).pin_memory()
         owners.append(t)
         fields[f] = t.numpy()
@@ -219,6 +225,15 @@ def make_workload(name: str, seed: int = 0, scale: float = 1.0, permute: int = -
         if permute >= 0:
             lp = lpgen.permuted(lp, permute)
             desc += ", rows and columns permuted (seed %d)" % permute
+    elif name == "qp":
+        # the same LP with a diagonal quadratic objective x'Qx/2 + c'x
+        # (Q_jj ~ U(0, 2) on 60 % of the columns, c shifted so that the
+        # planted pair stays optimal)
+        m, n, nnz = int(round(1e6 * scale)), int(round(2e6 * scale)), int(round(2e7 * scale))
+        lp = lpgen.planted_qp(lpgen.large_lp(seed, m=m, n=n, nnz=nnz), seed)
+        desc = ("planted QP min x'Qx/2 + c'x, Q diagonal (60%% of Q_jj ~ U(0,2), the rest 0), over the planted LP "
+                "m=%d (40%% eq) n=%d nnz=%d, Zipf(1.5) row lengths (max %d), lognormal(0,2) values"
+                % (m, n, lp.nnz, lp.meta["max_row"]))
     elif name == "tiny":
         lp = lpgen.tiny_lp(seed)
         desc = "planted LP m=200 (100 eq) n=500 nnz=%d, 2%% density, N(0,1), 0<=x<=10" % lp.nnz
@@ -232,19 +247,30 @@ def algorithmic_bytes(lp, kernel: str, value_bytes: int = 8) -> float:
     k_primal: K' (row_ptr, col_idx, val) + gather of y (m) + read x, c, l, u,
               sx + write g, x', sx' (8 n-vectors);
     k_dual:   K + gather of x' (n) + read y, q, Kx, sy + write y', Kx', sy'
-              (7 m-vectors)."""
+              (7 m-vectors).
+    A QP's primal step also reads the diagonal of Q (one more n-vector)."""
     m, n, nnz = lp.m, lp.n, lp.nnz
     per_nz = 4.0 + value_bytes
+    qp = 8.0 * n if getattr(lp, "qdiag", None) is not None else 0.0
     if kernel == "k_primal":
-        return 4.0 * (n + 1) + per_nz * nnz + 8.0 * m + 8 * 8.0 * n
+        return 4.0 * (n + 1) + per_nz * nnz + 8.0 * m + 8 * 8.0 * n + qp
     if kernel == "k_dual":
         return 4.0 * (m + 1) + per_nz * nnz + 8.0 * n + 7 * 8.0 * m
     if kernel == "k_primal_reuse_g":
-        return 9 * 8.0 * n
+        return 9 * 8.0 * n + qp
     raise KeyError(kernel)
 
 
-def fp64_warp_instructions(layout: dict, kernel: str) -> float:
+def objective(lp, x) -> float:
+    """c'x, plus x'Qx/2 for a QP (Q = diag(qdiag))."""
+    import numpy as np
+
+    qd = getattr(lp, "qdiag", None)
+    obj = float(np.dot(lp.c, x))
+    return obj + 0.5 * float(np.dot(qd * x, x)) if qd is not None else obj
+
+
+def fp64_warp_instructions(layout: dict, kernel: str, qp: bool = False) -> float:
     """FP64 warp instructions one launch issues, counted from the kernels'
     source: one FMA per stored entry (a warp instruction covers 32 stored
     entries), one epilogue per slice (k_dual 8 FP64 operations per row:
@@ -252,11 +278,13 @@ def fp64_warp_instructions(layout: dict, kernel: str) -> float:
     running sum, 1 subtraction + 2 FMA + 1 subtraction for the two partial
     sums; k_primal 5: 1 subtraction + 1 FMA for the step, 1 FMA for the
     running sum, 1 subtraction + 1 FMA for ||x' - x||^2), and per 32 long
-    rows a 31-addition butterfly plus one epilogue."""
+    rows a 31-addition butterfly plus one epilogue.  A QP's primal step adds
+    an FMA and a division per row, each counted as one instruction (so the
+    count is a lower bound there)."""
     if kernel == "k_dual":
         stored, slices, longs, epi = layout["K_stored"], layout["K_slices"], layout["K_long_rows"], 8
     elif kernel == "k_primal":
-        stored, slices, longs, epi = layout["KT_stored"], layout["KT_slices"], layout["KT_long_rows"], 5
+        stored, slices, longs, epi = layout["KT_stored"], layout["KT_slices"], layout["KT_long_rows"], 7 if qp else 5
     else:
         raise KeyError(kernel)
     return stored / 32.0 + epi * slices + (31 + epi) * ((longs + 31) // 32)
@@ -634,7 +662,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "tiny", "batch", "warmstart", "sweep"])
+    ap.add_argument("--workload", default="large", choices=["large", "qp", "tiny", "batch", "warmstart", "sweep"])
     ap.add_argument("--sweep-nnz", default="1e5,1e6,1e7,5e7,1e8", help="comma-separated nonzero counts (sweep)")
     ap.add_argument("--sweep-cpu-s", type=float, default=5.0, help="oracle sample budget per size (sweep)")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -656,11 +684,11 @@ def main():
     ap.add_argument("--trace-out", default="", help="append each time-to-tolerance solve's per-check records "
                                                     "(k, trials, restarts, KKT, omega, step, Sec. 4.1 measures) "
                                                     "to this file as JSON lines")
-    ap.add_argument("--seed", type=int, default=0, help="generator seed of the large / tiny workload")
+    ap.add_argument("--seed", type=int, default=0, help="generator seed of the large / qp / tiny workload")
     ap.add_argument("--permute-seed", type=int, default=-1,
                     help="large workload: the same LP with rows (within their group) and columns permuted")
     ap.add_argument("--lp-scale", type=float, default=1.0,
-                    help="large workload: m, n and nnz scaled by this factor (1 = the 1e6 x 2e6 LP)")
+                    help="large / qp workload: m, n and nnz scaled by this factor (1 = the 1e6 x 2e6 LP)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--value-bits", type=int, default=64, choices=[64, 32],
                     help="32: step kernels read an FP32 copy of K (FP64 gathers, accumulation, iterates)")
@@ -752,7 +780,7 @@ def main():
         if k not in cands:
             continue
         t_k = cands[k][0] / cands[k][1] / 1000.0
-        wi = fp64_warp_instructions(lay, k)
+        wi = fp64_warp_instructions(lay, k, qp=getattr(lp, "qdiag", None) is not None)
         roofs[k] = {
             "seconds": t_k,
             "hbm": {"floor_s": algorithmic_bytes(lp, k, vb) / (peak * 1e9),
@@ -783,6 +811,8 @@ def main():
     # out: K''s row starts (read back at create for its sliced-ELL layout), x, y
     h2d = (4 * (lp.m + 1) + 12 * lp.nnz + 8 * 3 * lp.n + 8 * lp.m)
     d2h = 4 * (lp.n + 1) + 4 + 8 * (lp.n + lp.m)
+    if getattr(lp, "qdiag", None) is not None:
+        h2d += 8 * lp.n
     e2e_val = it2 / e2e_s * world
 
     ttt = None
@@ -794,10 +824,10 @@ def main():
                 _ = s3.solve(tol=tol, max_iter=10**9)
                 stt, itt = _[2], _[3]
                 x_t, y_t = _[0], _[1]
+                obj = objective(lp, x_t)
                 ttt["%g" % tol] = {"seconds": time.perf_counter() - t, "status": P.STATUS_NAMES.get(stt, stt),
-                                   "iters": itt, "setup_excluded": True, "objective": float(np.dot(lp.c, x_t)),
-                                   "obj_rel_err_vs_planted": abs(float(np.dot(lp.c, x_t)) - lp.obj_star)
-                                   / abs(lp.obj_star)}
+                                   "iters": itt, "setup_excluded": True, "objective": obj,
+                                   "obj_rel_err_vs_planted": abs(obj - lp.obj_star) / abs(lp.obj_star)}
                 inf = s3.info()
                 ttt["%g" % tol]["seconds_with_setup"] = ttt["%g" % tol]["seconds"] + inf["setup_ms"] / 1000.0
                 ttt["%g" % tol].update({

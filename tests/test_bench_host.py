@@ -52,3 +52,20 @@ def test_trace_export_writes_one_json_line_per_check(tmp_path):
     assert lines[0]["restart"] == 4 and lines[2]["rel_gap"] == 1e-3
     assert lines[3]["tol"] == 1e-6 and lines[3]["checks_recorded"] == 1
     assert set(lines[0]) == {"tol", "checks_recorded", *P.CHECK_DTYPE.names}
+
+
+def test_qp_workload_counts_the_diagonal_of_q():
+    """The QP workload is the default LP with a diagonal quadratic objective:
+    its primal step reads one more n-vector (Q's diagonal) and issues an FMA
+    and a division more per row; its objective adds x'Qx/2, zero error at
+    the planted optimum."""
+    lp, desc = bench.make_workload("qp", seed=1, scale=0.002)
+    base, _ = bench.make_workload("large", seed=1, scale=0.002)
+    assert lp.qdiag is not None and lp.qdiag.shape == (lp.n,) and "QP" in desc
+    assert np.array_equal(lp.val, base.val) and not np.array_equal(lp.c, base.c)
+    assert bench.algorithmic_bytes(lp, "k_primal") == bench.algorithmic_bytes(base, "k_primal") + 8 * lp.n
+    assert bench.algorithmic_bytes(lp, "k_dual") == bench.algorithmic_bytes(base, "k_dual")
+    lay = {"KT_stored": 3200, "KT_slices": 100, "KT_long_rows": 0}
+    assert bench.fp64_warp_instructions(lay, "k_primal", qp=True) == 3200 / 32 + 7 * 100
+    assert bench.objective(lp, lp.x_star) == lp.obj_star
+    assert bench.objective(base, base.x_star) == float(np.dot(base.c, base.x_star))
