@@ -105,3 +105,36 @@ def test_first_qp_step_is_the_proximal_step():
     r = oracle.solve(qp, tol=1e-30, max_iter=1, check_period=1, ruiz_iters=0, pc_alpha=-1.0)
     assert r.iters == 1
     np.testing.assert_allclose(r.x, np.clip(-c / (1 + qd), l, u), rtol=1e-15, atol=0)
+
+
+def test_every_accepted_qp_step_is_the_proximal_pdhg_step():
+    """Along a QP trajectory (no scaling, check period 1), every step
+    accepted at its first trial maps the iterates of the solve stopped
+    before it to those of the solve stopped after it by the proximal primal
+    step x' = proj_X((x - tau (c - K'y)) / (1 + tau Q_jj)) and the
+    extrapolated dual step y' = proj_Y(y + sigma (q - K(2x' - x))), with
+    tau = eta / omega, sigma = eta omega from the record in between: the
+    Hessian enters every step, across restarts and primal-weight changes."""
+    lp = lpgen.planted_qp(lpgen.tiny_lp(2), seed=3)
+    kw = dict(tol=0.0, check_period=1, ruiz_iters=0, pc_alpha=-1.0)
+    N = 40
+    runs = [oracle.solve(lp, max_iter=k, **kw) for k in range(1, N + 1)]
+    tr = runs[-1].trace  # record i: the check after step i + 1
+    assert np.array_equal(tr["k"], np.arange(1, N))
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)).toarray()
+    checked, omegas = 0, set()
+    for k in range(1, N - 1):
+        before, after = tr[k - 1], tr[k]
+        if after["attempts"] - before["attempts"] != 1 or before["restart"] != 0:
+            continue
+        x, y = runs[k - 1].x, runs[k - 1].y
+        eta, omega = before["eta_hat"], before["omega"]
+        tau, sigma = eta / omega, eta * omega
+        x1 = np.clip((x - tau * (lp.c - K.T @ y)) / (1.0 + tau * lp.qdiag), lp.l, lp.u)
+        y1 = y + sigma * (lp.q - K @ (2 * x1 - x))
+        y1[lp.n_eq:] = np.maximum(y1[lp.n_eq:], 0.0)
+        np.testing.assert_allclose(runs[k].x, x1, rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(runs[k].y, y1, rtol=1e-12, atol=1e-13)
+        checked += 1
+        omegas.add(float(omega))
+    assert checked >= 10 and len(omegas) >= 2
