@@ -595,3 +595,52 @@ def test_solve_stops_at_the_first_check_that_passes():
     earlier = oracle.solve(lp, tol=0.0, max_iter=r.iters - 64, check_period=64)
     assert not oracle.passes(lp, earlier.x, earlier.y, tol)
     assert oracle.relative_kkt(lp, earlier.x, earlier.y) == pytest.approx(worst[-1], rel=1e-9)
+
+
+def test_algorithm_2_replayed_in_numpy_reproduces_every_step():
+    """Algorithm 2 written out in numpy (trial step of eq. (pdhg), eta_bar
+    of eq. (step-size) with |dy'K dx|, the next trial min((1 - (k+2)^-0.3)
+    eta_bar, (1 + (k+2)^-0.6) eta) with k accepted steps so far, readings
+    1-2) and replayed from the iterates of a solve stopped before each step:
+    it takes as many trials as the solve recorded, lands on the iterates of
+    the solve stopped after the step, and leaves the recorded next step
+    size, rejected trials included.  A restart to the current iterate
+    leaves the start point as the stopped solve returns it (with the new
+    primal weight in the record); steps after a restart to the average
+    are skipped."""
+    lp = lpgen.tiny_lp(1)
+    kw = dict(tol=0.0, check_period=1, ruiz_iters=0, pc_alpha=-1.0)
+    N = 90
+    runs = [oracle.solve(lp, max_iter=k, **kw) for k in range(1, N + 1)]
+    tr = runs[-1].trace  # record i: the check after step i + 1
+    K = dense(lp)
+    replayed = rejections = restarted = 0
+    for k in range(1, N - 1):  # the step from k to k + 1 accepted steps
+        before, after = tr[k - 1], tr[k]
+        if before["restart"] != 0 and before["cand_avg"] == 1:
+            continue
+        x, y = runs[k - 1].x, runs[k - 1].y
+        eta, omega = before["eta_hat"], before["omega"]
+        trials = 0
+        while True:
+            trials += 1
+            x1 = np.clip(x - eta / omega * (lp.c - K.T @ y), lp.l, lp.u)
+            y1 = y + eta * omega * (lp.q - K @ (2 * x1 - x))
+            y1[lp.n_eq:] = np.maximum(y1[lp.n_eq:], 0.0)
+            dx, dy = x1 - x, y1 - y
+            inter = abs(dy @ (K @ dx))
+            eta_bar = (omega * (dx @ dx) + (dy @ dy) / omega) / (2.0 * inter) if inter > 0 else np.inf
+            kk = float(k + 2)
+            eta_next = min((1 - kk ** -0.3) * eta_bar, (1 + kk ** -0.6) * eta)
+            if eta <= eta_bar:
+                break
+            eta = eta_next
+            assert trials < 50
+        assert trials == after["attempts"] - before["attempts"], k
+        np.testing.assert_allclose(runs[k].x, x1, rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(runs[k].y, y1, rtol=1e-12, atol=1e-13)
+        assert after["eta_hat"] == pytest.approx(eta_next, rel=1e-10)
+        replayed += 1
+        rejections += trials - 1
+        restarted += before["restart"] != 0
+    assert replayed >= 60 and rejections >= 4 and restarted >= 1
