@@ -269,8 +269,8 @@ const char *pdlp_kernel_name(int32_t i);
  * the records of the last 65536 checks in a device ring buffer (written by
  * the check kernel, no per-check transfer); pdlp_get_trace copies up to cap
  * of the retained records, oldest first, into trace and stores the number
- * of checks recorded since the solve began (which may exceed 65536) in
- * *count. */
+ * of checks recorded since the solve began or its state was loaded (which
+ * may exceed 65536) in *count. */
 int pdlp_get_info(const pdlp_solver *s, pdlp_info *info);
 int pdlp_get_trace(const pdlp_solver *s, pdlp_check *trace, int32_t cap, int32_t *count);
 
