@@ -6,6 +6,7 @@ HiGHS (scipy) as an independent judge of which LPs are infeasible."""
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 import lpgen
 import oracle
@@ -140,3 +141,62 @@ def test_detection_leaves_feasible_solves_unchanged():
         off = oracle.solve(lp, tol=1e-8, max_iter=200000, eps_infeas=0.0)
         assert on.status == off.status == oracle.OPTIMAL
         assert on.iters == off.iters and np.array_equal(on.x, off.x) and np.array_equal(on.y, off.y)
+
+
+def _np_dual_ray_measures(lp, yr):
+    """Primal-infeasibility certificate measures of a dual ray yr, written
+    out in numpy: lambda = proj_Lambda(-K'yr) on the bounds' cone,
+    objective q'yr + l'lambda+ - u'lambda-, residual
+    ||(-K'yr - lambda, min(yr_G, 0))||."""
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)).toarray()
+    g = -K.T @ yr
+    lf, uf = np.isfinite(lp.l), np.isfinite(lp.u)
+    lam = np.where(lf & uf, g, np.where(lf, np.maximum(g, 0), np.where(uf, np.minimum(g, 0), 0.0)))
+    obj = lp.q @ yr + np.sum(np.where(lf, lp.l, 0.0) * np.maximum(lam, 0)) \
+        - np.sum(np.where(uf, lp.u, 0.0) * np.maximum(-lam, 0))
+    res = np.sqrt(np.sum((g - lam) ** 2) + np.sum(np.minimum(yr[lp.n_eq:], 0) ** 2))
+    return obj, res
+
+
+def _np_primal_ray_measures(lp, xr):
+    """Dual-infeasibility certificate measures of a primal ray xr: objective
+    -c'xr, residual ||(K_E xr, min(K_G xr, 0), xr's distance to the
+    recession cone of the bounds)||."""
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)).toarray()
+    kx = K @ xr
+    lf, uf = np.isfinite(lp.l), np.isfinite(lp.u)
+    cone = np.where(lf & uf, 0.0, np.where(lf, np.maximum(xr, 0), np.where(uf, np.minimum(xr, 0), xr)))
+    res = np.sqrt(np.sum(kx[:lp.n_eq] ** 2) + np.sum(np.minimum(kx[lp.n_eq:], 0) ** 2) + np.sum((xr - cone) ** 2))
+    return -lp.c @ xr, res
+
+
+@pytest.mark.parametrize("kind,seed", [("primal", 0), ("primal_bounds", 1), ("dual", 0)])
+def test_detection_fires_at_the_first_check_whose_difference_ray_certifies(kind, seed):
+    """Without scaling the difference ray is the difference of the iterates
+    that solves stopped at k and k - 1 return.  At the check where the
+    solve declares infeasibility that ray, as the test computes it, is the
+    returned ray and passes the certificate test written out in numpy; one
+    check earlier it does not, and a solve stopped there has not fired."""
+    eps = 1e-8
+    lp = lpgen.infeasible_lp(seed, kind)
+    kw = dict(tol=1e-8, ruiz_iters=0, pc_alpha=-1.0, check_period=64)
+    r = oracle.solve(lp, max_iter=200000, eps_infeas=eps, **kw)
+    primal = kind != "dual"
+    assert r.status == (oracle.PRIMAL_INFEASIBLE if primal else oracle.DUAL_INFEASIBLE) and r.which == 2
+
+    def ray(k):
+        a = oracle.solve(lp, max_iter=k, eps_infeas=0.0, **kw)
+        b = oracle.solve(lp, max_iter=k - 1, eps_infeas=0.0, **kw)
+        assert a.iters == k and b.iters == k - 1
+        return a.x - b.x, a.y - b.y
+
+    def certifies(xr, yr):
+        obj, res = _np_dual_ray_measures(lp, yr) if primal else _np_primal_ray_measures(lp, xr)
+        return obj > 0 and res <= eps * obj
+
+    xr, yr = ray(r.iters)
+    np.testing.assert_allclose(r.y if primal else r.x, yr if primal else xr, rtol=1e-12, atol=1e-300)
+    assert certifies(xr, yr)
+    assert not certifies(*ray(r.iters - 64))
+    earlier = oracle.solve(lp, max_iter=r.iters - 64, eps_infeas=eps, **kw)
+    assert earlier.status == oracle.ITER_LIMIT
