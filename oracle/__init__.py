@@ -7,7 +7,10 @@ and marshals numpy arrays through ctypes.
 
 Parity pins: see tests/test_oracle_*.py (brute-force vertex enumeration,
 closed forms, planted optima, an independent LP solver, hand-computed KKT and
-PDHG-step examples, Algorithm 3 restart behaviour).  The restart heuristics'
+PDHG-step examples, Algorithm 3 restart behaviour, and trajectories replayed
+in numpy from solves stopped before and after each step or check: Algorithm
+2's trials, the weighted average, the restart decisions, the primal-weight
+updates, termination and infeasibility detection).  The restart heuristics'
 constants (beta = 0.2 / 0.8 / 0.36, theta, check period) are "parity unpinned"
 beyond the oracle implementing the printed rules.
 """
