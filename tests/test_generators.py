@@ -39,3 +39,44 @@ def test_batch_subset_builds_the_same_members():
         assert np.array_equal(lp.val, full[i].val) and np.array_equal(lp.c, full[i].c)
     w = lpgen.batch_work(10, seed=3)
     assert np.corrcoef(w, [lp.nnz for lp in full])[0, 1] > 0.99
+
+
+def test_large_lp_follows_its_recipe():
+    """The 1e6 x 2e6 benchmark LP has the stated shape: 2e7 nonzeros within
+    0.1 %, 40 % equality rows, Zipf(1.5) row lengths (the tail P(L >= 2d) /
+    P(L >= d) of a Zipf(1.5) law is 2^-0.5; realised maximum ~910, mean 20),
+    lognormal(0, 2) magnitudes with random signs, bounds 50 % [0, inf),
+    30 % [l, u] with l in [-5, 0] and u in [0, 5], 20 % free; a valid CSR
+    matrix (sorted, distinct columns per row) whose planted pair is a KKT
+    point (b = A x*, c = K'y* + lambda*, complementary slackness)."""
+    lp = lpgen.large_lp(0)
+    m, n = lp.m, lp.n
+    L = np.diff(lp.row_ptr)
+    assert (m, n, lp.n_eq) == (1_000_000, 2_000_000, 400_000)
+    assert abs(lp.nnz - 20_000_000) <= 20_000 and L.min() >= 1 and 800 <= L.max() <= 1000
+    for d in (8, 16, 32, 64):
+        assert abs((L >= 2 * d).sum() / (L >= d).sum() - 2 ** -0.5) < 0.02, d
+    lv = np.log(np.abs(lp.val))
+    assert abs(lv.mean()) < 0.01 and abs(lv.std() - 2.0) < 0.01 and abs((lp.val < 0).mean() - 0.5) < 0.002
+    fl, fu = np.isfinite(lp.l), np.isfinite(lp.u)
+    assert abs((fl & ~fu).mean() - 0.5) < 0.002 and np.all(lp.l[fl & ~fu] == 0)
+    assert abs((fl & fu).mean() - 0.3) < 0.002 and abs((~fl & ~fu).mean() - 0.2) < 0.002
+    assert not np.any(~fl & fu)
+    box = fl & fu
+    assert lp.l[box].min() >= -5 and lp.l[box].max() <= 0 and lp.u[box].min() >= 0 and lp.u[box].max() <= 5
+    rows = np.repeat(np.arange(m), L)
+    key = rows.astype(np.int64) * n + lp.col_idx
+    assert np.all(np.diff(key) > 0) and lp.col_idx.min() >= 0 and lp.col_idx.max() < n
+    # the planted pair, in plain numpy over the CSR arrays
+    kx = np.bincount(rows, weights=lp.val * lp.x_star[lp.col_idx], minlength=m)
+    kty = np.bincount(lp.col_idx, weights=lp.val * lp.y_star[rows], minlength=n)
+    scale = 1.0 + np.abs(lp.q)
+    assert np.all(np.abs(kx[:lp.n_eq] - lp.q[:lp.n_eq]) <= 1e-9 * scale[:lp.n_eq])
+    assert np.all(kx[lp.n_eq:] - lp.q[lp.n_eq:] >= -1e-9 * scale[lp.n_eq:])
+    assert np.all(lp.y_star[lp.n_eq:] >= 0)
+    act = np.abs(kx[lp.n_eq:] - lp.q[lp.n_eq:]) * lp.y_star[lp.n_eq:]
+    assert np.all(act <= 1e-9 * (1 + np.abs(lp.q[lp.n_eq:])))
+    assert np.allclose(lp.c, kty + lp.lam_star, rtol=1e-12, atol=1e-9)
+    assert np.all((lp.x_star >= lp.l) & (lp.x_star <= lp.u))
+    assert np.all(lp.x_star[lp.lam_star > 0] == lp.l[lp.lam_star > 0])
+    assert np.all(lp.x_star[lp.lam_star < 0] == lp.u[lp.lam_star < 0])
