@@ -80,3 +80,29 @@ def test_large_lp_follows_its_recipe():
     assert np.all((lp.x_star >= lp.l) & (lp.x_star <= lp.u))
     assert np.all(lp.x_star[lp.lam_star > 0] == lp.l[lp.lam_star > 0])
     assert np.all(lp.x_star[lp.lam_star < 0] == lp.u[lp.lam_star < 0])
+
+
+def test_batch_shapes_and_members_follow_their_recipe():
+    """The 4096-LP batch: m log-uniform on [50, 4000], n / m log-uniform on
+    [2/3, 2.5], density uniform on [0.5 %, 5 %] (about 2.8e8 expected
+    nonzeros in all); sampled members have half equality rows, 0 <= x <= 10,
+    N(0, 1) values, every row and column covered, and the density drawn."""
+    import math
+
+    count = 4096
+    shapes = np.array(list(lpgen._batch_shapes(count, 0, 50, 4000, 0.005, 0.05)))
+    m, n, d = shapes[:, 0], shapes[:, 1], shapes[:, 2]
+    assert m.min() >= 50 and m.max() <= 4000
+    u = (np.log(m) - math.log(50)) / (math.log(4000) - math.log(50))
+    assert abs(u.mean() - 0.5) < 0.02 and abs(u.std() - (1 / 12) ** 0.5) < 0.02
+    r = np.log(n / m)
+    assert r.min() >= math.log(2 / 3) - 0.02 and r.max() <= math.log(2.5) + 0.01
+    assert abs(r.mean() - 0.5 * (math.log(2 / 3) + math.log(2.5))) < 0.02
+    assert d.min() >= 0.005 and d.max() <= 0.05 and abs(d.mean() - 0.0275) < 0.001
+    assert abs(lpgen.batch_work(count, 0).sum() / 2.8e8 - 1) < 0.02
+    for i, lp in zip((0, 7, 2581), lpgen.batch_subset([0, 7, 2581], count, seed=0)):
+        assert (lp.m, lp.n) == (m[i], n[i]) and lp.n_eq == lp.m // 2
+        assert np.all(lp.l == 0) and np.all(lp.u == 10)
+        assert np.all(np.diff(lp.row_ptr) >= 1) and np.unique(lp.col_idx).size == lp.n
+        assert abs(lp.nnz / (lp.m * lp.n) - d[i]) < 0.3 * d[i] + 2.0 / lp.n
+        assert abs(lp.val.mean()) < 0.2 and abs(lp.val.std() - 1) < 0.2
