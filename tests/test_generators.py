@@ -1,7 +1,10 @@
-"""Input generators (no solver arithmetic): single members of a batch are
-rebuilt exactly, so a batch member can be studied without its batch."""
+"""Input generators (no solver arithmetic): the benchmark LP, the uneven
+batch and the transportation family follow their stated recipes, and single
+members of a batch are rebuilt exactly, so a member can be studied without
+its batch."""
 
 import numpy as np
+import pytest
 
 import lpgen
 
@@ -106,3 +109,29 @@ def test_batch_shapes_and_members_follow_their_recipe():
         assert np.all(np.diff(lp.row_ptr) >= 1) and np.unique(lp.col_idx).size == lp.n
         assert abs(lp.nnz / (lp.m * lp.n) - d[i]) < 0.3 * d[i] + 2.0 / lp.n
         assert abs(lp.val.mean()) < 0.2 and abs(lp.val.std() - 1) < 0.2
+
+
+def test_transport_family_members_are_feasible_transportation_lps():
+    """A member of the warm-start family is a transportation LP: each column
+    x_ij appears once with +1 in sink j's equality row and once with -1 in
+    source i's ">=" row; supplies and demands are at least the floor and
+    total supply is 1.05 x total demand, so the proportional plan
+    x_ij = s_i d_j / S meets every demand and uses 1 / 1.05 of each supply."""
+    fam = lpgen.transport_family(0, sources=20, sinks=30)
+    lp = lpgen.transport_lp(fam, lpgen.transport_thetas(1, 0)[0], 0)
+    S, T = 20, 30
+    assert (lp.m, lp.n, lp.n_eq) == (S + T, S * T, T)
+    L = np.diff(lp.row_ptr)
+    assert np.all(L[:T] == S) and np.all(L[T:] == T)
+    rows = np.repeat(np.arange(lp.m), L)
+    j, i = lp.col_idx % T, lp.col_idx // T  # column i * T + j: source i, sink j
+    sink_part = rows < T
+    assert np.all(j[sink_part] == rows[sink_part]) and np.all(lp.val[sink_part] == 1)
+    assert np.all(i[~sink_part] == rows[~sink_part] - T) and np.all(lp.val[~sink_part] == -1)
+    assert np.array_equal(np.sort(lp.col_idx[sink_part]), np.arange(S * T))
+    d, s = lp.q[:T], -lp.q[T:]
+    assert d.min() >= 0.05 and s.sum() == pytest.approx(1.05 * d.sum(), rel=1e-12)
+    x = np.outer(s, d).ravel() / s.sum()
+    kx = np.bincount(rows, weights=lp.val * x[lp.col_idx], minlength=lp.m)
+    np.testing.assert_allclose(kx[:T], d, rtol=1e-12)
+    assert np.all(kx[T:] >= lp.q[T:]) and np.all(lp.l == 0) and np.all(np.isinf(lp.u))

@@ -191,9 +191,12 @@ def _highs(lp):
     return res.fun
 
 
-@pytest.mark.parametrize("case", ["tiny-mixed", "all-eq", "all-ineq", "power-law"])
+@pytest.mark.parametrize("case", ["tiny-mixed", "all-eq", "all-ineq", "power-law", "transport"])
 def test_against_highs(case):
-    if case == "tiny-mixed":
+    if case == "transport":  # a 20 x 30 member of the warm-start family (incidence K, free-cost noise)
+        fam = lpgen.transport_family(0, sources=20, sinks=30)
+        lp = lpgen.transport_lp(fam, lpgen.transport_thetas(1, 0)[0], 0)
+    elif case == "tiny-mixed":
         lp = lpgen.tiny_lp(7)
     elif case == "all-eq":
         lp = lpgen.tiny_lp(8, m_eq=120, m_ineq=0, n=300)
