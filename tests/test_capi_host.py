@@ -150,3 +150,29 @@ def test_noalloc_scaling_rejects_null_pointers_on_host(L, null):
                                      args["KT_idx"], args["KT_val"], 10, 1.0, args["D1"], args["D2"], None)
     assert rc == P.ERR_INVALID
     assert "null" in L.pdlp_last_error().decode()
+
+
+def test_error_message_is_per_thread(L):
+    """pdlp_last_error is thread-local: a rejected call on one thread sets
+    that thread's message and leaves another thread's untouched."""
+    import threading
+
+    L.pdlp_last_error.restype = C.c_char_p
+    lp = lpgen.tiny_lp(0)
+    bad = lpgen.tiny_lp(0)
+    bad.col_idx = bad.col_idx.copy()
+    bad.col_idx[3] = bad.n
+    seen = {}
+
+    def worker():
+        with pytest.raises(P.PdlpError):
+            _create(bad)
+        seen["worker"] = L.pdlp_last_error().decode()
+
+    assert L.pdlp_get_info(None, None) == P.ERR_INVALID
+    main_msg = L.pdlp_last_error().decode()
+    t = threading.Thread(target=worker)
+    t.start()
+    t.join()
+    assert "col_idx" in seen["worker"] and "3" in seen["worker"]
+    assert main_msg and L.pdlp_last_error().decode() == main_msg != seen["worker"]
