@@ -97,7 +97,9 @@ def _sample_rows(rng: np.random.Generator, lengths: np.ndarray, n: int):
     """Columns drawn uniformly without replacement inside each row, sorted.
 
     Returns (row_ptr int64, col int64).  Draws with replacement, then redraws
-    the duplicates until every row holds distinct columns."""
+    the duplicates until every row holds distinct columns; rows that still
+    hold duplicates after 200 rounds (nearly dense rows) take the rest of
+    their columns from the ones they lack, without replacement."""
     lengths = np.minimum(np.asarray(lengths, dtype=np.int64), n)
     m = lengths.shape[0]
     row_ptr = np.zeros(m + 1, dtype=np.int64)
@@ -116,7 +118,13 @@ def _sample_rows(rng: np.random.Generator, lengths: np.ndarray, n: int):
         if nd == 0:
             return row_ptr, cols
         cols[dup] = rng.integers(0, n, size=nd, dtype=np.int64)
-    raise RuntimeError("could not draw distinct columns (row too dense)")
+    for r in np.unique(rows[dup]):
+        a, b = int(row_ptr[r]), int(row_ptr[r + 1])
+        have = np.unique(cols[a:b])
+        missing = np.setdiff1d(np.arange(n, dtype=np.int64), have, assume_unique=True)
+        extra = rng.choice(missing, size=(b - a) - have.size, replace=False)
+        cols[a:b] = np.sort(np.concatenate([have, extra]))
+    return row_ptr, cols
 
 
 def _cover_columns(rng, row_ptr, cols, m, n):

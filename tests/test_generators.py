@@ -135,3 +135,15 @@ def test_transport_family_members_are_feasible_transportation_lps():
     kx = np.bincount(rows, weights=lp.val * x[lp.col_idx], minlength=lp.m)
     np.testing.assert_allclose(kx[:T], d, rtol=1e-12)
     assert np.all(kx[T:] >= lp.q[T:]) and np.all(lp.l == 0) and np.all(np.isinf(lp.u))
+
+
+def test_nearly_dense_rows_still_get_distinct_columns():
+    """A small power-law LP can draw a row as long as n (seed 4 below): its
+    columns are still distinct and sorted, every row of the matrix too."""
+    lp = lpgen.large_lp(4, m=300, n=600, nnz=3000)
+    L = np.diff(lp.row_ptr)
+    assert L.max() == lp.n
+    rows = np.repeat(np.arange(lp.m), L)
+    assert np.all(np.diff(rows.astype(np.int64) * lp.n + lp.col_idx) > 0)
+    dense = int(np.argmax(L))
+    assert np.array_equal(lp.col_idx[lp.row_ptr[dense]:lp.row_ptr[dense + 1]], np.arange(lp.n))
