@@ -647,3 +647,24 @@ def test_algorithm_2_replayed_in_numpy_reproduces_every_step():
         rejections += trials - 1
         restarted += before["restart"] != 0
     assert replayed >= 60 and rejections >= 4 and restarted >= 1
+
+
+def test_termination_tests_the_current_iterate_before_the_average():
+    """Reading 13's order: at the check where a solve ends on the average
+    (which = 1), the current iterate there, from a solve stopped at the same
+    step, fails the Sec. 4.1 test and the returned average passes it; at
+    the check where a solve ends on the current iterate, that iterate
+    is what a solve stopped there returns."""
+    tol = 1e-4
+    lp = lpgen.tiny_lp(3)
+    r = oracle.solve(lp, tol=tol, check_period=64)
+    assert r.status == oracle.OPTIMAL and r.which == 1
+    cur = oracle.solve(lp, tol=0.0, max_iter=r.iters, check_period=64)
+    assert cur.status == oracle.ITER_LIMIT and cur.iters == r.iters
+    assert not oracle.passes(lp, cur.x, cur.y, tol) and oracle.passes(lp, r.x, r.y, tol)
+    assert not np.array_equal(r.x, cur.x)
+    lp = lpgen.tiny_lp(0)
+    r = oracle.solve(lp, tol=1e-6, check_period=64)
+    assert r.status == oracle.OPTIMAL and r.which == 0
+    cur = oracle.solve(lp, tol=0.0, max_iter=r.iters, check_period=64)
+    assert np.array_equal(r.x, cur.x) and np.array_equal(r.y, cur.y)
