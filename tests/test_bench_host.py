@@ -69,3 +69,21 @@ def test_qp_workload_counts_the_diagonal_of_q():
     assert bench.fp64_warp_instructions(lay, "k_primal", qp=True) == 3200 / 32 + 7 * 100
     assert bench.objective(lp, lp.x_star) == lp.obj_star
     assert bench.objective(base, base.x_star) == float(np.dot(base.c, base.x_star))
+
+
+def test_clock_summary_reads_the_sampled_csv(tmp_path):
+    """The clocks record of a bench line: median SM clock under load, the
+    maximum clock, and every throttle reason seen active in any sample;
+    malformed lines are skipped."""
+    path = tmp_path / "clocks.csv"
+    path.write_text("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "garbage line\n"
+                    "0, 2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    c = bench.Clocks(0)
+    c.path = str(path)
+    c.proc = object()  # as if nvidia-smi had run
+    s = c.summary()
+    assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.proc = None
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
