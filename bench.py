@@ -1,7 +1,7 @@
 """Benchmark: restarted-PDHG iterations per second on the GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload large|qp|tiny|batch|warmstart|sweep] [--no-ttt] [--lp-scale S]
+                    [--workload large|qp|tiny|batch|warmstart|sweep|mlp] [--no-ttt] [--lp-scale S]
 
 Workload (default): the planted-optimum LP with m = 1e6 rows (4e5
 equalities), n = 2e6 variables, nnz = 2e7 with Zipf(1.5) row lengths and
@@ -32,7 +32,8 @@ cpu_baseline = the FP64 CPU oracle (single thread) on a bounded sample of
          the same LP.
 
 --workload qp runs the same measurement on a QP: the default LP with a
-diagonal quadratic objective x'Qx/2 + c'x whose planted pair stays optimal.
+diagonal quadratic objective x'Qx/2 + c'x whose planted pair stays optimal;
+--workload mlp times training steps of the warm-start network.
 
 Multi-GPU: the plain path has an exchange per half-step (Kx', K'y'), so this
 benchmark runs independent replicas, one per rank, and reports the sum.
@@ -377,6 +378,50 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def mlp_step_flops(din: int, hidden: int, dout: int, batch: int) -> float:
+    """FLOPs of one training step of the din-hidden-hidden-dout MLP: per
+    weight, 2 (forward) + 4 (the two backward products) per batch row."""
+    return 6.0 * batch * (din * hidden + hidden * hidden + hidden * dout)
+
+
+def run_mlp(args, rank, world):
+    """Training-step rate of the warm-start MLP (the tensor-core GEMMs, the
+    fused loss, Adam): the 16-256-256-60500 network of the transportation
+    workload at batch 256, He-uniform weights, 2048 random (theta, target)
+    rows; 5 untimed Adam steps, then --mlp-steps timed ones (wall clock
+    around the call, which waits for its per-step losses).  Rank 0 only."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    from paper_2311_12180_gb300 import _build
+    from paper_2311_12180_gb300 import pdlp as P
+    from paper_2311_12180_gb300.warmstart import init_params
+
+    _build.build()
+    din, hid, dout, B = 16, 256, 60500, 256
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((2048, din)).astype(np.float32)
+    T = rng.standard_normal((2048, dout)).astype(np.float32)
+    steps = int(args.mlp_steps)
+    with P.Mlp(din, hid, dout, max_batch=B) as net:
+        net.set_params(init_params(din, hid, dout, 0))
+        net.set_data(X, T)
+        idx = rng.integers(0, 2048, (steps, B)).astype(np.int32)
+        net.train(idx[:5])
+        t = time.perf_counter()
+        losses = net.train(idx)
+        dt = time.perf_counter() - t
+    flops = mlp_step_flops(din, hid, dout, B)
+    line = {"metric": "MLP training steps/s", "value": steps / dt, "unit": "steps/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "bf16 (FP32 accumulate, FP32 masters)", "data": "synthetic",
+            "config": {"workload": "MLP %d-%d-%d-%d, batch %d, 2048 random (theta, target) rows, Adam" %
+                       (din, hid, hid, dout, B)},
+            "ms_per_step": 1000.0 * dt / steps, "tflops": flops * steps / dt / 1e12,
+            "flops_per_step": flops, "steps": steps, "loss_first_last": [float(losses[0]), float(losses[-1])]}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, rank, world):
     """Batched mode: many uneven planted LPs (m ~ logU[50,4000], n ~ logU[2m/3,
     2.5m], density ~ U[0.5%,5%], N(0,1) values, half equality rows, 0<=x<=10)
@@ -662,7 +707,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="large", choices=["large", "qp", "tiny", "batch", "warmstart", "sweep"])
+    ap.add_argument("--workload", default="large", choices=["large", "qp", "tiny", "batch", "warmstart", "sweep", "mlp"])
+    ap.add_argument("--mlp-steps", type=int, default=200, help="mlp workload: timed training steps")
     ap.add_argument("--sweep-nnz", default="1e5,1e6,1e7,5e7,1e8", help="comma-separated nonzero counts (sweep)")
     ap.add_argument("--sweep-cpu-s", type=float, default=5.0, help="oracle sample budget per size (sweep)")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -707,6 +753,9 @@ def main():
         return
     if args.workload == "sweep":
         run_sweep(args, rank, world)
+        return
+    if args.workload == "mlp":
+        run_mlp(args, rank, world)
         return
 
     import numpy as np

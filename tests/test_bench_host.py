@@ -87,3 +87,10 @@ def test_clock_summary_reads_the_sampled_csv(tmp_path):
     assert s == {"sm_mhz": 2055.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     c.proc = None
     assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_mlp_step_flops():
+    """Six FLOPs per weight and batch row (forward product, the two backward
+    products): 23.9 GFLOP for the 16-256-256-60500 network at batch 256."""
+    assert bench.mlp_step_flops(16, 256, 60500, 256) == 6 * 256 * (16 * 256 + 256 * 256 + 256 * 60500)
+    assert abs(bench.mlp_step_flops(16, 256, 60500, 256) / 1e9 - 23.9) < 0.01
