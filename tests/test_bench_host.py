@@ -7,6 +7,7 @@ import os
 import sys
 
 import numpy as np
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
@@ -94,3 +95,46 @@ def test_mlp_step_flops():
     products): 23.9 GFLOP for the 16-256-256-60500 network at batch 256."""
     assert bench.mlp_step_flops(16, 256, 60500, 256) == 6 * 256 * (16 * 256 + 256 * 256 + 256 * 60500)
     assert abs(bench.mlp_step_flops(16, 256, 60500, 256) / 1e9 - 23.9) < 0.01
+
+
+def test_mlp_workload_line(monkeypatch, capsys):
+    """The mlp workload's glue on the host, with the network replaced by a
+    stand-in: 5 untimed steps, then the timed ones, and one JSON line with
+    the step rate and the TFLOP/s it implies."""
+    import types
+
+    from paper_2311_12180_gb300 import _build
+
+    calls = []
+
+    class _Net:
+        def __init__(self, din, hid, dout, max_batch):
+            calls.append(("create", din, hid, dout, max_batch))
+
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *a):
+            pass
+
+        def set_params(self, p):
+            calls.append(("params", p.size))
+
+        def set_data(self, X, T):
+            calls.append(("data", X.shape, T.shape))
+
+        def train(self, idx):
+            calls.append(("train", idx.shape))
+            return np.linspace(1.0, 0.5, len(idx))
+
+    monkeypatch.setattr(P, "Mlp", _Net)
+    monkeypatch.setattr(_build, "build", lambda: None)
+    bench.run_mlp(types.SimpleNamespace(mlp_steps=7), 0, 1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert calls[0] == ("create", 16, 256, 60500, 256) and calls[2] == ("data", (2048, 16), (2048, 60500))
+    assert calls[3] == ("train", (5, 256)) and calls[4] == ("train", (7, 256))
+    assert line["steps"] == 7 and line["unit"] == "steps/s" and line["value"] > 0
+    assert line["tflops"] == pytest.approx(line["value"] * bench.mlp_step_flops(16, 256, 60500, 256) / 1e12)
+    assert line["loss_first_last"] == [1.0, 0.5]
+    bench.run_mlp(types.SimpleNamespace(mlp_steps=7), 1, 2)  # other ranks print nothing
+    assert capsys.readouterr().out == ""
