@@ -138,3 +138,36 @@ def test_every_accepted_qp_step_is_the_proximal_pdhg_step():
         checked += 1
         omegas.add(float(omega))
     assert checked >= 10 and len(omegas) >= 2
+
+
+def test_fp32_values_mode_of_a_qp_step():
+    """The QP extension in the FP32-values mode of the steps: from a warm
+    start, one accepted step is the proximal primal step (with the start
+    point's K'y0 in FP64) and the extrapolated dual step whose product takes
+    K rounded to FP32; the Hessian and the rounding both matter."""
+    lp = lpgen.planted_qp(lpgen.tiny_lp(2), seed=1)
+    rng = np.random.default_rng(5)
+    x0 = np.clip(lp.x_star + rng.uniform(-0.5, 0.5, lp.n), lp.l + 0.1, lp.u - 0.1)
+    y0 = lp.y_star + rng.uniform(-0.1, 0.1, lp.m)
+    r = oracle.solve(lp, tol=0.0, max_iter=1, check_period=1, ruiz_iters=0, pc_alpha=-1.0, x0=x0, y0=y0,
+                     step_value_bits=32)
+    assert r.status == oracle.ITER_LIMIT and r.iters == 1 and r.attempts == 1
+    K = sp.csr_matrix((lp.val, lp.col_idx, lp.row_ptr), shape=(lp.m, lp.n)).toarray()
+    K32 = K.astype(np.float32).astype(np.float64)
+    eta = 1.0 / np.abs(lp.val).max()
+    omega = np.linalg.norm(lp.c) / np.linalg.norm(lp.q)
+    tau, sigma = eta / omega, eta * omega
+
+    def primal(qd):
+        return np.clip((x0 - tau * (lp.c - K.T @ y0)) / (1.0 + tau * qd), lp.l, lp.u)
+
+    def dual(Km, x1):
+        y1 = y0 + sigma * (lp.q - Km @ (2 * x1 - x0))
+        y1[lp.n_eq:] = np.maximum(y1[lp.n_eq:], 0)
+        return y1
+
+    x1 = primal(lp.qdiag)
+    np.testing.assert_allclose(r.x, x1, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(r.y, dual(K32, x1), rtol=1e-13, atol=1e-14)
+    assert np.abs(x1 - primal(0.0)).max() > 1e-6 * np.abs(x1).max()
+    assert np.abs(dual(K32, x1) - dual(K, x1)).max() > 1e-10 * np.abs(dual(K, x1)).max()
