@@ -80,3 +80,21 @@ def test_set_quadratic_rejects_negative_or_nonfinite_entries():
             with pytest.raises(P.PdlpError) as e:
                 s.set_quadratic(d)
             assert e.value.code == P.ERR_INVALID
+
+
+@pytest.mark.parametrize("case,N", [("tiny", 60), ("powerlaw", 30)])
+def test_qp_fp32_values_iterates_match_the_oracles_fp32_steps(case, N):
+    """A QP with FP32 matrix values in the steps (value_bits = 32) against
+    the oracle's FP32-values mode before the first check: the same trials
+    and the same iterates elementwise; the FP64 method is elsewhere."""
+    qp = _qp(case)
+    with P.Solver(qp, check_period=64, value_bits=32) as s:
+        x, y, st, it = s.solve(tol=1e-14, max_iter=N)
+        info = s.info()
+    r = oracle.solve(qp, tol=1e-14, max_iter=N, check_period=64, step_value_bits=32)
+    r64 = oracle.solve(qp, tol=1e-14, max_iter=N, check_period=64)
+    assert st == P.ITER_LIMIT == r.status and it == N == r.iters
+    assert info["attempts"] == r.attempts
+    np.testing.assert_allclose(x, r.x, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.x).max()))
+    np.testing.assert_allclose(y, r.y, rtol=1e-9, atol=1e-9 * max(1.0, np.abs(r.y).max()))
+    assert np.abs(y - r64.y).max() > 1e-7 * max(1.0, np.abs(r64.y).max())
