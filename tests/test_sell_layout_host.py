@@ -1,10 +1,11 @@
-"""Host side of the sliced-ELL layout (csrc/pdlp_sell.h), no GPU: the row
+"""Host-side create code, no GPU.  The sliced-ELL layout (csrc/pdlp_sell.h): the row
 renumbering, slices, long rows and work schedule that the step and check
 kernels walk, checked against the properties the kernels rely on (a
 permutation that keeps the equality rows first, rows by length inside each
 group, slices of 32 consecutive rows inside a group, long rows whole, every
 row in exactly one work item, disjoint storage that fills the total, items
-by cost).  The header is compiled into a small host program with nvcc."""
+by cost).  The threaded stable CSR transpose (csrc/pdlp_host.h) against
+scipy.  Each header is compiled into a small host program with nvcc."""
 
 import os
 import shutil
@@ -129,3 +130,47 @@ def test_edge_cases(layout_exe, case):
         assert L["nslices"] == 2 and L["total"] == 32 * 7 + 32 * 3
     if case == "boundary_48_49":
         assert L["nlong"] == 2
+
+
+@pytest.fixture(scope="module")
+def transpose_exe(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not found")
+    exe = str(tmp_path_factory.mktemp("tr") / "csr_transpose_host")
+    subprocess.run([nvcc, "-std=c++17", "-O1", "-x", "cu", "-gencode", "arch=compute_103a,code=sm_103a",
+                    "-I", os.path.join(ROOT, "paper_2311_12180_gb300", "csrc"),
+                    os.path.join(ROOT, "tests", "csr_transpose_host.cpp"), "-o", exe], check=True)
+    return exe
+
+
+@pytest.mark.parametrize("m,n,nnz", [(0, 5, 0), (7, 0, 0), (50, 40, 300), (3000, 5000, 200000)])
+def test_threaded_host_transpose_is_the_stable_transpose(transpose_exe, m, n, nnz):
+    """csr_transpose (several threads from 65536 nonzeros on) equals the
+    stable transpose: K' rows hold K's entries in increasing row order, the
+    values moved bit for bit (scipy's CSR -> CSC conversion as the judge);
+    empty rows and columns included."""
+    sp = pytest.importorskip("scipy.sparse")
+    rng = np.random.default_rng(m + n)
+    if nnz:
+        rows = np.sort(rng.integers(0, m, size=nnz))
+        cols = rng.integers(0, n, size=nnz)
+        keep = np.unique(rows.astype(np.int64) * n + cols, return_index=True)[1]
+        rows, cols = rows[keep], cols[keep]
+    else:
+        rows = cols = np.zeros(0, dtype=np.int64)
+    vals = rng.standard_normal(rows.size) * np.exp(rng.uniform(-30, 30, rows.size))
+    ptr = np.zeros(m + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=m), out=ptr[1:])
+    bits = vals.view(np.uint64)
+    text = "%d %d %d\n%s\n%s\n%s\n" % (m, n, rows.size, " ".join(map(str, ptr)), " ".join(map(str, cols)),
+                                     " ".join("%x" % b for b in bits))
+    out = subprocess.run([transpose_exe], input=text, capture_output=True, text=True, check=True).stdout.split("\n")
+    tp = np.array(out[0].split(), dtype=np.int64)
+    ti = np.array(out[1].split(), dtype=np.int64)
+    tv = np.array([int(h, 16) for h in out[2].split()], dtype=np.uint64).view(np.float64)
+    K = sp.csr_matrix((vals, cols, ptr), shape=(m, n))
+    C = K.tocsc()
+    C.sort_indices()
+    assert np.array_equal(tp, C.indptr) and np.array_equal(ti, C.indices)
+    assert np.array_equal(tv.view(np.uint64), np.asarray(C.data).view(np.uint64))
