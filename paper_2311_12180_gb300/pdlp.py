@@ -277,8 +277,25 @@ def _f64(a, n=None):
     return a
 
 
-def _i32(a):
-    return np.ascontiguousarray(a, dtype=np.int32)
+def _i32(a, n=None):
+    a = np.asarray(a)
+    if a.dtype != np.int32 and a.size and (a.min() < -2**31 or a.max() >= 2**31):
+        raise ValueError("index array does not fit in int32")
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    if n is not None and a.shape[0] != n:
+        raise ValueError("expected length %d, got %d" % (n, a.shape[0]))
+    return a
+
+
+def _csr(m, row_ptr, col_idx, val):
+    """K's CSR arrays as int32 / float64, with the lengths the C call reads:
+    m + 1 row starts and at least row_ptr[m] indices and values."""
+    row_ptr = _i32(row_ptr, m + 1)
+    nnz = int(row_ptr[m])
+    col_idx, val = _i32(col_idx), _f64(val)
+    if col_idx.shape[0] < nnz or val.shape[0] < nnz:
+        raise ValueError("row_ptr[m] = %d but col_idx has %d and val %d entries" % (nnz, col_idx.shape[0], val.shape[0]))
+    return row_ptr, col_idx, val
 
 
 # ---------------------------------------------------------------- C-named functions
@@ -294,7 +311,7 @@ def pdlp_create(m, n, n_eq, c, row_ptr, col_idx, val, q, l, u, params=None, stre
     """pdlp_create / pdlp_create_ex; returns the opaque handle (c_void_p)."""
     h = C.c_void_p()
     c, q, l, u = _f64(c, n), _f64(q, m), _f64(l, n), _f64(u, n)
-    row_ptr, col_idx, val = _i32(row_ptr), _i32(col_idx), _f64(val)
+    row_ptr, col_idx, val = _csr(m, row_ptr, col_idx, val)
     if params is None and stream is None:
         rc = lib().pdlp_create(C.byref(h), m, n, n_eq, _ptr(c), _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(q),
                                _ptr(l), _ptr(u))
@@ -519,8 +536,9 @@ class BatchSolver:
         arr = (pdlp_lp * len(lps))()
         self.ms, self.ns = [], []
         for i, lp in enumerate(lps):
-            c, q, l, u = _f64(lp.c), _f64(lp.q), _f64(lp.l), _f64(lp.u)
-            rp, ci, v = _i32(lp.row_ptr), _i32(lp.col_idx), _f64(lp.val)
+            m, n = int(lp.m), int(lp.n)
+            c, q, l, u = _f64(lp.c, n), _f64(lp.q, m), _f64(lp.l, n), _f64(lp.u, n)
+            rp, ci, v = _csr(m, lp.row_ptr, lp.col_idx, lp.val)
             q = q if q.size else np.zeros(1)
             ci = ci if ci.size else np.zeros(1, np.int32)
             v = v if v.size else np.zeros(1)

@@ -65,8 +65,10 @@ def test_invalid_input_rejected_on_host(L, defect):
         lp.col_idx[5] = lp.n
     elif defect == "row_ptr_order":
         lp.row_ptr[3] = lp.row_ptr[4] + 1
-    elif defect == "row_ptr_start":
+    elif defect == "row_ptr_start":  # lengths consistent, so the C side sees row_ptr[0] = 1
         lp.row_ptr = lp.row_ptr + 1
+        lp.col_idx = np.append(lp.col_idx, 0)
+        lp.val = np.append(lp.val, 1.0)
     elif defect == "nan_val":
         lp.val[0] = np.nan
     elif defect == "l_gt_u":
@@ -176,3 +178,33 @@ def test_error_message_is_per_thread(L):
     t.join()
     assert "col_idx" in seen["worker"] and "3" in seen["worker"]
     assert main_msg and L.pdlp_last_error().decode() == main_msg != seen["worker"]
+
+
+@pytest.mark.parametrize("defect", ["short_row_ptr", "short_col_idx", "short_val", "int32_overflow", "short_c",
+                                    "short_q"])
+def test_binding_checks_array_lengths_before_the_call(L, defect):
+    """The Python binding hands the C call only arrays of the lengths it
+    reads (m + 1 row starts, row_ptr[m] indices and values, n- and
+    m-vectors) and indices that fit in int32; anything else is a ValueError
+    before any C call."""
+    lp = lpgen.tiny_lp(0)
+    rp, ci, v, c, q = lp.row_ptr, lp.col_idx, lp.val, lp.c, lp.q
+    if defect == "short_row_ptr":
+        rp = rp[:-1]
+    elif defect == "short_col_idx":
+        ci = ci[:-1]
+    elif defect == "short_val":
+        v = v[:-1]
+    elif defect == "int32_overflow":
+        ci = ci.astype(np.int64)
+        ci[0] = 2**32
+    elif defect == "short_c":
+        c = c[:-1]
+    elif defect == "short_q":
+        q = q[:-1]
+    with pytest.raises(ValueError):
+        P.pdlp_create(lp.m, lp.n, lp.n_eq, c, rp, ci, v, q, lp.l, lp.u)
+    bad = lpgen.tiny_lp(1)
+    bad.row_ptr, bad.col_idx, bad.val, bad.c, bad.q = rp, ci, v, c, q
+    with pytest.raises(ValueError):
+        P.BatchSolver([lpgen.tiny_lp(2), bad])
