@@ -578,8 +578,11 @@ class BatchSolver:
         Y = np.empty(max(int(self.yo[-1]), 1))
         st = np.empty(self.count, dtype=np.int32)
         it = np.empty(self.count, dtype=np.int64)
-        x0p = None if x0 is None else _f64(np.concatenate(x0) if isinstance(x0, (list, tuple)) else x0)
-        y0p = None if y0 is None else _f64(np.concatenate(y0) if isinstance(y0, (list, tuple)) else y0)
+        # the start points of all LPs back to back: sum n and sum m entries
+        x0p = None if x0 is None else _f64(np.concatenate(x0) if isinstance(x0, (list, tuple)) else x0,
+                                           int(self.xo[-1]))
+        y0p = None if y0 is None else _f64(np.concatenate(y0) if isinstance(y0, (list, tuple)) else y0,
+                                           int(self.yo[-1]))
         _check(lib().pdlp_batch_solve(self.h, _ptr(x0p), _ptr(y0p), tol, int(max_iter), _ptr(X), _ptr(Y), _ptr(st),
                                       _ptr(it)))
         xs = [X[self.xo[i]:self.xo[i + 1]] for i in range(self.count)]
