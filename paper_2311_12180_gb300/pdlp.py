@@ -643,8 +643,9 @@ class Mlp:
         return int(lib().pdlp_mlp_param_count(self.h))
 
     def set_params(self, p):
-        p = _f32(p)
-        assert p.size == self.param_count
+        p = _f32(p).ravel()
+        if p.size != self.param_count:
+            raise ValueError("expected %d parameters, got %d" % (self.param_count, p.size))
         _check(lib().pdlp_mlp_set_params(self.h, _ptr(p)))
 
     def get_params(self):
@@ -654,12 +655,16 @@ class Mlp:
 
     def set_data(self, X, T):
         X, T = _f32(X), _f32(T)
-        assert X.shape[1] == self.in_dim and T.shape[1] == self.out_dim and X.shape[0] == T.shape[0]
+        if X.ndim != 2 or T.ndim != 2 or X.shape[1] != self.in_dim or T.shape[1] != self.out_dim \
+                or X.shape[0] != T.shape[0]:
+            raise ValueError("need X (samples, %d) and T (samples, %d)" % (self.in_dim, self.out_dim))
         _check(lib().pdlp_mlp_set_data(self.h, X.shape[0], _ptr(X), _ptr(T)))
 
     def train(self, idx, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         """idx: (steps, batch) int array of data-set rows; returns per-step losses."""
         idx = np.ascontiguousarray(idx, dtype=np.int32)
+        if idx.ndim != 2:
+            raise ValueError("idx must be (steps, batch)")
         steps, batch = idx.shape
         losses = np.empty(steps, dtype=np.float32)
         _check(lib().pdlp_mlp_train(self.h, steps, batch, _ptr(idx), lr, beta1, beta2, eps, _ptr(losses)))
@@ -667,6 +672,8 @@ class Mlp:
 
     def predict(self, X):
         X = _f32(X)
+        if X.ndim != 2 or X.shape[1] != self.in_dim:
+            raise ValueError("need X (count, %d)" % self.in_dim)
         Y = np.empty((X.shape[0], self.out_dim), dtype=np.float32)
         _check(lib().pdlp_mlp_predict(self.h, X.shape[0], _ptr(X), _ptr(Y)))
         return Y
