@@ -208,3 +208,20 @@ def test_binding_checks_array_lengths_before_the_call(L, defect):
     bad.row_ptr, bad.col_idx, bad.val, bad.c, bad.q = rp, ci, v, c, q
     with pytest.raises(ValueError):
         P.BatchSolver([lpgen.tiny_lp(2), bad])
+
+
+def test_mlp_binding_rejects_bad_shapes_before_the_call(L):
+    """The MLP binding checks array shapes before any C call (a handle that
+    was never created is enough to reach the checks)."""
+    net = object.__new__(P.Mlp)
+    net.in_dim, net.hidden, net.out_dim, net.max_batch, net.h = 4, 8, 3, 16, None
+    with pytest.raises(ValueError):
+        net.set_data(np.zeros((5, 3)), np.zeros((5, 3)))  # X has the wrong width
+    with pytest.raises(ValueError):
+        net.set_data(np.zeros((5, 4)), np.zeros((6, 3)))  # row counts differ
+    with pytest.raises(ValueError):
+        net.train(np.zeros(7, dtype=np.int32))  # not (steps, batch)
+    with pytest.raises(ValueError):
+        net.predict(np.zeros((2, 5)))
+    with pytest.raises(ValueError):
+        net.set_params(np.zeros(3))  # param_count of a NULL handle is 0, 3 != 0
